@@ -1,0 +1,107 @@
+"""Planted mistakes: each plausible bug, planted in the oracle on the CPU, must fail a pin."""
+import numpy as np
+import pytest
+
+from oracle import fmm
+from oracle import geometry as G
+from oracle import m2l as M
+from oracle import operators as O
+
+
+def _fmm_error(p=4):
+    rng = np.random.default_rng(1)
+    pts = rng.random((600, 3))
+    q = rng.random(600)
+    return M.rel_l2_error(fmm.direct(pts, q), fmm.fmm(pts, q, 3, p))
+
+
+def test_reference_fmm_error_is_small():
+    assert _fmm_error() < 1e-3
+
+
+def test_source_on_wrong_surface_is_caught(monkeypatch):
+    """M2L source taken on the outer (upward check) radius instead of its equivalent surface."""
+    def bad(p, width):
+        return (G.surface_points(p, np.zeros(3), width, G.ALPHA_INNER),
+                G.surface_points(p, np.zeros(3), width, G.ALPHA_OUTER))
+    monkeypatch.setattr(M, "m2l_surfaces", bad)
+    assert not _fmm_error() < 1e-3  # NaN (coincident points) fails the pin as well
+
+
+def test_wrong_check_radius_is_caught(monkeypatch):
+    """Target check points moved off the inner radius."""
+    def bad(p, width):
+        return (G.surface_points(p, np.zeros(3), width, 1.5),
+                G.surface_points(p, np.zeros(3), width, G.ALPHA_INNER))
+    monkeypatch.setattr(M, "m2l_surfaces", bad)
+    assert not _fmm_error() < 1e-3  # NaN (coincident points) fails the pin as well
+
+
+def test_adjacent_sources_in_list_are_caught(monkeypatch):
+    monkeypatch.setattr(G, "is_adjacent_or_same", lambda a, b: bool(np.all(np.asarray(a) == np.asarray(b))))
+    sizes = [len(G.interaction_list(tau, 3)) for tau in G.all_boxes(3)[::17]]
+    assert max(sizes) != 189
+
+
+def test_flipped_transfer_vector_is_caught(rng, monkeypatch):
+    p, level = 3, 3
+    q = rng.standard_normal((512, 1, G.n_surface(p)))
+    tg = np.arange(0, 512, 31)
+    _, phi_d = M.m2l_dense(p, level, q, targets=tg)
+    orig = O.m2l_matrix
+    monkeypatch.setattr(O, "m2l_matrix", lambda p, t, width=1.0: orig(p, -np.asarray(t), width))
+    ops = O.compressed_operators(p, 0.0, G.box_width(level))
+    _, phi_c = M.m2l_compressed(p, level, q, ops, targets=tg)
+    assert M.rel_l2_error(phi_d, phi_c) > 1e-6
+
+
+def test_transposed_operator_is_caught(rng, monkeypatch):
+    p, level = 3, 3
+    q = rng.standard_normal((512, 1, G.n_surface(p)))
+    tg = np.arange(0, 512, 31)
+    _, phi_d = M.m2l_dense(p, level, q, targets=tg)
+    orig = O.m2l_matrix
+    monkeypatch.setattr(O, "m2l_matrix", lambda p, t, width=1.0: orig(p, t, width).T)
+    ops = O.compressed_operators(p, 0.0, G.box_width(level))
+    _, phi_c = M.m2l_compressed(p, level, q, ops, targets=tg)
+    assert M.rel_l2_error(phi_d, phi_c) > 1e-6
+
+
+def test_shifted_kernel_grid_is_caught(rng, monkeypatch):
+    p, level = 3, 2
+    q = rng.standard_normal((64, 1, G.n_surface(p)))
+    tg = np.arange(0, 64, 9)
+    _, phi_d = M.m2l_dense(p, level, q, targets=tg)
+    orig = O.kernel_grid
+    monkeypatch.setattr(O, "kernel_grid", lambda p, t, width=1.0, g=None: np.roll(orig(p, t, width, g), 1, axis=2))
+    _, phi_f = M.m2l_fft(p, level, q, targets=tg)
+    assert M.rel_l2_error(phi_d, phi_f) > 1e-6
+
+
+def test_dropped_term_in_direct_sum_is_caught(rng, monkeypatch):
+    """Drop the last source of every list: the brute-force pin disagrees."""
+    p, level = 3, 2
+    q = rng.standard_normal((64, 1, G.n_surface(p)))
+    good = M.check_potentials(p, level, q, targets=[0])
+    orig = G.interaction_lists_vectorised
+
+    def bad(targets, level, source_slot=None):
+        off, src, rows = orig(targets, level, source_slot)
+        keep = np.ones(len(rows), bool)
+        keep[off[1:] - 1] = False
+        new_off = off - np.arange(len(off))
+        return new_off, src[keep], rows[keep]
+    monkeypatch.setattr(G, "interaction_lists_vectorised", bad)
+    assert M.rel_l2_error(good, M.check_potentials(p, level, q, targets=[0])) > 1e-6
+
+
+def test_loose_pinv_threshold_is_caught(monkeypatch):
+    from scipy import linalg
+    p = 5
+    x = G.surface_points(p, np.zeros(3), 1.0, G.ALPHA_INNER)
+    y = G.surface_points(p, np.zeros(3), 1.0, G.ALPHA_OUTER)
+    A = O.laplace(x, y)
+    V, _ = O.pinv_factors(A, alpha=1e-6)
+    s = np.linalg.svd(A, compute_uv=False)
+    assert V.shape[1] != np.sum(s > max(A.shape) * np.finfo(float).eps * s[0])
+    assert np.linalg.matrix_rank(linalg.pinv(A)) != V.shape[1]
