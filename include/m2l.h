@@ -1,0 +1,181 @@
+/*
+ * m2l.h - C ABI of the GB300 (sm_103a) multipole-to-local (M2L) library for the 3D Laplace
+ * kernel-independent FMM on a uniform octree (arxiv 2408.07436).
+ *
+ * What one call computes (Sec. 2.2, Eq. 11): for every target box tau at a level and every
+ * right-hand side r,
+ *        q_tau = (K_tau)^+  sum_{sigma in I_tau}  K_{sigma,tau} q_sigma
+ * where q_sigma are the upward-equivalent densities of the source boxes (the multipoles),
+ * K_{sigma,tau} is the 3D Laplace kernel 1/(4 pi |x - y|) (Eq. 2) between the downward-check
+ * points of tau and the upward-equivalent points of sigma, (K_tau)^+ is the regularised
+ * pseudo-inverse of the downward check -> downward equivalent kernel matrix (Eqs. 7-10,
+ * alpha = 0), and q_tau are the downward-equivalent densities (the locals).
+ * I_tau holds the children of the parent's neighbours that are not adjacent to tau
+ * (|I_tau| <= 189; Sec. 2). Two forms are provided:
+ *   BLAS-M2L (Sec. 3.1-3.2): SVD-compressed operators C_t = U^T K_t S over the 316
+ *            transfer vectors, applied as dense contractions on the GPU.
+ *   FFT-M2L  (App. A.1): kernel spectra on the 2p convolution grid, Hadamard products of
+ *            the transformed densities, inverse transform.
+ *
+ * Geometry (stated once, used by every call):
+ *   - n = 6(p-1)^2 + 2 surface points per box (App. A.3), the boundary points of a p^3
+ *     lattice, lexicographic (x slowest). Upward-equivalent and downward-check surfaces sit
+ *     at 1.05 box half-widths, downward-equivalent (and upward-check) at 2.95.
+ *   - Boxes at level l are indexed by Morton key (x in the lowest bit of each triple).
+ *   - The map is scale free (Laplace homogeneity, Sec. 3.1): K_t scales as 1/w and (K_tau)^+
+ *     as w, so no box width is passed and one set of operators serves every level.
+ *
+ * Data layout of multipoles / locals for one level: [B_l boxes][n_rhs][n], row major,
+ * boxes in ascending Morton order (every box of the level unless m2l_set_boxes gave a
+ * sparse set). For level = -1 the buffer is levels 2..depth concatenated in ascending order.
+ * Element type: double for M2L_PREC_FP64, float for every other precision.
+ *
+ * Pointers: multipoles and locals may be device pointers (the normal case) or host
+ * pointers (pinned or pageable); host buffers are staged through the plan's device
+ * workspace with copies on the plan's stream, and the call then returns after the result
+ * has been copied back. Device buffers are owned by the caller; the plan owns its operator
+ * tables and workspace (device memory allocated by the plan) until m2l_destroy.
+ * Device-pointer calls are asynchronous on the plan's stream.
+ *
+ * Errors: every function that returns int returns M2L_OK (0) or a negative M2L_E* code;
+ * functions returning pointers return NULL on error. m2l_last_error() gives a message for
+ * the calling thread. Invalid arguments are rejected before any launch. CUDA failures map to
+ * M2L_ECUDA. No call aborts, traps or exits the process.
+ */
+#ifndef M2L_GB300_H
+#define M2L_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct m2l_plan_s m2l_plan_t;
+
+enum m2l_kernel_e { M2L_LAPLACE3D = 0 };
+
+enum m2l_status_e {
+    M2L_OK = 0,
+    M2L_EINVAL = -1,        /* invalid argument or call order */
+    M2L_ENOMEM = -2,        /* host or device allocation failed */
+    M2L_ECUDA = -3,         /* a CUDA runtime or launch error */
+    M2L_ETIMEOUT = -4,      /* a device-side bounded wait ran out */
+    M2L_EUNSUPPORTED = -5   /* valid request this build does not implement */
+};
+
+enum m2l_option_e {
+    M2L_OPT_FORM = 1,        /* M2L_FORM_*; default M2L_FORM_BLAS */
+    M2L_OPT_PRECISION = 2,   /* M2L_PREC_*; default M2L_PREC_FP64 */
+    M2L_OPT_ACCUMULATE = 3,  /* 0: locals are overwritten (default); 1: locals += M2L result */
+    M2L_OPT_OUTPUT = 4,      /* M2L_OUT_*; default M2L_OUT_LOCALS */
+    M2L_OPT_TARGET_TOL = 5,  /* accuracy asked of M2L_FORM_AUTO: the bits of a double */
+    M2L_OPT_FFT_GRID = 6,    /* convolution grid side: 0 = 2p (default), else 2p-1 <= g <= 2p */
+    M2L_OPT_TIMING = 7       /* 1: record CUDA events around every stage (see m2l_stage_times) */
+};
+
+/* Stages of one application, as indexed by m2l_stage_times. */
+enum m2l_stage_e {
+    M2L_STAGE_COMPRESS = 0,    /* B1: q~ = S^T q                           (Sec. 3.2 step 2) */
+    M2L_STAGE_CONTRACT = 1,    /* B2: phi~ = sum_t C_t q~, gathered        (Sec. 3.2 steps 3-5) */
+    M2L_STAGE_EXPAND = 2,      /* B3: locals = V_eps Ut_eps U phi~          (Sec. 3.2 step 5, Eq. 9) */
+    M2L_STAGE_FFT_FORWARD = 3, /* F1+F2: embed and transform               (App. A.1 step 2) */
+    M2L_STAGE_HADAMARD = 4,    /* F3: Hadamard products over I_tau          (App. A.1 step 4) */
+    M2L_STAGE_FFT_INVERSE = 5, /* F4+F5: inverse transform, check surface   (App. A.1 step 6) */
+    M2L_STAGE_PINV = 6,        /* F6: locals = V_eps Ut_eps phi             (Eq. 9) */
+    M2L_NUM_STAGES = 7
+};
+
+enum m2l_form_e { M2L_FORM_AUTO = 0, M2L_FORM_BLAS = 1, M2L_FORM_FFT = 2 };
+
+enum m2l_precision_e {
+    M2L_PREC_AUTO = -1,   /* chosen per (p, n_rhs, M2L_OPT_TARGET_TOL) by the library */
+    M2L_PREC_FP64 = 0,    /* FP64 data and arithmetic */
+    M2L_PREC_FP32 = 1,    /* FP32 data and arithmetic (CUDA cores) */
+    M2L_PREC_TF32X3 = 2,  /* FP32 data; BLAS contractions as three TF32 tensor-core products */
+    M2L_PREC_BF16X3 = 3   /* FP32 data; BLAS contractions as three BF16 tensor-core products */
+};
+
+enum m2l_output_e {
+    M2L_OUT_LOCALS = 0,          /* downward-equivalent densities q_tau (Eq. 11) */
+    M2L_OUT_CHECK_POTENTIAL = 1  /* the check potential sum_{sigma} K_{sigma,tau} q_sigma before
+                                    the pseudo-inverse, in units of a box of width 1 */
+};
+
+enum m2l_query_e {
+    M2L_Q_N = 1,          /* surface points per box, n */
+    M2L_Q_RANK = 2,       /* SVD rank k of the BLAS form (n at full rank) */
+    M2L_Q_BOXES = 3,      /* boxes at `level` (after m2l_set_boxes) */
+    M2L_Q_PAIRS = 4,      /* (target, source) M2L pairs at `level`; level -1: all levels */
+    M2L_Q_GRID = 5,       /* convolution grid side g of the FFT form */
+    M2L_Q_FREQS = 6,      /* complex half-spectrum length g*g*(g/2+1) */
+    M2L_Q_PINV_RANK = 7,  /* singular values kept by the pseudo-inverse */
+    M2L_Q_ROWS = 8,       /* boxes summed over levels 2..depth */
+    M2L_Q_FORM = 9,       /* form the next apply will run (resolves AUTO) */
+    M2L_Q_PRECISION = 10, /* precision the next apply will run (resolves AUTO) */
+    M2L_Q_LAUNCHES = 11   /* kernels launched by the last apply */
+};
+
+/* Build a plan (host, FP64; arxiv 2408.07436 Sec. 3.1 for the BLAS operators and App. A.1
+ * step 1 for the kernel spectra). depth in [2, 8]; p in [2, 16]; kernel = M2L_LAPLACE3D.
+ * rank_tol <= 0: full rank (k = n, exact). rank_tol > 0: keep the singular values of the
+ * stacked operators K_fat and K_thin (Eqs. 12-13) with s_i / s_0 >= rank_tol.
+ * Operator tables are built lazily on the first apply that needs them.
+ * Returns NULL on error (see m2l_last_error). Uses the current CUDA device. */
+m2l_plan_t *m2l_plan(int depth, int p, int kernel, double rank_tol);
+
+/* Apply M2L (Eq. 11) at `level` in [2, depth], or at every level 2..depth when level == -1.
+ * multipoles: [rows][n_rhs][n] (see the layout above), read only.
+ * locals:     same shape; overwritten, or accumulated when M2L_OPT_ACCUMULATE is 1; with
+ *             M2L_OPT_OUTPUT = M2L_OUT_CHECK_POTENTIAL it receives the check potentials.
+ * n_rhs >= 1. The two buffers must not overlap.
+ * Returns M2L_OK, M2L_EINVAL (bad level / n_rhs / NULL / overlapping buffers),
+ * M2L_EUNSUPPORTED (precision not offered by the chosen form), M2L_ENOMEM or M2L_ECUDA. */
+int m2l_apply(m2l_plan_t *plan, const void *multipoles, void *locals, int level, int n_rhs);
+
+/* Release the plan and its device memory. NULL-safe. Synchronises the plan's stream. */
+void m2l_destroy(m2l_plan_t *plan);
+
+/* Message for the last error on the calling thread ("" if none). Valid until the next call. */
+const char *m2l_last_error(void);
+
+/* Set an option (enum m2l_option_e). Takes effect at the next apply. M2L_EINVAL on an unknown
+ * key or value. */
+int m2l_set_option(m2l_plan_t *plan, int key, long long value);
+
+/* Stream the plan launches on (a cudaStream_t; NULL = legacy default stream). */
+int m2l_set_stream(m2l_plan_t *plan, void *stream);
+
+/* Restrict `level` to the non-empty boxes listed by `keys` (n strictly ascending Morton keys
+ * < 8^level, host memory, copied). Empty boxes are neither sources nor targets (the pruning of
+ * empty branches, Sec. 2.1). n == 8^level with keys == NULL restores the full level. */
+int m2l_set_boxes(m2l_plan_t *plan, int level, const uint64_t *keys, long long n);
+
+/* Apply several independent plans (uneven FMM instances) with device buffers, every level
+ * of each (level = -1 semantics), in one pass on the first plan's stream: plans with equal
+ * (p, form, precision, rank) share launches, and the whole pass is replayed from a CUDA
+ * graph captured on the first call with the same arguments.
+ * plans[i], multipoles[i], locals[i], n_rhs[i] as for m2l_apply. */
+int m2l_apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *multipoles,
+                    void *const *locals, const int *n_rhs);
+
+/* Integer facts about a plan (enum m2l_query_e). `level` is used by M2L_Q_BOXES/PAIRS. */
+int m2l_query(const m2l_plan_t *plan, int what, int level, long long *out);
+
+/* Device time in milliseconds of every stage of the last application made with
+ * M2L_OPT_TIMING = 1, measured with CUDA events on the plan's stream (waits for them).
+ * ms must hold M2L_NUM_STAGES doubles; stages that did not run read 0. Also reports the
+ * number of kernel launches of each stage in `launches` (may be NULL). */
+int m2l_stage_times(m2l_plan_t *plan, double *ms, long long *launches);
+
+/* Copy a plan operator to host memory (FP64), for tests and inspection:
+ * which = 0: U (n x k), 1: S (n x k), 2: C_t (316 x k x k), 3: singular values of K_fat (n),
+ *         4: pseudo-inverse factor V_eps (n x r), 5: Ut_eps = Sigma_eps^-1 U_eps^T (r x n).
+ * *count receives the number of doubles; dst may be NULL to query the size. */
+int m2l_get_operator(m2l_plan_t *plan, int which, double *dst, long long *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* M2L_GB300_H */

@@ -1,0 +1,134 @@
+// Internal structures of the M2L library: the plan (host FP64 operators, device tables and
+// workspace) and the helpers shared by the host code and the launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/m2l.h"
+
+namespace m2l {
+
+constexpr int kNumTransfer = 316;   // |T| = 7^3 - 3^3 (Sec. 3.1)
+constexpr int kPerOctant = 189;     // far pairs per target octant, 6^3 - 3^3 (Sec. 3.1)
+constexpr int kDirections = 26;     // source clusters around a target cluster (App. A.1)
+constexpr double kAlphaInner = 1.05;  // upward-equivalent / downward-check radius (box half-widths)
+constexpr double kAlphaOuter = 2.95;  // downward-equivalent / upward-check radius
+constexpr int kMaxDepth = 8;
+
+void set_error(const char *fmt, ...);
+void clear_error();
+
+// Index of transfer vector (x, y, z) in [-3,3]^3 \ [-1,1]^3, enumerated x slowest then y, z.
+int transfer_index(int x, int y, int z);
+void transfer_vector(int idx, int &x, int &y, int &z);
+
+struct LevelSet {
+    bool dense = true;
+    std::vector<uint64_t> keys;  // sorted Morton keys when sparse
+    long long nboxes = 0;
+};
+
+// Device copy of the operators in one arithmetic precision.
+struct DevOps {
+    bool ready = false;
+    int elt = 8;                 // bytes per real (8: double, 4: float)
+    // BLAS form (row-major, inner dimension padded to kp / rp)
+    void *St = nullptr;          // [kp][np_]   S^T
+    void *C = nullptr;           // [316][kp][kp] C_t
+    void *A = nullptr;           // [rp][kp]    Ut_eps * U
+    void *V = nullptr;           // [n][rp]     V_eps
+    void *Uc = nullptr;          // [n][kp]     U (check-potential output)
+    void *C_hi = nullptr, *C_lo = nullptr;  // split C_t for the tensor-core forms
+    // FFT form
+    void *Khat = nullptr;        // [316+1][F] complex kernel spectra (last row zero)
+    void *Ut = nullptr;          // [rp][np_]   Ut_eps
+    void *tw = nullptr;          // [g] complex twiddles exp(-2 pi i m / g)
+};
+
+struct LevelDev {
+    int level = 0;
+    long long nboxes = 0, base = 0;     // compact boxes and their first global row
+    long long nclusters = 0, cbase = 0; // non-empty parents (FFT clusters) and first global cluster
+    int *slot = nullptr;                // [8^l] grid (x + N(y + N z)) -> compact box or -1
+    uint32_t *xyz = nullptr;            // [nboxes] packed x | y << 10 | z << 20
+    int *perm = nullptr;                // [nboxes] compact boxes sorted by (octant, Morton)
+    long long oct_start[9] = {0};       // segment of each octant in perm
+    int *cslot = nullptr;               // [8^(l-1)] parent grid -> cluster or -1
+    uint32_t *cxyz = nullptr;           // [nclusters] packed parent coordinates
+    int *cchild = nullptr;              // [nclusters][8] compact child box or -1
+    long long pairs = 0;                // M2L (target, source) pairs
+    // host copies (built without a GPU; uploaded on first use)
+    std::vector<int> h_slot, h_perm, h_cslot, h_cchild;
+    std::vector<uint32_t> h_xyz, h_cxyz;
+    bool on_device = false;
+};
+
+struct Workspace {
+    void *buf = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace m2l
+
+struct m2l_plan_s {
+    int depth = 0, p = 0, n = 0, kernel = 0;
+    double rank_tol = 0.0;
+    // options
+    int form = M2L_FORM_BLAS, precision = M2L_PREC_FP64, accumulate = 0, output = M2L_OUT_LOCALS;
+    double target_tol = 1e-6;
+    int fft_grid_opt = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 148;
+    // geometry
+    std::vector<int> lattice;                 // n x 3
+    int *lattice_dev = nullptr;               // packed a << 16 | b << 8 | c
+    m2l::LevelSet levels[m2l::kMaxDepth + 1];
+    // host operators (FP64)
+    bool blas_host_ready = false, fft_host_ready = false, pinv_ready = false;
+    int k = 0, kp = 0, r = 0, rp = 0, np_ = 0;
+    std::vector<double> U, S, C, s_fat, s_thin;   // U, S: n x k (row-major [n][k]); C: 316 x k x k
+    std::vector<double> Veps, Uteps;              // [n][r], [r][n]
+    std::vector<double> Aop;                      // [r][k] = Uteps * U
+    int g = 0, F = 0;
+    std::vector<double> Khat;                     // [316][F][2]
+    std::vector<double> twiddle;                  // [g][2]
+    // device
+    m2l::DevOps dev[4];                           // by precision (FP64, FP32, TF32X3, BF16X3 share FP32 data)
+    bool levels_dirty = true;
+    m2l::LevelDev ldev[m2l::kMaxDepth + 1];
+    long long total_rows = 0, total_clusters = 0;
+    m2l::Workspace ws, stage_in, stage_out;
+    void *tiles = nullptr;                         // device tile list for the contraction
+    long long ntiles = 0;
+    int tiles_rhs = -1, tiles_level = -2, tiles_rows = 0;
+    long long launches = 0;
+    // stage timing (M2L_OPT_TIMING)
+    int timing = 0;
+    struct StageEvent { int stage; cudaEvent_t a, b; long long launches; };
+    std::vector<StageEvent> events;   // recorded by the last apply
+    std::vector<cudaEvent_t> event_pool;
+    size_t events_used = 0;
+};
+
+namespace m2l {
+// plan.cpp
+int build_pinv(m2l_plan_t *pl);
+int build_blas_host(m2l_plan_t *pl);
+int build_fft_host(m2l_plan_t *pl);
+int build_level_tables(m2l_plan_t *pl);     // host tables and pair counts
+int upload_level_tables(m2l_plan_t *pl);    // device copies
+int upload_ops(m2l_plan_t *pl, int precision, int form);
+void free_device(m2l_plan_t *pl);
+// autotune.cpp
+int resolve_form(const m2l_plan_t *pl, int R, int *form, int *precision);
+// apply.cu
+void stage_begin(m2l_plan_t *pl, int stage);
+void stage_end(m2l_plan_t *pl, long long launches);
+int apply_device(m2l_plan_t *pl, const void *q, void *L, int level, int nrhs);
+}  // namespace m2l

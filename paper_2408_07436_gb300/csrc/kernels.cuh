@@ -1,0 +1,63 @@
+// Device-side declarations shared by the kernel translation units and the launcher.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace m2l {
+
+constexpr int kMaxLevels = 7;  // levels 2..8
+
+// Per-level box tables as seen by the kernels.
+struct LevelView {
+    const int *slot;        // [N^3] grid (x + N(y + N z)) -> compact box or -1
+    const uint32_t *xyz;    // [nboxes] packed x | y << 10 | z << 20
+    const int *perm;        // [nboxes] boxes grouped by octant
+    const int *cslot;       // [(N/2)^3] parent grid -> cluster or -1
+    const uint32_t *cxyz;   // [nclusters] packed parent coordinates
+    const int *cchild;      // [nclusters][8] compact child box or -1
+    long long base;         // first global box row of the level
+    long long cbase;        // first global cluster of the level
+    long long nboxes, nclusters;
+    long long oct_start[9];
+    int N;                  // boxes per axis, 2^level
+};
+
+struct LevelsArg {
+    LevelView L[kMaxLevels];
+    int count;
+};
+
+// One CTA of the contraction: rows [j0, j0 + rows) of the octant segment `oct` of level `lev`
+// (index into LevelsArg), where segment row j is (target perm[oct_start + j / R], rhs j % R).
+struct ContractTile {
+    int lev;
+    int oct;
+    int j0;
+    int rows;
+};
+
+// Y[r][o] (+)= sum_i X[r][i] W[o][i]; X rows x K (row stride ldx), W O x K (stride ldw).
+template <class T>
+int launch_gemm_xwt(const T *X, long long ldx, const T *W, long long ldw, T *Y, long long ldy,
+                    long long rows, int O, int K, int acc, cudaStream_t s);
+
+// B2 on CUDA cores: phit[(base+b)R + r][:] = sum_t C_t qt[(base+src)R + r][:].
+template <class T>
+int launch_contract_simt(const LevelsArg &lv, const ContractTile *tiles, long long ntiles, int R,
+                         const T *qt, const T *C, int kp, long long zero_row, T *phit, cudaStream_t s);
+
+// FFT form, one level at a time.
+template <class T>
+int launch_fft_forward(const LevelView &L, int R, int p, int n, int g, const int *lattice,
+                       const T *tw, const T *q, T *qhat, cudaStream_t s);
+template <class T>
+int launch_hadamard(const LevelView &L, int R, int F, const T *Khat, const T *qhat, T *phihat,
+                    cudaStream_t s);
+template <class T>
+int launch_fft_inverse(const LevelView &L, int R, int p, int n, int g, const int *lattice,
+                       const T *tw, const T *phihat, T *phi, long long ldphi, int acc, cudaStream_t s);
+
+// Constant tables (transfer index lookup and the cluster-pair table); once per device.
+int ensure_constants(int device);
+
+}  // namespace m2l

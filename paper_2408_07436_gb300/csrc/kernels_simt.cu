@@ -1,0 +1,555 @@
+// CUDA-core kernels of the M2L library (FP64 and FP32): the small GEMMs of the BLAS form
+// (compress S^T q, uncompress + pseudo-inverse), the gathered contraction over the 189
+// transfer vectors of each target octant, and the three stages of the FFT form.
+#include <cstdio>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace m2l {
+
+// ----------------------------------------------------------------------------------------------
+// Constant tables.
+//   c_tidx[x+3][y+3][z+3]: index of transfer vector (x, y, z) in [-3,3]^3 \ [-1,1]^3 (x slowest), or -1.
+//   c_clu[d][8 i + j]:     transfer vector from child j of the source cluster in direction d to
+//                          child i of the target cluster, or -1 when the two boxes are adjacent
+//                          (App. A.1 cluster formulation: 26 directions x 64 pairs).
+//   c_dir[d]:              the 26 parent offsets in [-1,1]^3 \ {0}, x slowest.
+__constant__ short c_tidx[7][7][7];
+__constant__ short c_clu[26][64];
+__constant__ signed char c_dir[26][3];
+
+int ensure_constants(int device) {
+    static bool done[64] = {false};
+    if (device < 0 || device >= 64) return M2L_EINVAL;
+    if (done[device]) return M2L_OK;
+    short tidx[7][7][7];
+    for (int x = -3; x <= 3; ++x)
+        for (int y = -3; y <= 3; ++y)
+            for (int z = -3; z <= 3; ++z) tidx[x + 3][y + 3][z + 3] = (short)transfer_index(x, y, z);
+    short clu[26][64];
+    signed char dir[26][3];
+    int d = 0;
+    for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz) {
+                if (!dx && !dy && !dz) continue;
+                dir[d][0] = (signed char)dx; dir[d][1] = (signed char)dy; dir[d][2] = (signed char)dz;
+                for (int i = 0; i < 8; ++i)
+                    for (int j = 0; j < 8; ++j) {
+                        int tx = 2 * dx + (j & 1) - (i & 1);
+                        int ty = 2 * dy + ((j >> 1) & 1) - ((i >> 1) & 1);
+                        int tz = 2 * dz + ((j >> 2) & 1) - ((i >> 2) & 1);
+                        clu[d][8 * i + j] = (short)transfer_index(tx, ty, tz);
+                    }
+                ++d;
+            }
+    if (cudaMemcpyToSymbol(c_tidx, tidx, sizeof tidx) != cudaSuccess ||
+        cudaMemcpyToSymbol(c_clu, clu, sizeof clu) != cudaSuccess ||
+        cudaMemcpyToSymbol(c_dir, dir, sizeof dir) != cudaSuccess) {
+        set_error("uploading constant tables failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return M2L_ECUDA;
+    }
+    done[device] = true;
+    return M2L_OK;
+}
+
+static int check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("%s launch failed: %s", what, cudaGetErrorString(e));
+        return M2L_ECUDA;
+    }
+    return M2L_OK;
+}
+
+// ----------------------------------------------------------------------------------------------
+// Y = X W^T (+ Y): 64 x 64 output tile per CTA, 4 x 4 per thread, K in steps of 16.
+template <class T>
+__global__ void __launch_bounds__(256) gemm_xwt_kernel(const T *__restrict__ X, long long ldx,
+                                                       const T *__restrict__ W, long long ldw,
+                                                       T *__restrict__ Y, long long ldy, long long rows,
+                                                       int O, int K, int acc) {
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ T Xs[BK][BM + 4];
+    __shared__ T Ws[BK][BN + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const long long row0 = (long long)blockIdx.x * BM;
+    const int col0 = blockIdx.y * BN;
+    T a[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[i][j] = T(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += 256) {
+            int r = e / BK, kk = e % BK;
+            long long gr = row0 + r;
+            int gk = k0 + kk, gc = col0 + r;
+            Xs[kk][r] = (gr < rows && gk < K) ? X[gr * ldx + gk] : T(0);
+            Ws[kk][r] = (gc < O && gk < K) ? W[(long long)gc * ldw + gk] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T xa[4], wb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                xa[i] = Xs[kk][ty * 4 + i];
+                wb[i] = Ws[kk][tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a[i][j] = fma(xa[i], wb[j], a[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        long long r = row0 + ty * 4 + i;
+        if (r >= rows) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int c = col0 + tx * 4 + j;
+            if (c < O) {
+                T v = a[i][j];
+                if (acc) v += Y[r * ldy + c];
+                Y[r * ldy + c] = v;
+            }
+        }
+    }
+}
+
+template <class T>
+int launch_gemm_xwt(const T *X, long long ldx, const T *W, long long ldw, T *Y, long long ldy,
+                    long long rows, int O, int K, int acc, cudaStream_t s) {
+    if (rows <= 0 || O <= 0) return M2L_OK;
+    dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((O + 63) / 64));
+    gemm_xwt_kernel<T><<<grid, 256, 0, s>>>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc);
+    return check_launch("gemm");
+}
+
+// ----------------------------------------------------------------------------------------------
+// B2 on CUDA cores: for a tile of (target, rhs) rows of one octant, accumulate over the 189
+// transfer vectors of that octant phit[row] += C_t qt[source(row, t)] (Sec. 3.2 steps 3-5 fused:
+// sources are gathered on the fly, nothing is materialised per transfer vector).
+template <class T>
+__global__ void __launch_bounds__(256) contract_simt_kernel(LevelsArg lv, const ContractTile *__restrict__ tiles,
+                                                            int R, const T *__restrict__ qt,
+                                                            const T *__restrict__ C, int kp,
+                                                            long long zero_row, T *__restrict__ phit) {
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ T Xs[BK][BM + 4];
+    __shared__ T Ws[BK][BN + 4];
+    __shared__ long long src_row[BM];
+    __shared__ int tgt_b[BM], tgt_r[BM];
+    __shared__ uint32_t tgt_xyz[BM];
+    const ContractTile tile = tiles[blockIdx.x];
+    const LevelView &L = lv.L[tile.lev];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int col0 = blockIdx.y * BN;
+    if (tid < BM) {
+        if (tid < tile.rows) {
+            long long j = (long long)tile.j0 + tid;
+            int b = L.perm[L.oct_start[tile.oct] + j / R];
+            tgt_b[tid] = b;
+            tgt_r[tid] = (int)(j % R);
+            tgt_xyz[tid] = L.xyz[b];
+        } else {
+            tgt_b[tid] = -1;
+            tgt_r[tid] = 0;
+            tgt_xyz[tid] = 0;
+        }
+    }
+    T a[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[i][j] = T(0);
+    const int cx = tile.oct & 1, cy = (tile.oct >> 1) & 1, cz = (tile.oct >> 2) & 1;
+    const int N = L.N;
+    for (int dx = -2 - cx; dx <= 3 - cx; ++dx)
+        for (int dy = -2 - cy; dy <= 3 - cy; ++dy)
+            for (int dz = -2 - cz; dz <= 3 - cz; ++dz) {
+                int ti = c_tidx[dx + 3][dy + 3][dz + 3];
+                if (ti < 0) continue;  // adjacent: near field
+                __syncthreads();       // previous src_row fully consumed
+                if (tid < BM) {
+                    long long sr = zero_row;
+                    if (tgt_b[tid] >= 0) {
+                        uint32_t p = tgt_xyz[tid];
+                        int x = (int)(p & 1023) + dx, y = (int)((p >> 10) & 1023) + dy, z = (int)((p >> 20) & 1023) + dz;
+                        if (x >= 0 && y >= 0 && z >= 0 && x < N && y < N && z < N) {
+                            int s = L.slot[((long long)z * N + y) * N + x];
+                            if (s >= 0) sr = (L.base + s) * R + tgt_r[tid];
+                        }
+                    }
+                    src_row[tid] = sr;
+                }
+                __syncthreads();
+                const T *Ct = C + (long long)ti * kp * kp;
+                for (int k0 = 0; k0 < kp; k0 += BK) {
+                    for (int e = tid; e < BM * BK; e += 256) {
+                        int r = e / BK, kk = e % BK;
+                        Xs[kk][r] = qt[src_row[r] * kp + k0 + kk];
+                        int gc = col0 + r;
+                        Ws[kk][r] = gc < kp ? Ct[(long long)gc * kp + k0 + kk] : T(0);
+                    }
+                    __syncthreads();
+#pragma unroll
+                    for (int kk = 0; kk < BK; ++kk) {
+                        T xa[4], wb[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            xa[i] = Xs[kk][ty * 4 + i];
+                            wb[i] = Ws[kk][tx * 4 + i];
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) a[i][j] = fma(xa[i], wb[j], a[i][j]);
+                    }
+                    __syncthreads();
+                }
+            }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int r = ty * 4 + i;
+        if (r >= tile.rows) continue;
+        long long orow = (L.base + tgt_b[r]) * R + tgt_r[r];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int c = col0 + tx * 4 + j;
+            if (c < kp) phit[orow * kp + c] = a[i][j];
+        }
+    }
+}
+
+template <class T>
+int launch_contract_simt(const LevelsArg &lv, const ContractTile *tiles, long long ntiles, int R,
+                         const T *qt, const T *C, int kp, long long zero_row, T *phit, cudaStream_t s) {
+    if (ntiles <= 0) return M2L_OK;
+    dim3 grid((unsigned)ntiles, (unsigned)((kp + 63) / 64));
+    contract_simt_kernel<T><<<grid, 256, 0, s>>>(lv, tiles, R, qt, C, kp, zero_row, phit);
+    return check_launch("contract");
+}
+
+// ----------------------------------------------------------------------------------------------
+// FFT form. Lattice entries are packed a << 16 | b << 8 | c. Spectra are stored per
+// (cluster, rhs) as [F][8] complex: the eight siblings of a cluster interleaved by frequency
+// (App. A.1 steps 3 and 5: "frequency order").
+
+__device__ inline uint32_t parent_linear(uint32_t xyz, int Np) {
+    int x = (xyz & 1023) >> 1, y = ((xyz >> 10) & 1023) >> 1, z = ((xyz >> 20) & 1023) >> 1;
+    return ((uint32_t)z * Np + y) * Np + x;
+}
+__device__ inline int octant_of(uint32_t xyz) {
+    return (xyz & 1) | (((xyz >> 10) & 1) << 1) | (((xyz >> 20) & 1) << 2);
+}
+
+// Embed the n densities of one (box, rhs) on the g^3 grid (lattice points [0, p)^3) and take the
+// real 3D DFT, pruned to the nonzero input cube: along z (real -> kz in [0, g/2]), then y, then x.
+template <class T>
+__global__ void __launch_bounds__(128) fft_forward_kernel(LevelView L, int R, int p, int n, int g,
+                                                          const int *__restrict__ lattice,
+                                                          const T *__restrict__ tw,
+                                                          const T *__restrict__ q, T *__restrict__ qhat) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int H = g / 2 + 1, F = g * g * H;
+    T *tws = reinterpret_cast<T *>(smem_raw);     // 2g
+    T *xs = tws + 2 * g;                          // p^3
+    T *Y1 = xs + p * p * p;                       // p*p*H complex
+    T *Y2 = Y1 + 2 * p * p * H;                   // p*g*H complex
+    const long long row = blockIdx.x + (long long)blockIdx.y * gridDim.x;
+    if (row >= L.nboxes * R) return;
+    const long long b = row / R;
+    const int r = (int)(row % R);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < 2 * g; i += nt) tws[i] = tw[i];
+    for (int i = tid; i < p * p * p; i += nt) xs[i] = T(0);
+    __syncthreads();
+    const T *qrow = q + (b * R + r) * (long long)n;
+    for (int i = tid; i < n; i += nt) {
+        int lat = lattice[i];
+        int a = lat >> 16, bb = (lat >> 8) & 255, c = lat & 255;
+        xs[(a * p + bb) * p + c] = qrow[i];
+    }
+    __syncthreads();
+    for (int e = tid; e < p * p * H; e += nt) {
+        int ab = e / H, kz = e % H;
+        T re = 0, im = 0;
+        int m = 0;
+        for (int c = 0; c < p; ++c) {
+            T v = xs[ab * p + c];
+            re = fma(v, tws[2 * m], re);
+            im = fma(v, tws[2 * m + 1], im);
+            m += kz;
+            if (m >= g) m -= g;
+        }
+        Y1[2 * e] = re;
+        Y1[2 * e + 1] = im;
+    }
+    __syncthreads();
+    for (int e = tid; e < p * g * H; e += nt) {
+        int a = e / (g * H), ky = (e / H) % g, kz = e % H;
+        T re = 0, im = 0;
+        int m = 0;
+        for (int bb = 0; bb < p; ++bb) {
+            int o = ((a * p + bb) * H + kz) * 2;
+            T xr = Y1[o], xi = Y1[o + 1], wr = tws[2 * m], wi = tws[2 * m + 1];
+            re = fma(xr, wr, fma(-xi, wi, re));
+            im = fma(xr, wi, fma(xi, wr, im));
+            m += ky;
+            if (m >= g) m -= g;
+        }
+        Y2[2 * e] = re;
+        Y2[2 * e + 1] = im;
+    }
+    __syncthreads();
+    const uint32_t xyz = L.xyz[b];
+    const int oct = octant_of(xyz);
+    const int cl = L.cslot[parent_linear(xyz, L.N / 2)];
+    T *out = qhat + ((L.cbase + cl) * R + r) * (long long)F * 16;
+    for (int f = tid; f < F; f += nt) {
+        int kx = f / (g * H), ky = (f / H) % g, kz = f % H;
+        T re = 0, im = 0;
+        int m = 0;
+        for (int a = 0; a < p; ++a) {
+            int o = ((a * g + ky) * H + kz) * 2;
+            T xr = Y2[o], xi = Y2[o + 1], wr = tws[2 * m], wi = tws[2 * m + 1];
+            re = fma(xr, wr, fma(-xi, wi, re));
+            im = fma(xr, wi, fma(xi, wr, im));
+            m += kx;
+            if (m >= g) m -= g;
+        }
+        out[(long long)f * 16 + 2 * oct] = re;
+        out[(long long)f * 16 + 2 * oct + 1] = im;
+    }
+}
+
+template <class T>
+static size_t fft_forward_smem(int p, int g) {
+    int H = g / 2 + 1;
+    return sizeof(T) * (size_t)(2 * g + p * p * p + 2 * p * p * H + 2 * p * g * H);
+}
+template <class T>
+static size_t fft_inverse_smem(int p, int g) {
+    int H = g / 2 + 1;
+    size_t F = (size_t)g * g * H;
+    return sizeof(T) * (2 * g + 2 * F + 2 * (size_t)p * g * H);
+}
+
+template <class T>
+int launch_fft_forward(const LevelView &L, int R, int p, int n, int g, const int *lattice, const T *tw,
+                       const T *q, T *qhat, cudaStream_t s) {
+    long long rows = L.nboxes * R;
+    if (rows <= 0) return M2L_OK;
+    size_t smem = fft_forward_smem<T>(p, g);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(fft_forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    unsigned gx = (unsigned)(rows < 65535 ? rows : 65535);
+    unsigned gy = (unsigned)((rows + gx - 1) / gx);
+    fft_forward_kernel<T><<<dim3(gx, gy), 128, smem, s>>>(L, R, p, n, g, lattice, tw, q, qhat);
+    return check_launch("fft_forward");
+}
+
+// F3: for each target cluster, rhs and frequency, sum over the 26 source clusters the 8 x 8
+// complex products phihat[i] += Khat_{t(d,i,j)} qhat[j] (App. A.1, Hadamard component), skipping
+// adjacent pairs. The kernel spectra of a block of FB frequencies sit in shared memory.
+template <class T, int FB>
+__global__ void __launch_bounds__(256) hadamard_kernel(LevelView L, int R, int F, const T *__restrict__ Khat,
+                                                       const T *__restrict__ qhat, T *__restrict__ phihat) {
+    __shared__ T Ks[(kNumTransfer + 1) * FB * 2];
+    const int f0 = blockIdx.x * FB;
+    for (int e = threadIdx.x; e < (kNumTransfer + 1) * FB; e += blockDim.x) {
+        int ti = e / FB, fl = e % FB, f = f0 + fl;
+        T re = 0, im = 0;
+        if (f < F) {
+            re = Khat[((long long)ti * F + f) * 2];
+            im = Khat[((long long)ti * F + f) * 2 + 1];
+        }
+        Ks[2 * e] = re;
+        Ks[2 * e + 1] = im;
+    }
+    __syncthreads();
+    constexpr int TC = 256 / FB;
+    const int fl = threadIdx.x % FB, tcl = threadIdx.x / FB;
+    const int f = f0 + fl;
+    if (f >= F) return;
+    const int Np = L.N / 2;
+    const long long items = L.nclusters * R;
+    for (long long item = (long long)blockIdx.y * TC + tcl; item < items; item += (long long)gridDim.y * TC) {
+        const long long tc = item / R;
+        const int r = (int)(item % R);
+        const uint32_t pc = L.cxyz[tc];
+        const int px = pc & 1023, py = (pc >> 10) & 1023, pz = (pc >> 20) & 1023;
+        T ar[8], ai[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ar[i] = ai[i] = T(0);
+        for (int d = 0; d < kDirections; ++d) {
+            int sx = px + c_dir[d][0], sy = py + c_dir[d][1], sz = pz + c_dir[d][2];
+            if (sx < 0 || sy < 0 || sz < 0 || sx >= Np || sy >= Np || sz >= Np) continue;
+            int sc = L.cslot[((long long)sz * Np + sy) * Np + sx];
+            if (sc < 0) continue;
+            const T *qs = qhat + (((L.cbase + sc) * R + r) * (long long)F + f) * 16;
+            T qr[8], qi[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                qr[j] = qs[2 * j];
+                qi[j] = qs[2 * j + 1];
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    int ti = c_clu[d][8 * i + j];
+                    if (ti >= 0) {
+                        T kr = Ks[(ti * FB + fl) * 2], ki = Ks[(ti * FB + fl) * 2 + 1];
+                        ar[i] = fma(kr, qr[j], fma(-ki, qi[j], ar[i]));
+                        ai[i] = fma(kr, qi[j], fma(ki, qr[j], ai[i]));
+                    }
+                }
+        }
+        T *out = phihat + (((L.cbase + tc) * R + r) * (long long)F + f) * 16;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            out[2 * i] = ar[i];
+            out[2 * i + 1] = ai[i];
+        }
+    }
+}
+
+template <class T>
+int launch_hadamard(const LevelView &L, int R, int F, const T *Khat, const T *qhat, T *phihat, cudaStream_t s) {
+    constexpr int FB = 8, TC = 256 / FB;
+    long long items = L.nclusters * R;
+    if (items <= 0) return M2L_OK;
+    unsigned gx = (unsigned)((F + FB - 1) / FB);
+    long long gy = (items + TC * 8 - 1) / (TC * 8);
+    if (gy < 1) gy = 1;
+    if (gy > 65535) gy = 65535;
+    hadamard_kernel<T, FB><<<dim3(gx, (unsigned)gy), 256, 0, s>>>(L, R, F, Khat, qhat, phihat);
+    return check_launch("hadamard");
+}
+
+// F4 + F5: inverse DFT of one (box, rhs) spectrum, evaluated only at the surface points of the
+// lattice cube [0, p)^3 (along x, then y, then the Hermitian half along z), scaled by 1/g^3.
+template <class T>
+__global__ void __launch_bounds__(128) fft_inverse_kernel(LevelView L, int R, int p, int n, int g,
+                                                          const int *__restrict__ lattice,
+                                                          const T *__restrict__ tw,
+                                                          const T *__restrict__ phihat, T *__restrict__ phi,
+                                                          long long ldphi, int acc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int H = g / 2 + 1, F = g * g * H;
+    T *tws = reinterpret_cast<T *>(smem_raw);  // 2g
+    T *X = tws + 2 * g;                        // F complex; reused for Z2 (p*p*H complex)
+    T *Z1 = X + 2 * F;                         // p*g*H complex
+    const long long row = blockIdx.x + (long long)blockIdx.y * gridDim.x;
+    if (row >= L.nboxes * R) return;
+    const long long b = row / R;
+    const int r = (int)(row % R);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t xyz = L.xyz[b];
+    const int oct = octant_of(xyz);
+    const int cl = L.cslot[parent_linear(xyz, L.N / 2)];
+    const T *in = phihat + ((L.cbase + cl) * R + r) * (long long)F * 16 + 2 * oct;
+    for (int i = tid; i < 2 * g; i += nt) tws[i] = tw[i];
+    for (int f = tid; f < F; f += nt) {
+        X[2 * f] = in[(long long)f * 16];
+        X[2 * f + 1] = in[(long long)f * 16 + 1];
+    }
+    __syncthreads();
+    // along x: Z1[a][ky][kz] = sum_kx X[kx][ky][kz] conj(w^(a kx)), a < p
+    for (int e = tid; e < p * g * H; e += nt) {
+        int a = e / (g * H), kykz = e % (g * H);
+        T re = 0, im = 0;
+        int m = 0;
+        for (int kx = 0; kx < g; ++kx) {
+            int o = (kx * g * H + kykz) * 2;
+            T xr = X[o], xi = X[o + 1], wr = tws[2 * m], wi = -tws[2 * m + 1];
+            re = fma(xr, wr, fma(-xi, wi, re));
+            im = fma(xr, wi, fma(xi, wr, im));
+            m += a;
+            if (m >= g) m -= g;
+        }
+        Z1[2 * e] = re;
+        Z1[2 * e + 1] = im;
+    }
+    __syncthreads();
+    // along y: Z2[a][b][kz] = sum_ky Z1[a][ky][kz] conj(w^(b ky)), b < p  (stored over X)
+    T *Z2 = X;
+    for (int e = tid; e < p * p * H; e += nt) {
+        int a = e / (p * H), bb = (e / H) % p, kz = e % H;
+        T re = 0, im = 0;
+        int m = 0;
+        for (int ky = 0; ky < g; ++ky) {
+            int o = ((a * g + ky) * H + kz) * 2;
+            T xr = Z1[o], xi = Z1[o + 1], wr = tws[2 * m], wi = -tws[2 * m + 1];
+            re = fma(xr, wr, fma(-xi, wi, re));
+            im = fma(xr, wi, fma(xi, wr, im));
+            m += bb;
+            if (m >= g) m -= g;
+        }
+        Z2[2 * e] = re;
+        Z2[2 * e + 1] = im;
+    }
+    __syncthreads();
+    // along z (Hermitian): out = Re Z2[0] + sum_{kz>=1} w_kz Re(Z2[kz] conj(w^(c kz))), at surface points
+    const T scale = T(1) / (T)((long long)g * g * g);
+    const bool even = (g % 2) == 0;
+    T *outrow = phi + (b * R + r) * ldphi;
+    for (int i = tid; i < n; i += nt) {
+        int lat = lattice[i];
+        int a = lat >> 16, bb = (lat >> 8) & 255, c = lat & 255;
+        const T *z = Z2 + ((a * p + bb) * H) * 2;
+        T v = z[0];
+        int m = c;
+        for (int kz = 1; kz < H; ++kz) {
+            T wgt = (even && kz == H - 1) ? T(1) : T(2);
+            // Re(Z2[kz] e^{+2 pi i c kz / g}); tws holds e^{-2 pi i m / g}
+            v = fma(wgt, fma(z[2 * kz], tws[2 * m], z[2 * kz + 1] * tws[2 * m + 1]), v);
+            m += c;
+            if (m >= g) m -= g;
+        }
+        v *= scale;
+        if (acc) v += outrow[i];
+        outrow[i] = v;
+    }
+}
+
+template <class T>
+int launch_fft_inverse(const LevelView &L, int R, int p, int n, int g, const int *lattice, const T *tw,
+                       const T *phihat, T *phi, long long ldphi, int acc, cudaStream_t s) {
+    long long rows = L.nboxes * R;
+    if (rows <= 0) return M2L_OK;
+    size_t smem = fft_inverse_smem<T>(p, g);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(fft_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    unsigned gx = (unsigned)(rows < 65535 ? rows : 65535);
+    unsigned gy = (unsigned)((rows + gx - 1) / gx);
+    fft_inverse_kernel<T><<<dim3(gx, gy), 128, smem, s>>>(L, R, p, n, g, lattice, tw, phihat, phi, ldphi, acc);
+    return check_launch("fft_inverse");
+}
+
+size_t fft_smem_bytes(int p, int g, int elt) {
+    size_t a = elt == 8 ? fft_forward_smem<double>(p, g) : fft_forward_smem<float>(p, g);
+    size_t b = elt == 8 ? fft_inverse_smem<double>(p, g) : fft_inverse_smem<float>(p, g);
+    return a > b ? a : b;
+}
+
+#define M2L_INSTANTIATE(T)                                                                              \
+    template int launch_gemm_xwt<T>(const T *, long long, const T *, long long, T *, long long, long long, \
+                                    int, int, int, cudaStream_t);                                       \
+    template int launch_contract_simt<T>(const LevelsArg &, const ContractTile *, long long, int, const T *, \
+                                         const T *, int, long long, T *, cudaStream_t);                 \
+    template int launch_fft_forward<T>(const LevelView &, int, int, int, int, const int *, const T *,   \
+                                       const T *, T *, cudaStream_t);                                   \
+    template int launch_hadamard<T>(const LevelView &, int, int, const T *, const T *, T *, cudaStream_t); \
+    template int launch_fft_inverse<T>(const LevelView &, int, int, int, int, const int *, const T *,   \
+                                       const T *, T *, long long, int, cudaStream_t);
+M2L_INSTANTIATE(double)
+M2L_INSTANTIATE(float)
+
+}  // namespace m2l

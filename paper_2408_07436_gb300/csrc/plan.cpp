@@ -1,0 +1,538 @@
+// Plan construction (host, FP64): surfaces, M2L operators, pseudo-inverse, SVD compression,
+// kernel spectra and the per-level box tables; upload of the device copies.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <numeric>
+
+#include "internal.h"
+#include "linalg.h"
+
+namespace m2l {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+const char *last_error() { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------------------------
+// Transfer vectors: [-3,3]^3 minus [-1,1]^3, x slowest (Sec. 3.1).
+static int g_tidx[7][7][7];
+static int g_tvec[kNumTransfer][3];
+static bool g_tready = false;
+
+static void init_transfer() {
+    if (g_tready) return;
+    int k = 0;
+    for (int x = -3; x <= 3; ++x)
+        for (int y = -3; y <= 3; ++y)
+            for (int z = -3; z <= 3; ++z) {
+                int m = std::max(std::abs(x), std::max(std::abs(y), std::abs(z)));
+                if (m >= 2) {
+                    g_tidx[x + 3][y + 3][z + 3] = k;
+                    g_tvec[k][0] = x; g_tvec[k][1] = y; g_tvec[k][2] = z;
+                    ++k;
+                } else {
+                    g_tidx[x + 3][y + 3][z + 3] = -1;
+                }
+            }
+    g_tready = true;
+}
+
+int transfer_index(int x, int y, int z) {
+    init_transfer();
+    if (x < -3 || x > 3 || y < -3 || y > 3 || z < -3 || z > 3) return -1;
+    return g_tidx[x + 3][y + 3][z + 3];
+}
+
+void transfer_vector(int idx, int &x, int &y, int &z) {
+    init_transfer();
+    x = g_tvec[idx][0]; y = g_tvec[idx][1]; z = g_tvec[idx][2];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Surfaces (Sec. 2.1.1; App. A.3 point count): boundary points of the p^3 lattice, x slowest.
+static void surface(const m2l_plan_t *pl, double cx, double cy, double cz, double alpha,
+                    std::vector<double> &pts) {
+    int n = pl->n, p = pl->p;
+    pts.resize((size_t)3 * n);
+    for (int i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) {
+            double c = a == 0 ? cx : (a == 1 ? cy : cz);
+            pts[3 * i + a] = c + alpha * 0.5 * (-1.0 + 2.0 * pl->lattice[3 * i + a] / (p - 1));
+        }
+    }
+}
+
+static inline double laplace(const double *x, const double *y) {
+    double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+    return 1.0 / (4.0 * M_PI * std::sqrt(d0 * d0 + d1 * d1 + d2 * d2));
+}
+
+// K_t (n x n, row-major [i][j]): downward-check of the unit target at the origin against the
+// upward-equivalent points of the unit source at t (Sec. 2.2).
+static void m2l_matrix(const m2l_plan_t *pl, int t, std::vector<double> &K) {
+    int x, y, z;
+    transfer_vector(t, x, y, z);
+    std::vector<double> xs, ys;
+    surface(pl, 0, 0, 0, kAlphaInner, xs);
+    surface(pl, x, y, z, kAlphaInner, ys);
+    int n = pl->n;
+    K.resize((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) K[(size_t)i * n + j] = laplace(&xs[3 * i], &ys[3 * j]);
+}
+
+static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Pseudo-inverse of the downward check -> equivalent matrix (Eqs. 7-10, alpha = 0), kept as
+// V_eps and Ut_eps = Sigma_eps^-1 U_eps^T (the two-factor storage of the Sec. 2.1.1 footnote).
+int build_pinv(m2l_plan_t *pl) {
+    if (pl->pinv_ready) return M2L_OK;
+    int n = pl->n;
+    std::vector<double> xs, ys;
+    surface(pl, 0, 0, 0, kAlphaInner, xs);   // downward check
+    surface(pl, 0, 0, 0, kAlphaOuter, ys);   // downward equivalent
+    std::vector<double> K((size_t)n * n);    // column-major
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) K[(size_t)j * n + i] = laplace(&xs[3 * i], &ys[3 * j]);
+    std::vector<double> U, s, V;
+    jacobi_svd(K, n, n, U, s, V);
+    double thresh = n * 2.220446049250313e-16 * s[0];
+    int r = 0;
+    while (r < n && s[r] > thresh) ++r;
+    pl->r = r;
+    pl->rp = round_up(r, 16);
+    pl->Veps.assign((size_t)n * r, 0.0);
+    pl->Uteps.assign((size_t)r * n, 0.0);
+    for (int a = 0; a < r; ++a)
+        for (int i = 0; i < n; ++i) {
+            pl->Veps[(size_t)i * r + a] = V[(size_t)a * n + i];
+            pl->Uteps[(size_t)a * n + i] = U[(size_t)a * n + i] / s[a];
+        }
+    pl->pinv_ready = true;
+    return M2L_OK;
+}
+
+// SVD compression of Sec. 3.1 (Eqs. 12-14). Full rank (rank_tol <= 0) uses U = S = I: the
+// compressed form is then exact for any orthonormal bases, so no SVD is needed.
+int build_blas_host(m2l_plan_t *pl) {
+    if (pl->blas_host_ready) return M2L_OK;
+    int rc = build_pinv(pl);
+    if (rc) return rc;
+    int n = pl->n;
+    std::vector<std::vector<double>> Ks(kNumTransfer);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int t = 0; t < kNumTransfer; ++t) m2l_matrix(pl, t, Ks[t]);
+    int k;
+    if (pl->rank_tol <= 0) {
+        k = n;
+        pl->U.assign((size_t)n * k, 0.0);
+        for (int i = 0; i < n; ++i) pl->U[(size_t)i * k + i] = 1.0;
+        pl->S = pl->U;
+        pl->s_fat.clear();
+        pl->s_thin.clear();
+    } else {
+        // K_thin = [K_1; ...; K_316]: stack the column-major K_t. K_fat^T = [K_1^T; ...]:
+        // a row-major K_t read as column-major is K_t^T.
+        std::vector<std::vector<double>> thin(kNumTransfer), fatT(kNumTransfer);
+        for (int t = 0; t < kNumTransfer; ++t) {
+            fatT[t] = Ks[t];
+            thin[t].resize((size_t)n * n);
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) thin[t][(size_t)j * n + i] = Ks[t][(size_t)i * n + j];
+        }
+        std::vector<double> Rf = stacked_r_factor(std::move(fatT), n);
+        std::vector<double> Rt = stacked_r_factor(std::move(thin), n);
+        std::vector<double> Uf, Vf, Ut_, Vt_;
+        jacobi_svd(Rf, n, n, Uf, pl->s_fat, Vf);
+        jacobi_svd(Rt, n, n, Ut_, pl->s_thin, Vt_);
+        int kf = 0, kt = 0;
+        while (kf < n && pl->s_fat[kf] / pl->s_fat[0] >= pl->rank_tol) ++kf;
+        while (kt < n && pl->s_thin[kt] / pl->s_thin[0] >= pl->rank_tol) ++kt;
+        k = std::max(kf, kt);
+        if (k < 1) k = 1;
+        // U: left singular vectors of K_fat = right singular vectors of K_fat^T (and of Rf).
+        pl->U.assign((size_t)n * k, 0.0);
+        pl->S.assign((size_t)n * k, 0.0);
+        for (int c = 0; c < k; ++c)
+            for (int i = 0; i < n; ++i) {
+                pl->U[(size_t)i * k + c] = Vf[(size_t)c * n + i];
+                pl->S[(size_t)i * k + c] = Vt_[(size_t)c * n + i];
+            }
+    }
+    pl->k = k;
+    pl->kp = round_up(k, 16);
+    // C_t = U^T K_t S  (k x k, row-major)
+    pl->C.assign((size_t)kNumTransfer * k * k, 0.0);
+#pragma omp parallel for schedule(dynamic, 2)
+    for (int t = 0; t < kNumTransfer; ++t) {
+        std::vector<double> KS((size_t)n * k, 0.0);
+        const double *K = Ks[t].data();
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double kij = K[(size_t)i * n + j];
+                const double *srow = &pl->S[(size_t)j * k];
+                double *dst = &KS[(size_t)i * k];
+                for (int c = 0; c < k; ++c) dst[c] += kij * srow[c];
+            }
+        double *C = &pl->C[(size_t)t * k * k];
+        for (int i = 0; i < n; ++i) {
+            const double *urow = &pl->U[(size_t)i * k];
+            const double *ks = &KS[(size_t)i * k];
+            for (int a = 0; a < k; ++a) {
+                double u = urow[a];
+                if (u == 0.0) continue;
+                for (int c = 0; c < k; ++c) C[(size_t)a * k + c] += u * ks[c];
+            }
+        }
+    }
+    // A = Ut_eps U  (r x k): the scaled factor of the pseudo-inverse times the uncompression.
+    int r = pl->r;
+    pl->Aop.assign((size_t)r * k, 0.0);
+    for (int a = 0; a < r; ++a)
+        for (int i = 0; i < n; ++i) {
+            double u = pl->Uteps[(size_t)a * n + i];
+            for (int c = 0; c < k; ++c) pl->Aop[(size_t)a * k + c] += u * pl->U[(size_t)i * k + c];
+        }
+    pl->blas_host_ready = true;
+    return M2L_OK;
+}
+
+// Kernel spectra (App. A.1 step 1): for each transfer vector the kernel sequence
+// G_t(m) = K(-t + h m), h = alpha_inner / (p - 1), m in [-(p-1), p-1]^3, placed at m mod g on the
+// g^3 grid, then its 3D real DFT keeping kz in [0, g/2] (f = (kx g + ky)(g/2+1) + kz).
+int build_fft_host(m2l_plan_t *pl) {
+    if (pl->fft_host_ready) return M2L_OK;
+    int rc = build_pinv(pl);
+    if (rc) return rc;
+    int p = pl->p;
+    int g = pl->fft_grid_opt ? pl->fft_grid_opt : 2 * p;
+    int H = g / 2 + 1;
+    pl->g = g;
+    pl->F = g * g * H;
+    pl->twiddle.resize((size_t)2 * g);
+    for (int m = 0; m < g; ++m) {
+        pl->twiddle[2 * m] = std::cos(2.0 * M_PI * m / g);
+        pl->twiddle[2 * m + 1] = -std::sin(2.0 * M_PI * m / g);
+    }
+    const double h = kAlphaInner / (p - 1);
+    pl->Khat.assign((size_t)kNumTransfer * pl->F * 2, 0.0);
+    const double *w = pl->twiddle.data();
+#pragma omp parallel for schedule(dynamic, 2)
+    for (int t = 0; t < kNumTransfer; ++t) {
+        int tx, ty, tz;
+        transfer_vector(t, tx, ty, tz);
+        std::vector<double> grid((size_t)g * g * g, 0.0);
+        for (int mx = -(p - 1); mx <= p - 1; ++mx)
+            for (int my = -(p - 1); my <= p - 1; ++my)
+                for (int mz = -(p - 1); mz <= p - 1; ++mz) {
+                    double d0 = -tx + h * mx, d1 = -ty + h * my, d2 = -tz + h * mz;
+                    double v = 1.0 / (4.0 * M_PI * std::sqrt(d0 * d0 + d1 * d1 + d2 * d2));
+                    int a = ((mx % g) + g) % g, b = ((my % g) + g) % g, c = ((mz % g) + g) % g;
+                    grid[((size_t)a * g + b) * g + c] = v;
+                }
+        // along z (real -> half spectrum)
+        std::vector<double> Y1((size_t)g * g * H * 2, 0.0);
+        for (int a = 0; a < g; ++a)
+            for (int b = 0; b < g; ++b)
+                for (int kz = 0; kz < H; ++kz) {
+                    double re = 0, im = 0;
+                    for (int c = 0; c < g; ++c) {
+                        double v = grid[((size_t)a * g + b) * g + c];
+                        int m = (c * kz) % g;
+                        re += v * w[2 * m];
+                        im += v * w[2 * m + 1];
+                    }
+                    size_t o = (((size_t)a * g + b) * H + kz) * 2;
+                    Y1[o] = re; Y1[o + 1] = im;
+                }
+        // along y
+        std::vector<double> Y2((size_t)g * g * H * 2, 0.0);
+        for (int a = 0; a < g; ++a)
+            for (int ky = 0; ky < g; ++ky)
+                for (int kz = 0; kz < H; ++kz) {
+                    double re = 0, im = 0;
+                    for (int b = 0; b < g; ++b) {
+                        size_t o = (((size_t)a * g + b) * H + kz) * 2;
+                        int m = (b * ky) % g;
+                        double xr = Y1[o], xi = Y1[o + 1], wr = w[2 * m], wi = w[2 * m + 1];
+                        re += xr * wr - xi * wi;
+                        im += xr * wi + xi * wr;
+                    }
+                    size_t o = (((size_t)a * g + ky) * H + kz) * 2;
+                    Y2[o] = re; Y2[o + 1] = im;
+                }
+        // along x
+        double *out = &pl->Khat[(size_t)t * pl->F * 2];
+        for (int kx = 0; kx < g; ++kx)
+            for (int ky = 0; ky < g; ++ky)
+                for (int kz = 0; kz < H; ++kz) {
+                    double re = 0, im = 0;
+                    for (int a = 0; a < g; ++a) {
+                        size_t o = (((size_t)a * g + ky) * H + kz) * 2;
+                        int m = (a * kx) % g;
+                        double xr = Y2[o], xi = Y2[o + 1], wr = w[2 * m], wi = w[2 * m + 1];
+                        re += xr * wr - xi * wi;
+                        im += xr * wi + xi * wr;
+                    }
+                    size_t f = ((size_t)kx * g + ky) * H + kz;
+                    out[2 * f] = re; out[2 * f + 1] = im;
+                }
+    }
+    pl->fft_host_ready = true;
+    return M2L_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Box tables per level.
+
+static inline uint64_t spread3(uint32_t v) {
+    uint64_t out = 0;
+    for (int b = 0; b < 21; ++b) out |= (uint64_t)((v >> b) & 1u) << (3 * b);
+    return out;
+}
+static inline uint32_t compact3(uint64_t v) {
+    uint32_t out = 0;
+    for (int b = 0; b < 21; ++b) out |= (uint32_t)((v >> (3 * b)) & 1u) << b;
+    return out;
+}
+
+template <class T>
+static int dev_upload(T *&dst, const std::vector<T> &src) {
+    if (dst) cudaFree(dst);
+    dst = nullptr;
+    size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+    if (cudaMalloc((void **)&dst, bytes) != cudaSuccess) {
+        set_error("cudaMalloc of %zu bytes failed", bytes);
+        return M2L_ENOMEM;
+    }
+    if (!src.empty() && cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error("cudaMemcpy to device failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return M2L_ECUDA;
+    }
+    return M2L_OK;
+}
+
+static void free_level(LevelDev &L) {
+    void *ptrs[] = {L.slot, L.xyz, L.perm, L.cslot, L.cxyz, L.cchild};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    L.slot = nullptr; L.xyz = nullptr; L.perm = nullptr;
+    L.cslot = nullptr; L.cxyz = nullptr; L.cchild = nullptr;
+}
+
+int build_level_tables(m2l_plan_t *pl) {
+    if (!pl->levels_dirty) return M2L_OK;
+    long long base = 0, cbase = 0;
+    for (int l = 2; l <= pl->depth; ++l) {
+        LevelDev &L = pl->ldev[l];
+        free_level(L);
+        L.on_device = false;
+        const LevelSet &S = pl->levels[l];
+        uint32_t N = 1u << l;
+        long long B = S.dense ? (1LL << (3 * l)) : (long long)S.keys.size();
+        std::vector<uint64_t> keys(B);
+        if (S.dense) std::iota(keys.begin(), keys.end(), 0ull);
+        else keys = S.keys;
+        std::vector<uint32_t> &xyz = L.h_xyz;
+        std::vector<int> &slot = L.h_slot;
+        xyz.assign(B, 0);
+        slot.assign((size_t)N * N * N, -1);
+        for (long long b = 0; b < B; ++b) {
+            uint32_t x = compact3(keys[b]), y = compact3(keys[b] >> 1), z = compact3(keys[b] >> 2);
+            xyz[b] = x | (y << 10) | (z << 20);
+            slot[((size_t)z * N + y) * N + x] = (int)b;
+        }
+        // targets grouped by octant (the low three bits of the key), Morton order inside
+        std::vector<int> &perm = L.h_perm;
+        perm.clear();
+        perm.reserve(B);
+        for (int c = 0; c < 8; ++c) {
+            L.oct_start[c] = (long long)perm.size();
+            for (long long b = 0; b < B; ++b)
+                if ((int)(keys[b] & 7) == c) perm.push_back((int)b);
+        }
+        L.oct_start[8] = (long long)perm.size();
+        // clusters: non-empty parents (App. A.1), Morton order
+        std::vector<uint64_t> pk;
+        for (long long b = 0; b < B; ++b)
+            if (pk.empty() || pk.back() != (keys[b] >> 3)) pk.push_back(keys[b] >> 3);
+        uint32_t Np = N / 2;
+        std::vector<int> &cslot = L.h_cslot, &cchild = L.h_cchild;
+        std::vector<uint32_t> &cxyz = L.h_cxyz;
+        cslot.assign((size_t)Np * Np * Np, -1);
+        cchild.assign(pk.size() * 8, -1);
+        cxyz.assign(pk.size(), 0);
+        for (size_t c = 0; c < pk.size(); ++c) {
+            uint32_t x = compact3(pk[c]), y = compact3(pk[c] >> 1), z = compact3(pk[c] >> 2);
+            cxyz[c] = x | (y << 10) | (z << 20);
+            cslot[((size_t)z * Np + y) * Np + x] = (int)c;
+        }
+        {
+            size_t c = 0;
+            for (long long b = 0; b < B; ++b) {
+                while (pk[c] != (keys[b] >> 3)) ++c;
+                cchild[c * 8 + (keys[b] & 7)] = (int)b;
+            }
+        }
+        // pairs: targets x sources that exist, over the 189 transfer vectors of each octant
+        long long pairs = 0;
+#pragma omp parallel for reduction(+ : pairs) schedule(static)
+        for (long long b = 0; b < B; ++b) {
+            int x = xyz[b] & 1023, y = (xyz[b] >> 10) & 1023, z = (xyz[b] >> 20) & 1023;
+            int cx = x & 1, cy = y & 1, cz = z & 1;
+            for (int tx = -2 - cx; tx <= 3 - cx; ++tx)
+                for (int ty = -2 - cy; ty <= 3 - cy; ++ty)
+                    for (int tz = -2 - cz; tz <= 3 - cz; ++tz) {
+                        if (std::max(std::abs(tx), std::max(std::abs(ty), std::abs(tz))) < 2) continue;
+                        int sx = x + tx, sy = y + ty, sz = z + tz;
+                        if (sx < 0 || sy < 0 || sz < 0 || sx >= (int)N || sy >= (int)N || sz >= (int)N) continue;
+                        if (slot[((size_t)sz * N + sy) * N + sx] >= 0) ++pairs;
+                    }
+        }
+        L.level = l;
+        L.nboxes = B;
+        L.base = base;
+        L.nclusters = (long long)pk.size();
+        L.cbase = cbase;
+        L.pairs = pairs;
+        base += B;
+        cbase += (long long)pk.size();
+    }
+    pl->total_rows = base;
+    pl->total_clusters = cbase;
+    pl->levels_dirty = false;
+    pl->tiles_rhs = -1;  // tile lists depend on the box sets
+    return M2L_OK;
+}
+
+int upload_level_tables(m2l_plan_t *pl) {
+    int rc = build_level_tables(pl);
+    if (rc) return rc;
+    for (int l = 2; l <= pl->depth; ++l) {
+        LevelDev &L = pl->ldev[l];
+        if (L.on_device) continue;
+        if ((rc = dev_upload(L.slot, L.h_slot)) || (rc = dev_upload(L.xyz, L.h_xyz)) ||
+            (rc = dev_upload(L.perm, L.h_perm)) || (rc = dev_upload(L.cslot, L.h_cslot)) ||
+            (rc = dev_upload(L.cxyz, L.h_cxyz)) || (rc = dev_upload(L.cchild, L.h_cchild)))
+            return rc;
+        L.on_device = true;
+    }
+    return M2L_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Device copies of the operators.
+
+template <class T>
+static std::vector<T> pad2(const std::vector<double> &src, int rows, int cols, int prow, int pcol) {
+    std::vector<T> out((size_t)prow * pcol, T(0));
+    for (int i = 0; i < rows; ++i)
+        for (int j = 0; j < cols; ++j) out[(size_t)i * pcol + j] = (T)src[(size_t)i * cols + j];
+    return out;
+}
+
+template <class T>
+static int upload_vec(void *&dst, const std::vector<T> &v) {
+    T *d = nullptr;
+    int rc = dev_upload(d, v);
+    if (dst) cudaFree(dst);
+    dst = d;
+    return rc;
+}
+
+int split_tc_operators(m2l_plan_t *pl, int precision);  // kernels_tc.cu
+
+template <class T>
+static int upload_typed(m2l_plan_t *pl, DevOps &D, int form) {
+    int n = pl->n, k = pl->k, kp = pl->kp, r = pl->r, rp = pl->rp;
+    int rc = M2L_OK;
+    if (form == M2L_FORM_BLAS) {
+        // S^T  [kp][n]
+        std::vector<double> St((size_t)k * n);
+        for (int c = 0; c < k; ++c)
+            for (int i = 0; i < n; ++i) St[(size_t)c * n + i] = pl->S[(size_t)i * k + c];
+        std::vector<T> Cp((size_t)kNumTransfer * kp * kp, T(0));
+        for (int t = 0; t < kNumTransfer; ++t)
+            for (int a = 0; a < k; ++a)
+                for (int c = 0; c < k; ++c)
+                    Cp[((size_t)t * kp + a) * kp + c] = (T)pl->C[((size_t)t * k + a) * k + c];
+        if ((rc = upload_vec(D.St, pad2<T>(St, k, n, kp, n)))) return rc;
+        if ((rc = upload_vec(D.C, Cp))) return rc;
+        if ((rc = upload_vec(D.A, pad2<T>(pl->Aop, r, k, rp, kp)))) return rc;
+        if ((rc = upload_vec(D.V, pad2<T>(pl->Veps, n, r, n, rp)))) return rc;
+        if ((rc = upload_vec(D.Uc, pad2<T>(pl->U, n, k, n, kp)))) return rc;
+    } else {
+        int F = pl->F;
+        std::vector<T> K((size_t)(kNumTransfer + 1) * F * 2, T(0));
+        for (size_t i = 0; i < (size_t)kNumTransfer * F * 2; ++i) K[i] = (T)pl->Khat[i];
+        std::vector<T> tw(pl->twiddle.size());
+        for (size_t i = 0; i < tw.size(); ++i) tw[i] = (T)pl->twiddle[i];
+        if ((rc = upload_vec(D.Khat, K))) return rc;
+        if ((rc = upload_vec(D.tw, tw))) return rc;
+        if ((rc = upload_vec(D.Ut, pad2<T>(pl->Uteps, r, n, rp, n)))) return rc;
+        if ((rc = upload_vec(D.V, pad2<T>(pl->Veps, n, r, n, rp)))) return rc;
+    }
+    return rc;
+}
+
+int upload_ops(m2l_plan_t *pl, int precision, int form) {
+    int slot = precision * 2 + (form == M2L_FORM_FFT ? 1 : 0);
+    (void)slot;
+    DevOps &D = pl->dev[precision];
+    // one DevOps per precision holds both forms; track readiness per form with the pointers
+    bool have = form == M2L_FORM_BLAS ? (D.C != nullptr) : (D.Khat != nullptr);
+    if (have) return M2L_OK;
+    int rc = form == M2L_FORM_BLAS ? build_blas_host(pl) : build_fft_host(pl);
+    if (rc) return rc;
+    if (precision == M2L_PREC_FP64) {
+        D.elt = 8;
+        rc = upload_typed<double>(pl, D, form);
+    } else {
+        D.elt = 4;
+        rc = upload_typed<float>(pl, D, form);
+        if (!rc && form == M2L_FORM_BLAS && (precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3))
+            rc = split_tc_operators(pl, precision);
+    }
+    D.ready = rc == M2L_OK;
+    return rc;
+}
+
+void free_device(m2l_plan_t *pl) {
+    for (auto &D : pl->dev) {
+        void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Uc, &D.C_hi, &D.C_lo, &D.Khat, &D.Ut, &D.tw};
+        for (void **pp : ptrs) {
+            if (*pp) cudaFree(*pp);
+            *pp = nullptr;
+        }
+        D.ready = false;
+    }
+    for (int l = 0; l <= kMaxDepth; ++l) free_level(pl->ldev[l]);
+    if (pl->ws.buf) cudaFree(pl->ws.buf);
+    if (pl->stage_in.buf) cudaFree(pl->stage_in.buf);
+    if (pl->stage_out.buf) cudaFree(pl->stage_out.buf);
+    if (pl->tiles) cudaFree(pl->tiles);
+    if (pl->lattice_dev) cudaFree(pl->lattice_dev);
+    pl->lattice_dev = nullptr;
+    for (cudaEvent_t e : pl->event_pool) cudaEventDestroy(e);
+    pl->event_pool.clear();
+    pl->events.clear();
+    pl->events_used = 0;
+    pl->ws = {};
+    pl->stage_in = {};
+    pl->stage_out = {};
+    pl->tiles = nullptr;
+}
+
+}  // namespace m2l

@@ -124,8 +124,9 @@ def c1() -> Workload:
     return uniform_cube("c1", 1, 8_000, 3, 4, 1, 0.0, "u01")
 
 
-def c2(rank_tol: float = 1e-7) -> Workload:
-    return uniform_cube("c2", 2, 1_000_000, 5, 6, 1, rank_tol, "u11")
+def c2(rank_tol: float = 1e-7, depth: int = 5) -> Workload:
+    """The 1M-point workload; ``depth`` < 5 gives the same shape on a shallower tree (profiling)."""
+    return uniform_cube("c2", 2, 1_000_000, depth, 6, 1, rank_tol, "u11")
 
 
 def c3(bin_points: bool = True) -> Workload:

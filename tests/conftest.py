@@ -17,3 +17,12 @@ def pytest_configure(config):
 def rng():
     import numpy as np
     return np.random.default_rng(2408)
+
+
+@pytest.fixture(scope="session")
+def lib():
+    """The compiled C-ABI library through its Python binding (built on demand)."""
+    from paper_2408_07436_gb300 import build as b
+    b.build()
+    from paper_2408_07436_gb300 import m2l
+    return m2l

@@ -1,0 +1,153 @@
+"""The C-ABI library on the CPU: it loads, exports every declared symbol, validates arguments,
+and its host-side plan (pseudo-inverse, SVD compression, box tables) agrees with the oracle.
+No test here launches a kernel."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import geometry as G
+from oracle import m2l as M
+from oracle import operators as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "m2l.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(m2l_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert "m2l_plan" in names and "m2l_apply" in names and "m2l_destroy" in names
+    dll = ctypes.CDLL(lib.LIB_PATH)
+    for name in names:
+        assert hasattr(dll, name), name
+
+
+def test_plan_rejects_bad_arguments(lib):
+    for args, word in [((1, 4, 0, 0.0), "depth"), ((9, 4, 0, 0.0), "depth"), ((3, 1, 0, 0.0), "order"),
+                       ((3, 4, 7, 0.0), "kernel"), ((3, 4, 0, float("nan")), "rank_tol")]:
+        with pytest.raises(lib.M2LError) as e:
+            lib.m2l_plan(*args)
+        assert word in str(e.value)
+
+
+def test_options_and_boxes_are_validated(lib):
+    h = lib.m2l_plan(3, 4, 0, 0.0)
+    try:
+        assert lib.m2l_set_option(h, 99, 0) == lib.M2L_EINVAL
+        assert lib.m2l_set_option(h, lib.M2L_OPT_FORM, 7) == lib.M2L_EINVAL
+        assert lib.m2l_set_option(h, lib.M2L_OPT_PRECISION, 9) == lib.M2L_EINVAL
+        assert lib.m2l_set_option(h, lib.M2L_OPT_FFT_GRID, 5) == lib.M2L_EINVAL      # < 2p - 1
+        assert lib.m2l_set_option(h, lib.M2L_OPT_FFT_GRID, 7) == lib.M2L_OK
+        bad = np.array([5, 3], dtype=np.uint64)
+        assert lib.m2l_set_boxes(h, 2, bad.ctypes.data, 2) == lib.M2L_EINVAL         # not ascending
+        big = np.array([64], dtype=np.uint64)
+        assert lib.m2l_set_boxes(h, 2, big.ctypes.data, 1) == lib.M2L_EINVAL         # >= 8^level
+        assert lib.m2l_set_boxes(h, 1, bad.ctypes.data, 2) == lib.M2L_EINVAL         # level < 2
+        assert lib.m2l_apply(h, 1, 2, 5, 1) == lib.M2L_EINVAL                         # level > depth
+        assert lib.m2l_apply(h, 1, 2, -1, 0) == lib.M2L_EINVAL                        # n_rhs < 1
+    finally:
+        lib.m2l_destroy(h)
+    lib.m2l_destroy(None)  # NULL-safe
+
+
+@pytest.mark.parametrize("level", [2, 3, 4])
+def test_pair_counts_match_oracle_dense(lib, level):
+    h = lib.m2l_plan(4, 4, 0, 0.0)
+    try:
+        assert lib.m2l_query(h, lib.M2L_Q_PAIRS, level) == M.pair_count(level)
+        assert lib.m2l_query(h, lib.M2L_Q_BOXES, level) == 8 ** level
+    finally:
+        lib.m2l_destroy(h)
+
+
+def test_pair_counts_match_oracle_sparse(lib):
+    rng = np.random.default_rng(9)
+    h = lib.m2l_plan(4, 4, 0, 0.0)
+    try:
+        for level in (2, 3, 4):
+            keys = np.sort(rng.choice(8 ** level, size=max(3, 8 ** level // 5), replace=False)).astype(np.uint64)
+            assert lib.m2l_set_boxes(h, level, keys.ctypes.data, len(keys)) == lib.M2L_OK
+            assert lib.m2l_query(h, lib.M2L_Q_PAIRS, level) == M.pair_count(level, keys.astype(np.int64))
+            assert lib.m2l_query(h, lib.M2L_Q_BOXES, level) == len(keys)
+    finally:
+        lib.m2l_destroy(h)
+
+
+@pytest.mark.parametrize("p", [3, 4, 6])
+def test_plan_pseudo_inverse_matches_oracle(lib, p):
+    h = lib.m2l_plan(3, p, 0, 0.0)
+    try:
+        n = G.n_surface(p)
+        V = lib.m2l_get_operator(h, 4)
+        Ut = lib.m2l_get_operator(h, 5)
+        r = lib.m2l_query(h, lib.M2L_Q_PINV_RANK)
+        V = V.reshape(n, r)
+        Ut = Ut.reshape(r, n)
+        Vo, Uto = O.down_pinv(p, 0)          # level 0: a box of width 1, the plan's unit geometry
+        assert r == Vo.shape[1]
+        x = G.surface_points(p, np.zeros(3), 1.0, G.ALPHA_INNER)
+        y = G.surface_points(p, np.zeros(3), 1.0, G.ALPHA_OUTER)
+        K = O.laplace(x, y)
+        s = np.linalg.svd(K, compute_uv=False)
+        kappa = s[0] / s[r - 1]
+        ref = Vo @ Uto
+        assert np.linalg.norm(V @ Ut - ref) <= n * np.finfo(float).eps * kappa * np.linalg.norm(ref)
+    finally:
+        lib.m2l_destroy(h)
+
+
+@pytest.mark.parametrize("p,tol", [(4, 1e-4), (5, 1e-6), (6, 1e-7)])
+def test_plan_compression_matches_oracle(lib, p, tol):
+    """Same singular values, same rank rule, same compressed operator U C_t S^T (basis free)."""
+    h = lib.m2l_plan(3, p, 0, tol)
+    try:
+        n = G.n_surface(p)
+        k = lib.m2l_query(h, lib.M2L_Q_RANK)
+        s = lib.m2l_get_operator(h, 3)
+        U = lib.m2l_get_operator(h, 0).reshape(n, k)
+        S = lib.m2l_get_operator(h, 1).reshape(n, k)
+        C = lib.m2l_get_operator(h, 2).reshape(316, k, k)
+        ops = O.compressed_operators(p, tol, 1.0)
+        assert k == ops["k"]
+        assert np.allclose(s, ops["s_fat"], rtol=0, atol=1e-12 * s[0])
+        assert np.allclose(U.T @ U, np.eye(k), atol=1e-12)
+        assert np.allclose(S.T @ S, np.eye(k), atol=1e-12)
+        for t in (0, 57, 150, 315):
+            mine = U @ C[t] @ S.T
+            ref = ops["U"] @ ops["C"][t] @ ops["S"].T
+            assert np.linalg.norm(mine - ref) <= 1e-11 * np.linalg.norm(ops["K"][t])
+    finally:
+        lib.m2l_destroy(h)
+
+
+def test_full_rank_operators_are_exact(lib):
+    p = 4
+    h = lib.m2l_plan(3, p, 0, 0.0)
+    try:
+        n = G.n_surface(p)
+        assert lib.m2l_query(h, lib.M2L_Q_RANK) == n
+        C = lib.m2l_get_operator(h, 2).reshape(316, n, n)
+        tv = G.transfer_vectors()
+        for t in (0, 100, 315):
+            assert np.allclose(C[t], O.m2l_matrix(p, tv[t], 1.0), rtol=1e-14, atol=0)
+    finally:
+        lib.m2l_destroy(h)
+
+
+def test_fft_grid_queries(lib):
+    h = lib.m2l_plan(3, 6, 0, 0.0)
+    try:
+        assert lib.m2l_query(h, lib.M2L_Q_GRID) == 12
+        assert lib.m2l_query(h, lib.M2L_Q_FREQS) == 12 * 12 * 7
+        assert lib.m2l_set_option(h, lib.M2L_OPT_FFT_GRID, 11) == lib.M2L_OK
+        assert lib.m2l_query(h, lib.M2L_Q_GRID) == 11
+        assert lib.m2l_query(h, lib.M2L_Q_FREQS) == 11 * 11 * 6
+    finally:
+        lib.m2l_destroy(h)

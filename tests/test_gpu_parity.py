@@ -1,0 +1,179 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
+
+Check potentials are compared with Eq. 16 directly. Locals are compared through the check
+potential they reproduce (oracle.m2l.check_norm_error): the pseudo-inverse amplifies rounding
+by up to cond(K_tau) (1e5 at p = 4, 1e9 at p = 6), and the FMM only ever uses the locals
+through potentials they generate (the footnote of Sec. 2.1.1).
+
+Tolerances: FP64 paths 1e-12 (the benchmark spec's bound). FP32 paths: the relative rounding of a
+sum of 189 n products in single precision, bounded by 5e-6 on check potentials.
+"""
+import numpy as np
+import pytest
+
+from oracle import m2l as M
+from oracle import operators as O
+from oracle import geometry as G
+from paper_2408_07436_gb300 import workloads as W
+
+from gpu_util import levels_of, oracle_level, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 5e-6
+
+
+def _qs(wl, dtype=np.float64):
+    return {l: wl.multipoles(l) for l in wl.levels}
+
+
+@pytest.mark.parametrize("form", ["blas", "fft"])
+def test_c1_fp64_all_levels(lib, form):
+    wl = W.c1()
+    qs = _qs(wl)
+    chk = run_gpu(lib, wl.depth, wl.p, qs, form=form, output="check")
+    loc = run_gpu(lib, wl.depth, wl.p, qs, form=form, output="locals")
+    for l in wl.levels:
+        L_ref, phi_ref = oracle_level(wl.p, l, qs[l])
+        assert M.rel_l2_error(phi_ref, chk[l]) < FP64_TOL, (form, l)
+        assert M.check_norm_error(wl.p, l, L_ref, loc[l]) < FP64_TOL, (form, l)
+
+
+def test_fft_odd_grid_equals_dense(lib):
+    wl = W.small(depth=3, p=4)
+    qs = _qs(wl)
+    chk = run_gpu(lib, 3, 4, qs, form="fft", output="check", fft_grid=7)
+    for l in wl.levels:
+        _, phi_ref = oracle_level(4, l, qs[l])
+        assert M.rel_l2_error(phi_ref, chk[l]) < FP64_TOL
+
+
+@pytest.mark.parametrize("p", [2, 3, 5])
+def test_other_orders_fp64(lib, p):
+    wl = W.small(depth=3, p=p, density="normal")
+    qs = _qs(wl)
+    for form in ("blas", "fft"):
+        chk = run_gpu(lib, 3, p, qs, form=form, output="check")
+        for l in wl.levels:
+            _, phi_ref = oracle_level(p, l, qs[l])
+            assert M.rel_l2_error(phi_ref, chk[l]) < FP64_TOL, (form, p, l)
+
+
+def test_truncated_blas_matches_compressed_oracle(lib):
+    p, tol, depth = 6, 1e-7, 3
+    wl = W.small(depth=depth, p=p, density="u11", rank_tol=tol)
+    qs = _qs(wl)
+    chk = run_gpu(lib, depth, p, qs, rank_tol=tol, output="check")
+    ops = O.compressed_operators(p, tol, 1.0)
+    for l in wl.levels:
+        _, phi_c = M.m2l_compressed(p, l, qs[l], ops)   # unit-width operators: unit check potential
+        assert M.rel_l2_error(phi_c, chk[l]) < 1e-11
+        _, phi_d = oracle_level(p, l, qs[l])
+        assert M.rel_l2_error(phi_d, chk[l]) < 1e-6      # the truncation itself
+
+
+@pytest.mark.parametrize("form", ["blas", "fft"])
+def test_sparse_boxes_and_multiple_rhs(lib, form):
+    wl = W.small(depth=4, p=4, n_rhs=3, n_points=400, density="normal")
+    assert wl.is_sparse()
+    qs = _qs(wl)
+    keys = {l: wl.keys[l] for l in wl.levels}
+    chk = run_gpu(lib, wl.depth, wl.p, qs, keys=keys, form=form, output="check", R=3)
+    loc = run_gpu(lib, wl.depth, wl.p, qs, keys=keys, form=form, output="locals", R=3)
+    for l in wl.levels:
+        k = None if keys[l] is None else keys[l].astype(np.int64)
+        L_ref, phi_ref = oracle_level(wl.p, l, qs[l], keys=k)
+        assert M.rel_l2_error(phi_ref, chk[l]) < FP64_TOL, (form, l)
+        assert M.check_norm_error(wl.p, l, L_ref, loc[l]) < FP64_TOL, (form, l)
+
+
+@pytest.mark.parametrize("form", ["blas", "fft"])
+def test_single_level_and_accumulate(lib, form):
+    wl = W.small(depth=3, p=3, n_rhs=2)
+    qs = _qs(wl)
+    allv = run_gpu(lib, 3, 3, qs, form=form, R=2)
+    one = run_gpu(lib, 3, 3, {3: qs[3]}, form=form, level=3, R=2)
+    assert np.allclose(one[3], allv[3], rtol=0, atol=1e-13 * np.abs(allv[3]).max())
+    init = {l: np.ones_like(qs[l]) for l in wl.levels}
+    acc = run_gpu(lib, 3, 3, qs, form=form, R=2, accumulate=True, init=init)
+    for l in wl.levels:
+        assert np.allclose(acc[l], allv[l] + 1.0, rtol=1e-12, atol=1e-12 * np.abs(allv[l]).max())
+
+
+def test_host_buffers_equal_device_buffers(lib):
+    wl = W.small(depth=3, p=4)
+    qs = _qs(wl)
+    a = run_gpu(lib, 3, 4, qs)
+    b = run_gpu(lib, 3, 4, qs, host=True)
+    for l in wl.levels:
+        assert np.array_equal(a[l], b[l])
+
+
+@pytest.mark.parametrize("form", ["blas", "fft"])
+def test_fp32_forms(lib, form):
+    wl = W.small(depth=3, p=4, density="u11")
+    qs = _qs(wl)
+    chk = run_gpu(lib, 3, 4, qs, form=form, precision="fp32", output="check")
+    for l in wl.levels:
+        _, phi_ref = oracle_level(4, l, qs[l])
+        assert M.rel_l2_error(phi_ref, chk[l]) < FP32_TOL, (form, l)
+
+
+def test_edge_cases(lib):
+    # depth 2: one level, every pair in the box's far field interacts
+    wl = W.small(depth=2, p=3)
+    qs = _qs(wl)
+    for form in ("blas", "fft"):
+        chk = run_gpu(lib, 2, 3, qs, form=form, output="check")
+        _, phi_ref = oracle_level(3, 2, qs[2])
+        assert M.rel_l2_error(phi_ref, chk[2]) < FP64_TOL
+    # a single non-empty box at every level: no interactions, zero output
+    keys = {2: np.array([5], dtype=np.uint64), 3: np.array([40], dtype=np.uint64)}
+    qs1 = {2: np.ones((1, 1, G.n_surface(3))), 3: np.ones((1, 1, G.n_surface(3)))}
+    for form in ("blas", "fft"):
+        out = run_gpu(lib, 3, 3, qs1, keys=keys, form=form)
+        assert np.all(out[2] == 0) and np.all(out[3] == 0)
+    # two far boxes only: each sees exactly the other
+    keys = {2: np.array([0, 63], dtype=np.uint64)}
+    q2 = {2: np.random.default_rng(4).random((2, 1, G.n_surface(3)))}
+    for form in ("blas", "fft"):
+        chk = run_gpu(lib, 2, 3, q2, keys=keys, form=form, output="check")
+        _, phi_ref = oracle_level(3, 2, q2[2], keys=keys[2].astype(np.int64))
+        assert M.rel_l2_error(phi_ref, chk[2]) < FP64_TOL
+
+
+def test_error_codes(lib):
+    import torch
+    h = lib.m2l_plan(3, 4, 0, 0.0)
+    try:
+        q = torch.zeros(584 * 56, dtype=torch.float32, device="cuda")
+        o = torch.zeros_like(q)
+        lib.m2l_set_option(h, lib.M2L_OPT_FORM, lib.M2L_FORM_FFT)
+        lib.m2l_set_option(h, lib.M2L_OPT_PRECISION, lib.M2L_PREC_TF32X3)
+        assert lib.m2l_apply(h, q.data_ptr(), o.data_ptr(), -1, 1) == lib.M2L_EUNSUPPORTED
+        lib.m2l_set_option(h, lib.M2L_OPT_PRECISION, lib.M2L_PREC_FP32)
+        assert lib.m2l_apply(h, q.data_ptr(), q.data_ptr() + 64, -1, 1) == lib.M2L_EINVAL   # overlap
+        assert "overlap" in lib.m2l_last_error()
+    finally:
+        lib.m2l_destroy(h)
+
+
+@pytest.mark.parametrize("form,precision", [("blas", "fp64"), ("fft", "fp64"), ("blas", "fp32"), ("fft", "fp32")])
+def test_c2_full_size_sampled(lib, form, precision):
+    """The 1M-point, depth-5, p = 6 workload at full size, sampled targets checked one by one."""
+    wl = W.c2()
+    qs = _qs(wl)
+    tol = wl.rank_tol if form == "blas" else 0.0
+    chk = run_gpu(lib, wl.depth, wl.p, qs, rank_tol=tol, form=form, precision=precision, output="check")
+    bound = FP64_TOL if precision == "fp64" else FP32_TOL
+    ops = O.compressed_operators(wl.p, tol, 1.0) if form == "blas" else None
+    rng = np.random.default_rng(5)
+    for l in wl.levels:
+        B = wl.n_boxes(l)
+        sample = np.sort(rng.choice(B, size=min(B, 48), replace=False))
+        if form == "blas":
+            _, phi_ref = M.m2l_compressed(wl.p, l, qs[l], ops, targets=sample)
+        else:
+            _, phi_ref = oracle_level(wl.p, l, qs[l], targets=sample)
+        assert M.rel_l2_error(phi_ref, chk[l][sample]) < bound * (10 if form == "blas" else 1), (l,)
