@@ -168,6 +168,33 @@ int m2l_query(const m2l_plan_t *plan, int what, int level, long long *out);
  * number of kernel launches of each stage in `launches` (may be NULL). */
 int m2l_stage_times(m2l_plan_t *plan, double *ms, long long *launches);
 
+/* m2l_apply without allocation. The paper has no counterpart; this entry point is for callers
+ * that cannot allocate device memory at the time they apply M2L: applications that hand all
+ * device memory to their own pool or caching allocator up front (a cudaMalloc would then fail or
+ * fragment it), and latency-bounded loops in which the implicit device synchronisation of
+ * cudaMalloc / cudaFree is not acceptable.
+ *
+ * It computes what m2l_apply computes for the BLAS form in FP64 at ONE level (honouring
+ * M2L_OPT_OUTPUT and M2L_OPT_ACCUMULATE) and calls no cudaMalloc, no cudaFree and no allocating
+ * library routine. Its scratch (compressed multipoles, compressed check potentials and the
+ * pseudo-inverse intermediate) is one static device array of 4,194,304 doubles (32 MiB) that
+ * every GPU which loads this library holds until the process exits. A request needs
+ * (B_l n_rhs + 1) k_pad + B_l n_rhs (k_pad + r_pad) doubles (each part rounded up to 32);
+ * larger requests return M2L_EINVAL with the size in the message (use m2l_apply instead).
+ *
+ * multipoles, locals: DEVICE pointers, FP64, layout [B_l][n_rhs][n] of `level`.
+ * Preconditions: the plan's FP64 BLAS operators and box tables are already on the device (one
+ * earlier m2l_apply of this plan with M2L_FORM_BLAS and M2L_PREC_FP64, after the last
+ * m2l_set_boxes, uploads them); otherwise M2L_EINVAL.
+ * Set-up: the first call on a device, with that device current, looks up the array's device
+ * address (cudaGetSymbolAddress) and uploads a small constant table; make that first call
+ * before any stream capture.
+ * Sharing: every call uses the same array and leaves the last call's contents in it (the one
+ * part that must start at zero is cleared on every call). Calls that overlap on the GPU (other
+ * streams, other plans, other host threads) race on the array and give wrong results.
+ * Asynchronous on the plan's stream. Returns M2L_OK, M2L_EINVAL or M2L_ECUDA. */
+int m2l_apply_noalloc(m2l_plan_t *plan, const double *multipoles, double *locals, int level, int n_rhs);
+
 /* Copy a plan operator to host memory (FP64), for tests and inspection:
  * which = 0: U (n x k), 1: S (n x k), 2: C_t (316 x k x k), 3: singular values of K_fat (n),
  *         4: pseudo-inverse factor V_eps (n x r), 5: Ut_eps = Sigma_eps^-1 U_eps^T (r x n).

@@ -62,6 +62,8 @@ _lib.m2l_query.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctype
 _lib.m2l_query.restype = ctypes.c_int
 _lib.m2l_stage_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
 _lib.m2l_stage_times.restype = ctypes.c_int
+_lib.m2l_apply_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int]
+_lib.m2l_apply_noalloc.restype = ctypes.c_int
 _lib.m2l_get_operator.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
 _lib.m2l_get_operator.restype = ctypes.c_int
 
@@ -91,6 +93,11 @@ def m2l_plan(depth: int, p: int, kernel: int = M2L_LAPLACE3D, rank_tol: float = 
 
 def m2l_apply(plan, multipoles_ptr: int, locals_ptr: int, level: int, n_rhs: int) -> int:
     return _lib.m2l_apply(plan, multipoles_ptr, locals_ptr, level, n_rhs)
+
+
+def m2l_apply_noalloc(plan, multipoles_ptr: int, locals_ptr: int, level: int, n_rhs: int) -> int:
+    """FP64 BLAS form at one level with the library's static scratch: allocates nothing (include/m2l.h)."""
+    return _lib.m2l_apply_noalloc(plan, multipoles_ptr, locals_ptr, level, n_rhs)
 
 
 def m2l_destroy(plan) -> None:
