@@ -113,7 +113,10 @@ enum m2l_query_e {
     M2L_Q_ROWS = 8,       /* boxes summed over levels 2..depth */
     M2L_Q_FORM = 9,       /* form the next apply will run (resolves AUTO) */
     M2L_Q_PRECISION = 10, /* precision the next apply will run (resolves AUTO) */
-    M2L_Q_LAUNCHES = 11   /* kernels launched by the last apply */
+    M2L_Q_LAUNCHES = 11,  /* kernels launched by the last apply */
+    M2L_Q_DEVICE_STATUS = 12 /* waits for the plan's stream, returns the device status word (0: no
+                                bounded wait ran out since the last query, else a stage code) and
+                                clears it; a nonzero value means results since then are invalid */
 };
 
 /* Build a plan (host, FP64; arxiv 2408.07436 Sec. 3.1 for the BLAS operators and App. A.1

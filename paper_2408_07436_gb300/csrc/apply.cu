@@ -75,20 +75,20 @@ static LevelView view_of(const LevelDev &D) {
     return v;
 }
 
-static int ensure_tiles(m2l_plan_t *pl, int l0, int l1, int R) {
+static int ensure_tiles(m2l_plan_t *pl, int l0, int l1, int R, int rows_per_tile) {
     int key = l0 == l1 ? l0 : -1;
-    if (pl->tiles && pl->tiles_rhs == R && pl->tiles_level == key) return M2L_OK;
+    if (pl->tiles && pl->tiles_rhs == R && pl->tiles_level == key && pl->tiles_rows == rows_per_tile) return M2L_OK;
     std::vector<ContractTile> t;
     for (int l = l0; l <= l1; ++l) {
         const LevelDev &D = pl->ldev[l];
         for (int oct = 0; oct < 8; ++oct) {
             long long segrows = (D.oct_start[oct + 1] - D.oct_start[oct]) * (long long)R;
-            for (long long j0 = 0; j0 < segrows; j0 += 64) {
+            for (long long j0 = 0; j0 < segrows; j0 += rows_per_tile) {
                 ContractTile c;
                 c.lev = l - l0;
                 c.oct = oct;
                 c.j0 = (int)j0;
-                c.rows = (int)std::min<long long>(64, segrows - j0);
+                c.rows = (int)std::min<long long>(rows_per_tile, segrows - j0);
                 t.push_back(c);
             }
         }
@@ -108,6 +108,7 @@ static int ensure_tiles(m2l_plan_t *pl, int l0, int l1, int R) {
     pl->ntiles = (long long)t.size();
     pl->tiles_rhs = R;
     pl->tiles_level = key;
+    pl->tiles_rows = rows_per_tile;
     return M2L_OK;
 }
 
@@ -160,7 +161,7 @@ static int apply_blas(m2l_plan_t *pl, const T *q, T *out, int l0, int l1, int R,
     cudaMemsetAsync(qt + allrows * kp, 0, kp * e, s);
     stage_end(pl, 1);
     // B2: gathered contraction over the transfer vectors of each target octant
-    M2L_TRY(ensure_tiles(pl, l0, l1, R));
+    M2L_TRY(ensure_tiles(pl, l0, l1, R, tc ? 128 : 64));
     LevelsArg lv;
     lv.count = l1 - l0 + 1;
     for (int l = l0; l <= l1; ++l) lv.L[l - l0] = view_of(pl->ldev[l]);
@@ -265,6 +266,14 @@ int apply_device(m2l_plan_t *pl, const void *q, void *L, int level, int R) {
         return M2L_EUNSUPPORTED;
     }
     M2L_TRY(upload_ops(pl, precision, form));
+    if (!pl->dev_status) {
+        if (cudaMalloc((void **)&pl->dev_status, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("status word allocation failed");
+            return M2L_ENOMEM;
+        }
+        cudaMemset(pl->dev_status, 0, sizeof(int));
+    }
     pl->launches = 0;
     pl->events.clear();
     pl->events_used = 0;

@@ -343,6 +343,19 @@ int m2l_query(const m2l_plan_t *cpl, int what, int level, long long *out) {
         case M2L_Q_LAUNCHES:
             *out = pl->launches;
             return M2L_OK;
+        case M2L_Q_DEVICE_STATUS: {
+            *out = 0;
+            if (pl->device < 0 || !pl->dev_status) return M2L_OK;
+            int v = 0;
+            if (cudaStreamSynchronize(pl->stream) != cudaSuccess ||
+                cudaMemcpy(&v, pl->dev_status, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                set_error("reading the device status failed: %s", cudaGetErrorString(cudaGetLastError()));
+                return M2L_ECUDA;
+            }
+            if (v) cudaMemset(pl->dev_status, 0, sizeof(int));
+            *out = v;
+            return M2L_OK;
+        }
         default:
             set_error("unknown query %d", what);
             return M2L_EINVAL;

@@ -44,6 +44,7 @@ struct DevOps {
     void *V = nullptr;           // [n][rp]     V_eps
     void *Uc = nullptr;          // [n][kp]     U (check-potential output)
     void *C_hi = nullptr, *C_lo = nullptr;  // split C_t for the tensor-core forms
+    alignas(64) unsigned char tmap[2][128] = {};  // TMA maps (CUtensorMap) of C_hi and C_lo
     // FFT form
     void *Khat = nullptr;        // [316+1][F] complex kernel spectra (last row zero)
     void *Ut = nullptr;          // [rp][np_]   Ut_eps
@@ -106,8 +107,9 @@ struct m2l_plan_s {
     m2l::Workspace ws, stage_in, stage_out;
     void *tiles = nullptr;                         // device tile list for the contraction
     long long ntiles = 0;
-    int tiles_rhs = -1, tiles_level = -2, tiles_rows = 0;
+    int tiles_rhs = -1, tiles_level = -2, tiles_rows = 0;  // cache key of the tile list
     long long launches = 0;
+    int *dev_status = nullptr;                     // device status word written by bounded waits
     // stage timing (M2L_OPT_TIMING)
     int timing = 0;
     struct StageEvent { int stage; cudaEvent_t a, b; long long launches; };

@@ -1,30 +1,621 @@
-// Tensor-core (tcgen05) contraction for the split precisions TF32x3 and BF16x3.
+// B2 on the 5th-generation tensor cores (tcgen05) for the split precisions TF32x3 and BF16x3.
+//
+// phi~[row] = sum over the 189 transfer vectors t of the row's octant of C_t q~[source(row, t)],
+// every operand split as x = x_hi + x_lo and each product taken as hi*hi + hi*lo + lo*hi with FP32
+// accumulation in tensor memory (the dropped lo*lo term is below the FP32 rounding of the
+// result for TF32 pieces, about 2^-16 relative for BF16 pieces).
+//
+// One persistent CTA per SM loops over tiles of 128 (target, rhs) rows of one octant of one
+// level. Per (tile, t, 128-byte K chunk) a pipeline stage holds
+//   A_hi, A_lo: the 128 gathered source rows of q~ (cp.async, 16-byte pieces written with the
+//               128-byte swizzle), one row per producer thread;
+//   B_hi, B_lo: the chunk of C_t (k_pad x 128 bytes), loaded by TMA with SWIZZLE_128B.
+// Warps: 0-3 gather A; 4 issues TMA for B; 5 owns tensor memory and issues the MMAs
+// (M = 128 rows, N = k_pad, K = 32 bytes per instruction); 6-9 drain the accumulator
+// (double-buffered in tensor memory) to phi~. Every wait is bounded; a wait that runs out sets
+// the plan's device status word and the CTA winds down.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cstring>
+#include <vector>
+
 #include "internal.h"
 #include "kernels.cuh"
 
 namespace m2l {
 
-int split_tc_operators(m2l_plan_t *pl, int precision) {
-    (void)pl;
-    (void)precision;
-    set_error("split tensor-core precisions are not built yet");
-    return M2L_EUNSUPPORTED;
+namespace {
+
+constexpr int kRows = 128;            // MMA M, rows per tile
+constexpr int kChunk = 128;           // bytes of K per stage (one 128-byte swizzle row)
+constexpr int kThreads = 320;
+constexpr long long kWaitLimit = 1LL << 24;
+
+struct TcParams {
+    LevelsArg lv;
+    const ContractTile *tiles;
+    long long ntiles;
+    int R;
+    const unsigned char *qhi, *qlo;   // [(rows + 1)][kp] elements
+    long long zero_row;
+    float *phit;                       // [rows][kp]
+    int kp, elt, nchunks, stages;
+    uint32_t idesc;
+    int tmem_cols;
+    int nbuf;                          // partial-sum buffers in tensor memory (1 or 2)
+    int *status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
 }
 
-int launch_split_rows(const float *, long long, int, void *, void *, int, cudaStream_t) {
-    set_error("split tensor-core precisions are not built yet");
-    return M2L_EUNSUPPORTED;
+// Bounded wait; on expiry records `code` in the status word and raises the CTA's abort flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *status, int code) {
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+    }
+    atomicCAS(status, 0, code);
+    *abort_flag = 1;
+    return false;
 }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (KIND == 0)
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                     "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                     "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+                   "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+                 "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+                 : "memory");
+}
+
+struct RowInfo {
+    int b;         // compact target box, -1 for a padding row
+    int r;         // rhs
+    uint32_t xyz;  // packed coordinates
+};
+
+__device__ __forceinline__ RowInfo row_info(const LevelView &L, const ContractTile &T, int R, int row) {
+    RowInfo ri;
+    if (row < T.rows) {
+        long long j = (long long)T.j0 + row;
+        ri.b = L.perm[L.oct_start[T.oct] + j / R];
+        ri.r = (int)(j % R);
+        ri.xyz = L.xyz[ri.b];
+    } else {
+        ri.b = -1;
+        ri.r = 0;
+        ri.xyz = 0;
+    }
+    return ri;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads, 1)
+    contract_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, const TcParams P) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[4], empty_bar[4], accf_bar[2], acce_bar[2], drain_bar;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ volatile int abort_flag;
+
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int S = P.stages;
+    const int kp = P.kp;
+    const uint32_t a_bytes = kRows * kChunk;               // 16 KB
+    const uint32_t b_bytes = (uint32_t)kp * kChunk;        // k_pad rows x 128 B
+    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    auto sA_hi = [&](int s) { return smem + (size_t)s * stage_bytes; };
+    auto sA_lo = [&](int s) { return smem + (size_t)s * stage_bytes + a_bytes; };
+    auto sB_hi = [&](int s) { return smem + (size_t)s * stage_bytes + 2 * a_bytes; };
+    auto sB_lo = [&](int s) { return smem + (size_t)s * stage_bytes + 2 * a_bytes + b_bytes; };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nbuf = P.nbuf;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), kRows + 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&accf_bar[b]), 1);
+            mbar_init(smem_u32(&acce_bar[b]), kRows);
+        }
+        mbar_init(smem_u32(&drain_bar), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(P.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem_base = tmem_base_s;
+    const int chunk_elems = kChunk / P.elt;
+    const int kbytes = kp * P.elt;  // valid bytes of a row
+    // tensor memory: partial sums of one transfer vector in D[0..nbuf), the running sum in R
+    const uint32_t tm_R = tmem_base + (uint32_t)(nbuf * kp);
+
+    if (warp < 4) {
+        // ---------------- A producers: 8 lanes per row, each a 16-byte piece; 8 rows per thread ----
+        const int piece = tid & 7, rgrp = tid >> 3;  // rows rgrp + 16 i
+        long long it = 0;
+        long long pend[4];  // stages whose copies are in flight, oldest first
+        int npend = 0;
+        for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
+            const ContractTile T = P.tiles[tile];
+            const LevelView &L = P.lv.L[T.lev];
+            RowInfo ri[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) ri[i] = row_info(L, T, P.R, rgrp + 16 * i);
+            const int cx = T.oct & 1, cy = (T.oct >> 1) & 1, cz = (T.oct >> 2) & 1;
+            const int N = L.N;
+            for (int dx = -2 - cx; dx <= 3 - cx; ++dx)
+                for (int dy = -2 - cy; dy <= 3 - cy; ++dy)
+                    for (int dz = -2 - cz; dz <= 3 - cz; ++dz) {
+                        int m = max(abs(dx), max(abs(dy), abs(dz)));
+                        if (m < 2) continue;
+                        long long src[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            src[i] = P.zero_row;
+                            if (ri[i].b >= 0) {
+                                int x = (int)(ri[i].xyz & 1023) + dx, y = (int)((ri[i].xyz >> 10) & 1023) + dy,
+                                    z = (int)((ri[i].xyz >> 20) & 1023) + dz;
+                                if (x >= 0 && y >= 0 && z >= 0 && x < N && y < N && z < N) {
+                                    int sl = L.slot[((long long)z * N + y) * N + x];
+                                    if (sl >= 0) src[i] = (L.base + sl) * P.R + ri[i].r;
+                                }
+                            }
+                        }
+                        for (int c = 0; c < P.nchunks; ++c, ++it) {
+                            const int s = (int)(it % S);
+                            if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) - 1) & 1), &abort_flag,
+                                                      P.status, 1))
+                                goto producer_done;
+                            if (c * kChunk + piece * 16 < kbytes) {
+                                const long long goff = (long long)c * kChunk + piece * 16;
+                                const uint32_t bh = smem_u32(sA_hi(s)), bl = smem_u32(sA_lo(s));
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) {
+                                    const int row = rgrp + 16 * i;
+                                    const uint32_t off = (uint32_t)(row * kChunk + ((piece ^ (row & 7)) * 16));
+                                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(bh + off),
+                                                 "l"(P.qhi + src[i] * kbytes + goff)
+                                                 : "memory");
+                                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(bl + off),
+                                                 "l"(P.qlo + src[i] * kbytes + goff)
+                                                 : "memory");
+                                }
+                            }
+                            asm volatile("cp.async.commit_group;" ::: "memory");
+                            pend[npend++] = it;
+                            if (npend > S - 1) {
+                                // keep S - 1 groups in flight: retire the oldest
+                                if (S == 2) asm volatile("cp.async.wait_group 1;" ::: "memory");
+                                else if (S == 3) asm volatile("cp.async.wait_group 2;" ::: "memory");
+                                else asm volatile("cp.async.wait_group 3;" ::: "memory");
+                                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                                mbar_arrive(smem_u32(&full_bar[pend[0] % S]));
+                                for (int q = 1; q < npend; ++q) pend[q - 1] = pend[q];
+                                --npend;
+                            }
+                        }
+                    }
+        }
+    producer_done:
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int q = 0; q < npend; ++q) mbar_arrive(smem_u32(&full_bar[pend[q] % S]));
+    } else if (warp == 4) {
+        // ---------------- B producer: TMA loads of C_t chunks ----------------
+        if (lane == 0) {
+            long long it = 0;
+            int last_parity[4] = {-1, -1, -1, -1};
+            for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
+                const ContractTile T = P.tiles[tile];
+                const int cx = T.oct & 1, cy = (T.oct >> 1) & 1, cz = (T.oct >> 2) & 1;
+                for (int dx = -2 - cx; dx <= 3 - cx; ++dx)
+                    for (int dy = -2 - cy; dy <= 3 - cy; ++dy)
+                        for (int dz = -2 - cz; dz <= 3 - cz; ++dz) {
+                            int m = max(abs(dx), max(abs(dy), abs(dz)));
+                            if (m < 2) continue;
+                            // transfer index of (dx, dy, dz): [-3,3]^3 minus [-1,1]^3, x slowest
+                            int lin = ((dx + 3) * 7 + (dy + 3)) * 7 + (dz + 3);
+                            int before = 0;  // near vectors preceding lin in the enumeration
+                            for (int ax = -1; ax <= 1; ++ax)
+                                for (int ay = -1; ay <= 1; ++ay)
+                                    for (int az = -1; az <= 1; ++az)
+                                        before += (((ax + 3) * 7 + (ay + 3)) * 7 + (az + 3)) < lin;
+                            const int ti = lin - before;
+                            for (int c = 0; c < P.nchunks; ++c, ++it) {
+                                const int s = (int)(it % S);
+                                if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) - 1) & 1), &abort_flag,
+                                                          P.status, 2))
+                                    goto tma_done;
+                                const uint32_t bar = smem_u32(&full_bar[s]);
+                                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2 * b_bytes)
+                                             : "memory");
+                                const int x = c * chunk_elems, y = ti * kp;
+                                asm volatile(
+                                    "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                                        smem_u32(sB_hi(s))),
+                                    "l"(&tm_hi), "r"(x), "r"(y), "r"(bar)
+                                    : "memory");
+                                asm volatile(
+                                    "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                                        smem_u32(sB_lo(s))),
+                                    "l"(&tm_lo), "r"(x), "r"(y), "r"(bar)
+                                    : "memory");
+                                last_parity[s] = (int)((it / S) & 1);
+                            }
+                        }
+            }
+        tma_done:
+            if (abort_flag) {
+                // let loads already issued land before the CTA leaves
+                for (int s = 0; s < S; ++s)
+                    if (last_parity[s] >= 0)
+                        for (long long w = 0; w < kWaitLimit && !mbar_try(smem_u32(&full_bar[s]), (uint32_t)last_parity[s]); ++w) {
+                        }
+            }
+        }
+    } else if (warp == 5) {
+        // ---------------- MMA issuer: one partial sum per transfer vector ----------------
+        if (lane == 0) {
+            long long it = 0, u = 0;
+            bool pending = false;
+            for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
+                for (int tv = 0; tv < kPerOctant; ++tv, ++u) {
+                    const int buf = (int)(u % nbuf);
+                    if (u >= nbuf &&
+                        !mbar_wait(smem_u32(&acce_bar[buf]), (uint32_t)(((u / nbuf) - 1) & 1), &abort_flag, P.status, 3))
+                        goto mma_done;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t d = tmem_base + (uint32_t)(buf * kp);
+                    uint32_t accflag = 0;
+                    for (int c = 0; c < P.nchunks; ++c, ++it) {
+                        const int s = (int)(it % S);
+                        if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((it / S) & 1), &abort_flag, P.status, 4)) goto mma_done;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const int steps = min(4, (kbytes - c * kChunk) / 32);
+                        const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
+                        const uint32_t bh = smem_u32(sB_hi(s)), bl = smem_u32(sB_lo(s));
+                        for (int k = 0; k < steps; ++k) {
+                            const uint64_t dah = smem_desc(ah + 32 * k), dal = smem_desc(al + 32 * k);
+                            const uint64_t dbh = smem_desc(bh + 32 * k), dbl = smem_desc(bl + 32 * k);
+                            mma<KIND>(d, dal, dbh, P.idesc, accflag);
+                            accflag = 1;
+                            mma<KIND>(d, dah, dbl, P.idesc, 1);
+                            mma<KIND>(d, dah, dbh, P.idesc, 1);
+                        }
+                        mma_commit(smem_u32(&empty_bar[s]));
+                        pending = true;
+                    }
+                    mma_commit(smem_u32(&accf_bar[buf]));
+                }
+            }
+        mma_done:
+            if (abort_flag && pending) {
+                // no MMA may still write tensor memory when it is released
+                mma_commit(smem_u32(&drain_bar));
+                for (long long w = 0; w < kWaitLimit && !mbar_try(smem_u32(&drain_bar), 0); ++w) {
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: R += D per transfer vector (FP32, round to nearest); R -> phi~ ----
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        long long u = 0;
+        for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
+            const ContractTile T = P.tiles[tile];
+            const LevelView &L = P.lv.L[T.lev];
+            const RowInfo ri = row_info(L, T, P.R, row);
+            float *dst = ri.b >= 0 ? P.phit + ((L.base + ri.b) * P.R + ri.r) * (long long)kp : nullptr;
+            for (int tv = 0; tv < kPerOctant; ++tv, ++u) {
+                const int buf = (int)(u % nbuf);
+                if (!mbar_wait(smem_u32(&accf_bar[buf]), (uint32_t)((u / nbuf) & 1), &abort_flag, P.status, 5)) goto epi_done;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t tD = tmem_base + lane_off + (uint32_t)(buf * kp), tR = tm_R + lane_off;
+                for (int c0 = 0; c0 < kp; c0 += 16) {
+                    uint32_t dv[16], rv[16];
+                    tmem_ld16(tD + c0, dv);
+                    if (tv > 0) tmem_ld16(tR + c0, rv);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (tv > 0) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) dv[j] = __float_as_uint(__fadd_rn(__uint_as_float(rv[j]), __uint_as_float(dv[j])));
+                    }
+                    if (tv + 1 < kPerOctant) {
+                        tmem_st16(tR + c0, dv);
+                    } else if (dst) {
+                        float4 *o = reinterpret_cast<float4 *>(dst + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            o[j] = make_float4(__uint_as_float(dv[4 * j]), __uint_as_float(dv[4 * j + 1]),
+                                               __uint_as_float(dv[4 * j + 2]), __uint_as_float(dv[4 * j + 3]));
+                    }
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(smem_u32(&acce_bar[buf]));
+            }
+        }
+    epi_done:;
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 5) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(P.tmem_cols));
+    }
+}
+
+// hi/lo split of q~ rows: TF32 pieces (FP32 containers, low 13 bits zero) or BF16 pieces.
+__global__ void split_rows_kernel(const float *__restrict__ src, long long count, int kind, unsigned char *__restrict__ hi,
+                                  unsigned char *__restrict__ lo) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (; i < count; i += stride) {
+        const float x = src[i];
+        if (kind == 0) {
+            uint32_t h, l;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+            const float r = x - __uint_as_float(h);
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+            reinterpret_cast<uint32_t *>(hi)[i] = h;
+            reinterpret_cast<uint32_t *>(lo)[i] = l;
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+            reinterpret_cast<__nv_bfloat16 *>(hi)[i] = h;
+            reinterpret_cast<__nv_bfloat16 *>(lo)[i] = l;
+        }
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Host rounding of a double to the pieces the tensor cores read (round to nearest).
+inline uint32_t f32_bits(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return u;
+}
+inline float bits_f32(uint32_t u) {
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+inline float tf32_round(float x) {  // nearest, ties away from zero, on the 10-bit mantissa
+    uint32_t u = f32_bits(x);
+    if ((u & 0x7F800000u) == 0x7F800000u) return x;
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    return bits_f32(u);
+}
+inline uint16_t bf16_round(float x) {  // nearest, ties to even
+    uint32_t u = f32_bits(x);
+    if ((u & 0x7F800000u) == 0x7F800000u) return (uint16_t)(u >> 16);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+inline float bf16_value(uint16_t h) { return bits_f32((uint32_t)h << 16); }
+
+}  // namespace
+
+// Split C_t (FP64 on the host) into hi/lo pieces, upload them and encode their TMA maps.
+int split_tc_operators(m2l_plan_t *pl, int precision) {
+    DevOps &D = pl->dev[precision];
+    const int k = pl->k, kp = pl->kp;
+    if (kp > 256) {
+        set_error("split tensor-core contraction supports a rank of at most 256 (k_pad = %d)", kp);
+        return M2L_EUNSUPPORTED;
+    }
+    const size_t count = (size_t)kNumTransfer * kp * kp;
+    const int kind = precision == M2L_PREC_TF32X3 ? 0 : 1;
+    const size_t elt = kind == 0 ? 4 : 2;
+    std::vector<unsigned char> hi(count * elt, 0), lo(count * elt, 0);
+    for (int t = 0; t < kNumTransfer; ++t)
+        for (int a = 0; a < k; ++a)
+            for (int c = 0; c < k; ++c) {
+                const double v = pl->C[((size_t)t * k + a) * k + c];
+                const size_t i = ((size_t)t * kp + a) * kp + c;
+                if (kind == 0) {
+                    float h = tf32_round((float)v);
+                    float l = tf32_round((float)(v - (double)h));
+                    std::memcpy(&hi[i * 4], &h, 4);
+                    std::memcpy(&lo[i * 4], &l, 4);
+                } else {
+                    uint16_t h = bf16_round((float)v);
+                    uint16_t l = bf16_round((float)(v - (double)bf16_value(h)));
+                    std::memcpy(&hi[i * 2], &h, 2);
+                    std::memcpy(&lo[i * 2], &l, 2);
+                }
+            }
+    for (void **pp : {&D.C_hi, &D.C_lo})
+        if (*pp) cudaFree(*pp);
+    D.C_hi = D.C_lo = nullptr;
+    if (cudaMalloc(&D.C_hi, hi.size()) != cudaSuccess || cudaMalloc(&D.C_lo, lo.size()) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("allocating split operators failed");
+        return M2L_ENOMEM;
+    }
+    cudaMemcpy(D.C_hi, hi.data(), hi.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(D.C_lo, lo.data(), lo.size(), cudaMemcpyHostToDevice);
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return M2L_ECUDA;
+    }
+    // C_t as a 2D tensor: inner dimension k_pad elements, kNumTransfer * k_pad rows; a box is one
+    // 128-byte chunk of K for all k_pad output rows of one transfer vector.
+    const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)kNumTransfer * kp};
+    const cuuint64_t strides[1] = {(cuuint64_t)kp * elt};
+    const cuuint32_t box[2] = {(cuuint32_t)(128 / elt), (cuuint32_t)kp};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapDataType dt = kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    void *bases[2] = {D.C_hi, D.C_lo};
+    for (int i = 0; i < 2; ++i) {
+        CUresult r = enc(reinterpret_cast<CUtensorMap *>(D.tmap[i]), dt, 2, bases[i], dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+            return M2L_ECUDA;
+        }
+    }
+    return M2L_OK;
+}
+
+int launch_split_rows(const float *src, long long rows, int kp, void *hi, void *lo, int precision, cudaStream_t s) {
+    const long long count = rows * kp;
+    const int kind = precision == M2L_PREC_TF32X3 ? 0 : 1;
+    long long blocks = (count + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    split_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, count, kind, (unsigned char *)hi, (unsigned char *)lo);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("split launch failed: %s", cudaGetErrorString(e));
+        return M2L_ECUDA;
+    }
+    return M2L_OK;
+}
+
+size_t tc_stage_bytes(int kp) { return 2 * (size_t)kRows * kChunk + 2 * (size_t)kp * kChunk; }
 
 template <class T>
-int launch_contract_tc(m2l_plan_t *, const LevelsArg &, const ContractTile *, long long, int, const void *,
-                       const void *, long long, T *, int, cudaStream_t) {
-    set_error("split tensor-core precisions are not built yet");
-    return M2L_EUNSUPPORTED;
+int launch_contract_tc(m2l_plan_t *pl, const LevelsArg &lv, const ContractTile *tiles, long long ntiles, int R,
+                       const void *qt_hi, const void *qt_lo, long long zero_row, T *phit, int precision, cudaStream_t s) {
+    if constexpr (sizeof(T) != 4) {
+        set_error("the tensor-core contraction writes FP32");
+        return M2L_EINVAL;
+    } else {
+        if (ntiles <= 0) return M2L_OK;
+        DevOps &D = pl->dev[precision];
+        const int kp = pl->kp;
+        const int kind = precision == M2L_PREC_TF32X3 ? 0 : 1;
+        TcParams P;
+        P.lv = lv;
+        P.tiles = tiles;
+        P.ntiles = ntiles;
+        P.R = R;
+        P.qhi = (const unsigned char *)qt_hi;
+        P.qlo = (const unsigned char *)qt_lo;
+        P.zero_row = zero_row;
+        P.phit = reinterpret_cast<float *>(phit);
+        P.kp = kp;
+        P.elt = kind == 0 ? 4 : 2;
+        P.nchunks = (kp * P.elt + kChunk - 1) / kChunk;
+        const size_t stage = tc_stage_bytes(kp);
+        const size_t budget = 227 * 1024 - 1024 - 256;
+        int S = (int)(budget / stage);
+        if (S > 4) S = 4;
+        if (S < 2) {
+            set_error("rank %d too large for the tensor-core pipeline", kp);
+            return M2L_EUNSUPPORTED;
+        }
+        P.stages = S;
+        uint32_t idesc = 1u << 4;  // FP32 accumulator
+        idesc |= (kind == 0 ? 2u : 1u) << 7;
+        idesc |= (kind == 0 ? 2u : 1u) << 10;
+        idesc |= (uint32_t)(kp >> 3) << 17;
+        idesc |= (uint32_t)(kRows >> 4) << 24;
+        P.idesc = idesc;
+        // tensor memory: nbuf partial-sum buffers and the running sum, kp columns each
+        P.nbuf = 3 * kp <= 512 ? 2 : 1;
+        const int need = (P.nbuf + 1) * kp;
+        P.tmem_cols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
+        P.status = pl->dev_status;
+        const size_t smem = (size_t)S * stage + 1024;
+        const int grid = (int)(ntiles < pl->num_sms ? ntiles : pl->num_sms);
+        const CUtensorMap *thi = reinterpret_cast<const CUtensorMap *>(D.tmap[0]);
+        const CUtensorMap *tlo = reinterpret_cast<const CUtensorMap *>(D.tmap[1]);
+        cudaError_t e;
+        if (kind == 0) {
+            cudaFuncSetAttribute(contract_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            contract_tc_kernel<0><<<grid, kThreads, smem, s>>>(*thi, *tlo, P);
+        } else {
+            cudaFuncSetAttribute(contract_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            contract_tc_kernel<1><<<grid, kThreads, smem, s>>>(*thi, *tlo, P);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_error("tensor-core contraction launch failed: %s", cudaGetErrorString(e));
+            return M2L_ECUDA;
+        }
+        return M2L_OK;
+    }
 }
-template int launch_contract_tc<float>(m2l_plan_t *, const LevelsArg &, const ContractTile *, long long, int,
-                                       const void *, const void *, long long, float *, int, cudaStream_t);
-template int launch_contract_tc<double>(m2l_plan_t *, const LevelsArg &, const ContractTile *, long long, int,
-                                        const void *, const void *, long long, double *, int, cudaStream_t);
+template int launch_contract_tc<float>(m2l_plan_t *, const LevelsArg &, const ContractTile *, long long, int, const void *,
+                                       const void *, long long, float *, int, cudaStream_t);
+template int launch_contract_tc<double>(m2l_plan_t *, const LevelsArg &, const ContractTile *, long long, int, const void *,
+                                        const void *, long long, double *, int, cudaStream_t);
 
 }  // namespace m2l

@@ -525,6 +525,8 @@ void free_device(m2l_plan_t *pl) {
     if (pl->tiles) cudaFree(pl->tiles);
     if (pl->lattice_dev) cudaFree(pl->lattice_dev);
     pl->lattice_dev = nullptr;
+    if (pl->dev_status) cudaFree(pl->dev_status);
+    pl->dev_status = nullptr;
     for (cudaEvent_t e : pl->event_pool) cudaEventDestroy(e);
     pl->event_pool.clear();
     pl->events.clear();

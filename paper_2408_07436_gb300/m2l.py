@@ -34,7 +34,7 @@ M2L_FORM_AUTO, M2L_FORM_BLAS, M2L_FORM_FFT = 0, 1, 2
 M2L_PREC_AUTO, M2L_PREC_FP64, M2L_PREC_FP32, M2L_PREC_TF32X3, M2L_PREC_BF16X3 = -1, 0, 1, 2, 3
 M2L_OUT_LOCALS, M2L_OUT_CHECK_POTENTIAL = 0, 1
 (M2L_Q_N, M2L_Q_RANK, M2L_Q_BOXES, M2L_Q_PAIRS, M2L_Q_GRID, M2L_Q_FREQS, M2L_Q_PINV_RANK, M2L_Q_ROWS,
- M2L_Q_FORM, M2L_Q_PRECISION, M2L_Q_LAUNCHES) = range(1, 12)
+ M2L_Q_FORM, M2L_Q_PRECISION, M2L_Q_LAUNCHES, M2L_Q_DEVICE_STATUS) = range(1, 13)
 
 FORMS = {"auto": M2L_FORM_AUTO, "blas": M2L_FORM_BLAS, "fft": M2L_FORM_FFT}
 PRECISIONS = {"auto": M2L_PREC_AUTO, "fp64": M2L_PREC_FP64, "fp32": M2L_PREC_FP32,

@@ -177,3 +177,69 @@ def test_c2_full_size_sampled(lib, form, precision):
         else:
             _, phi_ref = oracle_level(wl.p, l, qs[l], targets=sample)
         assert M.rel_l2_error(phi_ref, chk[l][sample]) < bound * (10 if form == "blas" else 1), (l,)
+
+
+# Split tensor-core precisions (tcgen05): bounds on check potentials. TF32x3 pieces carry 22
+# mantissa bits, so the result sits at FP32 rounding (measured 4e-7 to 1.6e-6 for p = 4..8);
+# BF16x3 pieces carry about 17 (measured 3e-7 to 8.3e-6, largest for densities of both signs).
+TC_TOL = {"tf32x3": 5e-6, "bf16x3": 2e-5}
+
+
+def _status(lib, handle):
+    return lib.m2l_query(handle, lib.M2L_Q_DEVICE_STATUS)
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+def test_tensor_core_forms_small(lib, precision):
+    wl = W.small(depth=3, p=4, density="u11")
+    qs = _qs(wl)
+    chk = run_gpu(lib, 3, 4, qs, precision=precision, output="check")
+    loc = run_gpu(lib, 3, 4, qs, precision=precision, output="locals")
+    for l in wl.levels:
+        L_ref, phi_ref = oracle_level(4, l, qs[l])
+        e = M.rel_l2_error(phi_ref, chk[l])
+        assert e < TC_TOL[precision], (precision, l, e)
+        assert M.check_norm_error(4, l, L_ref, loc[l]) < 10 * TC_TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+def test_tensor_core_sparse_multi_rhs_truncated(lib, precision):
+    wl = W.small(depth=4, p=5, n_rhs=3, n_points=500, density="normal", rank_tol=1e-6)
+    qs = _qs(wl)
+    keys = {l: wl.keys[l] for l in wl.levels}
+    chk = run_gpu(lib, wl.depth, wl.p, qs, keys=keys, rank_tol=1e-6, precision=precision, output="check", R=3)
+    ops = O.compressed_operators(wl.p, 1e-6, 1.0)
+    for l in wl.levels:
+        k = None if keys[l] is None else keys[l].astype(np.int64)
+        _, phi_c = M.m2l_compressed(wl.p, l, qs[l], ops, keys=k)
+        e = M.rel_l2_error(phi_c, chk[l])
+        assert e < TC_TOL[precision], (precision, l, e)
+
+
+def test_tensor_core_status_clear(lib):
+    import torch
+    wl = W.small(depth=3, p=4)
+    plan = lib.Plan(3, 4, 0.0, form="blas", precision="tf32x3")
+    try:
+        plan.set_stream()
+        q = torch.from_numpy(wl.all_multipoles()).float().cuda()
+        o = torch.empty_like(q)
+        plan.apply(q, o, -1, 1)
+        assert _status(lib, plan.handle) == 0
+        assert torch.isfinite(o).all()
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+def test_c2_full_size_sampled_tensor_cores(lib, precision):
+    wl = W.c2()
+    qs = _qs(wl)
+    chk = run_gpu(lib, wl.depth, wl.p, qs, rank_tol=wl.rank_tol, precision=precision, output="check")
+    ops = O.compressed_operators(wl.p, wl.rank_tol, 1.0)
+    rng = np.random.default_rng(6)
+    for l in wl.levels:
+        B = wl.n_boxes(l)
+        sample = np.sort(rng.choice(B, size=min(B, 48), replace=False))
+        _, phi_ref = M.m2l_compressed(wl.p, l, qs[l], ops, targets=sample)
+        assert M.rel_l2_error(phi_ref, chk[l][sample]) < TC_TOL[precision], (precision, l)
