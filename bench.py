@@ -2,9 +2,10 @@
 """M2L interactions/s on GB300 for the 3D Laplace kiFMM (arxiv 2408.07436).
 
 One step = one pass of the whole M2L hot path over the 1M-point workload (uniform cube,
-depth 5, p = 6, 1 RHS; levels 2..5, 6,039,504 target/source pairs) in the four variants the
-workload names: BLAS-M2L (SVD truncated at 1e-7) in FP64 and FP32, and FFT-M2L in FP64 and
-FP32. Each variant is one m2l_apply over all levels through the C ABI.
+depth 5, p = 6, 1 RHS; levels 2..5, 6,039,504 target/source pairs) in every precision the
+library offers for it: BLAS-M2L (SVD truncated at 1e-7) in FP64, FP32 and the split tensor-core
+forms TF32x3 and BF16x3, and FFT-M2L in FP64 and FP32. Each variant is one m2l_apply over all
+levels (one launch per stage covers every level) through the C ABI.
 
   value      whole-job M2L interactions/s (pairs x RHS x variants per step / device time per
              step), inputs resident in HBM, L2 flushed between timed steps, CUDA events on the
@@ -40,10 +41,10 @@ sys.path.insert(0, ROOT)
 
 from paper_2408_07436_gb300 import workloads as W  # noqa: E402
 
-VARIANTS = ["blas-fp64", "blas-fp32", "fft-fp64", "fft-fp32"]
+VARIANTS = ["blas-fp64", "blas-fp32", "blas-tf32x3", "blas-bf16x3", "fft-fp64", "fft-fp32"]
 METRIC = "M2L interactions/s and % roofline: mixed+batched vs FP64 GPU at stated rel err"
 UNIT = "interactions/s"
-WORKLOAD = "laplace3d-m2l uniform-cube 1M points depth5 p6 1rhs blas(rank_tol 1e-7)+fft fp64+fp32"
+WORKLOAD = "laplace3d-m2l uniform-cube 1M points depth5 p6 1rhs blas(rank_tol 1e-7)+fft fp64+fp32+tf32x3+bf16x3"
 
 # Nominal per-GPU figures (GB300) used where no measured peak exists.
 NOMINAL_FP64_TFLOPS = 1.25       # FP64 (vector and tensor) dense
@@ -241,18 +242,34 @@ def run_ours(args, rank, world, local_rank):
                       "ms": var_ms[v] / args.steps, "stages": stages}
         if form == "blas":
             var_out[v]["rank"] = plans[v].query(lib.M2L_Q_RANK)
+    def peak_for(prec):
+        if prec == "fp64":
+            return NOMINAL_FP64_TFLOPS, "alu", "nominal GB300 FP64 1.25 TFLOP/s"
+        if prec == "fp32":
+            return fp32_alu_peak_tflops(), "alu", "152 SM x 128 FP32 lanes x 2 flops x 2070 MHz"
+        bf = peaks.get("bf16_tflops_sustained", 1700.0)
+        if prec == "bf16x3":
+            return bf / 3.0, "tensor", "of measured: bf16 sustained / 3 (each useful product is 3 MMAs)"
+        return bf / 2.0 / 3.0, "tensor", "of measured: bf16 sustained / 2 (nominal tf32 ratio) / 3 (3 MMAs per product)"
+
+    def roof(v, name, ms_total, nl, flops_launch):
+        prec = variant_parts(v)[1]
+        pk, bound, note = peak_for(prec)
+        per_launch_ms = ms_total / nl
+        ach = flops_launch / (per_launch_ms / 1e3) / 1e12
+        return {"bound": bound, "kernel": f"{v}:{name}", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk, "traffic": None, "peak_source": note}
+
+    for v in variants:
+        st = {n: a for n, a in stage_acc[v].items() if a[1] > 0}
+        if not st:
+            continue
+        name = max(st, key=lambda n: st[n][0])
+        ms_tot, nl = st[name]
+        work = algorithmic_work(plans[v], *variant_parts(v), R)
+        var_out[v]["roofline"] = roof(v, name, ms_tot, nl, work.get(name, 0.0) * args.steps / nl)
     _, bv, bname, bms, bflops, bprec = best
-    if bprec == "fp64":
-        peak, peak_note = NOMINAL_FP64_TFLOPS, "nominal GB300 FP64 1.25 TFLOP/s"
-    elif bprec == "fp32":
-        peak, peak_note = fp32_alu_peak_tflops(), "152 SM x 128 FP32 lanes x 2 x 2070 MHz"
-    else:
-        peak = peaks.get("bf16_tflops_sustained", 1700.0) / 2.0
-        peak_note = "of measured: bf16 sustained / 2 (tf32 nominal ratio)"
-    achieved = bflops / (bms / 1e3) / 1e12
-    roofline = {"bound": "alu" if bprec in ("fp64", "fp32") else "tensor", "kernel": f"{bv}:{bname}",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_note}
+    roofline = roof(bv, bname, bms * 1.0, 1, bflops)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -282,13 +299,22 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": world * inter_step * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    mixed = [v for v in variants if variant_parts(v)[1] in ("tf32x3", "bf16x3", "fp32")]
+    fp64 = [v for v in variants if variant_parts(v)[1] == "fp64"]
+    headline = None
+    if mixed and fp64:
+        bm = max(mixed, key=lambda v: var_out[v]["interactions_per_s"])
+        bf = max(fp64, key=lambda v: var_out[v]["interactions_per_s"])
+        headline = {"fastest_reduced_precision": bm, "fastest_fp64": bf,
+                    "speedup": var_out[bm]["interactions_per_s"] / var_out[bf]["interactions_per_s"]}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+           "vs_baseline": None, "dtype": "+".join(sorted({variant_parts(v)[1] for v in variants})), "data": "synthetic",
            "config": {"workload": WORKLOAD, "levels": wl.levels, "pairs_per_variant": pairs, "n_rhs": R,
                       "variants": variants, "l2": "flushed between timed steps (512 MB write)",
                       "instances": "one independent instance per rank"},
-           "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e, "variants": var_out}
+           "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e, "variants": var_out,
+           "mixed_vs_fp64": headline}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, q64, plans, bufs, args.cpu_seconds)
     for pl in plans.values():

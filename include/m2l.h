@@ -71,7 +71,10 @@ enum m2l_option_e {
     M2L_OPT_OUTPUT = 4,      /* M2L_OUT_*; default M2L_OUT_LOCALS */
     M2L_OPT_TARGET_TOL = 5,  /* accuracy asked of M2L_FORM_AUTO: the bits of a double */
     M2L_OPT_FFT_GRID = 6,    /* convolution grid side: 0 = 2p (default), else 2p-1 <= g <= 2p */
-    M2L_OPT_TIMING = 7       /* 1: record CUDA events around every stage (see m2l_stage_times) */
+    M2L_OPT_TIMING = 7,      /* 1: record CUDA events around every stage (see m2l_stage_times) */
+    M2L_OPT_TC_GROUP = 8     /* split tensor-core forms: transfer vectors summed in tensor memory before
+                                each round-to-nearest FP32 drain, 1..189 (default 1). Larger is faster;
+                                the tensor cores' truncating accumulation grows with it */
 };
 
 /* Stages of one application, as indexed by m2l_stage_times. */

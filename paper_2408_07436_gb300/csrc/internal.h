@@ -83,6 +83,7 @@ struct m2l_plan_s {
     int form = M2L_FORM_BLAS, precision = M2L_PREC_FP64, accumulate = 0, output = M2L_OUT_LOCALS;
     double target_tol = 1e-6;
     int fft_grid_opt = 0;
+    int tc_group = 1;                           // transfer vectors per tensor-memory partial sum
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 148;

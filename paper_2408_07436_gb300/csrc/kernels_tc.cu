@@ -7,13 +7,16 @@
 //
 // One persistent CTA per SM loops over tiles of 128 (target, rhs) rows of one octant of one
 // level. Per (tile, t, 128-byte K chunk) a pipeline stage holds
-//   A_hi, A_lo: the 128 gathered source rows of q~ (cp.async, 16-byte pieces written with the
-//               128-byte swizzle), one row per producer thread;
+//   A_hi, A_lo: the 128 gathered source rows of q~: cp.async, 8 lanes per 128-byte row piece so
+//               every request is a full line, written with the 128-byte swizzle (measured faster
+//               than TMA tile::gather4 row gathers for these 128-byte pieces);
 //   B_hi, B_lo: the chunk of C_t (k_pad x 128 bytes), loaded by TMA with SWIZZLE_128B.
-// Warps: 0-3 gather A; 4 issues TMA for B; 5 owns tensor memory and issues the MMAs
-// (M = 128 rows, N = k_pad, K = 32 bytes per instruction); 6-9 drain the accumulator
-// (double-buffered in tensor memory) to phi~. Every wait is bounded; a wait that runs out sets
-// the plan's device status word and the CTA winds down.
+// Warps: 0-3 gather A (the next transfer vector's source rows are looked up while the current
+// chunks are in flight); 4 issues TMA for B; 5 owns tensor memory and issues the MMAs (M = 128
+// rows, N = k_pad, K = 32 bytes per instruction); 6-9 drain each transfer vector's partial sum
+// (double-buffered in tensor memory) into the running sum.
+// Every wait is bounded; a wait that runs out sets the plan's device status word and the CTA
+// winds down.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cstring>
@@ -43,8 +46,13 @@ struct TcParams {
     uint32_t idesc;
     int tmem_cols;
     int nbuf;                          // partial-sum buffers in tensor memory (1 or 2)
+    int group;                         // transfer vectors per partial sum (drain interval)
     int *status;
 };
+
+// For target octant o, entry e < 189: the transfer vector (dx, dy, dz) packed as
+// (dx + 3) | (dy + 3) << 4 | (dz + 3) << 8 and its index in [-3,3]^3 \ [-1,1]^3 (x slowest) << 12.
+__constant__ int c_oct_tv[8][kPerOctant];
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -195,60 +203,64 @@ __global__ void __launch_bounds__(kThreads, 1)
             RowInfo ri[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) ri[i] = row_info(L, T, P.R, rgrp + 16 * i);
-            const int cx = T.oct & 1, cy = (T.oct >> 1) & 1, cz = (T.oct >> 2) & 1;
             const int N = L.N;
-            for (int dx = -2 - cx; dx <= 3 - cx; ++dx)
-                for (int dy = -2 - cy; dy <= 3 - cy; ++dy)
-                    for (int dz = -2 - cz; dz <= 3 - cz; ++dz) {
-                        int m = max(abs(dx), max(abs(dy), abs(dz)));
-                        if (m < 2) continue;
-                        long long src[8];
+            // source rows of the 8 rows this thread feeds, for table entry e
+            auto sources = [&](int e, long long (&src)[8]) {
+                const int pk = c_oct_tv[T.oct][e];
+                const int dx = (pk & 15) - 3, dy = ((pk >> 4) & 15) - 3, dz = ((pk >> 8) & 15) - 3;
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            src[i] = P.zero_row;
-                            if (ri[i].b >= 0) {
-                                int x = (int)(ri[i].xyz & 1023) + dx, y = (int)((ri[i].xyz >> 10) & 1023) + dy,
-                                    z = (int)((ri[i].xyz >> 20) & 1023) + dz;
-                                if (x >= 0 && y >= 0 && z >= 0 && x < N && y < N && z < N) {
-                                    int sl = L.slot[((long long)z * N + y) * N + x];
-                                    if (sl >= 0) src[i] = (L.base + sl) * P.R + ri[i].r;
-                                }
-                            }
-                        }
-                        for (int c = 0; c < P.nchunks; ++c, ++it) {
-                            const int s = (int)(it % S);
-                            if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) - 1) & 1), &abort_flag,
-                                                      P.status, 1))
-                                goto producer_done;
-                            if (c * kChunk + piece * 16 < kbytes) {
-                                const long long goff = (long long)c * kChunk + piece * 16;
-                                const uint32_t bh = smem_u32(sA_hi(s)), bl = smem_u32(sA_lo(s));
-#pragma unroll
-                                for (int i = 0; i < 8; ++i) {
-                                    const int row = rgrp + 16 * i;
-                                    const uint32_t off = (uint32_t)(row * kChunk + ((piece ^ (row & 7)) * 16));
-                                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(bh + off),
-                                                 "l"(P.qhi + src[i] * kbytes + goff)
-                                                 : "memory");
-                                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(bl + off),
-                                                 "l"(P.qlo + src[i] * kbytes + goff)
-                                                 : "memory");
-                                }
-                            }
-                            asm volatile("cp.async.commit_group;" ::: "memory");
-                            pend[npend++] = it;
-                            if (npend > S - 1) {
-                                // keep S - 1 groups in flight: retire the oldest
-                                if (S == 2) asm volatile("cp.async.wait_group 1;" ::: "memory");
-                                else if (S == 3) asm volatile("cp.async.wait_group 2;" ::: "memory");
-                                else asm volatile("cp.async.wait_group 3;" ::: "memory");
-                                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                                mbar_arrive(smem_u32(&full_bar[pend[0] % S]));
-                                for (int q = 1; q < npend; ++q) pend[q - 1] = pend[q];
-                                --npend;
-                            }
+                for (int i = 0; i < 8; ++i) {
+                    src[i] = P.zero_row;
+                    if (ri[i].b >= 0) {
+                        int x = (int)(ri[i].xyz & 1023) + dx, y = (int)((ri[i].xyz >> 10) & 1023) + dy,
+                            z = (int)((ri[i].xyz >> 20) & 1023) + dz;
+                        if (x >= 0 && y >= 0 && z >= 0 && x < N && y < N && z < N) {
+                            int sl = L.slot[((long long)z * N + y) * N + x];
+                            if (sl >= 0) src[i] = (L.base + sl) * P.R + ri[i].r;
                         }
                     }
+                }
+            };
+            long long src[8], nxt[8];
+            sources(0, nxt);
+            for (int e = 0; e < kPerOctant; ++e) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) src[i] = nxt[i];
+                if (e + 1 < kPerOctant) sources(e + 1, nxt);  // in flight while this vector's chunks go out
+                for (int c = 0; c < P.nchunks; ++c, ++it) {
+                    const int s = (int)(it % S);
+                    if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) - 1) & 1), &abort_flag,
+                                              P.status, 1))
+                        goto producer_done;
+                    if (c * kChunk + piece * 16 < kbytes) {
+                        const long long goff = (long long)c * kChunk + piece * 16;
+                        const uint32_t bh = smem_u32(sA_hi(s)), bl = smem_u32(sA_lo(s));
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int row = rgrp + 16 * i;
+                            const uint32_t off = (uint32_t)(row * kChunk + ((piece ^ (row & 7)) * 16));
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(bh + off),
+                                         "l"(P.qhi + src[i] * kbytes + goff)
+                                         : "memory");
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(bl + off),
+                                         "l"(P.qlo + src[i] * kbytes + goff)
+                                         : "memory");
+                        }
+                    }
+                    asm volatile("cp.async.commit_group;" ::: "memory");
+                    pend[npend++] = it;
+                    if (npend > S - 1) {
+                        // keep S - 1 groups in flight: retire the oldest
+                        if (S == 2) asm volatile("cp.async.wait_group 1;" ::: "memory");
+                        else if (S == 3) asm volatile("cp.async.wait_group 2;" ::: "memory");
+                        else asm volatile("cp.async.wait_group 3;" ::: "memory");
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        mbar_arrive(smem_u32(&full_bar[pend[0] % S]));
+                        for (int q = 1; q < npend; ++q) pend[q - 1] = pend[q];
+                        --npend;
+                    }
+                }
+            }
         }
     producer_done:
         asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -261,42 +273,30 @@ __global__ void __launch_bounds__(kThreads, 1)
             int last_parity[4] = {-1, -1, -1, -1};
             for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
                 const ContractTile T = P.tiles[tile];
-                const int cx = T.oct & 1, cy = (T.oct >> 1) & 1, cz = (T.oct >> 2) & 1;
-                for (int dx = -2 - cx; dx <= 3 - cx; ++dx)
-                    for (int dy = -2 - cy; dy <= 3 - cy; ++dy)
-                        for (int dz = -2 - cz; dz <= 3 - cz; ++dz) {
-                            int m = max(abs(dx), max(abs(dy), abs(dz)));
-                            if (m < 2) continue;
-                            // transfer index of (dx, dy, dz): [-3,3]^3 minus [-1,1]^3, x slowest
-                            int lin = ((dx + 3) * 7 + (dy + 3)) * 7 + (dz + 3);
-                            int before = 0;  // near vectors preceding lin in the enumeration
-                            for (int ax = -1; ax <= 1; ++ax)
-                                for (int ay = -1; ay <= 1; ++ay)
-                                    for (int az = -1; az <= 1; ++az)
-                                        before += (((ax + 3) * 7 + (ay + 3)) * 7 + (az + 3)) < lin;
-                            const int ti = lin - before;
-                            for (int c = 0; c < P.nchunks; ++c, ++it) {
-                                const int s = (int)(it % S);
-                                if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) - 1) & 1), &abort_flag,
-                                                          P.status, 2))
-                                    goto tma_done;
-                                const uint32_t bar = smem_u32(&full_bar[s]);
-                                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2 * b_bytes)
-                                             : "memory");
-                                const int x = c * chunk_elems, y = ti * kp;
-                                asm volatile(
-                                    "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-                                        smem_u32(sB_hi(s))),
-                                    "l"(&tm_hi), "r"(x), "r"(y), "r"(bar)
-                                    : "memory");
-                                asm volatile(
-                                    "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-                                        smem_u32(sB_lo(s))),
-                                    "l"(&tm_lo), "r"(x), "r"(y), "r"(bar)
-                                    : "memory");
-                                last_parity[s] = (int)((it / S) & 1);
-                            }
-                        }
+                for (int e = 0; e < kPerOctant; ++e) {
+                    const int ti = c_oct_tv[T.oct][e] >> 12;
+                    for (int c = 0; c < P.nchunks; ++c, ++it) {
+                        const int s = (int)(it % S);
+                        if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) - 1) & 1), &abort_flag,
+                                                  P.status, 2))
+                            goto tma_done;
+                        const uint32_t bar = smem_u32(&full_bar[s]);
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2 * b_bytes)
+                                     : "memory");
+                        const int x = c * chunk_elems, y = ti * kp;
+                        asm volatile(
+                            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                                smem_u32(sB_hi(s))),
+                            "l"(&tm_hi), "r"(x), "r"(y), "r"(bar)
+                            : "memory");
+                        asm volatile(
+                            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                                smem_u32(sB_lo(s))),
+                            "l"(&tm_lo), "r"(x), "r"(y), "r"(bar)
+                            : "memory");
+                        last_parity[s] = (int)((it / S) & 1);
+                    }
+                }
             }
         tma_done:
             if (abort_flag) {
@@ -313,7 +313,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             long long it = 0, u = 0;
             bool pending = false;
             for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
-                for (int tv = 0; tv < kPerOctant; ++tv, ++u) {
+                for (int g0 = 0; g0 < kPerOctant; g0 += P.group, ++u) {
+                    const int g1 = min(kPerOctant, g0 + P.group);
                     const int buf = (int)(u % nbuf);
                     if (u >= nbuf &&
                         !mbar_wait(smem_u32(&acce_bar[buf]), (uint32_t)(((u / nbuf) - 1) & 1), &abort_flag, P.status, 3))
@@ -321,23 +322,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t d = tmem_base + (uint32_t)(buf * kp);
                     uint32_t accflag = 0;
-                    for (int c = 0; c < P.nchunks; ++c, ++it) {
-                        const int s = (int)(it % S);
-                        if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((it / S) & 1), &abort_flag, P.status, 4)) goto mma_done;
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const int steps = min(4, (kbytes - c * kChunk) / 32);
-                        const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
-                        const uint32_t bh = smem_u32(sB_hi(s)), bl = smem_u32(sB_lo(s));
-                        for (int k = 0; k < steps; ++k) {
-                            const uint64_t dah = smem_desc(ah + 32 * k), dal = smem_desc(al + 32 * k);
-                            const uint64_t dbh = smem_desc(bh + 32 * k), dbl = smem_desc(bl + 32 * k);
-                            mma<KIND>(d, dal, dbh, P.idesc, accflag);
-                            accflag = 1;
-                            mma<KIND>(d, dah, dbl, P.idesc, 1);
-                            mma<KIND>(d, dah, dbh, P.idesc, 1);
+                    for (int tv = g0; tv < g1; ++tv) {
+                        for (int c = 0; c < P.nchunks; ++c, ++it) {
+                            const int s = (int)(it % S);
+                            if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((it / S) & 1), &abort_flag, P.status, 4)) goto mma_done;
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const int steps = min(4, (kbytes - c * kChunk) / 32);
+                            const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
+                            const uint32_t bh = smem_u32(sB_hi(s)), bl = smem_u32(sB_lo(s));
+                            for (int k = 0; k < steps; ++k) {
+                                const uint64_t dah = smem_desc(ah + 32 * k), dal = smem_desc(al + 32 * k);
+                                const uint64_t dbh = smem_desc(bh + 32 * k), dbl = smem_desc(bl + 32 * k);
+                                mma<KIND>(d, dal, dbh, P.idesc, accflag);
+                                accflag = 1;
+                                mma<KIND>(d, dah, dbl, P.idesc, 1);
+                                mma<KIND>(d, dah, dbh, P.idesc, 1);
+                            }
+                            mma_commit(smem_u32(&empty_bar[s]));
+                            pending = true;
                         }
-                        mma_commit(smem_u32(&empty_bar[s]));
-                        pending = true;
                     }
                     mma_commit(smem_u32(&accf_bar[buf]));
                 }
@@ -361,28 +364,39 @@ __global__ void __launch_bounds__(kThreads, 1)
             const LevelView &L = P.lv.L[T.lev];
             const RowInfo ri = row_info(L, T, P.R, row);
             float *dst = ri.b >= 0 ? P.phit + ((L.base + ri.b) * P.R + ri.r) * (long long)kp : nullptr;
-            for (int tv = 0; tv < kPerOctant; ++tv, ++u) {
+            for (int g0 = 0; g0 < kPerOctant; g0 += P.group, ++u) {
+                const bool first = g0 == 0, last = g0 + P.group >= kPerOctant;
                 const int buf = (int)(u % nbuf);
                 if (!mbar_wait(smem_u32(&accf_bar[buf]), (uint32_t)((u / nbuf) & 1), &abort_flag, P.status, 5)) goto epi_done;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t tD = tmem_base + lane_off + (uint32_t)(buf * kp), tR = tm_R + lane_off;
-                for (int c0 = 0; c0 < kp; c0 += 16) {
-                    uint32_t dv[16], rv[16];
-                    tmem_ld16(tD + c0, dv);
-                    if (tv > 0) tmem_ld16(tR + c0, rv);
+                for (int c0 = 0; c0 < kp; c0 += 48) {
+                    uint32_t dv[3][16], rv[3][16];
+                    const int nc = min(3, (kp - c0) / 16);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        if (q < nc) {
+                            tmem_ld16(tD + c0 + 16 * q, dv[q]);
+                            if (!first) tmem_ld16(tR + c0 + 16 * q, rv[q]);
+                        }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (tv > 0) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) dv[j] = __float_as_uint(__fadd_rn(__uint_as_float(rv[j]), __uint_as_float(dv[j])));
-                    }
-                    if (tv + 1 < kPerOctant) {
-                        tmem_st16(tR + c0, dv);
-                    } else if (dst) {
-                        float4 *o = reinterpret_cast<float4 *>(dst + c0);
+                    for (int q = 0; q < 3; ++q) {
+                        if (q >= nc) continue;
+                        if (!first) {
 #pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            o[j] = make_float4(__uint_as_float(dv[4 * j]), __uint_as_float(dv[4 * j + 1]),
-                                               __uint_as_float(dv[4 * j + 2]), __uint_as_float(dv[4 * j + 3]));
+                            for (int j = 0; j < 16; ++j)
+                                dv[q][j] = __float_as_uint(__fadd_rn(__uint_as_float(rv[q][j]), __uint_as_float(dv[q][j])));
+                        }
+                        if (!last) {
+                            tmem_st16(tR + c0 + 16 * q, dv[q]);
+                        } else if (dst) {
+                            float4 *o = reinterpret_cast<float4 *>(dst + c0 + 16 * q);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                o[j] = make_float4(__uint_as_float(dv[q][4 * j]), __uint_as_float(dv[q][4 * j + 1]),
+                                                   __uint_as_float(dv[q][4 * j + 2]), __uint_as_float(dv[q][4 * j + 3]));
+                        }
                     }
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -466,6 +480,29 @@ inline uint16_t bf16_round(float x) {  // nearest, ties to even
     return (uint16_t)(u >> 16);
 }
 inline float bf16_value(uint16_t h) { return bits_f32((uint32_t)h << 16); }
+
+int ensure_tc_constants(int device) {
+    static bool done[64] = {false};
+    if (device < 0 || device >= 64) return M2L_EINVAL;
+    if (done[device]) return M2L_OK;
+    int tab[8][kPerOctant];
+    for (int o = 0; o < 8; ++o) {
+        int cx = o & 1, cy = (o >> 1) & 1, cz = (o >> 2) & 1, e = 0;
+        for (int dx = -2 - cx; dx <= 3 - cx; ++dx)
+            for (int dy = -2 - cy; dy <= 3 - cy; ++dy)
+                for (int dz = -2 - cz; dz <= 3 - cz; ++dz) {
+                    int ti = transfer_index(dx, dy, dz);
+                    if (ti < 0) continue;
+                    tab[o][e++] = (dx + 3) | ((dy + 3) << 4) | ((dz + 3) << 8) | (ti << 12);
+                }
+    }
+    if (cudaMemcpyToSymbol(c_oct_tv, tab, sizeof tab) != cudaSuccess) {
+        set_error("uploading the octant table failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return M2L_ECUDA;
+    }
+    done[device] = true;
+    return M2L_OK;
+}
 
 }  // namespace
 
@@ -558,6 +595,8 @@ int launch_contract_tc(m2l_plan_t *pl, const LevelsArg &lv, const ContractTile *
         return M2L_EINVAL;
     } else {
         if (ntiles <= 0) return M2L_OK;
+        int crc = ensure_tc_constants(pl->device);
+        if (crc) return crc;
         DevOps &D = pl->dev[precision];
         const int kp = pl->kp;
         const int kind = precision == M2L_PREC_TF32X3 ? 0 : 1;
@@ -591,6 +630,7 @@ int launch_contract_tc(m2l_plan_t *pl, const LevelsArg &lv, const ContractTile *
         // tensor memory: nbuf partial-sum buffers and the running sum, kp columns each
         P.nbuf = 3 * kp <= 512 ? 2 : 1;
         const int need = (P.nbuf + 1) * kp;
+        P.group = pl->tc_group > 0 ? pl->tc_group : 1;
         P.tmem_cols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
         P.status = pl->dev_status;
         const size_t smem = (size_t)S * stage + 1024;

@@ -28,6 +28,7 @@ M2L_LAPLACE3D = 0
 M2L_OK, M2L_EINVAL, M2L_ENOMEM, M2L_ECUDA, M2L_ETIMEOUT, M2L_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 M2L_OPT_FORM, M2L_OPT_PRECISION, M2L_OPT_ACCUMULATE, M2L_OPT_OUTPUT, M2L_OPT_TARGET_TOL, M2L_OPT_FFT_GRID = 1, 2, 3, 4, 5, 6
 M2L_OPT_TIMING = 7
+M2L_OPT_TC_GROUP = 8
 STAGES = ["compress", "contract", "expand", "fft_forward", "hadamard", "fft_inverse", "pinv"]
 M2L_NUM_STAGES = 7
 M2L_FORM_AUTO, M2L_FORM_BLAS, M2L_FORM_FFT = 0, 1, 2
@@ -159,7 +160,7 @@ class Plan:
         self.set(form=form, precision=precision)
 
     def set(self, form=None, precision=None, accumulate=None, output=None, target_tol=None, fft_grid=None,
-            timing=None):
+            timing=None, tc_group=None):
         if form is not None:
             _check(m2l_set_option(self.handle, M2L_OPT_FORM, FORMS[form]))
         if precision is not None:
@@ -175,6 +176,8 @@ class Plan:
             _check(m2l_set_option(self.handle, M2L_OPT_FFT_GRID, fft_grid))
         if timing is not None:
             _check(m2l_set_option(self.handle, M2L_OPT_TIMING, int(bool(timing))))
+        if tc_group is not None:
+            _check(m2l_set_option(self.handle, M2L_OPT_TC_GROUP, int(tc_group)))
         return self
 
     def stage_times(self):
