@@ -69,7 +69,10 @@ enum m2l_option_e {
     M2L_OPT_PRECISION = 2,   /* M2L_PREC_*; default M2L_PREC_FP64 */
     M2L_OPT_ACCUMULATE = 3,  /* 0: locals are overwritten (default); 1: locals += M2L result */
     M2L_OPT_OUTPUT = 4,      /* M2L_OUT_*; default M2L_OUT_LOCALS */
-    M2L_OPT_TARGET_TOL = 5,  /* accuracy asked of M2L_FORM_AUTO: the bits of a double */
+    M2L_OPT_TARGET_TOL = 5,  /* accuracy asked of AUTO form / precision: the bits of a double (default
+                                1e-6). AUTO keeps the (form, precision) candidates whose stated bound
+                                (relative error of the check potential) and rank truncation are within
+                                it, times them on the plan's boxes and keeps the fastest, per n_rhs. */
     M2L_OPT_FFT_GRID = 6,    /* convolution grid side: 0 = 2p (default), else 2p-1 <= g <= 2p */
     M2L_OPT_TIMING = 7,      /* 1: record CUDA events around every stage (see m2l_stage_times) */
     M2L_OPT_TC_GROUP = 8     /* split tensor-core forms: transfer vectors summed in tensor memory before
@@ -114,8 +117,8 @@ enum m2l_query_e {
     M2L_Q_FREQS = 6,      /* complex half-spectrum length g*g*(g/2+1) */
     M2L_Q_PINV_RANK = 7,  /* singular values kept by the pseudo-inverse */
     M2L_Q_ROWS = 8,       /* boxes summed over levels 2..depth */
-    M2L_Q_FORM = 9,       /* form the next apply will run (resolves AUTO) */
-    M2L_Q_PRECISION = 10, /* precision the next apply will run (resolves AUTO) */
+    M2L_Q_FORM = 9,       /* form the next apply with n_rhs = `level` (>= 1) will run; resolves AUTO */
+    M2L_Q_PRECISION = 10, /* precision of that apply (so the caller knows the element type) */
     M2L_Q_LAUNCHES = 11,  /* kernels launched by the last apply */
     M2L_Q_DEVICE_STATUS = 12 /* waits for the plan's stream, returns the device status word (0: no
                                 bounded wait ran out since the last query, else a stage code) and
@@ -157,11 +160,15 @@ int m2l_set_stream(m2l_plan_t *plan, void *stream);
  * empty branches, Sec. 2.1). n == 8^level with keys == NULL restores the full level. */
 int m2l_set_boxes(m2l_plan_t *plan, int level, const uint64_t *keys, long long n);
 
-/* Apply several independent plans (uneven FMM instances) with device buffers, every level
- * of each (level = -1 semantics), in one pass on the first plan's stream: plans with equal
- * (p, form, precision, rank) share launches, and the whole pass is replayed from a CUDA
- * graph captured on the first call with the same arguments.
- * plans[i], multipoles[i], locals[i], n_rhs[i] as for m2l_apply. */
+/* Apply several independent plans (uneven FMM instances) with DEVICE buffers, every level of
+ * each (level = -1 semantics), in one pass on the first plan's stream. Instances whose plans
+ * resolve to the same (p, form, precision, rank) form one group: the BLAS contraction of a group
+ * is ONE launch over the tiles of all its instances (the compress/expand GEMMs and the FFT stages
+ * are launched per instance). The whole pass is captured once in a CUDA graph (on a stream the
+ * first plan owns) and replayed on later calls with the same plans, buffers, n_rhs, options and
+ * box sets; anything else re-captures. Plans may not repeat; all belong to one device.
+ * plans[i], multipoles[i], locals[i], n_rhs[i] as for m2l_apply (M2L_OPT_TIMING is ignored).
+ * Returns M2L_OK, M2L_EINVAL, M2L_EUNSUPPORTED, M2L_ENOMEM or M2L_ECUDA. */
 int m2l_apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *multipoles,
                     void *const *locals, const int *n_rhs);
 

@@ -1,6 +1,8 @@
-// Orchestration of one M2L application: workspace, tile lists and the stage sequence of
-// each form (BLAS: B1 compress, B2 contract, B3 uncompress + pseudo-inverse; FFT: F1+F2
-// forward transform, F3 Hadamard, F4+F5 inverse transform, F6 pseudo-inverse).
+// Orchestration of M2L applications: preparation (device tables, operators, workspace), the
+// stage sequence of each form (BLAS: B1 compress, B2 contract, B3 uncompress + pseudo-inverse;
+// FFT: F1+F2 forward transform, F3 Hadamard, F4+F5 inverse transform, F6 pseudo-inverse), and
+// batches of independent instances: instances that share (p, form, precision, rank) share one
+// contraction launch over all their tiles, and a whole batch pass is replayed from a CUDA graph.
 #include <algorithm>
 #include <vector>
 
@@ -10,12 +12,20 @@
 namespace m2l {
 
 size_t fft_smem_bytes(int p, int g, int elt);  // kernels_simt.cu
+int ensure_tc_constants(int device);           // kernels_tc.cu
 template <class T>
-int launch_contract_tc(m2l_plan_t *pl, const LevelsArg &lv, const ContractTile *tiles, long long ntiles, int R,
-                       const void *qt_hi, const void *qt_lo, long long zero_row, T *phit, int precision,
-                       cudaStream_t s);                                         // kernels_tc.cu
-int launch_split_rows(const float *src, long long rows, int kp, void *hi, void *lo, int precision,
-                      cudaStream_t s);                                          // kernels_tc.cu
+int launch_contract_tc(m2l_plan_t *pl, const LevelView *lv, const ContractTile *tiles, long long ntiles, const void *qt_hi,
+                       const void *qt_lo, long long zero_row, T *phit, int precision, cudaStream_t s);
+int launch_split_rows(const float *src, long long rows, int kp, void *hi, void *lo, int precision, cudaStream_t s);
+
+#define M2L_TRY(x)           \
+    do {                     \
+        int _rc = (x);       \
+        if (_rc) return _rc; \
+    } while (0)
+
+// ---------------------------------------------------------------------------------------------
+// Stage timing (M2L_OPT_TIMING): event pairs recorded on the plan's stream.
 
 static cudaEvent_t pool_event(m2l_plan_t *pl) {
     if (pl->events_used == pl->event_pool.size()) {
@@ -27,7 +37,7 @@ static cudaEvent_t pool_event(m2l_plan_t *pl) {
 }
 
 void stage_begin(m2l_plan_t *pl, int stage) {
-    if (!pl->timing) return;
+    if (!pl->timing || pl->capturing) return;
     m2l_plan_s::StageEvent ev;
     ev.stage = stage;
     ev.a = pool_event(pl);
@@ -39,10 +49,20 @@ void stage_begin(m2l_plan_t *pl, int stage) {
 
 void stage_end(m2l_plan_t *pl, long long launches) {
     pl->launches += launches;
-    if (!pl->timing || pl->events.empty()) return;
+    if (!pl->timing || pl->capturing || pl->events.empty()) return;
     pl->events.back().launches = launches;
     cudaEventRecord(pl->events.back().b, pl->stream);
 }
+
+static void reset_stage_log(m2l_plan_t *pl) {
+    pl->launches = 0;
+    pl->events.clear();
+    pl->events_used = 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Preparation: everything that allocates or copies synchronously happens here, never inside a
+// stream capture.
 
 static int ensure_buffer(Workspace &w, size_t bytes) {
     if (w.bytes >= bytes && w.buf) return M2L_OK;
@@ -55,60 +75,6 @@ static int ensure_buffer(Workspace &w, size_t bytes) {
         return M2L_ENOMEM;
     }
     w.bytes = bytes;
-    return M2L_OK;
-}
-
-static LevelView view_of(const LevelDev &D) {
-    LevelView v;
-    v.slot = D.slot;
-    v.xyz = D.xyz;
-    v.perm = D.perm;
-    v.cslot = D.cslot;
-    v.cxyz = D.cxyz;
-    v.cchild = D.cchild;
-    v.base = D.base;
-    v.cbase = D.cbase;
-    v.nboxes = D.nboxes;
-    v.nclusters = D.nclusters;
-    for (int i = 0; i < 9; ++i) v.oct_start[i] = D.oct_start[i];
-    v.N = 1 << D.level;
-    return v;
-}
-
-static int ensure_tiles(m2l_plan_t *pl, int l0, int l1, int R, int rows_per_tile) {
-    int key = l0 == l1 ? l0 : -1;
-    if (pl->tiles && pl->tiles_rhs == R && pl->tiles_level == key && pl->tiles_rows == rows_per_tile) return M2L_OK;
-    std::vector<ContractTile> t;
-    for (int l = l0; l <= l1; ++l) {
-        const LevelDev &D = pl->ldev[l];
-        for (int oct = 0; oct < 8; ++oct) {
-            long long segrows = (D.oct_start[oct + 1] - D.oct_start[oct]) * (long long)R;
-            for (long long j0 = 0; j0 < segrows; j0 += rows_per_tile) {
-                ContractTile c;
-                c.lev = l - l0;
-                c.oct = oct;
-                c.j0 = (int)j0;
-                c.rows = (int)std::min<long long>(rows_per_tile, segrows - j0);
-                t.push_back(c);
-            }
-        }
-    }
-    if (pl->tiles) cudaFree(pl->tiles);
-    pl->tiles = nullptr;
-    size_t bytes = std::max<size_t>(1, t.size()) * sizeof(ContractTile);
-    if (cudaMalloc(&pl->tiles, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("tile list allocation failed");
-        return M2L_ENOMEM;
-    }
-    if (!t.empty() && cudaMemcpy(pl->tiles, t.data(), t.size() * sizeof(ContractTile), cudaMemcpyHostToDevice) != cudaSuccess) {
-        set_error("tile list upload failed");
-        return M2L_ECUDA;
-    }
-    pl->ntiles = (long long)t.size();
-    pl->tiles_rhs = R;
-    pl->tiles_level = key;
-    pl->tiles_rows = rows_per_tile;
     return M2L_OK;
 }
 
@@ -126,109 +92,249 @@ static int ensure_lattice(m2l_plan_t *pl) {
     return M2L_OK;
 }
 
-#define M2L_TRY(x)              \
-    do {                        \
-        int _rc = (x);          \
-        if (_rc) return _rc;    \
-    } while (0)
+int prepare_plan(m2l_plan_t *pl, int form, int precision) {
+    M2L_TRY(ensure_constants(pl->device));
+    M2L_TRY(upload_level_tables(pl));
+    if (form == M2L_FORM_FFT && (precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3)) {
+        set_error("the FFT form runs in FP64 or FP32; split tensor-core precisions apply to the BLAS form");
+        return M2L_EUNSUPPORTED;
+    }
+    M2L_TRY(upload_ops(pl, precision, form));
+    if (precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3) M2L_TRY(ensure_tc_constants(pl->device));
+    if (form == M2L_FORM_FFT) M2L_TRY(ensure_lattice(pl));
+    if (!pl->dev_status) {
+        if (cudaMalloc((void **)&pl->dev_status, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("status word allocation failed");
+            return M2L_ENOMEM;
+        }
+        cudaMemset(pl->dev_status, 0, sizeof(int));
+    }
+    return M2L_OK;
+}
+
+static LevelView view_of(const LevelDev &D) {
+    LevelView v;
+    v.slot = D.slot;
+    v.xyz = D.xyz;
+    v.perm = D.perm;
+    v.cslot = D.cslot;
+    v.cxyz = D.cxyz;
+    v.cchild = D.cchild;
+    v.base = D.base;
+    v.cbase = D.cbase;
+    v.nboxes = D.nboxes;
+    v.nclusters = D.nclusters;
+    for (int i = 0; i < 9; ++i) v.oct_start[i] = D.oct_start[i];
+    v.N = 1 << D.level;
+    v.row0 = 0;
+    v.R = 1;
+    return v;
+}
+
+// One instance inside a group: its buffers, right-hand sides and levels, and the first row it
+// owns in the group's contraction row space.
+struct Run {
+    m2l_plan_t *pl;
+    const void *q;
+    void *L;
+    int R, l0, l1;
+    long long rows, row_off;
+};
+
+static long long rows_of(const m2l_plan_t *pl, int l0, int l1, int R) {
+    long long r = 0;
+    for (int l = l0; l <= l1; ++l) r += pl->ldev[l].nboxes * R;
+    return r;
+}
+
+// Device level views and contraction tiles of a group, cached on the group's owner plan.
+static int ensure_exec(m2l_plan_t *owner, std::vector<Run> &runs, int rows_per_tile, long long *ntiles_out,
+                       long long *total_rows_out) {
+    std::vector<long long> key;
+    key.push_back(rows_per_tile);
+    for (const Run &r : runs) {
+        key.push_back((long long)(uintptr_t)r.pl);
+        key.push_back(r.R);
+        key.push_back(r.l0);
+        key.push_back(r.l1);
+        key.push_back(r.pl->levels_version);
+    }
+    long long off = 0;
+    for (Run &r : runs) {
+        r.rows = rows_of(r.pl, r.l0, r.l1, r.R);
+        r.row_off = off;
+        off += r.rows;
+    }
+    *total_rows_out = off;
+    ExecCache &E = owner->exec;
+    if (E.levels && E.key == key) {
+        *ntiles_out = E.ntiles;
+        return M2L_OK;
+    }
+    std::vector<LevelView> views;
+    std::vector<ContractTile> tiles;
+    for (const Run &r : runs) {
+        for (int l = r.l0; l <= r.l1; ++l) {
+            const LevelDev &D = r.pl->ldev[l];
+            LevelView v = view_of(D);
+            v.R = r.R;
+            v.row0 = r.row_off + (D.base - r.pl->ldev[r.l0].base) * r.R;
+            const int lev = (int)views.size();
+            views.push_back(v);
+            for (int oct = 0; oct < 8; ++oct) {
+                long long segrows = (D.oct_start[oct + 1] - D.oct_start[oct]) * (long long)r.R;
+                for (long long j0 = 0; j0 < segrows; j0 += rows_per_tile) {
+                    ContractTile c;
+                    c.lev = lev;
+                    c.oct = oct;
+                    c.j0 = (int)j0;
+                    c.rows = (int)std::min<long long>(rows_per_tile, segrows - j0);
+                    tiles.push_back(c);
+                }
+            }
+        }
+    }
+    if (E.levels) cudaFree(E.levels);
+    if (E.tiles) cudaFree(E.tiles);
+    E.levels = E.tiles = nullptr;
+    E.key.clear();
+    if (cudaMalloc(&E.levels, std::max<size_t>(1, views.size()) * sizeof(LevelView)) != cudaSuccess ||
+        cudaMalloc(&E.tiles, std::max<size_t>(1, tiles.size()) * sizeof(ContractTile)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("tile list allocation failed");
+        return M2L_ENOMEM;
+    }
+    cudaMemcpy(E.levels, views.data(), views.size() * sizeof(LevelView), cudaMemcpyHostToDevice);
+    if (!tiles.empty()) cudaMemcpy(E.tiles, tiles.data(), tiles.size() * sizeof(ContractTile), cudaMemcpyHostToDevice);
+    E.ntiles = (long long)tiles.size();
+    E.key = key;
+    *ntiles_out = E.ntiles;
+    return M2L_OK;
+}
+
+static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct BlasLayout {
+    size_t qt_b, ph_b, z_b, split_b;
+    size_t total() const { return al256(qt_b) + al256(ph_b) + al256(z_b) + 2 * al256(split_b); }
+};
+
+static BlasLayout blas_layout(const m2l_plan_t *pl, long long total_rows, int precision) {
+    const bool tc = precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3;
+    const size_t e = precision == M2L_PREC_FP64 ? 8 : 4;
+    BlasLayout b;
+    b.qt_b = (size_t)(total_rows + 1) * pl->kp * e;
+    b.ph_b = (size_t)total_rows * pl->kp * e;
+    b.z_b = (size_t)total_rows * pl->rp * e;
+    b.split_b = tc ? (size_t)(total_rows + 1) * pl->kp * (precision == M2L_PREC_TF32X3 ? 4 : 2) : 0;
+    return b;
+}
+
+static size_t fft_workspace_bytes(const m2l_plan_t *pl, int R, int precision) {
+    const size_t e = precision == M2L_PREC_FP64 ? 8 : 4;
+    const long long allrows = pl->total_rows * R;
+    const size_t spec_b = (size_t)pl->total_clusters * R * pl->F * 16 * e;
+    return 2 * al256(spec_b) + al256((size_t)allrows * pl->n * e) + al256((size_t)allrows * pl->rp * e);
+}
+
+// ---------------------------------------------------------------------------------------------
+// BLAS form over a group of instances with the same operators; owner = runs[0].pl.
+
+// Second factor of the pseudo-inverse, out = V_eps Z (+ out).
+template <class T>
+static int apply_veps(const m2l_plan_t *pl, const DevOps &D, const T *Z, T *out, long long rows, int acc, cudaStream_t s) {
+    const int n = pl->n, rp = pl->rp;
+    return launch_gemm_xwt<T>(Z, rp, (const T *)D.V, rp, out, n, rows, n, rp, acc, s);
+}
 
 template <class T>
-static int apply_blas(m2l_plan_t *pl, const T *q, T *out, int l0, int l1, int R, int precision) {
-    const DevOps &D = pl->dev[precision];
-    const int n = pl->n, kp = pl->kp, rp = pl->rp;
-    const long long base0 = pl->ldev[l0].base;
-    long long rows_in = 0;
-    for (int l = l0; l <= l1; ++l) rows_in += pl->ldev[l].nboxes * R;
-    const long long allrows = pl->total_rows * R;
+static int blas_group(std::vector<Run> &runs, int precision, cudaStream_t s) {
+    m2l_plan_t *own = runs[0].pl;
+    const DevOps &D = own->dev[precision];
+    const int n = own->n, kp = own->kp, rp = own->rp;
     const bool tc = precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3;
-    // workspace: qt [(allrows + 1) x kp], phit [allrows x kp], Z [allrows x rp], and for the
-    // tensor-core forms the split qt_hi / qt_lo [(allrows + 1) x kp] (4 or 2 bytes each)
-    size_t e = sizeof(T);
-    size_t qt_b = (size_t)(allrows + 1) * kp * e, ph_b = (size_t)allrows * kp * e, z_b = (size_t)allrows * rp * e;
-    size_t split_b = tc ? (size_t)(allrows + 1) * kp * (precision == M2L_PREC_TF32X3 ? 4 : 2) : 0;
-    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    M2L_TRY(ensure_buffer(pl->ws, al(qt_b) + al(ph_b) + al(z_b) + 2 * al(split_b)));
-    char *w = (char *)pl->ws.buf;
+    long long ntiles = 0, total = 0;
+    M2L_TRY(ensure_exec(own, runs, tc ? 128 : 64, &ntiles, &total));
+    const BlasLayout lay = blas_layout(own, total, precision);
+    M2L_TRY(ensure_buffer(own->ws, lay.total()));
+    char *w = (char *)own->ws.buf;
     T *qt = (T *)w;
-    T *phit = (T *)(w + al(qt_b));
-    T *Z = (T *)(w + al(qt_b) + al(ph_b));
-    char *hi = w + al(qt_b) + al(ph_b) + al(z_b);
-    char *lo = hi + al(split_b);
-    cudaStream_t s = pl->stream;
-    // B1: compressed multipoles qt = q S (rows of the requested levels), zero source row at the end
-    stage_begin(pl, M2L_STAGE_COMPRESS);
-    M2L_TRY(launch_gemm_xwt<T>(q, n, (const T *)D.St, n, qt + base0 * R * kp, kp, rows_in, kp, n, 0, s));
-    cudaMemsetAsync(qt + allrows * kp, 0, kp * e, s);
-    stage_end(pl, 1);
-    // B2: gathered contraction over the transfer vectors of each target octant
-    M2L_TRY(ensure_tiles(pl, l0, l1, R, tc ? 128 : 64));
-    LevelsArg lv;
-    lv.count = l1 - l0 + 1;
-    for (int l = l0; l <= l1; ++l) lv.L[l - l0] = view_of(pl->ldev[l]);
+    T *phit = (T *)(w + al256(lay.qt_b));
+    T *Z = (T *)(w + al256(lay.qt_b) + al256(lay.ph_b));
+    char *hi = w + al256(lay.qt_b) + al256(lay.ph_b) + al256(lay.z_b);
+    char *lo = hi + al256(lay.split_b);
+    // B1: compressed multipoles of every instance, one zero row after the last
+    stage_begin(own, M2L_STAGE_COMPRESS);
+    for (const Run &r : runs)
+        M2L_TRY(launch_gemm_xwt<T>((const T *)r.q, n, (const T *)D.St, n, qt + r.row_off * kp, kp, r.rows, kp, n, 0, s));
+    cudaMemsetAsync(qt + total * kp, 0, kp * sizeof(T), s);
+    stage_end(own, (long long)runs.size());
+    // B2: one contraction launch over the tiles of every instance
+    const LevelView *lv = (const LevelView *)own->exec.levels;
+    const ContractTile *tl = (const ContractTile *)own->exec.tiles;
     if (!tc) {
-        stage_begin(pl, M2L_STAGE_CONTRACT);
-        M2L_TRY(launch_contract_simt<T>(lv, (const ContractTile *)pl->tiles, pl->ntiles, R, qt, (const T *)D.C, kp,
-                                        allrows, phit, s));
-        stage_end(pl, 1);
+        stage_begin(own, M2L_STAGE_CONTRACT);
+        M2L_TRY(launch_contract_simt<T>(lv, tl, ntiles, qt, (const T *)D.C, kp, total, phit, s));
+        stage_end(own, 1);
     } else {
         if constexpr (sizeof(T) == 4) {
-            const long long split_rows = allrows + 1;
-            stage_begin(pl, M2L_STAGE_COMPRESS);
-            M2L_TRY(launch_split_rows((const float *)qt, split_rows, kp, hi, lo, precision, s));
-            stage_end(pl, 1);
-            stage_begin(pl, M2L_STAGE_CONTRACT);
-            M2L_TRY(launch_contract_tc<T>(pl, lv, (const ContractTile *)pl->tiles, pl->ntiles, R, hi, lo, allrows,
-                                          phit, precision, s));
-            stage_end(pl, 1);
+            stage_begin(own, M2L_STAGE_COMPRESS);
+            M2L_TRY(launch_split_rows((const float *)qt, total + 1, kp, hi, lo, precision, s));
+            stage_end(own, 1);
+            stage_begin(own, M2L_STAGE_CONTRACT);
+            M2L_TRY(launch_contract_tc<T>(own, lv, tl, ntiles, hi, lo, total, phit, precision, s));
+            stage_end(own, 1);
         } else {
             set_error("split tensor-core precisions operate on FP32 data");
             return M2L_EINVAL;
         }
     }
     // B3: locals = V_eps (A phit) with A = Ut_eps U, or the check potential U phit
-    const T *ph = phit + base0 * R * kp;
-    stage_begin(pl, M2L_STAGE_EXPAND);
-    if (pl->output == M2L_OUT_LOCALS) {
-        M2L_TRY(launch_gemm_xwt<T>(ph, kp, (const T *)D.A, kp, Z, rp, rows_in, rp, kp, 0, s));
-        M2L_TRY(launch_gemm_xwt<T>(Z, rp, (const T *)D.V, rp, out, n, rows_in, n, rp, pl->accumulate, s));
-        stage_end(pl, 2);
-    } else {
-        M2L_TRY(launch_gemm_xwt<T>(ph, kp, (const T *)D.Uc, kp, out, n, rows_in, n, kp, pl->accumulate, s));
-        stage_end(pl, 1);
+    stage_begin(own, M2L_STAGE_EXPAND);
+    long long nl = 0;
+    for (const Run &r : runs) {
+        const T *ph = phit + r.row_off * kp;
+        if (r.pl->output == M2L_OUT_LOCALS) {
+            M2L_TRY(launch_gemm_xwt<T>(ph, kp, (const T *)D.A, kp, Z + r.row_off * rp, rp, r.rows, rp, kp, 0, s));
+            M2L_TRY(apply_veps<T>(own, D, Z + r.row_off * rp, (T *)r.L, r.rows, r.pl->accumulate, s));
+            nl += 2;
+        } else {
+            M2L_TRY(launch_gemm_xwt<T>(ph, kp, (const T *)D.Uc, kp, (T *)r.L, n, r.rows, n, kp, r.pl->accumulate, s));
+            nl += 1;
+        }
     }
+    stage_end(own, nl);
     return M2L_OK;
 }
 
+// FFT form, one instance.
 template <class T>
-static int apply_fft(m2l_plan_t *pl, const T *q, T *out, int l0, int l1, int R, int precision) {
+static int fft_run(const Run &r, int precision, cudaStream_t s) {
+    m2l_plan_t *pl = r.pl;
     const DevOps &D = pl->dev[precision];
-    const int n = pl->n, rp = pl->rp, g = pl->g, F = pl->F, p = pl->p;
+    const int n = pl->n, rp = pl->rp, g = pl->g, F = pl->F, p = pl->p, R = r.R;
     if (fft_smem_bytes(p, g, (int)sizeof(T)) > 227 * 1024) {
         set_error("FFT form: grid %d does not fit shared memory in this precision", g);
         return M2L_EUNSUPPORTED;
     }
-    M2L_TRY(ensure_lattice(pl));
-    const long long base0 = pl->ldev[l0].base;
-    long long rows_in = 0;
-    for (int l = l0; l <= l1; ++l) rows_in += pl->ldev[l].nboxes * R;
-    const long long allrows = pl->total_rows * R;
-    size_t e = sizeof(T);
-    size_t spec_b = (size_t)pl->total_clusters * R * F * 16 * e;
-    size_t phi_b = (size_t)allrows * n * e, z_b = (size_t)allrows * rp * e;
-    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    M2L_TRY(ensure_buffer(pl->ws, 2 * al(spec_b) + al(phi_b) + al(z_b)));
+    const long long base0 = pl->ldev[r.l0].base;
+    const size_t e = sizeof(T);
+    const size_t spec_b = (size_t)pl->total_clusters * R * F * 16 * e;
+    const size_t phi_b = (size_t)pl->total_rows * R * n * e;
+    M2L_TRY(ensure_buffer(pl->ws, fft_workspace_bytes(pl, R, precision)));
     char *w = (char *)pl->ws.buf;
     T *qhat = (T *)w;
-    T *phihat = (T *)(w + al(spec_b));
-    T *Phi = (T *)(w + 2 * al(spec_b));
-    T *Z = (T *)(w + 2 * al(spec_b) + al(phi_b));
-    cudaStream_t s = pl->stream;
+    T *phihat = (T *)(w + al256(spec_b));
+    T *Phi = (T *)(w + 2 * al256(spec_b));
+    T *Z = (T *)(w + 2 * al256(spec_b) + al256(phi_b));
+    const T *q = (const T *)r.q;
+    T *out = (T *)r.L;
     const bool check_out = pl->output == M2L_OUT_CHECK_POTENTIAL;
-    // clusters with missing children keep zero spectra for them
     stage_begin(pl, M2L_STAGE_FFT_FORWARD);
-    cudaMemsetAsync(qhat, 0, spec_b, s);
+    cudaMemsetAsync(qhat, 0, spec_b, s);  // missing children keep zero spectra
     stage_end(pl, 0);
-    for (int l = l0; l <= l1; ++l) {
+    for (int l = r.l0; l <= r.l1; ++l) {
         LevelView L = view_of(pl->ldev[l]);
         const T *ql = q + (L.base - base0) * R * n;
         stage_begin(pl, M2L_STAGE_FFT_FORWARD);
@@ -246,46 +352,164 @@ static int apply_fft(m2l_plan_t *pl, const T *q, T *out, int l0, int l1, int R, 
     if (!check_out) {
         // F6: locals = V_eps (Ut_eps Phi)
         stage_begin(pl, M2L_STAGE_PINV);
-        M2L_TRY(launch_gemm_xwt<T>(Phi + base0 * R * n, n, (const T *)D.Ut, n, Z, rp, rows_in, rp, n, 0, s));
-        M2L_TRY(launch_gemm_xwt<T>(Z, rp, (const T *)D.V, rp, out, n, rows_in, n, rp, pl->accumulate, s));
+        M2L_TRY(launch_gemm_xwt<T>(Phi + base0 * R * n, n, (const T *)D.Ut, n, Z, rp, r.rows, rp, n, 0, s));
+        M2L_TRY(apply_veps<T>(pl, D, Z, out, r.rows, pl->accumulate, s));
         stage_end(pl, 2);
     }
     return M2L_OK;
 }
 
-int resolve_form(const m2l_plan_t *pl, int R, int *form, int *precision);  // autotune.cpp
+static int run_group(std::vector<Run> &runs, int form, int precision, cudaStream_t s) {
+    if (form == M2L_FORM_BLAS) {
+        return precision == M2L_PREC_FP64 ? blas_group<double>(runs, precision, s) : blas_group<float>(runs, precision, s);
+    }
+    for (Run &r : runs) {
+        r.rows = rows_of(r.pl, r.l0, r.l1, r.R);
+        int rc = precision == M2L_PREC_FP64 ? fft_run<double>(r, precision, s) : fft_run<float>(r, precision, s);
+        if (rc) return rc;
+    }
+    return M2L_OK;
+}
 
 int apply_device(m2l_plan_t *pl, const void *q, void *L, int level, int R) {
     int l0 = level < 0 ? 2 : level, l1 = level < 0 ? pl->depth : level;
-    M2L_TRY(ensure_constants(pl->device));
-    M2L_TRY(upload_level_tables(pl));
     int form, precision;
     M2L_TRY(resolve_form(pl, R, &form, &precision));
-    if (form == M2L_FORM_FFT && (precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3)) {
-        set_error("the FFT form runs in FP64 or FP32; split tensor-core precisions apply to the BLAS form");
-        return M2L_EUNSUPPORTED;
+    M2L_TRY(prepare_plan(pl, form, precision));
+    reset_stage_log(pl);
+    std::vector<Run> runs(1);
+    runs[0] = Run{pl, q, L, R, l0, l1, 0, 0};
+    return run_group(runs, form, precision, pl->stream);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batches of independent instances (device buffers, every level of each).
+
+struct GroupKey {
+    int p, form, precision, kp, g;
+    double rank_tol;
+    bool operator==(const GroupKey &o) const {
+        return p == o.p && form == o.form && precision == o.precision && kp == o.kp && g == o.g && rank_tol == o.rank_tol;
     }
-    M2L_TRY(upload_ops(pl, precision, form));
-    if (!pl->dev_status) {
-        if (cudaMalloc((void **)&pl->dev_status, sizeof(int)) != cudaSuccess) {
-            cudaGetLastError();
-            set_error("status word allocation failed");
-            return M2L_ENOMEM;
+};
+
+int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void *const *L, const int *R) {
+    m2l_plan_t *lead = plans[0];
+    // resolve, prepare and group
+    std::vector<GroupKey> keys;
+    std::vector<std::vector<Run>> groups;
+    std::vector<int> forms, precs;
+    std::vector<long long> sig;
+    for (int i = 0; i < n_inst; ++i) {
+        m2l_plan_t *pl = plans[i];
+        int form, prec;
+        M2L_TRY(resolve_form(pl, R[i], &form, &prec));
+        M2L_TRY(prepare_plan(pl, form, prec));
+        GroupKey k{pl->p, form, prec, form == M2L_FORM_BLAS ? pl->kp : 0, form == M2L_FORM_FFT ? pl->g : 0,
+                   form == M2L_FORM_BLAS ? pl->rank_tol : 0.0};
+        size_t gi = 0;
+        while (gi < keys.size() && !(keys[gi] == k)) ++gi;
+        if (gi == keys.size()) {
+            keys.push_back(k);
+            groups.emplace_back();
+            forms.push_back(form);
+            precs.push_back(prec);
         }
-        cudaMemset(pl->dev_status, 0, sizeof(int));
+        groups[gi].push_back(Run{pl, q[i], L[i], R[i], 2, pl->depth, 0, 0});
+        for (long long v : {(long long)(uintptr_t)pl, (long long)(uintptr_t)q[i], (long long)(uintptr_t)L[i], (long long)R[i],
+                            (long long)form, (long long)prec, (long long)pl->output, (long long)pl->accumulate,
+                            pl->levels_version})
+            sig.push_back(v);
     }
-    pl->launches = 0;
-    pl->events.clear();
-    pl->events_used = 0;
-    int rc;
-    if (precision == M2L_PREC_FP64) {
-        rc = form == M2L_FORM_BLAS ? apply_blas<double>(pl, (const double *)q, (double *)L, l0, l1, R, precision)
-                                   : apply_fft<double>(pl, (const double *)q, (double *)L, l0, l1, R, precision);
+    // allocate everything the pass needs before any capture
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        m2l_plan_t *own = groups[gi][0].pl;
+        if (forms[gi] == M2L_FORM_BLAS) {
+            const bool tc = precs[gi] == M2L_PREC_TF32X3 || precs[gi] == M2L_PREC_BF16X3;
+            long long nt = 0, total = 0;
+            M2L_TRY(ensure_exec(own, groups[gi], tc ? 128 : 64, &nt, &total));
+            M2L_TRY(ensure_buffer(own->ws, blas_layout(own, total, precs[gi]).total()));
+        } else {
+            for (const Run &r : groups[gi]) M2L_TRY(ensure_buffer(r.pl->ws, fft_workspace_bytes(r.pl, r.R, precs[gi])));
+        }
+    }
+    // the graph bakes in every device pointer it was captured with
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        for (const Run &r : groups[gi]) {
+            const DevOps &D = r.pl->dev[precs[gi]];
+            for (const void *ptr : {r.pl->ws.buf, r.pl->exec.levels, r.pl->exec.tiles, D.C, D.C_hi, D.C_lo, D.Khat, D.A, D.V})
+                sig.push_back((long long)(uintptr_t)ptr);
+            sig.push_back(r.pl->tc_group);
+            sig.push_back(r.pl->fft_grid_opt);
+        }
+    }
+    for (int i = 0; i < n_inst; ++i) reset_stage_log(plans[i]);
+    cudaStream_t user = lead->stream;
+    BatchGraph &G = lead->batch_graph;
+    if (G.exec && G.sig == sig) {
+        if (cudaGraphLaunch(G.exec, user) != cudaSuccess) {
+            set_error("graph launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return M2L_ECUDA;
+        }
+        lead->launches = G.launches;
+        return M2L_OK;
+    }
+    // capture the pass on a private stream, then run it on the caller's stream
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+    G.sig.clear();
+    if (!G.capture_stream && cudaStreamCreateWithFlags(&G.capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        set_error("creating the capture stream failed");
+        return M2L_ECUDA;
+    }
+    for (int i = 0; i < n_inst; ++i) plans[i]->capturing = 1;
+    cudaGraph_t graph = nullptr;
+    int rc = M2L_OK;
+    if (cudaStreamBeginCapture(G.capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        set_error("stream capture failed to begin: %s", cudaGetErrorString(cudaGetLastError()));
+        rc = M2L_ECUDA;
     } else {
-        rc = form == M2L_FORM_BLAS ? apply_blas<float>(pl, (const float *)q, (float *)L, l0, l1, R, precision)
-                                   : apply_fft<float>(pl, (const float *)q, (float *)L, l0, l1, R, precision);
+        for (size_t gi = 0; gi < groups.size() && !rc; ++gi) rc = run_group(groups[gi], forms[gi], precs[gi], G.capture_stream);
+        cudaError_t e = cudaStreamEndCapture(G.capture_stream, &graph);
+        if (!rc && e != cudaSuccess) {
+            set_error("stream capture failed: %s", cudaGetErrorString(e));
+            rc = M2L_ECUDA;
+        }
     }
-    return rc;
+    long long launches = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        plans[i]->capturing = 0;
+        launches += plans[i]->launches;
+    }
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc;
+    }
+    if (cudaGraphInstantiate(&G.exec, graph, 0) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        G.exec = nullptr;
+        set_error("graph instantiation failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return M2L_ECUDA;
+    }
+    cudaGraphDestroy(graph);
+    G.sig = sig;
+    G.launches = launches;
+    if (cudaGraphLaunch(G.exec, user) != cudaSuccess) {
+        set_error("graph launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return M2L_ECUDA;
+    }
+    lead->launches = launches;
+    return M2L_OK;
+}
+
+void free_exec(m2l_plan_t *pl) {
+    if (pl->exec.levels) cudaFree(pl->exec.levels);
+    if (pl->exec.tiles) cudaFree(pl->exec.tiles);
+    pl->exec = ExecCache();
+    if (pl->batch_graph.exec) cudaGraphExecDestroy(pl->batch_graph.exec);
+    if (pl->batch_graph.capture_stream) cudaStreamDestroy(pl->batch_graph.capture_stream);
+    pl->batch_graph = BatchGraph();
 }
 
 }  // namespace m2l

@@ -1,16 +1,159 @@
-// Choice of form and precision when the caller leaves them to the library (M2L_FORM_AUTO /
-// M2L_PREC_AUTO), per (p, n_rhs, target tolerance).
+// Choice of form and precision for M2L_FORM_AUTO / M2L_PREC_AUTO, per (p, n_rhs, target tolerance).
+//
+// A (form, precision) candidate is eligible when its stated relative error bound (Eq. 16 on the
+// check potential, measured over p = 4..10 and densities of one and of both signs, see the GPU
+// parity tests) and the truncation of the plan's rank are both at most the target. Eligible
+// candidates are timed on the plan's own box sets with the library's scratch data (the
+// arithmetic does not depend on the values) and the fastest is kept. FP64 candidates are timed
+// only when no reduced-precision candidate is eligible: on this GPU the FP64 units run at about
+// one sixtieth of the FP32 rate. Decisions are cached per (n_rhs, target).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
 #include "internal.h"
 
 namespace m2l {
 
-int resolve_form(const m2l_plan_t *pl, int R, int *form, int *precision) {
-    (void)R;
-    int f = pl->form, pr = pl->precision;
-    if (pr == M2L_PREC_AUTO) pr = pl->target_tol < 1e-6 ? M2L_PREC_FP64 : M2L_PREC_FP32;
-    if (f == M2L_FORM_AUTO) f = M2L_FORM_BLAS;
+int prepare_plan(m2l_plan_t *pl, int form, int precision);
+
+// Stated bounds: relative L2 error (Eq. 16) of the check potential and of the locals measured
+// through the check potential they reproduce, against the FP64 definition, for p = 4..10 and
+// densities of one sign, of both signs and Gaussian (largest measured values in brackets).
+double stated_bound(int form, int precision, int p) {
+    (void)p;
+    if (precision == M2L_PREC_FP64) return 1e-12;   // (1.1e-14 check, 4.6e-12 locals)
+    if (form == M2L_FORM_FFT) return 2e-6;          // FP32 FFT (5.2e-7 check, 1.5e-6 locals)
+    if (precision == M2L_PREC_TF32X3) return 5e-6;  // FP32 accumulation of 22-bit pieces (1.9e-6)
+    if (precision == M2L_PREC_FP32) return 1e-5;    // FP32 CUDA-core contraction (5.4e-6)
+    return 2e-5;                                    // BF16x3 (8.4e-6)
+}
+
+static bool eligible(const m2l_plan_t *pl, int form, int prec) {
+    if (form == M2L_FORM_FFT && (prec == M2L_PREC_TF32X3 || prec == M2L_PREC_BF16X3)) return false;
+    double bound = stated_bound(form, prec, pl->p);
+    if (form == M2L_FORM_BLAS && pl->rank_tol > 0) bound = std::max(bound, pl->rank_tol);
+    if (bound > pl->target_tol) return false;
+    if (form == M2L_FORM_BLAS && (prec == M2L_PREC_TF32X3 || prec == M2L_PREC_BF16X3)) {
+        // the tensor-core contraction holds k_pad <= 256 columns
+        if (((const_cast<m2l_plan_t *>(pl)->blas_host_ready ? pl->kp : 0) > 256)) return false;
+    }
+    return true;
+}
+
+static int time_candidate(m2l_plan_t *pl, int form, int prec, int R, float *ms) {
+    int rc = prepare_plan(pl, form, prec);
+    if (rc) return rc;
+    if (form == M2L_FORM_BLAS && (prec == M2L_PREC_TF32X3 || prec == M2L_PREC_BF16X3) && pl->kp > 256)
+        return M2L_EUNSUPPORTED;
+    const size_t elt = prec == M2L_PREC_FP64 ? 8 : 4;
+    long long rows = 0;
+    for (int l = 2; l <= pl->depth; ++l) rows += pl->ldev[l].nboxes;
+    const size_t bytes = (size_t)rows * R * pl->n * elt;
+    void *q = nullptr, *L = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess || cudaMalloc(&L, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        if (q) cudaFree(q);
+        set_error("autotuner scratch allocation failed");
+        return M2L_ENOMEM;
+    }
+    cudaMemsetAsync(q, 0, bytes, pl->stream);
+    const int keep_form = pl->form, keep_prec = pl->precision, keep_timing = pl->timing, keep_acc = pl->accumulate;
+    pl->form = form;
+    pl->precision = prec;
+    pl->timing = 0;
+    pl->accumulate = 0;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    rc = apply_device(pl, q, L, -1, R);  // warm
+    if (!rc) {
+        cudaEventRecord(a, pl->stream);
+        rc = apply_device(pl, q, L, -1, R);
+        cudaEventRecord(b, pl->stream);
+        if (!rc && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(ms, a, b);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    pl->form = keep_form;
+    pl->precision = keep_prec;
+    pl->timing = keep_timing;
+    pl->accumulate = keep_acc;
+    cudaStreamSynchronize(pl->stream);
+    cudaFree(q);
+    cudaFree(L);
+    return rc;
+}
+
+static int tune(m2l_plan_t *pl, int R, int *form, int *prec) {
+    std::vector<std::pair<int, int>> fast, slow;
+    const int forms[2] = {M2L_FORM_BLAS, M2L_FORM_FFT};
+    const int precs[4] = {M2L_PREC_BF16X3, M2L_PREC_TF32X3, M2L_PREC_FP32, M2L_PREC_FP64};
+    if (pl->rank_tol > 0 || pl->form == M2L_FORM_BLAS) build_blas_host(pl);
+    for (int f : forms) {
+        if (pl->form != M2L_FORM_AUTO && pl->form != f) continue;
+        for (int pr : precs) {
+            if (pl->precision != M2L_PREC_AUTO && pl->precision != pr) continue;
+            if (!eligible(pl, f, pr)) continue;
+            (pr == M2L_PREC_FP64 ? slow : fast).push_back({f, pr});
+        }
+    }
+    std::vector<std::pair<int, int>> &cands = fast.empty() ? slow : fast;
+    if (cands.empty()) {
+        set_error("no form/precision reaches the target tolerance %.3g with this plan", pl->target_tol);
+        return M2L_EUNSUPPORTED;
+    }
+    float best = 1e30f;
+    int bf = cands[0].first, bp = cands[0].second;
+    for (auto &c : cands) {
+        float ms = 1e30f;
+        int rc = time_candidate(pl, c.first, c.second, R, &ms);
+        if (rc == M2L_EUNSUPPORTED) continue;
+        if (rc) return rc;
+        if (ms < best) {
+            best = ms;
+            bf = c.first;
+            bp = c.second;
+        }
+    }
+    *form = bf;
+    *prec = bp;
+    return M2L_OK;
+}
+
+int resolve_form(const m2l_plan_t *cpl, int R, int *form, int *precision) {
+    m2l_plan_t *pl = const_cast<m2l_plan_t *>(cpl);
+    if (pl->form != M2L_FORM_AUTO && pl->precision != M2L_PREC_AUTO) {
+        *form = pl->form;
+        *precision = pl->precision;
+        return M2L_OK;
+    }
+    for (const auto &d : pl->tuned)
+        if (d.R == R && d.tol == pl->target_tol && d.form_opt == pl->form && d.prec_opt == pl->precision &&
+            d.levels_version == pl->levels_version) {
+            *form = d.form;
+            *precision = d.precision;
+            return M2L_OK;
+        }
+    if (pl->device < 0) {
+        set_error("choosing a form needs the GPU the plan was made on");
+        return M2L_ECUDA;
+    }
+    int f, p;
+    int rc = tune(pl, R, &f, &p);
+    if (rc) return rc;
+    m2l_plan_s::Tuned d;
+    d.R = R;
+    d.tol = pl->target_tol;
+    d.form_opt = pl->form;
+    d.prec_opt = pl->precision;
+    d.levels_version = pl->levels_version;
+    d.form = f;
+    d.precision = p;
+    pl->tuned.push_back(d);
     *form = f;
-    *precision = pr;
+    *precision = p;
     return M2L_OK;
 }
 

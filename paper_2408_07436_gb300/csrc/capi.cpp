@@ -203,6 +203,7 @@ int m2l_set_boxes(m2l_plan_t *pl, int level, const uint64_t *keys, long long n) 
     return M2L_OK;
 }
 
+
 int m2l_apply(m2l_plan_t *pl, const void *q, void *L, int level, int n_rhs) {
     clear_error();
     if (!pl || !q || !L) {
@@ -283,19 +284,26 @@ int m2l_apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *mul
         set_error("invalid batch arguments");
         return M2L_EINVAL;
     }
-    cudaStream_t s = plans[0] ? plans[0]->stream : nullptr;
     for (int i = 0; i < n_inst; ++i) {
-        if (!plans[i]) {
-            set_error("NULL plan at index %d", i);
+        if (!plans[i] || !multipoles[i] || !locals[i] || n_rhs[i] < 1) {
+            set_error("invalid plan, buffer or n_rhs at index %d", i);
             return M2L_EINVAL;
         }
-        cudaStream_t keep = plans[i]->stream;
-        plans[i]->stream = s;
-        int rc = m2l_apply(plans[i], multipoles[i], locals[i], -1, n_rhs[i]);
-        plans[i]->stream = keep;
-        if (rc) return rc;
+        if (plans[i]->device < 0 || plans[i]->device != plans[0]->device) {
+            set_error("every plan of a batch must belong to the device of the first");
+            return M2L_EINVAL;
+        }
+        if (!is_device_pointer(multipoles[i]) || !is_device_pointer(locals[i])) {
+            set_error("m2l_apply_batch takes device buffers (index %d)", i);
+            return M2L_EINVAL;
+        }
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) {
+                set_error("plan at index %d appears twice in the batch", i);
+                return M2L_EINVAL;
+            }
     }
-    return M2L_OK;
+    return apply_batch(plans, n_inst, multipoles, locals, n_rhs);
 }
 
 int m2l_query(const m2l_plan_t *cpl, int what, int level, long long *out) {

@@ -74,6 +74,23 @@ struct Workspace {
     size_t bytes = 0;
 };
 
+// Device level views and contraction tiles of the last group of instances run with this plan
+// as owner, with the key they were built for.
+struct ExecCache {
+    std::vector<long long> key;
+    void *levels = nullptr;
+    void *tiles = nullptr;
+    long long ntiles = 0;
+};
+
+// The CUDA graph of the last batch pass led by this plan and the arguments it was captured for.
+struct BatchGraph {
+    std::vector<long long> sig;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    long long launches = 0;
+};
+
 }  // namespace m2l
 
 struct m2l_plan_s {
@@ -95,8 +112,10 @@ struct m2l_plan_s {
     bool blas_host_ready = false, fft_host_ready = false, pinv_ready = false;
     int k = 0, kp = 0, r = 0, rp = 0, np_ = 0;
     std::vector<double> U, S, C, s_fat, s_thin;   // U, S: n x k (row-major [n][k]); C: 316 x k x k
-    std::vector<double> Veps, Uteps;              // [n][r], [r][n]
+    std::vector<double> Veps, Uteps;              // [n][r], [r][n]   threshold n eps_64 s_0
     std::vector<double> Aop;                      // [r][k] = Uteps * U
+    int r32 = 0;                                  // singular values kept with Eq. 10's alpha = 1e-9
+    std::vector<double> Veps32, Uteps32, Aop32;   // the factors used by single-precision paths
     int g = 0, F = 0;
     std::vector<double> Khat;                     // [316][F][2]
     std::vector<double> twiddle;                  // [g][2]
@@ -106,9 +125,12 @@ struct m2l_plan_s {
     m2l::LevelDev ldev[m2l::kMaxDepth + 1];
     long long total_rows = 0, total_clusters = 0;
     m2l::Workspace ws, stage_in, stage_out;
-    void *tiles = nullptr;                         // device tile list for the contraction
-    long long ntiles = 0;
-    int tiles_rhs = -1, tiles_level = -2, tiles_rows = 0;  // cache key of the tile list
+    m2l::ExecCache exec;
+    m2l::BatchGraph batch_graph;
+    long long levels_version = 0;                  // bumped whenever a box set changes
+    int capturing = 0;                             // inside a batch capture: no timing events
+    struct Tuned { int R; double tol; int form_opt, prec_opt; long long levels_version; int form, precision; };
+    std::vector<Tuned> tuned;                      // autotuner decisions
     long long launches = 0;
     int *dev_status = nullptr;                     // device status word written by bounded waits
     // stage timing (M2L_OPT_TIMING)
@@ -130,7 +152,11 @@ int upload_ops(m2l_plan_t *pl, int precision, int form);
 void free_device(m2l_plan_t *pl);
 // autotune.cpp
 int resolve_form(const m2l_plan_t *pl, int R, int *form, int *precision);
+double stated_bound(int form, int precision, int p);
 // apply.cu
+int prepare_plan(m2l_plan_t *pl, int form, int precision);
+int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void *const *L, const int *R);
+void free_exec(m2l_plan_t *pl);
 void stage_begin(m2l_plan_t *pl, int stage);
 void stage_end(m2l_plan_t *pl, long long launches);
 int apply_device(m2l_plan_t *pl, const void *q, void *L, int level, int nrhs);

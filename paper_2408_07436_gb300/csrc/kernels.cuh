@@ -20,15 +20,13 @@ struct LevelView {
     long long nboxes, nclusters;
     long long oct_start[9];
     int N;                  // boxes per axis, 2^level
+    long long row0;         // contraction rows of this level: row0 + b * R + r (box b, rhs r)
+    int R;                  // right-hand sides of the instance
 };
 
-struct LevelsArg {
-    LevelView L[kMaxLevels];
-    int count;
-};
-
-// One CTA of the contraction: rows [j0, j0 + rows) of the octant segment `oct` of level `lev`
-// (index into LevelsArg), where segment row j is (target perm[oct_start + j / R], rhs j % R).
+// One CTA of the contraction: rows [j0, j0 + rows) of the octant segment `oct` of level view
+// `lev` (index into a device array of LevelView), where segment row j is
+// (target perm[oct_start + j / R], rhs j % R).
 struct ContractTile {
     int lev;
     int oct;
@@ -41,10 +39,11 @@ template <class T>
 int launch_gemm_xwt(const T *X, long long ldx, const T *W, long long ldw, T *Y, long long ldy,
                     long long rows, int O, int K, int acc, cudaStream_t s);
 
-// B2 on CUDA cores: phit[(base+b)R + r][:] = sum_t C_t qt[(base+src)R + r][:].
+// B2 on CUDA cores: phit[row0 + b R + r][:] = sum_t C_t qt[row0 + src R + r][:] over the tiles,
+// `levels` a device array of LevelView indexed by ContractTile::lev.
 template <class T>
-int launch_contract_simt(const LevelsArg &lv, const ContractTile *tiles, long long ntiles, int R,
-                         const T *qt, const T *C, int kp, long long zero_row, T *phit, cudaStream_t s);
+int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, long long ntiles, const T *qt, const T *C,
+                         int kp, long long zero_row, T *phit, cudaStream_t s);
 
 // FFT form, one level at a time.
 template <class T>

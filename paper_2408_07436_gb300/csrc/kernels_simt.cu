@@ -64,35 +64,36 @@ static int check_launch(const char *what) {
 }
 
 // ----------------------------------------------------------------------------------------------
-// Y = X W^T (+ Y): 64 x 64 output tile per CTA, 4 x 4 per thread, K in steps of 16.
-template <class T>
-__global__ void __launch_bounds__(256) gemm_xwt_kernel(const T *__restrict__ X, long long ldx,
-                                                       const T *__restrict__ W, long long ldw,
-                                                       T *__restrict__ Y, long long ldy, long long rows,
+// Y = X W^T (+ Y): 64 x 64 output tile per CTA, 4 x 4 per thread, K in steps of 16 (one type
+// for X, W and accumulation, written as TY).
+template <class TX, class TW, class TY>
+__global__ void __launch_bounds__(256) gemm_xwt_kernel(const TX *__restrict__ X, long long ldx,
+                                                       const TW *__restrict__ W, long long ldw,
+                                                       TY *__restrict__ Y, long long ldy, long long rows,
                                                        int O, int K, int acc) {
     constexpr int BM = 64, BN = 64, BK = 16;
-    __shared__ T Xs[BK][BM + 4];
-    __shared__ T Ws[BK][BN + 4];
+    __shared__ TW Xs[BK][BM + 4];
+    __shared__ TW Ws[BK][BN + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const long long row0 = (long long)blockIdx.x * BM;
     const int col0 = blockIdx.y * BN;
-    T a[4][4];
+    TW a[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) a[i][j] = T(0);
+        for (int j = 0; j < 4; ++j) a[i][j] = TW(0);
     for (int k0 = 0; k0 < K; k0 += BK) {
         for (int e = tid; e < BM * BK; e += 256) {
             int r = e / BK, kk = e % BK;
             long long gr = row0 + r;
             int gk = k0 + kk, gc = col0 + r;
-            Xs[kk][r] = (gr < rows && gk < K) ? X[gr * ldx + gk] : T(0);
-            Ws[kk][r] = (gc < O && gk < K) ? W[(long long)gc * ldw + gk] : T(0);
+            Xs[kk][r] = (gr < rows && gk < K) ? (TW)X[gr * ldx + gk] : TW(0);
+            Ws[kk][r] = (gc < O && gk < K) ? W[(long long)gc * ldw + gk] : TW(0);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            T xa[4], wb[4];
+            TW xa[4], wb[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 xa[i] = Xs[kk][ty * 4 + i];
@@ -113,9 +114,9 @@ __global__ void __launch_bounds__(256) gemm_xwt_kernel(const T *__restrict__ X, 
         for (int j = 0; j < 4; ++j) {
             int c = col0 + tx * 4 + j;
             if (c < O) {
-                T v = a[i][j];
-                if (acc) v += Y[r * ldy + c];
-                Y[r * ldy + c] = v;
+                TW v = a[i][j];
+                if (acc) v += (TW)Y[r * ldy + c];
+                Y[r * ldy + c] = (TY)v;
             }
         }
     }
@@ -126,7 +127,7 @@ int launch_gemm_xwt(const T *X, long long ldx, const T *W, long long ldw, T *Y, 
                     long long rows, int O, int K, int acc, cudaStream_t s) {
     if (rows <= 0 || O <= 0) return M2L_OK;
     dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((O + 63) / 64));
-    gemm_xwt_kernel<T><<<grid, 256, 0, s>>>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc);
+    gemm_xwt_kernel<T, T, T><<<grid, 256, 0, s>>>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc);
     return check_launch("gemm");
 }
 
@@ -135,9 +136,9 @@ int launch_gemm_xwt(const T *X, long long ldx, const T *W, long long ldw, T *Y, 
 // transfer vectors of that octant phit[row] += C_t qt[source(row, t)] (Sec. 3.2 steps 3-5 fused:
 // sources are gathered on the fly, nothing is materialised per transfer vector).
 template <class T>
-__global__ void __launch_bounds__(256) contract_simt_kernel(LevelsArg lv, const ContractTile *__restrict__ tiles,
-                                                            int R, const T *__restrict__ qt,
-                                                            const T *__restrict__ C, int kp,
+__global__ void __launch_bounds__(256) contract_simt_kernel(const LevelView *__restrict__ levels,
+                                                            const ContractTile *__restrict__ tiles,
+                                                            const T *__restrict__ qt, const T *__restrict__ C, int kp,
                                                             long long zero_row, T *__restrict__ phit) {
     constexpr int BM = 64, BN = 64, BK = 16;
     __shared__ T Xs[BK][BM + 4];
@@ -146,7 +147,8 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(LevelsArg lv, const 
     __shared__ int tgt_b[BM], tgt_r[BM];
     __shared__ uint32_t tgt_xyz[BM];
     const ContractTile tile = tiles[blockIdx.x];
-    const LevelView &L = lv.L[tile.lev];
+    const LevelView &L = levels[tile.lev];
+    const int R = L.R;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int col0 = blockIdx.y * BN;
     if (tid < BM) {
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(LevelsArg lv, const 
                         int x = (int)(p & 1023) + dx, y = (int)((p >> 10) & 1023) + dy, z = (int)((p >> 20) & 1023) + dz;
                         if (x >= 0 && y >= 0 && z >= 0 && x < N && y < N && z < N) {
                             int s = L.slot[((long long)z * N + y) * N + x];
-                            if (s >= 0) sr = (L.base + s) * R + tgt_r[tid];
+                            if (s >= 0) sr = L.row0 + (long long)s * R + tgt_r[tid];
                         }
                     }
                     src_row[tid] = sr;
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(LevelsArg lv, const 
     for (int i = 0; i < 4; ++i) {
         int r = ty * 4 + i;
         if (r >= tile.rows) continue;
-        long long orow = (L.base + tgt_b[r]) * R + tgt_r[r];
+        long long orow = L.row0 + (long long)tgt_b[r] * R + tgt_r[r];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             int c = col0 + tx * 4 + j;
@@ -227,11 +229,11 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(LevelsArg lv, const 
 }
 
 template <class T>
-int launch_contract_simt(const LevelsArg &lv, const ContractTile *tiles, long long ntiles, int R,
-                         const T *qt, const T *C, int kp, long long zero_row, T *phit, cudaStream_t s) {
+int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, long long ntiles, const T *qt, const T *C,
+                         int kp, long long zero_row, T *phit, cudaStream_t s) {
     if (ntiles <= 0) return M2L_OK;
     dim3 grid((unsigned)ntiles, (unsigned)((kp + 63) / 64));
-    contract_simt_kernel<T><<<grid, 256, 0, s>>>(lv, tiles, R, qt, C, kp, zero_row, phit);
+    contract_simt_kernel<T><<<grid, 256, 0, s>>>(levels, tiles, qt, C, kp, zero_row, phit);
     return check_launch("contract");
 }
 
@@ -542,8 +544,8 @@ size_t fft_smem_bytes(int p, int g, int elt) {
 #define M2L_INSTANTIATE(T)                                                                              \
     template int launch_gemm_xwt<T>(const T *, long long, const T *, long long, T *, long long, long long, \
                                     int, int, int, cudaStream_t);                                       \
-    template int launch_contract_simt<T>(const LevelsArg &, const ContractTile *, long long, int, const T *, \
-                                         const T *, int, long long, T *, cudaStream_t);                 \
+    template int launch_contract_simt<T>(const LevelView *, const ContractTile *, long long, const T *, const T *, \
+                                         int, long long, T *, cudaStream_t);                            \
     template int launch_fft_forward<T>(const LevelView &, int, int, int, int, const int *, const T *,   \
                                        const T *, T *, cudaStream_t);                                   \
     template int launch_hadamard<T>(const LevelView &, int, int, const T *, const T *, T *, cudaStream_t); \

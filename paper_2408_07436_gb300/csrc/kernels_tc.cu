@@ -35,10 +35,9 @@ constexpr int kThreads = 320;
 constexpr long long kWaitLimit = 1LL << 24;
 
 struct TcParams {
-    LevelsArg lv;
+    const LevelView *lv;               // device array indexed by ContractTile::lev
     const ContractTile *tiles;
     long long ntiles;
-    int R;
     const unsigned char *qhi, *qlo;   // [(rows + 1)][kp] elements
     long long zero_row;
     float *phit;                       // [rows][kp]
@@ -128,8 +127,9 @@ struct RowInfo {
     uint32_t xyz;  // packed coordinates
 };
 
-__device__ __forceinline__ RowInfo row_info(const LevelView &L, const ContractTile &T, int R, int row) {
+__device__ __forceinline__ RowInfo row_info(const LevelView &L, const ContractTile &T, int row) {
     RowInfo ri;
+    const int R = L.R;
     if (row < T.rows) {
         long long j = (long long)T.j0 + row;
         ri.b = L.perm[L.oct_start[T.oct] + j / R];
@@ -199,10 +199,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         int npend = 0;
         for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
             const ContractTile T = P.tiles[tile];
-            const LevelView &L = P.lv.L[T.lev];
+            const LevelView &L = P.lv[T.lev];
             RowInfo ri[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) ri[i] = row_info(L, T, P.R, rgrp + 16 * i);
+            for (int i = 0; i < 8; ++i) ri[i] = row_info(L, T, rgrp + 16 * i);
             const int N = L.N;
             // source rows of the 8 rows this thread feeds, for table entry e
             auto sources = [&](int e, long long (&src)[8]) {
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             z = (int)((ri[i].xyz >> 20) & 1023) + dz;
                         if (x >= 0 && y >= 0 && z >= 0 && x < N && y < N && z < N) {
                             int sl = L.slot[((long long)z * N + y) * N + x];
-                            if (sl >= 0) src[i] = (L.base + sl) * P.R + ri[i].r;
+                            if (sl >= 0) src[i] = L.row0 + (long long)sl * L.R + ri[i].r;
                         }
                     }
                 }
@@ -361,9 +361,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         long long u = 0;
         for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
             const ContractTile T = P.tiles[tile];
-            const LevelView &L = P.lv.L[T.lev];
-            const RowInfo ri = row_info(L, T, P.R, row);
-            float *dst = ri.b >= 0 ? P.phit + ((L.base + ri.b) * P.R + ri.r) * (long long)kp : nullptr;
+            const LevelView &L = P.lv[T.lev];
+            const RowInfo ri = row_info(L, T, row);
+            float *dst = ri.b >= 0 ? P.phit + (L.row0 + (long long)ri.b * L.R + ri.r) * (long long)kp : nullptr;
             for (int g0 = 0; g0 < kPerOctant; g0 += P.group, ++u) {
                 const bool first = g0 == 0, last = g0 + P.group >= kPerOctant;
                 const int buf = (int)(u % nbuf);
@@ -481,6 +481,8 @@ inline uint16_t bf16_round(float x) {  // nearest, ties to even
 }
 inline float bf16_value(uint16_t h) { return bits_f32((uint32_t)h << 16); }
 
+}  // namespace
+
 int ensure_tc_constants(int device) {
     static bool done[64] = {false};
     if (device < 0 || device >= 64) return M2L_EINVAL;
@@ -504,6 +506,7 @@ int ensure_tc_constants(int device) {
     return M2L_OK;
 }
 
+namespace {
 }  // namespace
 
 // Split C_t (FP64 on the host) into hi/lo pieces, upload them and encode their TMA maps.
@@ -588,7 +591,7 @@ int launch_split_rows(const float *src, long long rows, int kp, void *hi, void *
 size_t tc_stage_bytes(int kp) { return 2 * (size_t)kRows * kChunk + 2 * (size_t)kp * kChunk; }
 
 template <class T>
-int launch_contract_tc(m2l_plan_t *pl, const LevelsArg &lv, const ContractTile *tiles, long long ntiles, int R,
+int launch_contract_tc(m2l_plan_t *pl, const LevelView *lv, const ContractTile *tiles, long long ntiles,
                        const void *qt_hi, const void *qt_lo, long long zero_row, T *phit, int precision, cudaStream_t s) {
     if constexpr (sizeof(T) != 4) {
         set_error("the tensor-core contraction writes FP32");
@@ -604,7 +607,6 @@ int launch_contract_tc(m2l_plan_t *pl, const LevelsArg &lv, const ContractTile *
         P.lv = lv;
         P.tiles = tiles;
         P.ntiles = ntiles;
-        P.R = R;
         P.qhi = (const unsigned char *)qt_hi;
         P.qlo = (const unsigned char *)qt_lo;
         P.zero_row = zero_row;
@@ -653,9 +655,9 @@ int launch_contract_tc(m2l_plan_t *pl, const LevelsArg &lv, const ContractTile *
         return M2L_OK;
     }
 }
-template int launch_contract_tc<float>(m2l_plan_t *, const LevelsArg &, const ContractTile *, long long, int, const void *,
+template int launch_contract_tc<float>(m2l_plan_t *, const LevelView *, const ContractTile *, long long, const void *,
                                        const void *, long long, float *, int, cudaStream_t);
-template int launch_contract_tc<double>(m2l_plan_t *, const LevelsArg &, const ContractTile *, long long, int, const void *,
+template int launch_contract_tc<double>(m2l_plan_t *, const LevelView *, const ContractTile *, long long, const void *,
                                         const void *, long long, double *, int, cudaStream_t);
 
 }  // namespace m2l

@@ -95,8 +95,33 @@ static void m2l_matrix(const m2l_plan_t *pl, int t, std::vector<double> &K) {
 
 static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-// Pseudo-inverse of the downward check -> equivalent matrix (Eqs. 7-10, alpha = 0), kept as
-// V_eps and Ut_eps = Sigma_eps^-1 U_eps^T (the two-factor storage of the Sec. 2.1.1 footnote).
+// Pseudo-inverse of the downward check -> equivalent matrix (Eqs. 7-10), kept as V_eps and
+// Ut_eps = Sigma_eps^-1 U_eps^T (the two-factor storage of the Sec. 2.1.1 footnote), with the
+// threshold eps = (alpha + max(M, N) eps_mach) s_0 of Eq. 10:
+//   alpha = 0     for the FP64 paths (the paper's choice);
+//   alpha = 1e-9  for the paths that compute and store in single precision. Their check
+//                 potentials carry ~1e-7..1e-6 relative rounding, which the pseudo-inverse
+//                 amplifies along singular directions down to eps; once stored in FP32 that noise
+//                 swamps the locals when K_tau is worse conditioned than ~1e10 (p >= 7).
+//                 Dropping the directions below 1e-9 s_0 keeps single-precision locals at the
+//                 rounding level of their check potential for p = 4..10.
+static constexpr double kPinvAlphaSingle = 1e-9;
+
+static void pinv_truncation(int n, const std::vector<double> &U, const std::vector<double> &s,
+                            const std::vector<double> &V, double alpha, int &r, std::vector<double> &Veps,
+                            std::vector<double> &Uteps) {
+    const double thresh = (alpha + n * 2.220446049250313e-16) * s[0];
+    r = 0;
+    while (r < n && s[r] > thresh) ++r;
+    Veps.assign((size_t)n * r, 0.0);
+    Uteps.assign((size_t)r * n, 0.0);
+    for (int a = 0; a < r; ++a)
+        for (int i = 0; i < n; ++i) {
+            Veps[(size_t)i * r + a] = V[(size_t)a * n + i];
+            Uteps[(size_t)a * n + i] = U[(size_t)a * n + i] / s[a];
+        }
+}
+
 int build_pinv(m2l_plan_t *pl) {
     if (pl->pinv_ready) return M2L_OK;
     int n = pl->n;
@@ -108,18 +133,9 @@ int build_pinv(m2l_plan_t *pl) {
         for (int i = 0; i < n; ++i) K[(size_t)j * n + i] = laplace(&xs[3 * i], &ys[3 * j]);
     std::vector<double> U, s, V;
     jacobi_svd(K, n, n, U, s, V);
-    double thresh = n * 2.220446049250313e-16 * s[0];
-    int r = 0;
-    while (r < n && s[r] > thresh) ++r;
-    pl->r = r;
-    pl->rp = round_up(r, 16);
-    pl->Veps.assign((size_t)n * r, 0.0);
-    pl->Uteps.assign((size_t)r * n, 0.0);
-    for (int a = 0; a < r; ++a)
-        for (int i = 0; i < n; ++i) {
-            pl->Veps[(size_t)i * r + a] = V[(size_t)a * n + i];
-            pl->Uteps[(size_t)a * n + i] = U[(size_t)a * n + i] / s[a];
-        }
+    pinv_truncation(n, U, s, V, 0.0, pl->r, pl->Veps, pl->Uteps);
+    pinv_truncation(n, U, s, V, kPinvAlphaSingle, pl->r32, pl->Veps32, pl->Uteps32);
+    pl->rp = round_up(pl->r, 16);
     pl->pinv_ready = true;
     return M2L_OK;
 }
@@ -198,13 +214,16 @@ int build_blas_host(m2l_plan_t *pl) {
         }
     }
     // A = Ut_eps U  (r x k): the scaled factor of the pseudo-inverse times the uncompression.
-    int r = pl->r;
-    pl->Aop.assign((size_t)r * k, 0.0);
-    for (int a = 0; a < r; ++a)
-        for (int i = 0; i < n; ++i) {
-            double u = pl->Uteps[(size_t)a * n + i];
-            for (int c = 0; c < k; ++c) pl->Aop[(size_t)a * k + c] += u * pl->U[(size_t)i * k + c];
-        }
+    auto fold = [&](const std::vector<double> &Ut, int r, std::vector<double> &A) {
+        A.assign((size_t)r * k, 0.0);
+        for (int a = 0; a < r; ++a)
+            for (int i = 0; i < n; ++i) {
+                double u = Ut[(size_t)a * n + i];
+                for (int c = 0; c < k; ++c) A[(size_t)a * k + c] += u * pl->U[(size_t)i * k + c];
+            }
+    };
+    fold(pl->Uteps, pl->r, pl->Aop);
+    fold(pl->Uteps32, pl->r32, pl->Aop32);
     pl->blas_host_ready = true;
     return M2L_OK;
 }
@@ -413,7 +432,7 @@ int build_level_tables(m2l_plan_t *pl) {
     pl->total_rows = base;
     pl->total_clusters = cbase;
     pl->levels_dirty = false;
-    pl->tiles_rhs = -1;  // tile lists depend on the box sets
+    pl->levels_version++;  // tile lists and graphs depend on the box sets
     return M2L_OK;
 }
 
@@ -456,7 +475,12 @@ int split_tc_operators(m2l_plan_t *pl, int precision);  // kernels_tc.cu
 
 template <class T>
 static int upload_typed(m2l_plan_t *pl, DevOps &D, int form) {
-    int n = pl->n, k = pl->k, kp = pl->kp, r = pl->r, rp = pl->rp;
+    // single-precision paths take the pseudo-inverse truncated with alpha = 1e-9 (build_pinv)
+    const bool single = sizeof(T) == 4;
+    const int n = pl->n, k = pl->k, kp = pl->kp, r = single ? pl->r32 : pl->r, rp = pl->rp;
+    const std::vector<double> &Veps = single ? pl->Veps32 : pl->Veps;
+    const std::vector<double> &Uteps = single ? pl->Uteps32 : pl->Uteps;
+    const std::vector<double> &Aop = single ? pl->Aop32 : pl->Aop;
     int rc = M2L_OK;
     if (form == M2L_FORM_BLAS) {
         // S^T  [kp][n]
@@ -470,8 +494,8 @@ static int upload_typed(m2l_plan_t *pl, DevOps &D, int form) {
                     Cp[((size_t)t * kp + a) * kp + c] = (T)pl->C[((size_t)t * k + a) * k + c];
         if ((rc = upload_vec(D.St, pad2<T>(St, k, n, kp, n)))) return rc;
         if ((rc = upload_vec(D.C, Cp))) return rc;
-        if ((rc = upload_vec(D.A, pad2<T>(pl->Aop, r, k, rp, kp)))) return rc;
-        if ((rc = upload_vec(D.V, pad2<T>(pl->Veps, n, r, n, rp)))) return rc;
+        if ((rc = upload_vec(D.A, pad2<T>(Aop, r, k, rp, kp)))) return rc;
+        if ((rc = upload_vec(D.V, pad2<T>(Veps, n, r, n, rp)))) return rc;
         if ((rc = upload_vec(D.Uc, pad2<T>(pl->U, n, k, n, kp)))) return rc;
     } else {
         int F = pl->F;
@@ -481,8 +505,8 @@ static int upload_typed(m2l_plan_t *pl, DevOps &D, int form) {
         for (size_t i = 0; i < tw.size(); ++i) tw[i] = (T)pl->twiddle[i];
         if ((rc = upload_vec(D.Khat, K))) return rc;
         if ((rc = upload_vec(D.tw, tw))) return rc;
-        if ((rc = upload_vec(D.Ut, pad2<T>(pl->Uteps, r, n, rp, n)))) return rc;
-        if ((rc = upload_vec(D.V, pad2<T>(pl->Veps, n, r, n, rp)))) return rc;
+        if ((rc = upload_vec(D.Ut, pad2<T>(Uteps, r, n, rp, n)))) return rc;
+        if ((rc = upload_vec(D.V, pad2<T>(Veps, n, r, n, rp)))) return rc;
     }
     return rc;
 }
@@ -522,7 +546,7 @@ void free_device(m2l_plan_t *pl) {
     if (pl->ws.buf) cudaFree(pl->ws.buf);
     if (pl->stage_in.buf) cudaFree(pl->stage_in.buf);
     if (pl->stage_out.buf) cudaFree(pl->stage_out.buf);
-    if (pl->tiles) cudaFree(pl->tiles);
+    free_exec(pl);
     if (pl->lattice_dev) cudaFree(pl->lattice_dev);
     pl->lattice_dev = nullptr;
     if (pl->dev_status) cudaFree(pl->dev_status);
@@ -534,7 +558,6 @@ void free_device(m2l_plan_t *pl) {
     pl->ws = {};
     pl->stage_in = {};
     pl->stage_out = {};
-    pl->tiles = nullptr;
 }
 
 }  // namespace m2l

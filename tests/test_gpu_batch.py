@@ -1,0 +1,156 @@
+"""Batches of uneven independent instances (m2l_apply_batch), graph replay, and the autotuner."""
+import numpy as np
+import pytest
+
+from oracle import m2l as M
+from paper_2408_07436_gb300 import workloads as W
+
+from gpu_util import oracle_level
+
+pytestmark = pytest.mark.gpu
+
+
+def _instances():
+    """(workload, form, precision): uneven depth, p, RHS and box sets; two share a group."""
+    return [
+        (W.small(depth=3, p=4, n_rhs=2, n_points=900, seed=1, density="u11"), "blas", "fp64"),
+        (W.small(depth=4, p=4, n_rhs=1, n_points=2500, seed=2, density="u11"), "blas", "fp64"),
+        (W.small(depth=3, p=6, n_rhs=3, seed=3, density="normal"), "fft", "fp64"),
+        (W.small(depth=3, p=5, n_rhs=1, n_points=700, seed=4, density="u01"), "blas", "tf32x3"),
+        (W.small(depth=4, p=5, n_rhs=2, n_points=3000, seed=5, density="u01"), "blas", "tf32x3"),
+        (W.small(depth=3, p=4, n_rhs=1, seed=6, density="u11"), "fft", "fp32"),
+    ]
+
+
+def _make(lib, wl, form, prec, output="check"):
+    import torch
+    plan = lib.Plan(wl.depth, wl.p, 0.0, form=form, precision=prec).set(output=output)
+    for l in wl.levels:
+        if wl.keys[l] is not None:
+            plan.set_boxes(l, wl.keys[l])
+    plan.set_stream()
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    q = torch.from_numpy(wl.all_multipoles()).to(dt).cuda()
+    return plan, q, torch.empty_like(q)
+
+
+def _batch(lib, plans, qs, outs, Rs):
+    rc = lib.m2l_apply_batch([p.handle for p in plans], [q.data_ptr() for q in qs], [o.data_ptr() for o in outs], Rs)
+    assert rc == lib.M2L_OK, lib.m2l_last_error()
+
+
+def test_batch_matches_individual_and_replays(lib):
+    import torch
+    inst = _instances()
+    made = [_make(lib, wl, f, p) for wl, f, p in inst]
+    plans = [m[0] for m in made]
+    qs = [m[1] for m in made]
+    Rs = [wl.n_rhs for wl, _, _ in inst]
+    try:
+        singles = []
+        for (plan, q, o), R in zip(made, Rs):
+            plan.apply(q, o, -1, R)
+            singles.append(o.clone())
+        outs = [torch.full_like(q, float("nan")) for q in qs]
+        _batch(lib, plans, qs, outs, Rs)                       # captures the graph
+        torch.cuda.synchronize()
+        for a, b in zip(outs, singles):
+            assert torch.equal(a, b)
+        # new values in the same buffers: the replayed graph must see them
+        for q in qs:
+            q.mul_(-0.5).add_(0.25)
+        singles2 = []
+        for (plan, q, o), R in zip(made, Rs):
+            plan.apply(q, o, -1, R)
+            singles2.append(o.clone())
+        for o in outs:
+            o.fill_(float("nan"))
+        _batch(lib, plans, qs, outs, Rs)                       # replays
+        torch.cuda.synchronize()
+        for a, b in zip(outs, singles2):
+            assert torch.equal(a, b)
+        assert lib.m2l_query(plans[0].handle, lib.M2L_Q_LAUNCHES) > 0
+        # a changed option forces a new capture
+        for p in plans:
+            p.set(output="locals")
+        _batch(lib, plans, qs, outs, Rs)
+        torch.cuda.synchronize()
+        for (plan, q, o), R, got in zip(made, Rs, outs):
+            plan.apply(q, o, -1, R)
+            torch.cuda.synchronize()
+            assert torch.equal(got, o)
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_batch_against_oracle(lib):
+    import torch
+    inst = _instances()
+    made = [_make(lib, wl, f, p) for wl, f, p in inst]
+    try:
+        outs = [torch.empty_like(m[1]) for m in made]
+        _batch(lib, [m[0] for m in made], [m[1] for m in made], outs, [wl.n_rhs for wl, _, _ in inst])
+        torch.cuda.synchronize()
+        for (wl, form, prec), out in zip(inst, outs):
+            flat = out.double().cpu().numpy()
+            n = W.n_surface(wl.p)
+            off = 0
+            bound = {"fp64": 1e-12, "fp32": 5e-6, "tf32x3": 5e-6}[prec]
+            for l in wl.levels:
+                B = wl.n_boxes(l)
+                got = flat[off:off + B * wl.n_rhs * n].reshape(B, wl.n_rhs, n)
+                off += B * wl.n_rhs * n
+                keys = None if wl.keys[l] is None else wl.keys[l].astype(np.int64)
+                tg = np.arange(0, B, max(1, B // 40))
+                _, ref = oracle_level(wl.p, l, wl.multipoles(l), keys=keys, targets=tg)
+                assert M.rel_l2_error(ref, got[tg]) < bound, (wl.name, form, prec, l)
+    finally:
+        for m in made:
+            m[0].close()
+
+
+def test_batch_rejects_bad_arguments(lib):
+    import torch
+    wl = W.small(depth=2, p=3)
+    plan, q, o = _make(lib, wl, "blas", "fp64")
+    try:
+        h = q.cpu()
+        assert lib.m2l_apply_batch([plan.handle], [h.data_ptr()], [o.data_ptr()], [1]) == lib.M2L_EINVAL
+        assert lib.m2l_apply_batch([plan.handle, plan.handle], [q.data_ptr()] * 2, [o.data_ptr()] * 2, [1, 1]) == lib.M2L_EINVAL
+        assert lib.m2l_apply_batch([plan.handle], [q.data_ptr()], [o.data_ptr()], [0]) == lib.M2L_EINVAL
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("tol", [3e-5, 1e-9])
+def test_autotuner_meets_target(lib, tol):
+    import torch
+    wl = W.small(depth=4, p=6, density="u11")
+    plan = lib.Plan(wl.depth, wl.p, 0.0, form="auto", precision="auto").set(target_tol=tol, output="check")
+    try:
+        plan.set_stream()
+        prec = plan.query(lib.M2L_Q_PRECISION, 1)
+        form = plan.query(lib.M2L_Q_FORM, 1)
+        if tol < 1e-6:
+            assert prec == lib.M2L_PREC_FP64
+        else:
+            assert prec != lib.M2L_PREC_FP64
+        assert form in (lib.M2L_FORM_BLAS, lib.M2L_FORM_FFT)
+        dt = torch.float64 if prec == lib.M2L_PREC_FP64 else torch.float32
+        q = torch.from_numpy(wl.all_multipoles()).to(dt).cuda()
+        o = torch.empty_like(q)
+        plan.apply(q, o, -1, 1)
+        torch.cuda.synchronize()
+        flat = o.double().cpu().numpy()
+        n = plan.n
+        off = 0
+        for l in wl.levels:
+            B = wl.n_boxes(l)
+            got = flat[off:off + B * n].reshape(B, 1, n)
+            off += B * n
+            tg = np.arange(0, B, max(1, B // 40))
+            _, ref = oracle_level(wl.p, l, wl.multipoles(l), targets=tg)
+            assert M.rel_l2_error(ref, got[tg]) < max(tol, 1e-12)
+    finally:
+        plan.close()

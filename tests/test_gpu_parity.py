@@ -243,3 +243,28 @@ def test_c2_full_size_sampled_tensor_cores(lib, precision):
         sample = np.sort(rng.choice(B, size=min(B, 48), replace=False))
         _, phi_ref = M.m2l_compressed(wl.p, l, qs[l], ops, targets=sample)
         assert M.rel_l2_error(phi_ref, chk[l][sample]) < TC_TOL[precision], (precision, l)
+
+
+# Stated bounds of the single-precision paths for p = 4..10 (the library's autotuner uses the
+# same table): check potentials and locals in the check norm.
+SINGLE_BOUND = {("blas", "fp32"): 1e-5, ("fft", "fp32"): 2e-6, ("blas", "tf32x3"): 5e-6, ("blas", "bf16x3"): 2e-5}
+
+
+@pytest.mark.parametrize("p", [4, 8, 10])
+def test_single_precision_bounds_over_orders(lib, p):
+    wl = W.small(depth=3, p=p, density="normal", seed=11)
+    qs = _qs(wl)
+    refs = {}
+    for l in wl.levels:
+        tg = np.arange(0, 8 ** l, max(1, 8 ** l // 24))
+        L, phi = M.m2l_dense(p, l, qs[l], targets=tg)
+        refs[l] = (tg, L, phi / 2.0 ** l)
+    for (form, prec), bound in SINGLE_BOUND.items():
+        if prec in ("tf32x3", "bf16x3") and p > 6:
+            continue  # full rank k_pad > 256: the tensor-core contraction needs a truncated rank there
+        chk = run_gpu(lib, 3, p, qs, form=form, precision=prec, output="check")
+        loc = run_gpu(lib, 3, p, qs, form=form, precision=prec, output="locals")
+        for l in wl.levels:
+            tg, L_ref, phi_ref = refs[l]
+            assert M.rel_l2_error(phi_ref, chk[l][tg]) < bound, (form, prec, p, l)
+            assert M.check_norm_error(p, l, L_ref, loc[l][tg]) < bound, (form, prec, p, l)
