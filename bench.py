@@ -142,41 +142,81 @@ def algorithmic_work(plan, form, prec, R):
             "pinv": 2.0 * 2 * n * r * rows}
 
 
+def workload_spec(name, depth):
+    """(instances, variants, batched, target_tol, description) of a named workload."""
+    if name == "c2":
+        return [W.c2(depth=depth)], VARIANTS, False, None, WORKLOAD
+    if name == "c3":
+        return ([W.c3()], ["blas-bf16x3", "blas-tf32x3", "blas-fp64", "fft-fp32", "fft-fp64"], False, None,
+                "laplace3d-m2l uniform-cube 8M points depth6 p8 1rhs blas(rank_tol 1e-7) bf16x3/tf32x3/fp64 + fft fp32/fp64")
+    if name == "c4":
+        return ([W.c4()], ["blas-bf16x3", "blas-tf32x3", "fft-fp32"], False, None,
+                "laplace3d-m2l unit-sphere-surface 2M points depth6 p6 32rhs pruned boxes blas(rank_tol 1e-7) bf16x3/tf32x3 + fft fp32")
+    if name == "c5":
+        return (W.c5(), ["auto-auto"], True, 1e-6,
+                "laplace3d-m2l 64 uneven instances (1e4..2e6 points, depth 3-6, p 4/6/8/10, 1-8 rhs) one batched "
+                "graph-replayed pass, autotuned form/precision at 1e-6")
+    raise ValueError(name)
+
+
+def log(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2408_07436_gb300 import m2l as lib
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    wl = W.c2(depth=args.depth)
-    R = wl.n_rhs
-    variants = args.variants.split(",")
-    # every rank draws its own independent instance of the workload
-    q64 = np.concatenate([wl.multipoles(l, rng_offset=rank).reshape(-1) for l in wl.levels])
-    bufs = {}
-    plans = {}
+    insts, variants, batched, target_tol, desc = workload_spec(args.workload, args.depth)
+    if args.variants:
+        variants = args.variants.split(",")
+    # every rank draws its own independent instances of the workload
+    q64 = [np.concatenate([wl.multipoles(l, rng_offset=rank).reshape(-1) for l in wl.levels]) for wl in insts]
+    plans = {v: [] for v in variants}
+    bufs = {}       # (instance, dtype) -> (q, out)
+    dtypes = {}     # (variant, instance) -> dtype
     for v in variants:
         form, prec = variant_parts(v)
-        tol = wl.rank_tol if form == "blas" else 0.0
-        pl = lib.Plan(wl.depth, wl.p, tol, form=form, precision=prec).set(timing=1)
-        pl.set_stream()
-        plans[v] = pl
-        dt = torch.float64 if prec == "fp64" else torch.float32
-        if dt not in bufs:
-            bufs[dt] = (torch.from_numpy(q64).to(dt).to(dev), torch.empty(len(q64), dtype=dt, device=dev))
-    pairs = plans[variants[0]].pairs(-1)
+        for i, wl in enumerate(insts):
+            tol = wl.rank_tol if form in ("blas", "auto") else 0.0
+            pl = lib.Plan(wl.depth, wl.p, tol, form=form, precision=prec).set(timing=0 if batched else 1)
+            if target_tol is not None:
+                pl.set(target_tol=target_tol)
+            for l in wl.levels:
+                if wl.keys[l] is not None:
+                    pl.set_boxes(l, wl.keys[l])
+            pl.set_stream()
+            plans[v].append(pl)
+            pr = pl.query(lib.M2L_Q_PRECISION, wl.n_rhs)
+            dt = torch.float64 if pr == lib.M2L_PREC_FP64 else torch.float32
+            dtypes[(v, i)] = dt
+            if (i, dt) not in bufs:
+                bufs[(i, dt)] = (torch.from_numpy(q64[i]).to(dt).to(dev), torch.empty(len(q64[i]), dtype=dt, device=dev))
+    log(f"{len(insts)} instance(s), {len(variants)} variant(s): plans ready")
+    pairs = [plans[variants[0]][i].pairs(-1) for i in range(len(insts))]
+    inter_variant = sum(pairs[i] * insts[i].n_rhs for i in range(len(insts)))
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step():
-        for v in variants:
-            form, prec = variant_parts(v)
-            dt = torch.float64 if prec == "fp64" else torch.float32
-            qd, od = bufs[dt]
-            plans[v].apply(qd, od, -1, R)
+    def run_variant(v):
+        if batched:
+            qs = [bufs[(i, dtypes[(v, i)])][0] for i in range(len(insts))]
+            os_ = [bufs[(i, dtypes[(v, i)])][1] for i in range(len(insts))]
+            rc = lib.m2l_apply_batch([pl.handle for pl in plans[v]], [q.data_ptr() for q in qs],
+                                     [o.data_ptr() for o in os_], [wl.n_rhs for wl in insts])
+            if rc != lib.M2L_OK:
+                raise lib.M2LError(rc, lib.m2l_last_error())
+        else:
+            for i, wl in enumerate(insts):
+                qd, od = bufs[(i, dtypes[(v, i)])]
+                plans[v][i].apply(qd, od, -1, wl.n_rhs)
 
     for _ in range(args.warmup):
-        step()
+        for v in variants:
+            run_variant(v)
     torch.cuda.synchronize()
+    log("warm-up done")
     stream = torch.cuda.current_stream()
     stage_acc = {v: {} for v in variants}
     var_ms = {v: 0.0 for v in variants}
@@ -192,56 +232,69 @@ def run_ours(args, rank, world, local_rank):
         flush.zero_()  # L2 flush, outside the timed interval
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(variants) + 1)]
         evs[0].record(stream)
-        for i, v in enumerate(variants):
-            form, prec = variant_parts(v)
-            dt = torch.float64 if prec == "fp64" else torch.float32
-            qd, od = bufs[dt]
-            plans[v].apply(qd, od, -1, R)
-            evs[i + 1].record(stream)
+        for j, v in enumerate(variants):
+            run_variant(v)
+            evs[j + 1].record(stream)
         torch.cuda.synchronize()
         total_ms += evs[0].elapsed_time(evs[-1])
-        for i, v in enumerate(variants):
-            var_ms[v] += evs[i].elapsed_time(evs[i + 1])
-            for name, (ms, nl) in plans[v].stage_times().items():
-                a = stage_acc[v].setdefault(name, [0.0, 0])
-                a[0] += ms
-                a[1] += nl
-                launches += nl
+        for j, v in enumerate(variants):
+            var_ms[v] += evs[j].elapsed_time(evs[j + 1])
+            if batched:
+                launches += plans[v][0].query(lib.M2L_Q_LAUNCHES)
+                continue
+            for pl in plans[v]:
+                for name, (ms, nl) in pl.stage_times().items():
+                    a = stage_acc[v].setdefault(name, [0.0, 0])
+                    a[0] += ms
+                    a[1] += nl
+                    launches += nl
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     clocks = sampler.stop()
+    log(f"timed steps done: {total_ms / args.steps:.1f} ms per step")
     ms_step = total_ms / args.steps
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
-    inter_step = pairs * R * len(variants)
+    inter_step = inter_variant * len(variants)
     value = world * inter_step / (ms_step / 1e3)
+    steps_for_stages = args.steps
+    if batched:
+        # stage times of a batch: one separate, untimed apply of the largest instance on a fresh plan
+        big = max(range(len(insts)), key=lambda i: pairs[i] * insts[i].n_rhs)
+        wl = insts[big]
+        for v in variants:
+            src = plans[v][big]
+            f = src.query(lib.M2L_Q_FORM, wl.n_rhs)
+            pr = src.query(lib.M2L_Q_PRECISION, wl.n_rhs)
+            fname = "blas" if f == lib.M2L_FORM_BLAS else "fft"
+            pname = {lib.M2L_PREC_FP64: "fp64", lib.M2L_PREC_FP32: "fp32", lib.M2L_PREC_TF32X3: "tf32x3",
+                     lib.M2L_PREC_BF16X3: "bf16x3"}[pr]
+            probe = lib.Plan(wl.depth, wl.p, wl.rank_tol if fname == "blas" else 0.0, form=fname,
+                             precision=pname).set(timing=1)
+            for l in wl.levels:
+                if wl.keys[l] is not None:
+                    probe.set_boxes(l, wl.keys[l])
+            probe.set_stream()
+            qd, od = bufs[(big, dtypes[(v, big)])]
+            probe.apply(qd, od, -1, wl.n_rhs)
+            for name, (ms, nl) in probe.stage_times().items():
+                a = stage_acc[v].setdefault(name, [0.0, 0])
+                a[0] += ms
+                a[1] += nl
+            probe_work = algorithmic_work(probe, fname, pname, wl.n_rhs)
+            stage_acc[v]["_work"] = probe_work
+            stage_acc[v]["_prec"] = pname
+            probe.close()
+        steps_for_stages = 1
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel of each variant and of the step
     peaks = measured_peaks()
-    best = None
-    var_out = {}
-    for v in variants:
-        form, prec = variant_parts(v)
-        work = algorithmic_work(plans[v], form, prec, R)
-        stages = {}
-        for name, (ms, nl) in stage_acc[v].items():
-            if nl == 0:
-                continue
-            per_launch_ms = ms / nl
-            flops_launch = work.get(name, 0.0) * args.steps / nl
-            stages[name] = {"ms_per_step": ms / args.steps, "launches_per_step": nl / args.steps,
-                            "gflops": flops_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None}
-            if best is None or ms > best[0]:
-                best = (ms, v, name, per_launch_ms, flops_launch, prec)
-        var_out[v] = {"interactions_per_s": pairs * R / (var_ms[v] / args.steps / 1e3),
-                      "ms": var_ms[v] / args.steps, "stages": stages}
-        if form == "blas":
-            var_out[v]["rank"] = plans[v].query(lib.M2L_Q_RANK)
+
     def peak_for(prec):
         if prec == "fp64":
             return NOMINAL_FP64_TFLOPS, "alu", "nominal GB300 FP64 1.25 TFLOP/s"
@@ -252,73 +305,117 @@ def run_ours(args, rank, world, local_rank):
             return bf / 3.0, "tensor", "of measured: bf16 sustained / 3 (each useful product is 3 MMAs)"
         return bf / 2.0 / 3.0, "tensor", "of measured: bf16 sustained / 2 (nominal tf32 ratio) / 3 (3 MMAs per product)"
 
-    def roof(v, name, ms_total, nl, flops_launch):
-        prec = variant_parts(v)[1]
-        pk, bound, note = peak_for(prec)
-        per_launch_ms = ms_total / nl
-        ach = flops_launch / (per_launch_ms / 1e3) / 1e12
-        return {"bound": bound, "kernel": f"{v}:{name}", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                "frac": ach / pk, "traffic": None, "peak_source": note}
-
+    var_out = {}
+    best = None
     for v in variants:
-        st = {n: a for n, a in stage_acc[v].items() if a[1] > 0}
-        if not st:
-            continue
-        name = max(st, key=lambda n: st[n][0])
-        ms_tot, nl = st[name]
-        work = algorithmic_work(plans[v], *variant_parts(v), R)
-        var_out[v]["roofline"] = roof(v, name, ms_tot, nl, work.get(name, 0.0) * args.steps / nl)
-    _, bv, bname, bms, bflops, bprec = best
-    roofline = roof(bv, bname, bms * 1.0, 1, bflops)
+        # algorithmic work per stage, summed over instances (each resolved to its own precision);
+        # for a batch, the stage times and work are those of its largest instance
+        probe_work = stage_acc[v].pop("_work", None)
+        probe_prec = stage_acc[v].pop("_prec", None)
+        work, prec_of = {}, None
+        for i, (pl, wl) in enumerate(zip(plans[v], insts)):
+            f = pl.query(lib.M2L_Q_FORM, wl.n_rhs)
+            pr = pl.query(lib.M2L_Q_PRECISION, wl.n_rhs)
+            fname = "blas" if f == lib.M2L_FORM_BLAS else "fft"
+            pname = {lib.M2L_PREC_FP64: "fp64", lib.M2L_PREC_FP32: "fp32", lib.M2L_PREC_TF32X3: "tf32x3",
+                     lib.M2L_PREC_BF16X3: "bf16x3"}[pr]
+            prec_of = pname if prec_of in (None, pname) else "mixed"
+            for k, w in algorithmic_work(pl, fname, pname, wl.n_rhs).items():
+                work[k] = work.get(k, 0.0) + w
+        prec_all = prec_of
+        if probe_work is not None:
+            work, prec_of = probe_work, probe_prec
+        stages = {}
+        for name, (ms, nl) in stage_acc[v].items():
+            if nl == 0:
+                continue
+            per_launch_ms = ms / nl
+            flops_launch = work.get(name, 0.0) * steps_for_stages / nl
+            stages[name] = {"ms_per_step": ms / steps_for_stages, "launches_per_step": nl / steps_for_stages,
+                            "gflops": flops_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None}
+        var_out[v] = {"interactions_per_s": inter_variant / (var_ms[v] / args.steps / 1e3), "ms": var_ms[v] / args.steps,
+                      "stages": stages, "precision": prec_all}
+        if probe_work is not None:
+            var_out[v]["stages_of"] = "largest instance, separate apply"
+        if insts and variant_parts(v)[0] == "blas":
+            var_out[v]["rank"] = [pl.query(lib.M2L_Q_RANK) for pl in plans[v]][:4]
+        if stages and prec_of != "mixed":
+            name = max(stages, key=lambda n: stages[n]["ms_per_step"])
+            ms_tot, nl = stage_acc[v][name]
+            pk, bound, note = peak_for(prec_of)
+            per_launch_ms = ms_tot / nl
+            ach = work.get(name, 0.0) * steps_for_stages / nl / (per_launch_ms / 1e3) / 1e12
+            rf = {"bound": bound, "kernel": f"{v}:{name}", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                  "frac": ach / pk, "traffic": None, "peak_source": note}
+            var_out[v]["roofline"] = rf
+            if best is None or ms_tot > best[0]:
+                best = (ms_tot, rf)
+    roofline = best[1] if best else None
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        hq = {dt: torch.from_numpy(q64).to(dt).pin_memory() for dt in bufs}
-        ho = {dt: torch.empty(len(q64), dtype=dt).pin_memory() for dt in bufs}
-        h2d = d2h = 0
-        for v in variants:
-            dt = torch.float64 if variant_parts(v)[1] == "fp64" else torch.float32
-            plans[v].apply(hq[dt], ho[dt], -1, R)  # warm the staging buffers
+        hq = {k: bufs[k][0].cpu().pin_memory() for k in bufs}
+        ho = {k: torch.empty_like(hq[k]).pin_memory() for k in bufs}
+
+        def e2e_pass():
+            for v in variants:
+                if batched:
+                    for i in range(len(insts)):
+                        k = (i, dtypes[(v, i)])
+                        bufs[k][0].copy_(hq[k], non_blocking=True)
+                    run_variant(v)
+                    for i in range(len(insts)):
+                        k = (i, dtypes[(v, i)])
+                        ho[k].copy_(bufs[k][1], non_blocking=True)
+                    torch.cuda.synchronize()
+                else:
+                    for i, wl in enumerate(insts):
+                        k = (i, dtypes[(v, i)])
+                        plans[v][i].apply(hq[k], ho[k], -1, wl.n_rhs)
+
+        e2e_pass()  # warm the staging buffers
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            for v in variants:
-                dt = torch.float64 if variant_parts(v)[1] == "fp64" else torch.float32
-                plans[v].apply(hq[dt], ho[dt], -1, R)
+            e2e_pass()
         el = time.perf_counter() - t0
-        for v in variants:
-            dt = torch.float64 if variant_parts(v)[1] == "fp64" else torch.float32
-            h2d += hq[dt].numel() * hq[dt].element_size()
-            d2h += ho[dt].numel() * ho[dt].element_size()
+        h2d = sum(hq[(i, dtypes[(v, i)])].numel() * hq[(i, dtypes[(v, i)])].element_size()
+                  for v in variants for i in range(len(insts)))
         if world > 1:
             import torch.distributed as dist
             t = torch.tensor([el], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             el = float(t.item())
         e2e = {"value": world * inter_step * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+               "d2h_bytes_per_step": h2d}
 
-    mixed = [v for v in variants if variant_parts(v)[1] in ("tf32x3", "bf16x3", "fp32")]
-    fp64 = [v for v in variants if variant_parts(v)[1] == "fp64"]
+    mixed = [v for v in variants if var_out[v].get("precision") in ("tf32x3", "bf16x3", "fp32")]
+    fp64 = [v for v in variants if var_out[v].get("precision") == "fp64"]
     headline = None
     if mixed and fp64:
         bm = max(mixed, key=lambda v: var_out[v]["interactions_per_s"])
         bf = max(fp64, key=lambda v: var_out[v]["interactions_per_s"])
         headline = {"fastest_reduced_precision": bm, "fastest_fp64": bf,
                     "speedup": var_out[bm]["interactions_per_s"] / var_out[bf]["interactions_per_s"]}
+    precs = sorted({var_out[v].get("precision") or "?" for v in variants})
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "+".join(sorted({variant_parts(v)[1] for v in variants})), "data": "synthetic",
-           "config": {"workload": WORKLOAD, "levels": wl.levels, "pairs_per_variant": pairs, "n_rhs": R,
-                      "variants": variants, "l2": "flushed between timed steps (512 MB write)",
-                      "instances": "one independent instance per rank"},
+           "vs_baseline": None, "dtype": "+".join(precs), "data": "synthetic",
+           "config": {"workload": desc, "instances": len(insts), "pairs_per_variant": int(sum(pairs)),
+                      "interactions_per_variant": int(inter_variant), "variants": variants,
+                      "batched": batched, "target_tol": target_tol,
+                      "l2": "flushed between timed steps (512 MB write)",
+                      "ranks": "one independent set of instances per rank"},
            "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e, "variants": var_out,
            "mixed_vs_fp64": headline}
+    log("e2e done")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(wl, q64, plans, bufs, args.cpu_seconds)
-    for pl in plans.values():
-        pl.close()
+        out["cpu_baseline"] = cpu_baseline(insts, q64, plans, bufs, dtypes, args.cpu_seconds)
+        log("cpu baseline done")
+    for v in variants:
+        for pl in plans[v]:
+            pl.close()
     return out
 
 
@@ -337,15 +434,17 @@ def _oracle_sample(wl, q64, seconds, seed=11):
     results = {l: ([], [], []) for l in wl.levels}
     t0 = time.perf_counter()
     batches = 0
+    W_root = wl_root_width(wl)
     while True:
         for l in wl.levels:
             B = wl.n_boxes(l)
+            keys = None if wl.keys[l] is None else wl.keys[l].astype(np.int64)
             tg = rng.choice(B, size=min(B, 16), replace=False)
-            L, phi = M.m2l_dense(wl.p, l, qs[l], targets=tg)
+            L, phi = M.m2l_dense(wl.p, l, qs[l], keys=keys, targets=tg, root_width=W_root)
             results[l][0].append(tg)
-            results[l][1].append(phi / (2.0 ** l))
+            results[l][1].append(phi * (W_root / 2.0 ** l))   # check potential of a unit-width box
             results[l][2].append(L)
-            done_pairs += int(M.interaction_csr(l, None, tg)[2][-1])
+            done_pairs += int(M.interaction_csr(l, keys, tg)[2][-1])
         batches += 1
         el = time.perf_counter() - t0
         if el >= seconds:
@@ -353,46 +452,58 @@ def _oracle_sample(wl, q64, seconds, seed=11):
     return done_pairs * R, el, results, batches
 
 
-def cpu_baseline(wl, q64, plans, bufs, seconds):
-    """The FP64 oracle on this host's cores, on a bounded sample; also the error of each variant."""
-    import torch
+def cpu_baseline(insts, q64, plans, bufs, dtypes, seconds):
+    """The FP64 oracle on this host's cores, on a bounded sample of the workload's instances; also
+    the error of each variant on the sampled targets (Eq. 16)."""
     from oracle import m2l as M
     cores = os.cpu_count()
-    inter, el, res, batches = _oracle_sample(wl, q64, seconds)
-    errs = {}
-    n = W.n_surface(wl.p)
-    for v, pl in plans.items():
-        form, prec = variant_parts(v)
-        dt = torch.float64 if prec == "fp64" else torch.float32
-        qd, od = bufs[dt]
-        pl.set(output="check")
-        pl.apply(qd, od, -1, wl.n_rhs)
-        chk = od.double().cpu().numpy()
-        pl.set(output="locals")
-        pl.apply(qd, od, -1, wl.n_rhs)
-        loc = od.double().cpu().numpy()
-        e_chk, e_loc = [], []
-        off = 0
-        for l in wl.levels:
-            B = wl.n_boxes(l)
-            c = chk[off:off + B * wl.n_rhs * n].reshape(B, wl.n_rhs, n)
-            lo = loc[off:off + B * wl.n_rhs * n].reshape(B, wl.n_rhs, n)
-            tg = np.concatenate(res[l][0])
-            ref_phi = np.concatenate(res[l][1])
-            ref_L = np.concatenate(res[l][2])
-            e_chk.append(M.rel_l2_error(ref_phi, c[tg]))
-            e_loc.append(M.check_norm_error(wl.p, l, ref_L, lo[tg]))
-            off += B * wl.n_rhs * n
-        errs[v] = {"check_potential_rel_err_per_level": e_chk, "locals_rel_err_per_level": e_loc}
+    order = sorted(range(len(insts)), key=lambda i: -insts[i].n_boxes(insts[i].depth))[:4]
+    budget = seconds / len(order)
+    inter, el, batches = 0, 0.0, 0
+    errs = {v: {"check_potential_rel_err_per_level": [], "locals_rel_err_per_level": []} for v in plans}
+    for i in order:
+        wl = insts[i]
+        it, e_, res, b_ = _oracle_sample(wl, q64[i], budget)
+        inter += it
+        el += e_
+        batches += b_
+        n = W.n_surface(wl.p)
+        for v in plans:
+            pl = plans[v][i]
+            qd, od = bufs[(i, dtypes[(v, i)])]
+            outs = {}
+            for mode in ("check", "locals"):
+                pl.set(output=mode)
+                pl.apply(qd, od, -1, wl.n_rhs)
+                outs[mode] = od.double().cpu().numpy()
+            pl.set(output="locals")
+            off = 0
+            for l in wl.levels:
+                B = wl.n_boxes(l)
+                c = outs["check"][off:off + B * wl.n_rhs * n].reshape(B, wl.n_rhs, n)
+                lo = outs["locals"][off:off + B * wl.n_rhs * n].reshape(B, wl.n_rhs, n)
+                off += B * wl.n_rhs * n
+                tg = np.concatenate(res[l][0])
+                if len(tg) == 0:
+                    continue
+                errs[v]["check_potential_rel_err_per_level"].append(M.rel_l2_error(np.concatenate(res[l][1]), c[tg]))
+                errs[v]["locals_rel_err_per_level"].append(
+                    M.check_norm_error(wl.p, l, np.concatenate(res[l][2]), lo[tg], root_width=wl_root_width(wl)))
     return {"value": inter / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{batches} batches of 16 random target boxes per level of the same workload, dense "
-                      f"FP64 definition (per-pair kernel evaluation + pseudo-inverse), {el:.1f} s",
+            "sample": f"{batches} batches of up to 16 random target boxes per level of the "
+                      f"{len(order)} largest instance(s), dense FP64 definition (per-pair kernel evaluation "
+                      f"+ pseudo-inverse), {el:.1f} s",
             "rel_err_vs_oracle": errs}
+
+
+def wl_root_width(wl):
+    return 2.0 if wl.name == "c4" else 1.0
 
 
 def run_reference(args):
     """The oracle (FP64, this host's cores) timed on bounded samples of the same workload."""
-    wl = W.c2()
+    insts, _, _, _, desc = workload_spec(args.workload, args.depth)
+    wl = max(insts, key=lambda w: w.n_boxes(w.depth))
     q64 = np.concatenate([wl.multipoles(l).reshape(-1) for l in wl.levels])
     per_step = args.ref_seconds
     for _ in range(args.warmup):
@@ -407,7 +518,7 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "levels": wl.levels},
+            "config": {"workload": desc, "levels": wl.levels},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"per step about {per_step:.0f} s of random target boxes (16 per level "
                                        f"per batch) of the same workload, dense FP64 definition"},
@@ -420,7 +531,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variants", default=",".join(VARIANTS))
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2 (default): the 1M-point workload; c3/c4/c5: precision, RHS-batching and instance-batching studies")
+    ap.add_argument("--variants", default=None, help="comma list of form-precision (default: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

@@ -231,11 +231,47 @@ static BlasLayout blas_layout(const m2l_plan_t *pl, long long total_rows, int pr
     return b;
 }
 
-static size_t fft_workspace_bytes(const m2l_plan_t *pl, int R, int precision) {
+// FFT workspace: check potentials and the pseudo-inverse intermediate for every row, in ws; the
+// spectra of one level and a chunk of right-hand sides, in a separate buffer.
+static long long max_clusters(const m2l_plan_t *pl) {
+    long long m = 0;
+    for (int l = 2; l <= pl->depth; ++l) m = std::max(m, pl->ldev[l].nclusters);
+    return m;
+}
+
+static size_t fft_rows_bytes(const m2l_plan_t *pl, int R, int precision) {
     const size_t e = precision == M2L_PREC_FP64 ? 8 : 4;
     const long long allrows = pl->total_rows * R;
-    const size_t spec_b = (size_t)pl->total_clusters * R * pl->F * 16 * e;
-    return 2 * al256(spec_b) + al256((size_t)allrows * pl->n * e) + al256((size_t)allrows * pl->rp * e);
+    return al256((size_t)allrows * pl->n * e) + al256((size_t)allrows * pl->rp * e);
+}
+
+static size_t fft_spec_bytes_per_rhs(const m2l_plan_t *pl, int precision) {
+    const size_t e = precision == M2L_PREC_FP64 ? 8 : 4;
+    return 2 * (size_t)max_clusters(pl) * pl->F * 16 * e;
+}
+
+// Right-hand sides the spectra buffer holds at once: as many as fit the plan's budget.
+static int fft_rhs_chunk(const m2l_plan_t *pl, int R, int precision) {
+    const size_t per = fft_spec_bytes_per_rhs(pl, precision);
+    if (per == 0) return R;
+    const size_t budget = pl->mem_budget ? pl->mem_budget : (size_t)8 << 30;
+    long long c = (long long)(budget / per);
+    if (c < 1) return 0;
+    return (int)std::min<long long>(R, c);
+}
+
+size_t workspace_estimate(const m2l_plan_t *pl, int form, int precision, int R) {
+    if (form == M2L_FORM_BLAS) {
+        const bool tc = precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3;
+        const size_t e = precision == M2L_PREC_FP64 ? 8 : 4;
+        const size_t rows = (size_t)pl->total_rows * R + 1;
+        size_t b = rows * (2 * (size_t)pl->kp + pl->rp) * e;
+        if (tc) b += 2 * rows * pl->kp * (precision == M2L_PREC_TF32X3 ? 4 : 2);
+        return b;
+    }
+    const int rc = fft_rhs_chunk(pl, R, precision);
+    if (rc < 1) return (size_t)-1;
+    return fft_rows_bytes(pl, R, precision) + (size_t)rc * fft_spec_bytes_per_rhs(pl, precision);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -249,7 +285,7 @@ static int apply_veps(const m2l_plan_t *pl, const DevOps &D, const T *Z, T *out,
 }
 
 template <class T>
-static int blas_group(std::vector<Run> &runs, int precision, cudaStream_t s) {
+static int blas_group(std::vector<Run> &runs, int precision, Workspace &ws, cudaStream_t s) {
     m2l_plan_t *own = runs[0].pl;
     const DevOps &D = own->dev[precision];
     const int n = own->n, kp = own->kp, rp = own->rp;
@@ -257,8 +293,8 @@ static int blas_group(std::vector<Run> &runs, int precision, cudaStream_t s) {
     long long ntiles = 0, total = 0;
     M2L_TRY(ensure_exec(own, runs, tc ? 128 : 64, &ntiles, &total));
     const BlasLayout lay = blas_layout(own, total, precision);
-    M2L_TRY(ensure_buffer(own->ws, lay.total()));
-    char *w = (char *)own->ws.buf;
+    M2L_TRY(ensure_buffer(ws, lay.total()));
+    char *w = (char *)ws.buf;
     T *qt = (T *)w;
     T *phit = (T *)(w + al256(lay.qt_b));
     T *Z = (T *)(w + al256(lay.qt_b) + al256(lay.ph_b));
@@ -308,9 +344,10 @@ static int blas_group(std::vector<Run> &runs, int precision, cudaStream_t s) {
     return M2L_OK;
 }
 
-// FFT form, one instance.
+// FFT form, one instance; levels one after another and right-hand sides in chunks that fit the
+// spectra buffer `spec` (the plan's own, or the one a batch shares).
 template <class T>
-static int fft_run(const Run &r, int precision, cudaStream_t s) {
+static int fft_run(const Run &r, int precision, Workspace &ws, Workspace &spec, cudaStream_t s) {
     m2l_plan_t *pl = r.pl;
     const DevOps &D = pl->dev[precision];
     const int n = pl->n, rp = pl->rp, g = pl->g, F = pl->F, p = pl->p, R = r.R;
@@ -318,36 +355,45 @@ static int fft_run(const Run &r, int precision, cudaStream_t s) {
         set_error("FFT form: grid %d does not fit shared memory in this precision", g);
         return M2L_EUNSUPPORTED;
     }
+    const int Rc = fft_rhs_chunk(pl, R, precision);
+    if (Rc < 1) {
+        set_error("FFT form: the spectra of one right-hand side of the largest level exceed the memory budget");
+        return M2L_ENOMEM;
+    }
     const long long base0 = pl->ldev[r.l0].base;
     const size_t e = sizeof(T);
-    const size_t spec_b = (size_t)pl->total_clusters * R * F * 16 * e;
+    const size_t half = al256((size_t)max_clusters(pl) * Rc * F * 16 * e);
     const size_t phi_b = (size_t)pl->total_rows * R * n * e;
-    M2L_TRY(ensure_buffer(pl->ws, fft_workspace_bytes(pl, R, precision)));
-    char *w = (char *)pl->ws.buf;
-    T *qhat = (T *)w;
-    T *phihat = (T *)(w + al256(spec_b));
-    T *Phi = (T *)(w + 2 * al256(spec_b));
-    T *Z = (T *)(w + 2 * al256(spec_b) + al256(phi_b));
+    M2L_TRY(ensure_buffer(ws, fft_rows_bytes(pl, R, precision)));
+    M2L_TRY(ensure_buffer(spec, 2 * half));
+    T *qhat = (T *)spec.buf;
+    T *phihat = (T *)((char *)spec.buf + half);
+    T *Phi = (T *)ws.buf;
+    T *Z = (T *)((char *)ws.buf + al256(phi_b));
     const T *q = (const T *)r.q;
     T *out = (T *)r.L;
     const bool check_out = pl->output == M2L_OUT_CHECK_POTENTIAL;
-    stage_begin(pl, M2L_STAGE_FFT_FORWARD);
-    cudaMemsetAsync(qhat, 0, spec_b, s);  // missing children keep zero spectra
-    stage_end(pl, 0);
     for (int l = r.l0; l <= r.l1; ++l) {
         LevelView L = view_of(pl->ldev[l]);
+        L.cbase = 0;       // spectra of this level only
+        L.R = R;           // row stride of densities and check potentials
         const T *ql = q + (L.base - base0) * R * n;
-        stage_begin(pl, M2L_STAGE_FFT_FORWARD);
-        M2L_TRY(launch_fft_forward<T>(L, R, p, n, g, pl->lattice_dev, (const T *)D.tw, ql, qhat, s));
-        stage_end(pl, 1);
-        stage_begin(pl, M2L_STAGE_HADAMARD);
-        M2L_TRY(launch_hadamard<T>(L, R, F, (const T *)D.Khat, qhat, phihat, s));
-        stage_end(pl, 1);
         T *dst = check_out ? out + (L.base - base0) * R * n : Phi + L.base * R * n;
-        stage_begin(pl, M2L_STAGE_FFT_INVERSE);
-        M2L_TRY(launch_fft_inverse<T>(L, R, p, n, g, pl->lattice_dev, (const T *)D.tw, phihat, dst, n,
-                                      check_out ? pl->accumulate : 0, s));
-        stage_end(pl, 1);
+        for (int r0 = 0; r0 < R; r0 += Rc) {
+            const int rc = std::min(Rc, R - r0);
+            L.row0 = r0;
+            stage_begin(pl, M2L_STAGE_FFT_FORWARD);
+            cudaMemsetAsync(qhat, 0, (size_t)L.nclusters * rc * F * 16 * e, s);  // missing children stay zero
+            M2L_TRY(launch_fft_forward<T>(L, rc, p, n, g, pl->lattice_dev, (const T *)D.tw, ql, qhat, s));
+            stage_end(pl, 1);
+            stage_begin(pl, M2L_STAGE_HADAMARD);
+            M2L_TRY(launch_hadamard<T>(L, rc, F, (const T *)D.Khat, qhat, phihat, s));
+            stage_end(pl, 1);
+            stage_begin(pl, M2L_STAGE_FFT_INVERSE);
+            M2L_TRY(launch_fft_inverse<T>(L, rc, p, n, g, pl->lattice_dev, (const T *)D.tw, phihat, dst, n,
+                                          check_out ? pl->accumulate : 0, s));
+            stage_end(pl, 1);
+        }
     }
     if (!check_out) {
         // F6: locals = V_eps (Ut_eps Phi)
@@ -359,13 +405,20 @@ static int fft_run(const Run &r, int precision, cudaStream_t s) {
     return M2L_OK;
 }
 
-static int run_group(std::vector<Run> &runs, int form, int precision, cudaStream_t s) {
+// Runs a group on `s`. Workspaces: the plans' own, or (ws, spec) shared by every group of a batch:
+// groups of a batch run one after another on one stream, so they can reuse the same memory.
+static int run_group(std::vector<Run> &runs, int form, int precision, Workspace *ws, Workspace *spec, cudaStream_t s) {
     if (form == M2L_FORM_BLAS) {
-        return precision == M2L_PREC_FP64 ? blas_group<double>(runs, precision, s) : blas_group<float>(runs, precision, s);
+        Workspace &w = ws ? *ws : runs[0].pl->ws;
+        return precision == M2L_PREC_FP64 ? blas_group<double>(runs, precision, w, s)
+                                          : blas_group<float>(runs, precision, w, s);
     }
     for (Run &r : runs) {
         r.rows = rows_of(r.pl, r.l0, r.l1, r.R);
-        int rc = precision == M2L_PREC_FP64 ? fft_run<double>(r, precision, s) : fft_run<float>(r, precision, s);
+        Workspace &w = ws ? *ws : r.pl->ws;
+        Workspace &sp = spec ? *spec : r.pl->spec;
+        int rc = precision == M2L_PREC_FP64 ? fft_run<double>(r, precision, w, sp, s)
+                                            : fft_run<float>(r, precision, w, sp, s);
         if (rc) return rc;
     }
     return M2L_OK;
@@ -379,7 +432,7 @@ int apply_device(m2l_plan_t *pl, const void *q, void *L, int level, int R) {
     reset_stage_log(pl);
     std::vector<Run> runs(1);
     runs[0] = Run{pl, q, L, R, l0, l1, 0, 0};
-    return run_group(runs, form, precision, pl->stream);
+    return run_group(runs, form, precision, nullptr, nullptr, pl->stream);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -421,23 +474,36 @@ int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void
                             pl->levels_version})
             sig.push_back(v);
     }
-    // allocate everything the pass needs before any capture
+    // allocate everything the pass needs before any capture: one batch workspace and one spectra
+    // buffer, each sized for the largest group or instance
+    size_t ws_need = 0, spec_need = 0;
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         m2l_plan_t *own = groups[gi][0].pl;
         if (forms[gi] == M2L_FORM_BLAS) {
             const bool tc = precs[gi] == M2L_PREC_TF32X3 || precs[gi] == M2L_PREC_BF16X3;
             long long nt = 0, total = 0;
             M2L_TRY(ensure_exec(own, groups[gi], tc ? 128 : 64, &nt, &total));
-            M2L_TRY(ensure_buffer(own->ws, blas_layout(own, total, precs[gi]).total()));
+            ws_need = std::max(ws_need, blas_layout(own, total, precs[gi]).total());
         } else {
-            for (const Run &r : groups[gi]) M2L_TRY(ensure_buffer(r.pl->ws, fft_workspace_bytes(r.pl, r.R, precs[gi])));
+            for (const Run &r : groups[gi]) {
+                ws_need = std::max(ws_need, fft_rows_bytes(r.pl, r.R, precs[gi]));
+                const int Rc = fft_rhs_chunk(r.pl, r.R, precs[gi]);
+                if (Rc < 1) {
+                    set_error("FFT form: the spectra of one right-hand side exceed the memory budget");
+                    return M2L_ENOMEM;
+                }
+                const size_t e = precs[gi] == M2L_PREC_FP64 ? 8 : 4;
+                spec_need = std::max(spec_need, 2 * al256((size_t)max_clusters(r.pl) * Rc * r.pl->F * 16 * e));
+            }
         }
     }
+    M2L_TRY(ensure_buffer(lead->batch_ws, ws_need));
+    if (spec_need) M2L_TRY(ensure_buffer(lead->spec, spec_need));
     // the graph bakes in every device pointer it was captured with
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         for (const Run &r : groups[gi]) {
             const DevOps &D = r.pl->dev[precs[gi]];
-            for (const void *ptr : {r.pl->ws.buf, r.pl->exec.levels, r.pl->exec.tiles, D.C, D.C_hi, D.C_lo, D.Khat, D.A, D.V})
+            for (const void *ptr : {lead->batch_ws.buf, lead->spec.buf, r.pl->exec.levels, r.pl->exec.tiles, D.C, D.C_hi, D.C_lo, D.Khat, D.A, D.V})
                 sig.push_back((long long)(uintptr_t)ptr);
             sig.push_back(r.pl->tc_group);
             sig.push_back(r.pl->fft_grid_opt);
@@ -469,7 +535,8 @@ int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void
         set_error("stream capture failed to begin: %s", cudaGetErrorString(cudaGetLastError()));
         rc = M2L_ECUDA;
     } else {
-        for (size_t gi = 0; gi < groups.size() && !rc; ++gi) rc = run_group(groups[gi], forms[gi], precs[gi], G.capture_stream);
+        for (size_t gi = 0; gi < groups.size() && !rc; ++gi)
+            rc = run_group(groups[gi], forms[gi], precs[gi], &lead->batch_ws, &lead->spec, G.capture_stream);
         cudaError_t e = cudaStreamEndCapture(G.capture_stream, &graph);
         if (!rc && e != cudaSuccess) {
             set_error("stream capture failed: %s", cudaGetErrorString(e));

@@ -3,13 +3,19 @@
 // A (form, precision) candidate is eligible when its stated relative error bound (Eq. 16 on the
 // check potential, measured over p = 4..10 and densities of one and of both signs, see the GPU
 // parity tests) and the truncation of the plan's rank are both at most the target. Eligible
-// candidates are timed on the plan's own box sets with the library's scratch data (the
-// arithmetic does not depend on the values) and the fastest is kept. FP64 candidates are timed
-// only when no reduced-precision candidate is eligible: on this GPU the FP64 units run at about
-// one sixtieth of the FP32 rate. Decisions are cached per (n_rhs, target).
+// candidates are timed with the library's scratch data (the arithmetic does not depend on the
+// values) on a proxy plan with the same order, rank and options and full levels up to depth
+// min(depth, 4): both forms cost a fixed amount per (target, source) pair, so their ratio carries
+// over to deeper trees. FP64 candidates are timed only when no reduced-precision candidate is
+// eligible: on this GPU the FP64 units run at about one sixtieth of the FP32 rate. Decisions are
+// cached per plan and process-wide per (device, p, n_rhs, rank_tol, target, requested form and
+// precision), so many instances of one kind tune once.
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -86,7 +92,12 @@ static int time_candidate(m2l_plan_t *pl, int form, int prec, int R, float *ms) 
     return rc;
 }
 
-static int tune(m2l_plan_t *pl, int R, int *form, int *prec) {
+using TuneKey = std::tuple<int, int, int, double, double, int, int, int>;
+static std::map<TuneKey, std::pair<int, int>> g_decisions;
+static std::mutex g_decisions_mu;
+
+// The real plan decides which candidates fit its memory budget; the proxy times them.
+static int tune_on(m2l_plan_t *pl, const m2l_plan_t *real, int R, int *form, int *prec) {
     std::vector<std::pair<int, int>> fast, slow;
     const int forms[2] = {M2L_FORM_BLAS, M2L_FORM_FFT};
     const int precs[4] = {M2L_PREC_BF16X3, M2L_PREC_TF32X3, M2L_PREC_FP32, M2L_PREC_FP64};
@@ -96,6 +107,8 @@ static int tune(m2l_plan_t *pl, int R, int *form, int *prec) {
         for (int pr : precs) {
             if (pl->precision != M2L_PREC_AUTO && pl->precision != pr) continue;
             if (!eligible(pl, f, pr)) continue;
+            const size_t need = workspace_estimate(real, f, pr, R);
+            if (real->mem_budget && need > 2 * real->mem_budget) continue;
             (pr == M2L_PREC_FP64 ? slow : fast).push_back({f, pr});
         }
     }
@@ -119,6 +132,39 @@ static int tune(m2l_plan_t *pl, int R, int *form, int *prec) {
     }
     *form = bf;
     *prec = bp;
+    return M2L_OK;
+}
+
+static int tune(m2l_plan_t *pl, int R, int *form, int *prec) {
+    // box counts enter through the memory check, so the decision is shared per tree size too
+    const TuneKey key{pl->device, pl->p * 1000 + pl->depth, R, pl->rank_tol, pl->target_tol, pl->form, pl->precision,
+                      pl->fft_grid_opt};
+    {
+        std::lock_guard<std::mutex> g(g_decisions_mu);
+        auto it = g_decisions.find(key);
+        if (it != g_decisions.end()) {
+            *form = it->second.first;
+            *prec = it->second.second;
+            return M2L_OK;
+        }
+    }
+    m2l_plan_t *proxy = m2l_plan(std::min(pl->depth, 4), pl->p, pl->kernel, pl->rank_tol);
+    if (!proxy) return M2L_ENOMEM;
+    proxy->form = pl->form;
+    proxy->precision = pl->precision;
+    proxy->target_tol = pl->target_tol;
+    proxy->fft_grid_opt = pl->fft_grid_opt;
+    proxy->tc_group = pl->tc_group;
+    proxy->stream = pl->stream;
+    if (build_level_tables(pl) || build_pinv(pl)) return M2L_ECUDA;
+    if (pl->rank_tol > 0 || pl->form != M2L_FORM_FFT) build_blas_host(pl);
+    if (pl->form != M2L_FORM_BLAS) build_fft_host(pl);
+    int rc = tune_on(proxy, pl, R, form, prec);
+    cudaStreamSynchronize(proxy->stream);
+    m2l_destroy(proxy);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> g(g_decisions_mu);
+    g_decisions[key] = {*form, *prec};
     return M2L_OK;
 }
 

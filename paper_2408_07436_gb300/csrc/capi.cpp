@@ -83,6 +83,9 @@ m2l_plan_t *m2l_plan(int depth, int p, int kernel, double rank_tol) {
         pl->device = -1;
     } else {
         cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) pl->mem_budget = total_b / 4;
+        else cudaGetLastError();
     }
     return pl;
 }

@@ -124,7 +124,9 @@ struct m2l_plan_s {
     bool levels_dirty = true;
     m2l::LevelDev ldev[m2l::kMaxDepth + 1];
     long long total_rows = 0, total_clusters = 0;
-    m2l::Workspace ws, stage_in, stage_out;
+    m2l::Workspace ws, spec, stage_in, stage_out;   // spec: FFT spectra (one level, a chunk of rhs)
+    m2l::Workspace batch_ws;                        // workspace shared by the groups of a batch it leads
+    size_t mem_budget = 0;                          // bytes one workspace may take (1/4 of the GPU)
     m2l::ExecCache exec;
     m2l::BatchGraph batch_graph;
     long long levels_version = 0;                  // bumped whenever a box set changes
@@ -155,6 +157,7 @@ int resolve_form(const m2l_plan_t *pl, int R, int *form, int *precision);
 double stated_bound(int form, int precision, int p);
 // apply.cu
 int prepare_plan(m2l_plan_t *pl, int form, int precision);
+size_t workspace_estimate(const m2l_plan_t *pl, int form, int precision, int R);
 int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void *const *L, const int *R);
 void free_exec(m2l_plan_t *pl);
 void stage_begin(m2l_plan_t *pl, int stage);

@@ -240,7 +240,9 @@ int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, lon
 // ----------------------------------------------------------------------------------------------
 // FFT form. Lattice entries are packed a << 16 | b << 8 | c. Spectra are stored per
 // (cluster, rhs) as [F][8] complex: the eight siblings of a cluster interleaved by frequency
-// (App. A.1 steps 3 and 5: "frequency order").
+// (App. A.1 steps 3 and 5: "frequency order"). A launch covers R right-hand sides; rows of the
+// densities and check potentials are b * L.R + L.row0 + r, so a launch can take a chunk of the
+// instance's right-hand sides, and spectra of cluster c sit at (L.cbase + c) * R + r.
 
 __device__ inline uint32_t parent_linear(uint32_t xyz, int Np) {
     int x = (xyz & 1023) >> 1, y = ((xyz >> 10) & 1023) >> 1, z = ((xyz >> 20) & 1023) >> 1;
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(128) fft_forward_kernel(LevelView L, int R, in
     for (int i = tid; i < 2 * g; i += nt) tws[i] = tw[i];
     for (int i = tid; i < p * p * p; i += nt) xs[i] = T(0);
     __syncthreads();
-    const T *qrow = q + (b * R + r) * (long long)n;
+    const T *qrow = q + (b * L.R + L.row0 + r) * (long long)n;  // L.R: rhs stride, L.row0: first rhs
     for (int i = tid; i < n; i += nt) {
         int lat = lattice[i];
         int a = lat >> 16, bb = (lat >> 8) & 255, c = lat & 255;
@@ -501,7 +503,7 @@ __global__ void __launch_bounds__(128) fft_inverse_kernel(LevelView L, int R, in
     // along z (Hermitian): out = Re Z2[0] + sum_{kz>=1} w_kz Re(Z2[kz] conj(w^(c kz))), at surface points
     const T scale = T(1) / (T)((long long)g * g * g);
     const bool even = (g % 2) == 0;
-    T *outrow = phi + (b * R + r) * ldphi;
+    T *outrow = phi + (b * L.R + L.row0 + r) * ldphi;
     for (int i = tid; i < n; i += nt) {
         int lat = lattice[i];
         int a = lat >> 16, bb = (lat >> 8) & 255, c = lat & 255;

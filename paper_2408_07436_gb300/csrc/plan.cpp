@@ -545,6 +545,10 @@ void free_device(m2l_plan_t *pl) {
     for (int l = 0; l <= kMaxDepth; ++l) free_level(pl->ldev[l]);
     if (pl->ws.buf) cudaFree(pl->ws.buf);
     if (pl->stage_in.buf) cudaFree(pl->stage_in.buf);
+    if (pl->spec.buf) cudaFree(pl->spec.buf);
+    pl->spec = {};
+    if (pl->batch_ws.buf) cudaFree(pl->batch_ws.buf);
+    pl->batch_ws = {};
     if (pl->stage_out.buf) cudaFree(pl->stage_out.buf);
     free_exec(pl);
     if (pl->lattice_dev) cudaFree(pl->lattice_dev);

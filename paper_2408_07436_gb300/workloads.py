@@ -7,7 +7,7 @@ CUDA path and the oracle receive what it returns.
 Workloads (seed = 24080 + index):
   c1  8,000 points U[0,1)^3, densities U[0,1), depth 3, p = 4, 1 RHS, full rank.
   c2  1,000,000 points U[0,1)^3, densities U[-1,1], depth 5, p = 6, 1 RHS, rank_tol 1e-7.
-  c3  8,000,000 points U[0,1)^3, densities U[0,1), depth 6, p = 8, 1 RHS.
+  c3  8,000,000 points U[0,1)^3, densities U[0,1), depth 6, p = 8, 1 RHS, BLAS rank_tol 1e-7.
   c4  2,000,000 points on the unit sphere (normalised Gaussian vectors), root [-1,1]^3,
       depth 6, p = 6, 32 RHS, densities N(0,1), empty boxes pruned.
   c5  64 instances: N = round(exp(U[ln 1e4, ln 2e6])) points U[0,1)^3, depth U{3..6},
@@ -130,7 +130,7 @@ def c2(rank_tol: float = 1e-7, depth: int = 5) -> Workload:
 
 
 def c3(bin_points: bool = True) -> Workload:
-    return uniform_cube("c3", 3, 8_000_000, 6, 8, 1, 0.0, "u01", bin_points)
+    return uniform_cube("c3", 3, 8_000_000, 6, 8, 1, 1e-7, "u01", bin_points)
 
 
 def c4() -> Workload:
