@@ -44,7 +44,8 @@ from paper_2408_07436_gb300 import workloads as W  # noqa: E402
 VARIANTS = ["blas-fp64", "blas-fp32", "blas-tf32x3", "blas-bf16x3", "fft-fp64", "fft-fp32"]
 METRIC = "M2L interactions/s and % roofline: mixed+batched vs FP64 GPU at stated rel err"
 UNIT = "interactions/s"
-WORKLOAD = "laplace3d-m2l uniform-cube 1M points depth5 p6 1rhs blas(rank_tol 1e-7)+fft fp64+fp32+tf32x3+bf16x3"
+WORKLOAD = ("laplace3d-m2l uniform-cube 1M points depth5 p6 1rhs blas(rank_tol 1e-7)+fft(grid 11^3) "
+            "fp64+fp32+tf32x3+bf16x3")
 
 # Nominal per-GPU figures (GB300) used where no measured peak exists.
 NOMINAL_FP64_TFLOPS = 1.25       # FP64 (vector and tensor) dense
@@ -182,6 +183,8 @@ def run_ours(args, rank, world, local_rank):
         for i, wl in enumerate(insts):
             tol = wl.rank_tol if form in ("blas", "auto") else 0.0
             pl = lib.Plan(wl.depth, wl.p, tol, form=form, precision=prec).set(timing=0 if batched else 1)
+            if form == "fft" and wl.fft_grid:
+                pl.set(fft_grid=wl.fft_grid)
             if target_tol is not None:
                 pl.set(target_tol=target_tol)
             for l in wl.levels:

@@ -36,8 +36,6 @@ def _compile(src: str) -> str:
     if os.path.exists(obj) and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
         return obj
     cmd = [nvcc(), "-c", path, "-o", obj] + _flags()
-    if src.endswith(".cpp"):
-        cmd += ["-x", "cu"] if False else []
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -12,10 +12,9 @@
 namespace m2l {
 
 size_t fft_smem_bytes(int p, int g, int elt);  // kernels_simt.cu
-int ensure_tc_constants(int device);           // kernels_tc.cu
 template <class T>
-int launch_contract_tc(m2l_plan_t *pl, const LevelView *lv, const ContractTile *tiles, long long ntiles, const void *qt_hi,
-                       const void *qt_lo, long long zero_row, T *phit, int precision, cudaStream_t s);
+int launch_contract_tc(m2l_plan_t *pl, const LevelView *lv, const ContractTile *tiles, long long ntiles, const int *tvl,
+                       const void *qt_hi, const void *qt_lo, long long zero_row, T *phit, int precision, cudaStream_t s);
 int launch_split_rows(const float *src, long long rows, int kp, void *hi, void *lo, int precision, cudaStream_t s);
 
 #define M2L_TRY(x)           \
@@ -100,7 +99,6 @@ int prepare_plan(m2l_plan_t *pl, int form, int precision) {
         return M2L_EUNSUPPORTED;
     }
     M2L_TRY(upload_ops(pl, precision, form));
-    if (precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3) M2L_TRY(ensure_tc_constants(pl->device));
     if (form == M2L_FORM_FFT) M2L_TRY(ensure_lattice(pl));
     if (!pl->dev_status) {
         if (cudaMalloc((void **)&pl->dev_status, sizeof(int)) != cudaSuccess) {
@@ -148,7 +146,46 @@ static long long rows_of(const m2l_plan_t *pl, int l0, int l1, int R) {
     return r;
 }
 
-// Device level views and contraction tiles of a group, cached on the group's owner plan.
+// Transfer vectors of target octant o in the order the contraction visits them (dx slowest),
+// packed as the kernels read them (see ContractTile).
+static int octant_table(int o, int *tab) {
+    const int cx = o & 1, cy = (o >> 1) & 1, cz = (o >> 2) & 1;
+    int e = 0;
+    for (int dx = -2 - cx; dx <= 3 - cx; ++dx)
+        for (int dy = -2 - cy; dy <= 3 - cy; ++dy)
+            for (int dz = -2 - cz; dz <= 3 - cz; ++dz) {
+                const int ti = transfer_index(dx, dy, dz);
+                if (ti >= 0) tab[e++] = (dx + 3) | ((dy + 3) << 4) | ((dz + 3) << 8) | (ti << 12);
+            }
+    return e;
+}
+
+// The entries of `tab` that reach an existing box from at least one target of the tile (the
+// targets perm[oct_start + j / R] for its rows j); at least one entry, so the tile's rows are
+// always written.
+static int tile_vectors(const LevelDev &D, int R, const ContractTile &c, const int *tab, int *out) {
+    const int N = 1 << D.level;
+    const long long j0 = c.j0 / R, j1 = (c.j0 + c.rows - 1) / R;
+    int cnt = 0;
+    for (int e = 0; e < kPerOctant; ++e) {
+        const int pk = tab[e];
+        const int dx = (pk & 15) - 3, dy = ((pk >> 4) & 15) - 3, dz = ((pk >> 8) & 15) - 3;
+        for (long long j = j0; j <= j1; ++j) {
+            const uint32_t p = D.h_xyz[D.h_perm[D.oct_start[c.oct] + j]];
+            const int x = (int)(p & 1023) + dx, y = (int)((p >> 10) & 1023) + dy, z = (int)((p >> 20) & 1023) + dz;
+            if (x < 0 || y < 0 || z < 0 || x >= N || y >= N || z >= N) continue;
+            if (D.h_slot[((size_t)z * N + y) * N + x] >= 0) {
+                out[cnt++] = pk;
+                break;
+            }
+        }
+    }
+    if (cnt == 0) out[cnt++] = tab[0];
+    return cnt;
+}
+
+// Device level views, contraction tiles and the tiles' transfer vector lists of a group, cached on
+// the group's owner plan.
 static int ensure_exec(m2l_plan_t *owner, std::vector<Run> &runs, int rows_per_tile, long long *ntiles_out,
                        long long *total_rows_out) {
     std::vector<long long> key;
@@ -174,6 +211,8 @@ static int ensure_exec(m2l_plan_t *owner, std::vector<Run> &runs, int rows_per_t
     }
     std::vector<LevelView> views;
     std::vector<ContractTile> tiles;
+    std::vector<const LevelDev *> tile_level;
+    std::vector<int> tile_R;
     for (const Run &r : runs) {
         for (int l = r.l0; l <= r.l1; ++l) {
             const LevelDev &D = r.pl->ldev[l];
@@ -185,29 +224,60 @@ static int ensure_exec(m2l_plan_t *owner, std::vector<Run> &runs, int rows_per_t
             for (int oct = 0; oct < 8; ++oct) {
                 long long segrows = (D.oct_start[oct + 1] - D.oct_start[oct]) * (long long)r.R;
                 for (long long j0 = 0; j0 < segrows; j0 += rows_per_tile) {
-                    ContractTile c;
+                    ContractTile c{};
                     c.lev = lev;
                     c.oct = oct;
                     c.j0 = (int)j0;
                     c.rows = (int)std::min<long long>(rows_per_tile, segrows - j0);
                     tiles.push_back(c);
+                    tile_level.push_back(&D);
+                    tile_R.push_back(r.R);
                 }
             }
         }
     }
+    // transfer vector lists, built per tile in parallel, then packed
+    int tab[8][kPerOctant];
+    for (int o = 0; o < 8; ++o) octant_table(o, tab[o]);
+    const long long nt = (long long)tiles.size();
+    std::vector<int> lists((size_t)nt * kPerOctant);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long long i = 0; i < nt; ++i)
+        tiles[i].ntv = tile_vectors(*tile_level[i], tile_R[i], tiles[i], tab[tiles[i].oct], &lists[(size_t)i * kPerOctant]);
+    // longest lists first, so the last wave of CTAs holds the shortest tiles
+    std::vector<long long> order(nt);
+    for (long long i = 0; i < nt; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](long long x, long long y) { return tiles[x].ntv > tiles[y].ntv; });
+    std::vector<ContractTile> sorted(nt);
+    std::vector<int> packed;
+    packed.reserve(lists.size());
+    for (long long i = 0; i < nt; ++i) {
+        ContractTile c = tiles[order[i]];
+        c.tv0 = (long long)packed.size();
+        const int *src = &lists[(size_t)order[i] * kPerOctant];
+        packed.insert(packed.end(), src, src + c.ntv);
+        sorted[i] = c;
+    }
+    tiles.swap(sorted);
+    lists.swap(packed);
+    const long long nv = (long long)lists.size();
     if (E.levels) cudaFree(E.levels);
     if (E.tiles) cudaFree(E.tiles);
-    E.levels = E.tiles = nullptr;
+    if (E.tvl) cudaFree(E.tvl);
+    E.levels = E.tiles = E.tvl = nullptr;
     E.key.clear();
     if (cudaMalloc(&E.levels, std::max<size_t>(1, views.size()) * sizeof(LevelView)) != cudaSuccess ||
-        cudaMalloc(&E.tiles, std::max<size_t>(1, tiles.size()) * sizeof(ContractTile)) != cudaSuccess) {
+        cudaMalloc(&E.tiles, std::max<size_t>(1, tiles.size()) * sizeof(ContractTile)) != cudaSuccess ||
+        cudaMalloc(&E.tvl, std::max<size_t>(1, (size_t)nv) * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         set_error("tile list allocation failed");
         return M2L_ENOMEM;
     }
     cudaMemcpy(E.levels, views.data(), views.size() * sizeof(LevelView), cudaMemcpyHostToDevice);
     if (!tiles.empty()) cudaMemcpy(E.tiles, tiles.data(), tiles.size() * sizeof(ContractTile), cudaMemcpyHostToDevice);
-    E.ntiles = (long long)tiles.size();
+    if (nv) cudaMemcpy(E.tvl, lists.data(), (size_t)nv * sizeof(int), cudaMemcpyHostToDevice);
+    E.ntiles = nt;
+    E.nvectors = nv;
     E.key = key;
     *ntiles_out = E.ntiles;
     return M2L_OK;
@@ -309,9 +379,10 @@ static int blas_group(std::vector<Run> &runs, int precision, Workspace &ws, cuda
     // B2: one contraction launch over the tiles of every instance
     const LevelView *lv = (const LevelView *)own->exec.levels;
     const ContractTile *tl = (const ContractTile *)own->exec.tiles;
+    const int *tvl = (const int *)own->exec.tvl;
     if (!tc) {
         stage_begin(own, M2L_STAGE_CONTRACT);
-        M2L_TRY(launch_contract_simt<T>(lv, tl, ntiles, qt, (const T *)D.C, kp, total, phit, s));
+        M2L_TRY(launch_contract_simt<T>(lv, tl, ntiles, tvl, qt, (const T *)D.C, kp, total, phit, s));
         stage_end(own, 1);
     } else {
         if constexpr (sizeof(T) == 4) {
@@ -319,7 +390,7 @@ static int blas_group(std::vector<Run> &runs, int precision, Workspace &ws, cuda
             M2L_TRY(launch_split_rows((const float *)qt, total + 1, kp, hi, lo, precision, s));
             stage_end(own, 1);
             stage_begin(own, M2L_STAGE_CONTRACT);
-            M2L_TRY(launch_contract_tc<T>(own, lv, tl, ntiles, hi, lo, total, phit, precision, s));
+            M2L_TRY(launch_contract_tc<T>(own, lv, tl, ntiles, tvl, hi, lo, total, phit, precision, s));
             stage_end(own, 1);
         } else {
             set_error("split tensor-core precisions operate on FP32 data");
@@ -503,7 +574,7 @@ int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         for (const Run &r : groups[gi]) {
             const DevOps &D = r.pl->dev[precs[gi]];
-            for (const void *ptr : {lead->batch_ws.buf, lead->spec.buf, r.pl->exec.levels, r.pl->exec.tiles, D.C, D.C_hi, D.C_lo, D.Khat, D.A, D.V})
+            for (const void *ptr : {lead->batch_ws.buf, lead->spec.buf, r.pl->exec.levels, r.pl->exec.tiles, r.pl->exec.tvl, D.C, D.C_hi, D.C_lo, D.Khat, D.A, D.V})
                 sig.push_back((long long)(uintptr_t)ptr);
             sig.push_back(r.pl->tc_group);
             sig.push_back(r.pl->fft_grid_opt);
@@ -573,6 +644,7 @@ int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void
 void free_exec(m2l_plan_t *pl) {
     if (pl->exec.levels) cudaFree(pl->exec.levels);
     if (pl->exec.tiles) cudaFree(pl->exec.tiles);
+    if (pl->exec.tvl) cudaFree(pl->exec.tvl);
     pl->exec = ExecCache();
     if (pl->batch_graph.exec) cudaGraphExecDestroy(pl->batch_graph.exec);
     if (pl->batch_graph.capture_stream) cudaStreamDestroy(pl->batch_graph.capture_stream);

@@ -80,7 +80,9 @@ struct ExecCache {
     std::vector<long long> key;
     void *levels = nullptr;
     void *tiles = nullptr;
+    void *tvl = nullptr;               // transfer vector lists of the tiles
     long long ntiles = 0;
+    long long nvectors = 0;            // (tile, transfer vector) products the contraction runs
 };
 
 // The CUDA graph of the last batch pass led by this plan and the arguments it was captured for.

@@ -26,12 +26,19 @@ struct LevelView {
 
 // One CTA of the contraction: rows [j0, j0 + rows) of the octant segment `oct` of level view
 // `lev` (index into a device array of LevelView), where segment row j is
-// (target perm[oct_start + j / R], rhs j % R).
+// (target perm[oct_start + j / R], rhs j % R). The tile visits the ntv transfer vectors
+// tvl[tv0 .. tv0 + ntv) of a device list: those of the octant (189 at most, Sec. 3.1) that reach
+// an existing source from at least one of its targets, each packed as
+// (dx + 3) | (dy + 3) << 4 | (dz + 3) << 8 | (index in [-3,3]^3 \ [-1,1]^3, x slowest) << 12.
+// A tile with no source at all keeps one entry, so its rows are still written (as zeros).
 struct ContractTile {
     int lev;
     int oct;
     int j0;
     int rows;
+    long long tv0;
+    int ntv;
+    int pad_;
 };
 
 // Y[r][o] (+)= sum_i X[r][i] W[o][i]; X rows x K (row stride ldx), W O x K (stride ldw).
@@ -40,10 +47,11 @@ int launch_gemm_xwt(const T *X, long long ldx, const T *W, long long ldw, T *Y, 
                     long long rows, int O, int K, int acc, cudaStream_t s);
 
 // B2 on CUDA cores: phit[row0 + b R + r][:] = sum_t C_t qt[row0 + src R + r][:] over the tiles,
-// `levels` a device array of LevelView indexed by ContractTile::lev.
+// `levels` a device array of LevelView indexed by ContractTile::lev, `tvl` the tiles' transfer
+// vector lists.
 template <class T>
-int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, long long ntiles, const T *qt, const T *C,
-                         int kp, long long zero_row, T *phit, cudaStream_t s);
+int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
+                         const T *qt, const T *C, int kp, long long zero_row, T *phit, cudaStream_t s);
 
 // FFT form, one level at a time.
 template <class T>

@@ -132,15 +132,20 @@ int launch_gemm_xwt(const T *X, long long ldx, const T *W, long long ldw, T *Y, 
 }
 
 // ----------------------------------------------------------------------------------------------
-// B2 on CUDA cores: for a tile of (target, rhs) rows of one octant, accumulate over the 189
-// transfer vectors of that octant phit[row] += C_t qt[source(row, t)] (Sec. 3.2 steps 3-5 fused:
-// sources are gathered on the fly, nothing is materialised per transfer vector).
-template <class T>
+// B2 on CUDA cores: for a tile of (target, rhs) rows of one octant, accumulate over the transfer
+// vectors of that octant phit[row] += C_t qt[source(row, t)] (Sec. 3.2 steps 3-5 fused: sources
+// are gathered on the fly, nothing is materialised per transfer vector). The tile's list holds
+// only the transfer vectors that reach a source from one of its targets.
+// A CTA computes 64 rows x 16 TN columns, a thread 4 rows x TN columns; TN is picked per rank so
+// the column blocks cover k_pad with little padding (every padded column costs as much as a real
+// one on the FP64 units, which bound this kernel).
+template <class T, int TN>
 __global__ void __launch_bounds__(256) contract_simt_kernel(const LevelView *__restrict__ levels,
                                                             const ContractTile *__restrict__ tiles,
+                                                            const int *__restrict__ tvl,
                                                             const T *__restrict__ qt, const T *__restrict__ C, int kp,
                                                             long long zero_row, T *__restrict__ phit) {
-    constexpr int BM = 64, BN = 64, BK = 16;
+    constexpr int BM = 64, BN = 16 * TN, BK = 16;
     __shared__ T Xs[BK][BM + 4];
     __shared__ T Ws[BK][BN + 4];
     __shared__ long long src_row[BM];
@@ -164,76 +169,101 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(const LevelView *__r
             tgt_xyz[tid] = 0;
         }
     }
-    T a[4][4];
+    T a[4][TN];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) a[i][j] = T(0);
-    const int cx = tile.oct & 1, cy = (tile.oct >> 1) & 1, cz = (tile.oct >> 2) & 1;
+        for (int j = 0; j < TN; ++j) a[i][j] = T(0);
     const int N = L.N;
-    for (int dx = -2 - cx; dx <= 3 - cx; ++dx)
-        for (int dy = -2 - cy; dy <= 3 - cy; ++dy)
-            for (int dz = -2 - cz; dz <= 3 - cz; ++dz) {
-                int ti = c_tidx[dx + 3][dy + 3][dz + 3];
-                if (ti < 0) continue;  // adjacent: near field
-                __syncthreads();       // previous src_row fully consumed
-                if (tid < BM) {
-                    long long sr = zero_row;
-                    if (tgt_b[tid] >= 0) {
-                        uint32_t p = tgt_xyz[tid];
-                        int x = (int)(p & 1023) + dx, y = (int)((p >> 10) & 1023) + dy, z = (int)((p >> 20) & 1023) + dz;
-                        if (x >= 0 && y >= 0 && z >= 0 && x < N && y < N && z < N) {
-                            int s = L.slot[((long long)z * N + y) * N + x];
-                            if (s >= 0) sr = L.row0 + (long long)s * R + tgt_r[tid];
-                        }
-                    }
-                    src_row[tid] = sr;
-                }
-                __syncthreads();
-                const T *Ct = C + (long long)ti * kp * kp;
-                for (int k0 = 0; k0 < kp; k0 += BK) {
-                    for (int e = tid; e < BM * BK; e += 256) {
-                        int r = e / BK, kk = e % BK;
-                        Xs[kk][r] = qt[src_row[r] * kp + k0 + kk];
-                        int gc = col0 + r;
-                        Ws[kk][r] = gc < kp ? Ct[(long long)gc * kp + k0 + kk] : T(0);
-                    }
-                    __syncthreads();
-#pragma unroll
-                    for (int kk = 0; kk < BK; ++kk) {
-                        T xa[4], wb[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            xa[i] = Xs[kk][ty * 4 + i];
-                            wb[i] = Ws[kk][tx * 4 + i];
-                        }
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) a[i][j] = fma(xa[i], wb[j], a[i][j]);
-                    }
-                    __syncthreads();
+    for (int v = 0; v < tile.ntv; ++v) {
+        const int pk = tvl[tile.tv0 + v];
+        const int dx = (pk & 15) - 3, dy = ((pk >> 4) & 15) - 3, dz = ((pk >> 8) & 15) - 3;
+        const int ti = pk >> 12;
+        __syncthreads();  // previous src_row fully consumed
+        if (tid < BM) {
+            long long sr = zero_row;
+            if (tgt_b[tid] >= 0) {
+                uint32_t p = tgt_xyz[tid];
+                int x = (int)(p & 1023) + dx, y = (int)((p >> 10) & 1023) + dy, z = (int)((p >> 20) & 1023) + dz;
+                if (x >= 0 && y >= 0 && z >= 0 && x < N && y < N && z < N) {
+                    int s = L.slot[((long long)z * N + y) * N + x];
+                    if (s >= 0) sr = L.row0 + (long long)s * R + tgt_r[tid];
                 }
             }
+            src_row[tid] = sr;
+        }
+        __syncthreads();
+        const T *Ct = C + (long long)ti * kp * kp;
+        for (int k0 = 0; k0 < kp; k0 += BK) {
+            for (int e = tid; e < BM * BK; e += 256) {
+                const int r = e / BK, kk = e % BK;
+                Xs[kk][r] = qt[src_row[r] * kp + k0 + kk];
+            }
+            for (int e = tid; e < BN * BK; e += 256) {
+                const int c = e / BK, kk = e % BK, gc = col0 + c;
+                Ws[kk][c] = gc < kp ? Ct[(long long)gc * kp + k0 + kk] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                T xa[4], wb[TN];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) xa[i] = Xs[kk][ty * 4 + i];
+#pragma unroll
+                for (int j = 0; j < TN; ++j) wb[j] = Ws[kk][tx * TN + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) a[i][j] = fma(xa[i], wb[j], a[i][j]);
+            }
+            __syncthreads();
+        }
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         int r = ty * 4 + i;
         if (r >= tile.rows) continue;
         long long orow = L.row0 + (long long)tgt_b[r] * R + tgt_r[r];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int c = col0 + tx * 4 + j;
+        for (int j = 0; j < TN; ++j) {
+            int c = col0 + tx * TN + j;
             if (c < kp) phit[orow * kp + c] = a[i][j];
         }
     }
 }
 
+// Columns per thread for a rank: the fewest column blocks of at most 16 * max_tn columns, then
+// the narrowest blocks that still cover k_pad.
+inline int contract_tn(int kp, int max_tn) {
+    const int units = (kp + 15) / 16;
+    const int blocks = (units + max_tn - 1) / max_tn;
+    return (units + blocks - 1) / blocks;
+}
+
+template <class T, int TN>
+static void launch_contract_tn(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
+                               const T *qt, const T *C, int kp, long long zero_row, T *phit, cudaStream_t s) {
+    dim3 grid((unsigned)ntiles, (unsigned)((kp + 16 * TN - 1) / (16 * TN)));
+    contract_simt_kernel<T, TN><<<grid, 256, 0, s>>>(levels, tiles, tvl, qt, C, kp, zero_row, phit);
+}
+
 template <class T>
-int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, long long ntiles, const T *qt, const T *C,
-                         int kp, long long zero_row, T *phit, cudaStream_t s) {
+int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
+                         const T *qt, const T *C, int kp, long long zero_row, T *phit, cudaStream_t s) {
     if (ntiles <= 0) return M2L_OK;
-    dim3 grid((unsigned)ntiles, (unsigned)((kp + 63) / 64));
-    contract_simt_kernel<T><<<grid, 256, 0, s>>>(levels, tiles, qt, C, kp, zero_row, phit);
+    // FP64: one block of up to 192 columns keeps the FP64 units fed from registers; FP32 keeps
+    // more warps resident with narrower blocks
+    const int tn = contract_tn(kp, sizeof(T) == 8 ? 12 : 8);
+    switch (tn) {
+#define M2L_TN(n) \
+    case n: launch_contract_tn<T, n>(levels, tiles, ntiles, tvl, qt, C, kp, zero_row, phit, s); break;
+        M2L_TN(1) M2L_TN(2) M2L_TN(3) M2L_TN(4) M2L_TN(5) M2L_TN(6)
+        M2L_TN(7) M2L_TN(8) M2L_TN(9) M2L_TN(10) M2L_TN(11) M2L_TN(12)
+#undef M2L_TN
+        default:
+            set_error("contraction: no column tiling for k_pad = %d", kp);
+            return M2L_EINVAL;
+    }
     return check_launch("contract");
 }
 
@@ -546,8 +576,8 @@ size_t fft_smem_bytes(int p, int g, int elt) {
 #define M2L_INSTANTIATE(T)                                                                              \
     template int launch_gemm_xwt<T>(const T *, long long, const T *, long long, T *, long long, long long, \
                                     int, int, int, cudaStream_t);                                       \
-    template int launch_contract_simt<T>(const LevelView *, const ContractTile *, long long, const T *, const T *, \
-                                         int, long long, T *, cudaStream_t);                            \
+    template int launch_contract_simt<T>(const LevelView *, const ContractTile *, long long, const int *,       \
+                                         const T *, const T *, int, long long, T *, cudaStream_t);      \
     template int launch_fft_forward<T>(const LevelView &, int, int, int, int, const int *, const T *,   \
                                        const T *, T *, cudaStream_t);                                   \
     template int launch_hadamard<T>(const LevelView &, int, int, const T *, const T *, T *, cudaStream_t); \

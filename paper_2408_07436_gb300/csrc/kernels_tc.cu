@@ -1,6 +1,7 @@
 // B2 on the 5th-generation tensor cores (tcgen05) for the split precisions TF32x3 and BF16x3.
 //
-// phi~[row] = sum over the 189 transfer vectors t of the row's octant of C_t q~[source(row, t)],
+// phi~[row] = sum over the transfer vectors t of the row's octant (189 at most; a tile visits only
+// those that reach a source from one of its targets) of C_t q~[source(row, t)],
 // every operand split as x = x_hi + x_lo and each product taken as hi*hi + hi*lo + lo*hi with FP32
 // accumulation in tensor memory (the dropped lo*lo term is below the FP32 rounding of the
 // result for TF32 pieces, about 2^-16 relative for BF16 pieces).
@@ -37,6 +38,7 @@ constexpr long long kWaitLimit = 1LL << 24;
 struct TcParams {
     const LevelView *lv;               // device array indexed by ContractTile::lev
     const ContractTile *tiles;
+    const int *tvl;                    // the tiles' packed transfer vector lists
     long long ntiles;
     const unsigned char *qhi, *qlo;   // [(rows + 1)][kp] elements
     long long zero_row;
@@ -48,10 +50,6 @@ struct TcParams {
     int group;                         // transfer vectors per partial sum (drain interval)
     int *status;
 };
-
-// For target octant o, entry e < 189: the transfer vector (dx, dy, dz) packed as
-// (dx + 3) | (dy + 3) << 4 | (dz + 3) << 8 and its index in [-3,3]^3 \ [-1,1]^3 (x slowest) << 12.
-__constant__ int c_oct_tv[8][kPerOctant];
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -204,9 +202,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int i = 0; i < 8; ++i) ri[i] = row_info(L, T, rgrp + 16 * i);
             const int N = L.N;
-            // source rows of the 8 rows this thread feeds, for table entry e
+            // source rows of the 8 rows this thread feeds, for list entry e of the tile
             auto sources = [&](int e, long long (&src)[8]) {
-                const int pk = c_oct_tv[T.oct][e];
+                const int pk = P.tvl[T.tv0 + e];
                 const int dx = (pk & 15) - 3, dy = ((pk >> 4) & 15) - 3, dz = ((pk >> 8) & 15) - 3;
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -223,10 +221,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             };
             long long src[8], nxt[8];
             sources(0, nxt);
-            for (int e = 0; e < kPerOctant; ++e) {
+            for (int e = 0; e < T.ntv; ++e) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i) src[i] = nxt[i];
-                if (e + 1 < kPerOctant) sources(e + 1, nxt);  // in flight while this vector's chunks go out
+                if (e + 1 < T.ntv) sources(e + 1, nxt);  // in flight while this vector's chunks go out
                 for (int c = 0; c < P.nchunks; ++c, ++it) {
                     const int s = (int)(it % S);
                     if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) - 1) & 1), &abort_flag,
@@ -273,8 +271,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             int last_parity[4] = {-1, -1, -1, -1};
             for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
                 const ContractTile T = P.tiles[tile];
-                for (int e = 0; e < kPerOctant; ++e) {
-                    const int ti = c_oct_tv[T.oct][e] >> 12;
+                for (int e = 0; e < T.ntv; ++e) {
+                    const int ti = P.tvl[T.tv0 + e] >> 12;
                     for (int c = 0; c < P.nchunks; ++c, ++it) {
                         const int s = (int)(it % S);
                         if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) - 1) & 1), &abort_flag,
@@ -313,8 +311,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             long long it = 0, u = 0;
             bool pending = false;
             for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
-                for (int g0 = 0; g0 < kPerOctant; g0 += P.group, ++u) {
-                    const int g1 = min(kPerOctant, g0 + P.group);
+                const int ntv = P.tiles[tile].ntv;
+                for (int g0 = 0; g0 < ntv; g0 += P.group, ++u) {
+                    const int g1 = min(ntv, g0 + P.group);
                     const int buf = (int)(u % nbuf);
                     if (u >= nbuf &&
                         !mbar_wait(smem_u32(&acce_bar[buf]), (uint32_t)(((u / nbuf) - 1) & 1), &abort_flag, P.status, 3))
@@ -364,8 +363,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const LevelView &L = P.lv[T.lev];
             const RowInfo ri = row_info(L, T, row);
             float *dst = ri.b >= 0 ? P.phit + (L.row0 + (long long)ri.b * L.R + ri.r) * (long long)kp : nullptr;
-            for (int g0 = 0; g0 < kPerOctant; g0 += P.group, ++u) {
-                const bool first = g0 == 0, last = g0 + P.group >= kPerOctant;
+            for (int g0 = 0; g0 < T.ntv; g0 += P.group, ++u) {
+                const bool first = g0 == 0, last = g0 + P.group >= T.ntv;
                 const int buf = (int)(u % nbuf);
                 if (!mbar_wait(smem_u32(&accf_bar[buf]), (uint32_t)((u / nbuf) & 1), &abort_flag, P.status, 5)) goto epi_done;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -483,31 +482,6 @@ inline float bf16_value(uint16_t h) { return bits_f32((uint32_t)h << 16); }
 
 }  // namespace
 
-int ensure_tc_constants(int device) {
-    static bool done[64] = {false};
-    if (device < 0 || device >= 64) return M2L_EINVAL;
-    if (done[device]) return M2L_OK;
-    int tab[8][kPerOctant];
-    for (int o = 0; o < 8; ++o) {
-        int cx = o & 1, cy = (o >> 1) & 1, cz = (o >> 2) & 1, e = 0;
-        for (int dx = -2 - cx; dx <= 3 - cx; ++dx)
-            for (int dy = -2 - cy; dy <= 3 - cy; ++dy)
-                for (int dz = -2 - cz; dz <= 3 - cz; ++dz) {
-                    int ti = transfer_index(dx, dy, dz);
-                    if (ti < 0) continue;
-                    tab[o][e++] = (dx + 3) | ((dy + 3) << 4) | ((dz + 3) << 8) | (ti << 12);
-                }
-    }
-    if (cudaMemcpyToSymbol(c_oct_tv, tab, sizeof tab) != cudaSuccess) {
-        set_error("uploading the octant table failed: %s", cudaGetErrorString(cudaGetLastError()));
-        return M2L_ECUDA;
-    }
-    done[device] = true;
-    return M2L_OK;
-}
-
-namespace {
-}  // namespace
 
 // Split C_t (FP64 on the host) into hi/lo pieces, upload them and encode their TMA maps.
 int split_tc_operators(m2l_plan_t *pl, int precision) {
@@ -591,21 +565,20 @@ int launch_split_rows(const float *src, long long rows, int kp, void *hi, void *
 size_t tc_stage_bytes(int kp) { return 2 * (size_t)kRows * kChunk + 2 * (size_t)kp * kChunk; }
 
 template <class T>
-int launch_contract_tc(m2l_plan_t *pl, const LevelView *lv, const ContractTile *tiles, long long ntiles,
+int launch_contract_tc(m2l_plan_t *pl, const LevelView *lv, const ContractTile *tiles, long long ntiles, const int *tvl,
                        const void *qt_hi, const void *qt_lo, long long zero_row, T *phit, int precision, cudaStream_t s) {
     if constexpr (sizeof(T) != 4) {
         set_error("the tensor-core contraction writes FP32");
         return M2L_EINVAL;
     } else {
         if (ntiles <= 0) return M2L_OK;
-        int crc = ensure_tc_constants(pl->device);
-        if (crc) return crc;
         DevOps &D = pl->dev[precision];
         const int kp = pl->kp;
         const int kind = precision == M2L_PREC_TF32X3 ? 0 : 1;
         TcParams P;
         P.lv = lv;
         P.tiles = tiles;
+        P.tvl = tvl;
         P.ntiles = ntiles;
         P.qhi = (const unsigned char *)qt_hi;
         P.qlo = (const unsigned char *)qt_lo;
@@ -655,9 +628,9 @@ int launch_contract_tc(m2l_plan_t *pl, const LevelView *lv, const ContractTile *
         return M2L_OK;
     }
 }
-template int launch_contract_tc<float>(m2l_plan_t *, const LevelView *, const ContractTile *, long long, const void *,
-                                       const void *, long long, float *, int, cudaStream_t);
-template int launch_contract_tc<double>(m2l_plan_t *, const LevelView *, const ContractTile *, long long, const void *,
-                                        const void *, long long, double *, int, cudaStream_t);
+template int launch_contract_tc<float>(m2l_plan_t *, const LevelView *, const ContractTile *, long long, const int *,
+                                       const void *, const void *, long long, float *, int, cudaStream_t);
+template int launch_contract_tc<double>(m2l_plan_t *, const LevelView *, const ContractTile *, long long, const int *,
+                                        const void *, const void *, long long, double *, int, cudaStream_t);
 
 }  // namespace m2l

@@ -57,6 +57,7 @@ class Workload:
     density: str                       # "u01", "u11" or "normal"
     keys: dict                         # level -> sorted uint64 Morton keys, or None for a full level
     n_points: int = 0
+    fft_grid: int | None = None        # convolution grid side of the FFT form (None: 2p)
 
     @property
     def levels(self):
@@ -125,8 +126,13 @@ def c1() -> Workload:
 
 
 def c2(rank_tol: float = 1e-7, depth: int = 5) -> Workload:
-    """The 1M-point workload; ``depth`` < 5 gives the same shape on a shallower tree (profiling)."""
-    return uniform_cube("c2", 2, 1_000_000, depth, 6, 1, rank_tol, "u11")
+    """The 1M-point workload; ``depth`` < 5 gives the same shape on a shallower tree (profiling).
+
+    Its FFT form runs on the (2p-1)^3 grid: the 2p-1 values of the kernel sequence per axis without
+    the padding zero, still free of aliasing (App. A.1)."""
+    wl = uniform_cube("c2", 2, 1_000_000, depth, 6, 1, rank_tol, "u11")
+    wl.fft_grid = 2 * wl.p - 1
+    return wl
 
 
 def c3(bin_points: bool = True) -> Workload:

@@ -165,7 +165,9 @@ def test_c2_full_size_sampled(lib, form, precision):
     wl = W.c2()
     qs = _qs(wl)
     tol = wl.rank_tol if form == "blas" else 0.0
-    chk = run_gpu(lib, wl.depth, wl.p, qs, rank_tol=tol, form=form, precision=precision, output="check")
+    grid = wl.fft_grid if form == "fft" else None  # (2p-1)^3 grid for this workload
+    chk = run_gpu(lib, wl.depth, wl.p, qs, rank_tol=tol, form=form, precision=precision, output="check",
+                  fft_grid=grid)
     bound = FP64_TOL if precision == "fp64" else FP32_TOL
     ops = O.compressed_operators(wl.p, tol, 1.0) if form == "blas" else None
     rng = np.random.default_rng(5)
