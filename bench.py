@@ -414,7 +414,7 @@ def run_ours(args, rank, world, local_rank):
            "mixed_vs_fp64": headline}
     log("e2e done")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(insts, q64, plans, bufs, dtypes, args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(insts, q64, plans, bufs, dtypes, args.cpu_seconds, run_variant)
         log("cpu baseline done")
     for v in variants:
         for pl in plans[v]:
@@ -455,37 +455,43 @@ def _oracle_sample(wl, q64, seconds, seed=11):
     return done_pairs * R, el, results, batches
 
 
-def cpu_baseline(insts, q64, plans, bufs, dtypes, seconds):
+def cpu_baseline(insts, q64, plans, bufs, dtypes, seconds, run_variant):
     """The FP64 oracle on this host's cores, on a bounded sample of the workload's instances; also
-    the error of each variant on the sampled targets (Eq. 16)."""
+    the error of each variant on the sampled targets (Eq. 16). Each variant is re-run the way the
+    timed loop runs it (`run_variant`: one batch call for a batched workload), once with check
+    potentials and once with locals as output."""
+    import torch
     from oracle import m2l as M
     cores = os.cpu_count()
     order = sorted(range(len(insts)), key=lambda i: -insts[i].n_boxes(insts[i].depth))[:4]
     budget = seconds / len(order)
     inter, el, batches = 0, 0.0, 0
-    errs = {v: {"check_potential_rel_err_per_level": [], "locals_rel_err_per_level": []} for v in plans}
+    samples = {}
     for i in order:
-        wl = insts[i]
-        it, e_, res, b_ = _oracle_sample(wl, q64[i], budget)
+        it, e_, res, b_ = _oracle_sample(insts[i], q64[i], budget)
         inter += it
         el += e_
         batches += b_
-        n = W.n_surface(wl.p)
-        for v in plans:
-            pl = plans[v][i]
-            qd, od = bufs[(i, dtypes[(v, i)])]
-            outs = {}
-            for mode in ("check", "locals"):
+        samples[i] = res
+    errs = {v: {"check_potential_rel_err_per_level": [], "locals_rel_err_per_level": []} for v in plans}
+    for v in plans:
+        outs = {i: {} for i in order}
+        for mode in ("check", "locals"):
+            for pl in plans[v]:
                 pl.set(output=mode)
-                pl.apply(qd, od, -1, wl.n_rhs)
-                outs[mode] = od.double().cpu().numpy()
-            pl.set(output="locals")
+            run_variant(v)
+            torch.cuda.synchronize()
+            for i in order:
+                outs[i][mode] = bufs[(i, dtypes[(v, i)])][1].double().cpu().numpy()
+        for i in order:
+            wl, res = insts[i], samples[i]
+            n, R = W.n_surface(wl.p), wl.n_rhs
             off = 0
             for l in wl.levels:
                 B = wl.n_boxes(l)
-                c = outs["check"][off:off + B * wl.n_rhs * n].reshape(B, wl.n_rhs, n)
-                lo = outs["locals"][off:off + B * wl.n_rhs * n].reshape(B, wl.n_rhs, n)
-                off += B * wl.n_rhs * n
+                c = outs[i]["check"][off:off + B * R * n].reshape(B, R, n)
+                lo = outs[i]["locals"][off:off + B * R * n].reshape(B, R, n)
+                off += B * R * n
                 tg = np.concatenate(res[l][0])
                 if len(tg) == 0:
                     continue

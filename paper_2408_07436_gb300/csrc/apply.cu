@@ -347,10 +347,19 @@ size_t workspace_estimate(const m2l_plan_t *pl, int form, int precision, int R) 
 // ---------------------------------------------------------------------------------------------
 // BLAS form over a group of instances with the same operators; owner = runs[0].pl.
 
-// Second factor of the pseudo-inverse, out = V_eps Z (+ out).
+// Second factor of the pseudo-inverse, out = V_eps Z (+ out). Its sum cancels by up to the
+// inverse of the pseudo-inverse threshold, and plain FP32 accumulation leaves up to about 8e-7
+// of the check potential in the locals. `compensated` (FP32 only) takes the float-float product
+// with V_eps carried as hi + lo, which removes that term: the FFT form in FP32 uses it, as its
+// other stages stay below 5.2e-7; the BLAS forms' contraction error is larger than the term.
 template <class T>
-static int apply_veps(const m2l_plan_t *pl, const DevOps &D, const T *Z, T *out, long long rows, int acc, cudaStream_t s) {
+static int apply_veps(const m2l_plan_t *pl, const DevOps &D, const T *Z, T *out, long long rows, int acc, bool compensated,
+                      cudaStream_t s) {
     const int n = pl->n, rp = pl->rp;
+    if constexpr (sizeof(T) == 4) {
+        if (compensated)
+            return launch_gemm_xwt_ff(Z, rp, (const float *)D.V, (const float *)D.Vlo, rp, out, n, rows, n, rp, acc, s);
+    }
     return launch_gemm_xwt<T>(Z, rp, (const T *)D.V, rp, out, n, rows, n, rp, acc, s);
 }
 
@@ -404,7 +413,7 @@ static int blas_group(std::vector<Run> &runs, int precision, Workspace &ws, cuda
         const T *ph = phit + r.row_off * kp;
         if (r.pl->output == M2L_OUT_LOCALS) {
             M2L_TRY(launch_gemm_xwt<T>(ph, kp, (const T *)D.A, kp, Z + r.row_off * rp, rp, r.rows, rp, kp, 0, s));
-            M2L_TRY(apply_veps<T>(own, D, Z + r.row_off * rp, (T *)r.L, r.rows, r.pl->accumulate, s));
+            M2L_TRY(apply_veps<T>(own, D, Z + r.row_off * rp, (T *)r.L, r.rows, r.pl->accumulate, false, s));
             nl += 2;
         } else {
             M2L_TRY(launch_gemm_xwt<T>(ph, kp, (const T *)D.Uc, kp, (T *)r.L, n, r.rows, n, kp, r.pl->accumulate, s));
@@ -470,7 +479,7 @@ static int fft_run(const Run &r, int precision, Workspace &ws, Workspace &spec, 
         // F6: locals = V_eps (Ut_eps Phi)
         stage_begin(pl, M2L_STAGE_PINV);
         M2L_TRY(launch_gemm_xwt<T>(Phi + base0 * R * n, n, (const T *)D.Ut, n, Z, rp, r.rows, rp, n, 0, s));
-        M2L_TRY(apply_veps<T>(pl, D, Z, out, r.rows, pl->accumulate, s));
+        M2L_TRY(apply_veps<T>(pl, D, Z, out, r.rows, pl->accumulate, true, s));
         stage_end(pl, 2);
     }
     return M2L_OK;
@@ -574,7 +583,7 @@ int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         for (const Run &r : groups[gi]) {
             const DevOps &D = r.pl->dev[precs[gi]];
-            for (const void *ptr : {lead->batch_ws.buf, lead->spec.buf, r.pl->exec.levels, r.pl->exec.tiles, r.pl->exec.tvl, D.C, D.C_hi, D.C_lo, D.Khat, D.A, D.V})
+            for (const void *ptr : {lead->batch_ws.buf, lead->spec.buf, r.pl->exec.levels, r.pl->exec.tiles, r.pl->exec.tvl, D.C, D.C_hi, D.C_lo, D.Khat, D.A, D.V, D.Vlo})
                 sig.push_back((long long)(uintptr_t)ptr);
             sig.push_back(r.pl->tc_group);
             sig.push_back(r.pl->fft_grid_opt);

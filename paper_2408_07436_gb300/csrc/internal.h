@@ -42,6 +42,7 @@ struct DevOps {
     void *C = nullptr;           // [316][kp][kp] C_t
     void *A = nullptr;           // [rp][kp]    Ut_eps * U
     void *V = nullptr;           // [n][rp]     V_eps
+    void *Vlo = nullptr;         // [n][rp]     V_eps - fl32(V_eps) (single-precision plans)
     void *Uc = nullptr;          // [n][kp]     U (check-potential output)
     void *C_hi = nullptr, *C_lo = nullptr;  // split C_t for the tensor-core forms
     alignas(64) unsigned char tmap[2][128] = {};  // TMA maps (CUtensorMap) of C_hi and C_lo

@@ -46,6 +46,11 @@ template <class T>
 int launch_gemm_xwt(const T *X, long long ldx, const T *W, long long ldw, T *Y, long long ldy,
                     long long rows, int O, int K, int acc, cudaStream_t s);
 
+// Y[r][o] (+)= sum_i X[r][i] (Wh[o][i] + Wl[o][i]) with a compensated (float-float) sum, FP32 in
+// and out.
+int launch_gemm_xwt_ff(const float *X, long long ldx, const float *Wh, const float *Wl, long long ldw, float *Y,
+                       long long ldy, long long rows, int O, int K, int acc, cudaStream_t s);
+
 // B2 on CUDA cores: phit[row0 + b R + r][:] = sum_t C_t qt[row0 + src R + r][:] over the tiles,
 // `levels` a device array of LevelView indexed by ContractTile::lev, `tvl` the tiles' transfer
 // vector lists.

@@ -122,6 +122,88 @@ __global__ void __launch_bounds__(256) gemm_xwt_kernel(const TX *__restrict__ X,
     }
 }
 
+// Y = X (W_hi + W_lo)^T (+ Y) for FP32 data with about twice FP32's precision in the sum: every
+// product x w_hi is split exactly into p + e with one FMA, the running sum is an unevaluated
+// pair s + c updated by Knuth's TwoSum, and c also gathers e and the small term x w_lo (the
+// compensated dot product of Ogita, Rump and Oishi, "Accurate sum and dot product", 2005).
+// W_lo is the part of an FP64 operator below its FP32 rounding. Used for the second factor of
+// the pseudo-inverse (Eq. 9), whose sum cancels heavily: its terms reach 1 / (alpha s_0) times
+// the check potential while the result is of the size of the check potential.
+__global__ void __launch_bounds__(256) gemm_xwt_ff_kernel(const float *__restrict__ X, long long ldx,
+                                                          const float *__restrict__ Wh, const float *__restrict__ Wl,
+                                                          long long ldw, float *__restrict__ Y, long long ldy,
+                                                          long long rows, int O, int K, int acc) {
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ float Xs[BK][BM + 4];
+    __shared__ float Whs[BK][BN + 4];
+    __shared__ float Wls[BK][BN + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const long long row0 = (long long)blockIdx.x * BM;
+    const int col0 = blockIdx.y * BN;
+    float sh[4][4], sl[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += 256) {
+            const int r = e / BK, kk = e % BK;
+            const long long gr = row0 + r;
+            const int gk = k0 + kk, gc = col0 + r;
+            Xs[kk][r] = (gr < rows && gk < K) ? X[gr * ldx + gk] : 0.f;
+            const bool w = gc < O && gk < K;
+            Whs[kk][r] = w ? Wh[(long long)gc * ldw + gk] : 0.f;
+            Wls[kk][r] = w ? Wl[(long long)gc * ldw + gk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < BK; ++kk) {
+            float xa[4], wh[4], wl[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                xa[i] = Xs[kk][ty * 4 + i];
+                wh[i] = Whs[kk][tx * 4 + i];
+                wl[i] = Wls[kk][tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float p = __fmul_rn(xa[i], wh[j]);
+                    const float e = __fmaf_rn(xa[i], wh[j], -p);  // x w_hi = p + e exactly
+                    const float t = __fadd_rn(sh[i][j], p);
+                    const float z = __fsub_rn(t, sh[i][j]);
+                    const float d = __fadd_rn(__fsub_rn(sh[i][j], __fsub_rn(t, z)), __fsub_rn(p, z));  // s + p = t + d
+                    sh[i][j] = t;
+                    sl[i][j] = __fmaf_rn(xa[i], wl[j], __fadd_rn(sl[i][j], __fadd_rn(d, e)));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long long r = row0 + ty * 4 + i;
+        if (r >= rows) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = col0 + tx * 4 + j;
+            if (c < O) {
+                float v = __fadd_rn(sh[i][j], sl[i][j]);
+                if (acc) v = __fadd_rn(Y[r * ldy + c], v);
+                Y[r * ldy + c] = v;
+            }
+        }
+    }
+}
+
+int launch_gemm_xwt_ff(const float *X, long long ldx, const float *Wh, const float *Wl, long long ldw, float *Y,
+                       long long ldy, long long rows, int O, int K, int acc, cudaStream_t s) {
+    if (rows <= 0 || O <= 0) return M2L_OK;
+    dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((O + 63) / 64));
+    gemm_xwt_ff_kernel<<<grid, 256, 0, s>>>(X, ldx, Wh, Wl, ldw, Y, ldy, rows, O, K, acc);
+    return check_launch("gemm_ff");
+}
+
 template <class T>
 int launch_gemm_xwt(const T *X, long long ldx, const T *W, long long ldw, T *Y, long long ldy,
                     long long rows, int O, int K, int acc, cudaStream_t s) {

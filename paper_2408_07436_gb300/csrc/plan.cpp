@@ -495,7 +495,6 @@ static int upload_typed(m2l_plan_t *pl, DevOps &D, int form) {
         if ((rc = upload_vec(D.St, pad2<T>(St, k, n, kp, n)))) return rc;
         if ((rc = upload_vec(D.C, Cp))) return rc;
         if ((rc = upload_vec(D.A, pad2<T>(Aop, r, k, rp, kp)))) return rc;
-        if ((rc = upload_vec(D.V, pad2<T>(Veps, n, r, n, rp)))) return rc;
         if ((rc = upload_vec(D.Uc, pad2<T>(pl->U, n, k, n, kp)))) return rc;
     } else {
         int F = pl->F;
@@ -506,7 +505,16 @@ static int upload_typed(m2l_plan_t *pl, DevOps &D, int form) {
         if ((rc = upload_vec(D.Khat, K))) return rc;
         if ((rc = upload_vec(D.tw, tw))) return rc;
         if ((rc = upload_vec(D.Ut, pad2<T>(Uteps, r, n, rp, n)))) return rc;
+    }
+    // the second pseudo-inverse factor, shared by both forms; single-precision plans also keep the
+    // part of V_eps below its FP32 rounding for the compensated product
+    if (!D.V) {
         if ((rc = upload_vec(D.V, pad2<T>(Veps, n, r, n, rp)))) return rc;
+        if (single) {
+            std::vector<double> lo(Veps.size());
+            for (size_t i = 0; i < lo.size(); ++i) lo[i] = Veps[i] - (double)(float)Veps[i];
+            if ((rc = upload_vec(D.Vlo, pad2<T>(lo, n, r, n, rp)))) return rc;
+        }
     }
     return rc;
 }
@@ -535,7 +543,7 @@ int upload_ops(m2l_plan_t *pl, int precision, int form) {
 
 void free_device(m2l_plan_t *pl) {
     for (auto &D : pl->dev) {
-        void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Uc, &D.C_hi, &D.C_lo, &D.Khat, &D.Ut, &D.tw};
+        void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Vlo, &D.Uc, &D.C_hi, &D.C_lo, &D.Khat, &D.Ut, &D.tw};
         for (void **pp : ptrs) {
             if (*pp) cudaFree(*pp);
             *pp = nullptr;

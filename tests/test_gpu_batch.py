@@ -154,3 +154,32 @@ def test_autotuner_meets_target(lib, tol):
             assert M.rel_l2_error(ref, got[tg]) < max(tol, 1e-12)
     finally:
         plan.close()
+
+
+@pytest.mark.parametrize("p", [4, 10])
+def test_autotuner_at_1e6_stays_in_single_precision(lib, p):
+    """At a target of 1e-6 the FP32 FFT form (stated bound 1e-6) is eligible for every order, so no
+    FP64 pass is needed; the locals it returns meet the target against the FP64 oracle."""
+    import torch
+    wl = W.small(depth=3, p=p, density="normal", seed=5)
+    plan = lib.Plan(wl.depth, wl.p, 0.0, form="auto", precision="auto").set(target_tol=1e-6)
+    try:
+        plan.set_stream()
+        assert plan.query(lib.M2L_Q_PRECISION, 2) != lib.M2L_PREC_FP64
+        q = torch.from_numpy(np.concatenate([np.repeat(wl.multipoles(l), 2, axis=1).reshape(-1)
+                                             for l in wl.levels])).float().cuda()
+        o = torch.empty_like(q)
+        plan.apply(q, o, -1, 2)
+        torch.cuda.synchronize()
+        flat = o.double().cpu().numpy()
+        n, off = plan.n, 0
+        for l in wl.levels:
+            B = wl.n_boxes(l)
+            got = flat[off:off + B * 2 * n].reshape(B, 2, n)
+            off += B * 2 * n
+            tg = np.arange(0, B, max(1, B // 24))
+            L_ref, _ = oracle_level(wl.p, l, wl.multipoles(l), targets=tg)
+            for r in range(2):
+                assert M.check_norm_error(p, l, L_ref, got[tg, r:r + 1]) < 1e-6, (p, l, r)
+    finally:
+        plan.close()
