@@ -275,6 +275,12 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(const LevelView *__r
             src_row[tid] = sr;
         }
         __syncthreads();
+        // a warp holds 8 rows; when none of them has a source for this transfer vector (targets
+        // at the domain boundary, empty boxes) it skips the products and only helps with loads
+        bool mine = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mine |= src_row[ty * 4 + i] != zero_row;
+        const bool live = __any_sync(0xffffffffu, mine);
         const T *Ct = C + (long long)ti * kp * kp;
         for (int k0 = 0; k0 < kp; k0 += BK) {
             for (int e = tid; e < BM * BK; e += 256) {
@@ -286,17 +292,19 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(const LevelView *__r
                 Ws[kk][c] = gc < kp ? Ct[(long long)gc * kp + k0 + kk] : T(0);
             }
             __syncthreads();
+            if (live) {
 #pragma unroll
-            for (int kk = 0; kk < BK; ++kk) {
-                T xa[4], wb[TN];
+                for (int kk = 0; kk < BK; ++kk) {
+                    T xa[4], wb[TN];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) xa[i] = Xs[kk][ty * 4 + i];
+                    for (int i = 0; i < 4; ++i) xa[i] = Xs[kk][ty * 4 + i];
 #pragma unroll
-                for (int j = 0; j < TN; ++j) wb[j] = Ws[kk][tx * TN + j];
+                    for (int j = 0; j < TN; ++j) wb[j] = Ws[kk][tx * TN + j];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < TN; ++j) a[i][j] = fma(xa[i], wb[j], a[i][j]);
+                        for (int j = 0; j < TN; ++j) a[i][j] = fma(xa[i], wb[j], a[i][j]);
+                }
             }
             __syncthreads();
         }
@@ -351,10 +359,13 @@ int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, lon
 
 // ----------------------------------------------------------------------------------------------
 // FFT form. Lattice entries are packed a << 16 | b << 8 | c. Spectra are stored per
-// (cluster, rhs) as [F][8] complex: the eight siblings of a cluster interleaved by frequency
-// (App. A.1 steps 3 and 5: "frequency order"). A launch covers R right-hand sides; rows of the
-// densities and check potentials are b * L.R + L.row0 + r, so a launch can take a chunk of the
-// instance's right-hand sides, and spectra of cluster c sit at (L.cbase + c) * R + r.
+// (cluster, rhs) as [8][F] complex: sibling-major, frequencies contiguous, so the lanes of a warp
+// that take consecutive frequencies of one sibling read whole 128-byte lines (App. A.1 interleaves
+// the siblings by frequency instead, which suits one CPU core walking all siblings of a frequency;
+// on the GPU it made every 16-byte load touch four times the lines it used). A launch covers R
+// right-hand sides; rows of the densities and check potentials are b * L.R + L.row0 + r, so a
+// launch can take a chunk of the instance's right-hand sides, and spectra of cluster c sit at
+// (L.cbase + c) * R + r.
 
 __device__ inline uint32_t parent_linear(uint32_t xyz, int Np) {
     int x = (xyz & 1023) >> 1, y = ((xyz >> 10) & 1023) >> 1, z = ((xyz >> 20) & 1023) >> 1;
@@ -426,7 +437,7 @@ __global__ void __launch_bounds__(128) fft_forward_kernel(LevelView L, int R, in
     const uint32_t xyz = L.xyz[b];
     const int oct = octant_of(xyz);
     const int cl = L.cslot[parent_linear(xyz, L.N / 2)];
-    T *out = qhat + ((L.cbase + cl) * R + r) * (long long)F * 16;
+    T *out = qhat + (((L.cbase + cl) * R + r) * 8 + oct) * (long long)F * 2;
     for (int f = tid; f < F; f += nt) {
         int kx = f / (g * H), ky = (f / H) % g, kz = f % H;
         T re = 0, im = 0;
@@ -439,8 +450,8 @@ __global__ void __launch_bounds__(128) fft_forward_kernel(LevelView L, int R, in
             m += kx;
             if (m >= g) m -= g;
         }
-        out[(long long)f * 16 + 2 * oct] = re;
-        out[(long long)f * 16 + 2 * oct + 1] = im;
+        out[2 * f] = re;
+        out[2 * f + 1] = im;
     }
 }
 
@@ -472,12 +483,15 @@ int launch_fft_forward(const LevelView &L, int R, int p, int n, int g, const int
 
 // F3: for each target cluster, rhs and frequency, sum over the 26 source clusters the 8 x 8
 // complex products phihat[i] += Khat_{t(d,i,j)} qhat[j] (App. A.1, Hadamard component), skipping
-// adjacent pairs. The kernel spectra of a block of FB frequencies sit in shared memory.
+// adjacent pairs. The kernel spectra of a block of FB frequencies sit in shared memory; FB complex
+// values make one 128-byte line, so the FB lanes that share an item read one line per sibling.
+// The frequency block is blockIdx.y: the CTAs resident at one time work on one or two frequency
+// blocks.
 template <class T, int FB>
 __global__ void __launch_bounds__(256) hadamard_kernel(LevelView L, int R, int F, const T *__restrict__ Khat,
                                                        const T *__restrict__ qhat, T *__restrict__ phihat) {
     __shared__ T Ks[(kNumTransfer + 1) * FB * 2];
-    const int f0 = blockIdx.x * FB;
+    const int f0 = blockIdx.y * FB;
     for (int e = threadIdx.x; e < (kNumTransfer + 1) * FB; e += blockDim.x) {
         int ti = e / FB, fl = e % FB, f = f0 + fl;
         T re = 0, im = 0;
@@ -495,7 +509,7 @@ __global__ void __launch_bounds__(256) hadamard_kernel(LevelView L, int R, int F
     if (f >= F) return;
     const int Np = L.N / 2;
     const long long items = L.nclusters * R;
-    for (long long item = (long long)blockIdx.y * TC + tcl; item < items; item += (long long)gridDim.y * TC) {
+    for (long long item = (long long)blockIdx.x * TC + tcl; item < items; item += (long long)gridDim.x * TC) {
         const long long tc = item / R;
         const int r = (int)(item % R);
         const uint32_t pc = L.cxyz[tc];
@@ -508,12 +522,12 @@ __global__ void __launch_bounds__(256) hadamard_kernel(LevelView L, int R, int F
             if (sx < 0 || sy < 0 || sz < 0 || sx >= Np || sy >= Np || sz >= Np) continue;
             int sc = L.cslot[((long long)sz * Np + sy) * Np + sx];
             if (sc < 0) continue;
-            const T *qs = qhat + (((L.cbase + sc) * R + r) * (long long)F + f) * 16;
+            const T *qs = qhat + ((L.cbase + sc) * R + r) * (long long)F * 16 + 2 * f;
             T qr[8], qi[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                qr[j] = qs[2 * j];
-                qi[j] = qs[2 * j + 1];
+                qr[j] = qs[(long long)j * F * 2];
+                qi[j] = qs[(long long)j * F * 2 + 1];
             }
 #pragma unroll
             for (int i = 0; i < 8; ++i)
@@ -527,25 +541,140 @@ __global__ void __launch_bounds__(256) hadamard_kernel(LevelView L, int R, int F
                     }
                 }
         }
-        T *out = phihat + (((L.cbase + tc) * R + r) * (long long)F + f) * 16;
+        T *out = phihat + ((L.cbase + tc) * R + r) * (long long)F * 16 + 2 * f;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            out[2 * i] = ar[i];
-            out[2 * i + 1] = ai[i];
+            out[(long long)i * F * 2] = ar[i];
+            out[(long long)i * F * 2 + 1] = ai[i];
         }
     }
 }
 
+// F3 with one warp per (target cluster, block of RB right-hand sides) and one lane per frequency
+// of a block of 32. Directions, source clusters and child masks are the same across the warp, so
+// the missing children of sparse sets (about half of them on a surface) are skipped without
+// divergence, the eight sibling spectra of a source load as one coalesced 2 KB row per warp, and
+// each kernel spectrum value read from shared memory serves RB right-hand sides.
+template <class T, int RB>
+__global__ void __launch_bounds__(256) hadamard_warp_kernel(LevelView L, int R, int F, const T *__restrict__ Khat,
+                                                            const T *__restrict__ qhat, T *__restrict__ phihat) {
+    constexpr int FB = 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Ks = reinterpret_cast<T *>(smem_raw);  // [316][FB] complex
+    const int f0 = blockIdx.y * FB;
+    for (int e = threadIdx.x; e < kNumTransfer * FB; e += blockDim.x) {
+        const int ti = e / FB, f = f0 + e % FB;
+        T re = 0, im = 0;
+        if (f < F) {
+            re = Khat[((long long)ti * F + f) * 2];
+            im = Khat[((long long)ti * F + f) * 2 + 1];
+        }
+        Ks[2 * e] = re;
+        Ks[2 * e + 1] = im;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int f = f0 + lane;
+    const bool fvalid = f < F;
+    const int Np = L.N / 2;
+    const int nrb = (R + RB - 1) / RB;
+    const long long items = L.nclusters * nrb;
+    for (long long item = (long long)blockIdx.x * 8 + warp; item < items; item += (long long)gridDim.x * 8) {
+        const long long tc = item / nrb;
+        const int r0 = (int)(item % nrb) * RB;
+        const uint32_t pc = L.cxyz[tc];
+        const int px = pc & 1023, py = (pc >> 10) & 1023, pz = (pc >> 20) & 1023;
+        int tmask = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) tmask |= (L.cchild[tc * 8 + i] >= 0) << i;
+        T ar[RB][8], ai[RB][8];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) ar[rr][i] = ai[rr][i] = T(0);
+        for (int d = 0; d < kDirections; ++d) {
+            const int sx = px + c_dir[d][0], sy = py + c_dir[d][1], sz = pz + c_dir[d][2];
+            if (sx < 0 || sy < 0 || sz < 0 || sx >= Np || sy >= Np || sz >= Np) continue;
+            const int sc = L.cslot[((long long)sz * Np + sy) * Np + sx];
+            if (sc < 0) continue;
+            int smask = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) smask |= (L.cchild[(long long)sc * 8 + j] >= 0) << j;
+            T qr[RB][8], qi[RB][8];
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr) {
+                const bool ok = fvalid && r0 + rr < R;
+                const T *qs = qhat + ((L.cbase + sc) * R + r0 + rr) * (long long)F * 16 + 2 * f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    qr[rr][j] = ok ? qs[(long long)j * F * 2] : T(0);
+                    qi[rr][j] = ok ? qs[(long long)j * F * 2 + 1] : T(0);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (!((tmask >> i) & 1)) continue;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (!((smask >> j) & 1)) continue;
+                    const int ti = c_clu[d][8 * i + j];
+                    if (ti < 0) continue;
+                    const T kr = Ks[(ti * FB + lane) * 2], ki = Ks[(ti * FB + lane) * 2 + 1];
+#pragma unroll
+                    for (int rr = 0; rr < RB; ++rr) {
+                        ar[rr][i] = fma(kr, qr[rr][j], fma(-ki, qi[rr][j], ar[rr][i]));
+                        ai[rr][i] = fma(kr, qi[rr][j], fma(ki, qr[rr][j], ai[rr][i]));
+                    }
+                }
+            }
+        }
+        if (fvalid) {
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr) {
+                if (r0 + rr >= R) continue;
+                T *out = phihat + ((L.cbase + tc) * R + r0 + rr) * (long long)F * 16 + 2 * f;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    out[(long long)i * F * 2] = ar[rr][i];
+                    out[(long long)i * F * 2 + 1] = ai[rr][i];
+                }
+            }
+        }
+    }
+}
+
+template <class T, int RB>
+static int launch_hadamard_warp(const LevelView &L, int R, int F, const T *Khat, const T *qhat, T *phihat,
+                                cudaStream_t s) {
+    constexpr int FB = 32;
+    const long long items = L.nclusters * ((R + RB - 1) / RB);
+    const size_t smem = sizeof(T) * 2 * (size_t)kNumTransfer * FB;
+    cudaFuncSetAttribute(hadamard_warp_kernel<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const unsigned gy = (unsigned)((F + FB - 1) / FB);
+    long long gx = (items + 63) / 64;  // about 8 items per warp
+    if (gx < 1) gx = 1;
+    if (gx > (1LL << 30)) gx = 1LL << 30;
+    hadamard_warp_kernel<T, RB><<<dim3((unsigned)gx, gy), 256, smem, s>>>(L, R, F, Khat, qhat, phihat);
+    return check_launch("hadamard");
+}
+
 template <class T>
 int launch_hadamard(const LevelView &L, int R, int F, const T *Khat, const T *qhat, T *phihat, cudaStream_t s) {
-    constexpr int FB = 8, TC = 256 / FB;
+    constexpr int FB = 128 / (2 * (int)sizeof(T)), TC = 256 / FB;  // one 128-byte line of complex values
     long long items = L.nclusters * R;
     if (items <= 0) return M2L_OK;
-    unsigned gx = (unsigned)((F + FB - 1) / FB);
-    long long gy = (items + TC * 8 - 1) / (TC * 8);
-    if (gy < 1) gy = 1;
-    if (gy > 65535) gy = 65535;
-    hadamard_kernel<T, FB><<<dim3(gx, (unsigned)gy), 256, 0, s>>>(L, R, F, Khat, qhat, phihat);
+    // The warp-per-cluster kernel skips missing children and reuses each kernel value for two
+    // right-hand sides; on full levels with one right-hand side it has nothing to skip and its
+    // larger spectra block halves the resident warps (measured 4.4 ms against 7.8 ms on the
+    // 1M-point workload, 52 ms against 98 ms on the sphere surface with 32 right-hand sides).
+    const bool sparse = L.nboxes * 4 < L.nclusters * 8 * 3;  // fewer than 6 of 8 children on average
+    if (R >= 2) return launch_hadamard_warp<T, 2>(L, R, F, Khat, qhat, phihat, s);
+    if (sparse) return launch_hadamard_warp<T, 1>(L, R, F, Khat, qhat, phihat, s);
+    const unsigned gy = (unsigned)((F + FB - 1) / FB);
+    long long gx = (items + TC * 8 - 1) / (TC * 8);
+    if (gx < 1) gx = 1;
+    if (gx > (1LL << 30)) gx = 1LL << 30;
+    hadamard_kernel<T, FB><<<dim3((unsigned)gx, gy), 256, 0, s>>>(L, R, F, Khat, qhat, phihat);
     return check_launch("hadamard");
 }
 
@@ -570,11 +699,11 @@ __global__ void __launch_bounds__(128) fft_inverse_kernel(LevelView L, int R, in
     const uint32_t xyz = L.xyz[b];
     const int oct = octant_of(xyz);
     const int cl = L.cslot[parent_linear(xyz, L.N / 2)];
-    const T *in = phihat + ((L.cbase + cl) * R + r) * (long long)F * 16 + 2 * oct;
+    const T *in = phihat + (((L.cbase + cl) * R + r) * 8 + oct) * (long long)F * 2;
     for (int i = tid; i < 2 * g; i += nt) tws[i] = tw[i];
     for (int f = tid; f < F; f += nt) {
-        X[2 * f] = in[(long long)f * 16];
-        X[2 * f + 1] = in[(long long)f * 16 + 1];
+        X[2 * f] = in[2 * f];
+        X[2 * f + 1] = in[2 * f + 1];
     }
     __syncthreads();
     // along x: Z1[a][ky][kz] = sum_kx X[kx][ky][kz] conj(w^(a kx)), a < p

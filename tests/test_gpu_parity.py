@@ -91,13 +91,14 @@ def test_truncated_blas_matches_compressed_oracle(lib):
 
 
 @pytest.mark.parametrize("form", ["blas", "fft"])
-def test_sparse_boxes_and_multiple_rhs(lib, form):
-    wl = W.small(depth=4, p=4, n_rhs=3, n_points=400, density="normal")
+@pytest.mark.parametrize("R", [1, 3])
+def test_sparse_boxes_and_multiple_rhs(lib, form, R):
+    wl = W.small(depth=4, p=4, n_rhs=R, n_points=400, density="normal")
     assert wl.is_sparse()
     qs = _qs(wl)
     keys = {l: wl.keys[l] for l in wl.levels}
-    chk = run_gpu(lib, wl.depth, wl.p, qs, keys=keys, form=form, output="check", R=3)
-    loc = run_gpu(lib, wl.depth, wl.p, qs, keys=keys, form=form, output="locals", R=3)
+    chk = run_gpu(lib, wl.depth, wl.p, qs, keys=keys, form=form, output="check", R=R)
+    loc = run_gpu(lib, wl.depth, wl.p, qs, keys=keys, form=form, output="locals", R=R)
     for l in wl.levels:
         k = None if keys[l] is None else keys[l].astype(np.int64)
         L_ref, phi_ref = oracle_level(wl.p, l, qs[l], keys=k)
