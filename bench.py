@@ -26,6 +26,7 @@ collective on the data path).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -52,6 +53,28 @@ NOMINAL_FP64_TFLOPS = 1.25       # FP64 (vector and tensor) dense
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a workload's dominant
+# kernel from one ncu capture, with the SHA-256 of the source file the kernel was built from; the
+# summary and command are in profiles/. A source that has changed since reports null.
+TRAFFIC = {
+    ("c2", 5, "blas-fp64:contract"): {"bytes": None, "source": "paper_2408_07436_gb300/csrc/kernels_simt.cu",
+                                        "sha256": None},
+}
+
+
+def measured_traffic(workload, depth, kernel):
+    t = TRAFFIC.get((workload, depth, kernel))
+    if not t or t["bytes"] is None:
+        return None
+    try:
+        with open(os.path.join(ROOT, t["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
+                return None
+    except OSError:
+        return None
+    return t["bytes"]
 
 
 def fp32_alu_peak_tflops(mhz=SM_MAX_MHZ):
@@ -349,7 +372,8 @@ def run_ours(args, rank, world, local_rank):
             per_launch_ms = ms_tot / nl
             ach = work.get(name, 0.0) * steps_for_stages / nl / (per_launch_ms / 1e3) / 1e12
             rf = {"bound": bound, "kernel": f"{v}:{name}", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                  "frac": ach / pk, "traffic": None, "peak_source": note}
+                  "frac": ach / pk, "traffic": measured_traffic(args.workload, args.depth, f"{v}:{name}"),
+                  "peak_source": note}
             var_out[v]["roofline"] = rf
             if best is None or ms_tot > best[0]:
                 best = (ms_tot, rf)

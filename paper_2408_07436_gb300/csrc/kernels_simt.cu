@@ -1,6 +1,7 @@
 // CUDA-core kernels of the M2L library (FP64 and FP32): the small GEMMs of the BLAS form
 // (compress S^T q, uncompress + pseudo-inverse), the gathered contraction over the 189
 // transfer vectors of each target octant, and the three stages of the FFT form.
+#include <algorithm>
 #include <cstdio>
 
 #include "internal.h"
@@ -52,6 +53,18 @@ int ensure_constants(int device) {
     }
     done[device] = true;
     return M2L_OK;
+}
+
+// Streaming multiprocessors of the current device (launch shapes are sized in waves of CTAs).
+static int sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cached[dev]) {
+        int n = 0;
+        cached[dev] = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : 152;
+    }
+    return cached[dev];
 }
 
 static int check_launch(const char *what) {
@@ -487,20 +500,32 @@ int launch_fft_forward(const LevelView &L, int R, int p, int n, int g, const int
 // values make one 128-byte line, so the FB lanes that share an item read one line per sibling.
 // The frequency block is blockIdx.y: the CTAs resident at one time work on one or two frequency
 // blocks.
-template <class T, int FB>
+template <class T>
+struct Complex2;
+template <>
+struct Complex2<float> {
+    using type = float2;
+};
+template <>
+struct Complex2<double> {
+    using type = double2;
+};
+
+// A thread owns one frequency of IB consecutive items (target cluster, rhs): each kernel value it
+// reads from shared memory serves IB products, and the IB source loads of a direction are in
+// flight together.
+template <class T, int FB, int IB>
 __global__ void __launch_bounds__(256) hadamard_kernel(LevelView L, int R, int F, const T *__restrict__ Khat,
                                                        const T *__restrict__ qhat, T *__restrict__ phihat) {
-    __shared__ T Ks[(kNumTransfer + 1) * FB * 2];
+    using C2 = typename Complex2<T>::type;
+    __shared__ C2 Ks[kNumTransfer * FB];
     const int f0 = blockIdx.y * FB;
-    for (int e = threadIdx.x; e < (kNumTransfer + 1) * FB; e += blockDim.x) {
-        int ti = e / FB, fl = e % FB, f = f0 + fl;
-        T re = 0, im = 0;
-        if (f < F) {
-            re = Khat[((long long)ti * F + f) * 2];
-            im = Khat[((long long)ti * F + f) * 2 + 1];
-        }
-        Ks[2 * e] = re;
-        Ks[2 * e + 1] = im;
+    for (int e = threadIdx.x; e < kNumTransfer * FB; e += blockDim.x) {
+        const int ti = e / FB, f = f0 + e % FB;
+        C2 k;
+        k.x = f < F ? Khat[((long long)ti * F + f) * 2] : T(0);
+        k.y = f < F ? Khat[((long long)ti * F + f) * 2 + 1] : T(0);
+        Ks[e] = k;
     }
     __syncthreads();
     constexpr int TC = 256 / FB;
@@ -509,43 +534,79 @@ __global__ void __launch_bounds__(256) hadamard_kernel(LevelView L, int R, int F
     if (f >= F) return;
     const int Np = L.N / 2;
     const long long items = L.nclusters * R;
-    for (long long item = (long long)blockIdx.x * TC + tcl; item < items; item += (long long)gridDim.x * TC) {
-        const long long tc = item / R;
-        const int r = (int)(item % R);
-        const uint32_t pc = L.cxyz[tc];
-        const int px = pc & 1023, py = (pc >> 10) & 1023, pz = (pc >> 20) & 1023;
-        T ar[8], ai[8];
+    const C2 *q2 = reinterpret_cast<const C2 *>(qhat);
+    C2 *o2 = reinterpret_cast<C2 *>(phihat);
+    for (long long it0 = ((long long)blockIdx.x * TC + tcl) * IB; it0 < items; it0 += (long long)gridDim.x * TC * IB) {
+        long long row[IB];  // (cluster, rhs) block of the item, -1 past the end
+        int px[IB], py[IB], pz[IB], rr[IB];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) ar[i] = ai[i] = T(0);
-        for (int d = 0; d < kDirections; ++d) {
-            int sx = px + c_dir[d][0], sy = py + c_dir[d][1], sz = pz + c_dir[d][2];
-            if (sx < 0 || sy < 0 || sz < 0 || sx >= Np || sy >= Np || sz >= Np) continue;
-            int sc = L.cslot[((long long)sz * Np + sy) * Np + sx];
-            if (sc < 0) continue;
-            const T *qs = qhat + ((L.cbase + sc) * R + r) * (long long)F * 16 + 2 * f;
-            T qr[8], qi[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                qr[j] = qs[(long long)j * F * 2];
-                qi[j] = qs[(long long)j * F * 2 + 1];
+        for (int b = 0; b < IB; ++b) {
+            const long long it = it0 + b;
+            row[b] = -1;
+            px[b] = py[b] = pz[b] = rr[b] = 0;
+            if (it < items) {
+                const long long tc = it / R;
+                rr[b] = (int)(it % R);
+                row[b] = (L.cbase + tc) * R + rr[b];
+                const uint32_t pc = L.cxyz[tc];
+                px[b] = pc & 1023;
+                py[b] = (pc >> 10) & 1023;
+                pz[b] = (pc >> 20) & 1023;
             }
+        }
+        T ar[IB][8], ai[IB][8];
+#pragma unroll
+        for (int b = 0; b < IB; ++b)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) ar[b][i] = ai[b][i] = T(0);
+        for (int d = 0; d < kDirections; ++d) {
+            C2 q[IB][8];
+            bool any = false;
+#pragma unroll
+            for (int b = 0; b < IB; ++b) {
+                const int sx = px[b] + c_dir[d][0], sy = py[b] + c_dir[d][1], sz = pz[b] + c_dir[d][2];
+                int sc = -1;
+                if (row[b] >= 0 && sx >= 0 && sy >= 0 && sz >= 0 && sx < Np && sy < Np && sz < Np)
+                    sc = L.cslot[((long long)sz * Np + sy) * Np + sx];
+                const C2 *qs = q2 + ((L.cbase + (sc < 0 ? 0 : sc)) * R + rr[b]) * (long long)F * 8 + f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (sc >= 0) {
+                        q[b][j] = qs[(long long)j * F];
+                    } else {
+                        q[b][j].x = T(0);
+                        q[b][j].y = T(0);
+                    }
+                }
+                any |= sc >= 0;
+            }
+            if (!any) continue;
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    int ti = c_clu[d][8 * i + j];
+                    const int ti = c_clu[d][8 * i + j];
                     if (ti >= 0) {
-                        T kr = Ks[(ti * FB + fl) * 2], ki = Ks[(ti * FB + fl) * 2 + 1];
-                        ar[i] = fma(kr, qr[j], fma(-ki, qi[j], ar[i]));
-                        ai[i] = fma(kr, qi[j], fma(ki, qr[j], ai[i]));
+                        const C2 k = Ks[ti * FB + fl];
+#pragma unroll
+                        for (int b = 0; b < IB; ++b) {
+                            ar[b][i] = fma(k.x, q[b][j].x, fma(-k.y, q[b][j].y, ar[b][i]));
+                            ai[b][i] = fma(k.x, q[b][j].y, fma(k.y, q[b][j].x, ai[b][i]));
+                        }
                     }
                 }
         }
-        T *out = phihat + ((L.cbase + tc) * R + r) * (long long)F * 16 + 2 * f;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            out[(long long)i * F * 2] = ar[i];
-            out[(long long)i * F * 2 + 1] = ai[i];
+        for (int b = 0; b < IB; ++b) {
+            if (row[b] < 0) continue;
+            C2 *out = o2 + row[b] * (long long)F * 8 + f;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                C2 v;
+                v.x = ar[b][i];
+                v.y = ai[b][i];
+                out[(long long)i * F] = v;
+            }
         }
     }
 }
@@ -651,7 +712,9 @@ static int launch_hadamard_warp(const LevelView &L, int R, int F, const T *Khat,
     const size_t smem = sizeof(T) * 2 * (size_t)kNumTransfer * FB;
     cudaFuncSetAttribute(hadamard_warp_kernel<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const unsigned gy = (unsigned)((F + FB - 1) / FB);
-    long long gx = (items + 63) / 64;  // about 8 items per warp
+    // up to 8 items per warp, fewer when a level is too small to fill four waves of CTAs
+    const long long ipw = std::max(1LL, std::min(8LL, items * (long long)gy / (4LL * sm_count() * 8)));
+    long long gx = (items + 8 * ipw - 1) / (8 * ipw);
     if (gx < 1) gx = 1;
     if (gx > (1LL << 30)) gx = 1LL << 30;
     hadamard_warp_kernel<T, RB><<<dim3((unsigned)gx, gy), 256, smem, s>>>(L, R, F, Khat, qhat, phihat);
@@ -670,11 +733,17 @@ int launch_hadamard(const LevelView &L, int R, int F, const T *Khat, const T *qh
     const bool sparse = L.nboxes * 4 < L.nclusters * 8 * 3;  // fewer than 6 of 8 children on average
     if (R >= 2) return launch_hadamard_warp<T, 2>(L, R, F, Khat, qhat, phihat, s);
     if (sparse) return launch_hadamard_warp<T, 1>(L, R, F, Khat, qhat, phihat, s);
+    // FP32 takes two items per thread (its shared-memory loads, not its FMAs, were the limit);
+    // FP64 is bound by the FP64 units and keeps one
+    constexpr int IB = sizeof(T) == 4 ? 2 : 1;
     const unsigned gy = (unsigned)((F + FB - 1) / FB);
-    long long gx = (items + TC * 8 - 1) / (TC * 8);
+    // up to 8 item groups per thread, fewer when a level is too small to fill four waves of CTAs
+    const long long waves4 = 4LL * sm_count() * 2 * TC * IB;
+    const long long ipt = std::max(1LL, std::min(8LL, items * (long long)gy / waves4));
+    long long gx = (items + TC * IB * ipt - 1) / (TC * IB * ipt);
     if (gx < 1) gx = 1;
     if (gx > (1LL << 30)) gx = 1LL << 30;
-    hadamard_kernel<T, FB><<<dim3((unsigned)gx, gy), 256, 0, s>>>(L, R, F, Khat, qhat, phihat);
+    hadamard_kernel<T, FB, IB><<<dim3((unsigned)gx, gy), 256, 0, s>>>(L, R, F, Khat, qhat, phihat);
     return check_launch("hadamard");
 }
 
