@@ -120,9 +120,23 @@ enum m2l_query_e {
     M2L_Q_FORM = 9,       /* form the next apply with n_rhs = `level` (>= 1) will run; resolves AUTO */
     M2L_Q_PRECISION = 10, /* precision of that apply (so the caller knows the element type) */
     M2L_Q_LAUNCHES = 11,  /* kernels launched by the last apply */
-    M2L_Q_DEVICE_STATUS = 12 /* waits for the plan's stream, returns the device status word (0: no
-                                bounded wait ran out since the last query, else a stage code) and
-                                clears it; a nonzero value means results since then are invalid */
+    M2L_Q_DEVICE_STATUS = 12 /* waits for the plan's stream, reads the device status word into *out
+                                (0, or the m2l_wait_e code of the first bounded wait that ran out
+                                since the last query) and clears it; returns M2L_ETIMEOUT when it
+                                was nonzero: results written since the last query are invalid */
+};
+
+/* Where a bounded device wait ran out (the value of M2L_Q_DEVICE_STATUS). Every wait of a kernel
+ * that waits on other warps (the tensor-core contraction) polls at most a fixed number of times,
+ * then records its code, raises the CTA's abort flag, lets the copies and MMAs it issued finish
+ * and returns: no trap, no hang, and the CUDA context stays usable. */
+enum m2l_wait_e {
+    M2L_WAIT_GATHER = 1,     /* source-row producers waiting for a free pipeline stage */
+    M2L_WAIT_TMA = 2,        /* operator (TMA) producer waiting for a free pipeline stage */
+    M2L_WAIT_ACC_FREE = 3,   /* MMA issuer waiting for a drained tensor-memory accumulator */
+    M2L_WAIT_OPERANDS = 4,   /* MMA issuer waiting for a filled pipeline stage */
+    M2L_WAIT_ACC_READY = 5,  /* drain warps waiting for a finished partial sum */
+    M2L_WAIT_SELFTEST = 6    /* m2l_selftest_watchdog */
 };
 
 /* Build a plan (host, FP64; arxiv 2408.07436 Sec. 3.1 for the BLAS operators and App. A.1
@@ -207,6 +221,14 @@ int m2l_stage_times(m2l_plan_t *plan, double *ms, long long *launches);
  * streams, other plans, other host threads) race on the array and give wrong results.
  * Asynchronous on the plan's stream. Returns M2L_OK, M2L_EINVAL or M2L_ECUDA. */
 int m2l_apply_noalloc(m2l_plan_t *plan, const double *multipoles, double *locals, int level, int n_rhs);
+
+/* Exercise the device watchdog: one thread waits, with the same bounded-wait code the
+ * contraction uses, on a barrier that nothing completes, for at most `polls` polls (>= 1), then
+ * records M2L_WAIT_SELFTEST in the plan's status word and returns. No copy or MMA is in flight,
+ * so nothing else is affected. Asynchronous on the plan's stream; read the outcome with
+ * m2l_query(M2L_Q_DEVICE_STATUS), which then returns M2L_ETIMEOUT. The paper has no counterpart.
+ * Returns M2L_OK, M2L_EINVAL (no GPU plan, polls < 1) or M2L_ECUDA. */
+int m2l_selftest_watchdog(m2l_plan_t *plan, long long polls);
 
 /* Copy a plan operator to host memory (FP64), for tests and inspection:
  * which = 0: U (n x k), 1: S (n x k), 2: C_t (316 x k x k), 3: singular values of K_fat (n),

@@ -8,6 +8,7 @@
 
 namespace m2l {
 const char *last_error();
+int launch_watchdog_selftest(int *status, long long polls, cudaStream_t s);  // kernels_tc.cu
 }
 
 using namespace m2l;
@@ -367,8 +368,12 @@ int m2l_query(const m2l_plan_t *cpl, int what, int level, long long *out) {
                 set_error("reading the device status failed: %s", cudaGetErrorString(cudaGetLastError()));
                 return M2L_ECUDA;
             }
-            if (v) cudaMemset(pl->dev_status, 0, sizeof(int));
             *out = v;
+            if (v) {
+                cudaMemset(pl->dev_status, 0, sizeof(int));
+                set_error("a bounded device wait ran out (site %d); results since the last status query are invalid", v);
+                return M2L_ETIMEOUT;
+            }
             return M2L_OK;
         }
         default:
@@ -424,6 +429,27 @@ int m2l_get_operator(m2l_plan_t *pl, int which, double *dst, long long *count) {
     *count = (long long)src->size();
     if (dst && !src->empty()) std::memcpy(dst, src->data(), src->size() * sizeof(double));
     return M2L_OK;
+}
+
+int m2l_selftest_watchdog(m2l_plan_t *pl, long long polls) {
+    clear_error();
+    if (!pl || pl->device < 0) {
+        set_error("the watchdog self-test needs a plan made on a GPU");
+        return M2L_EINVAL;
+    }
+    if (polls < 1) {
+        set_error("polls must be at least 1");
+        return M2L_EINVAL;
+    }
+    if (!pl->dev_status) {
+        if (cudaMalloc((void **)&pl->dev_status, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("status word allocation failed");
+            return M2L_ENOMEM;
+        }
+        cudaMemset(pl->dev_status, 0, sizeof(int));
+    }
+    return launch_watchdog_selftest(pl->dev_status, polls, pl->stream);
 }
 
 }  // extern "C"

@@ -63,8 +63,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait; on expiry records `code` in the status word and raises the CTA's abort flag.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *status, int code) {
-    for (long long it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *status, int code,
+                                          long long limit = kWaitLimit) {
+    for (long long it = 0; it < limit; ++it) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
     }
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int c = 0; c < P.nchunks; ++c, ++it) {
                     const int s = (int)(it % S);
                     if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) - 1) & 1), &abort_flag,
-                                              P.status, 1))
+                                              P.status, M2L_WAIT_GATHER))
                         goto producer_done;
                     if (c * kChunk + piece * 16 < kbytes) {
                         const long long goff = (long long)c * kChunk + piece * 16;
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int c = 0; c < P.nchunks; ++c, ++it) {
                         const int s = (int)(it % S);
                         if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) - 1) & 1), &abort_flag,
-                                                  P.status, 2))
+                                                  P.status, M2L_WAIT_TMA))
                             goto tma_done;
                         const uint32_t bar = smem_u32(&full_bar[s]);
                         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2 * b_bytes)
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int g1 = min(ntv, g0 + P.group);
                     const int buf = (int)(u % nbuf);
                     if (u >= nbuf &&
-                        !mbar_wait(smem_u32(&acce_bar[buf]), (uint32_t)(((u / nbuf) - 1) & 1), &abort_flag, P.status, 3))
+                        !mbar_wait(smem_u32(&acce_bar[buf]), (uint32_t)(((u / nbuf) - 1) & 1), &abort_flag, P.status, M2L_WAIT_ACC_FREE))
                         goto mma_done;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t d = tmem_base + (uint32_t)(buf * kp);
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int tv = g0; tv < g1; ++tv) {
                         for (int c = 0; c < P.nchunks; ++c, ++it) {
                             const int s = (int)(it % S);
-                            if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((it / S) & 1), &abort_flag, P.status, 4)) goto mma_done;
+                            if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((it / S) & 1), &abort_flag, P.status, M2L_WAIT_OPERANDS)) goto mma_done;
                             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                             const int steps = min(4, (kbytes - c * kChunk) / 32);
                             const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int g0 = 0; g0 < T.ntv; g0 += P.group, ++u) {
                 const bool first = g0 == 0, last = g0 + P.group >= T.ntv;
                 const int buf = (int)(u % nbuf);
-                if (!mbar_wait(smem_u32(&accf_bar[buf]), (uint32_t)((u / nbuf) & 1), &abort_flag, P.status, 5)) goto epi_done;
+                if (!mbar_wait(smem_u32(&accf_bar[buf]), (uint32_t)((u / nbuf) & 1), &abort_flag, P.status, M2L_WAIT_ACC_READY)) goto epi_done;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t tD = tmem_base + lane_off + (uint32_t)(buf * kp), tR = tm_R + lane_off;
                 for (int c0 = 0; c0 < kp; c0 += 48) {
@@ -412,6 +413,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(P.tmem_cols));
     }
+}
+
+// One bounded wait on an mbarrier that nothing arrives at: the expiry path every wait of the
+// contraction takes (status word set, abort flag raised, the kernel returns; no trap), run with no
+// copy and no MMA in flight.
+__global__ void watchdog_selftest_kernel(int *status, long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ volatile int abort_flag;
+    if (threadIdx.x != 0) return;
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(smem_u32(&bar), 0, &abort_flag, status, M2L_WAIT_SELFTEST, limit);
 }
 
 // hi/lo split of q~ rows: TF32 pieces (FP32 containers, low 13 bits zero) or BF16 pieces.
@@ -557,6 +571,16 @@ int launch_split_rows(const float *src, long long rows, int kp, void *hi, void *
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("split launch failed: %s", cudaGetErrorString(e));
+        return M2L_ECUDA;
+    }
+    return M2L_OK;
+}
+
+int launch_watchdog_selftest(int *status, long long polls, cudaStream_t s) {
+    watchdog_selftest_kernel<<<1, 32, 0, s>>>(status, polls);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("watchdog self-test launch failed: %s", cudaGetErrorString(e));
         return M2L_ECUDA;
     }
     return M2L_OK;

@@ -34,6 +34,8 @@ M2L_NUM_STAGES = 7
 M2L_FORM_AUTO, M2L_FORM_BLAS, M2L_FORM_FFT = 0, 1, 2
 M2L_PREC_AUTO, M2L_PREC_FP64, M2L_PREC_FP32, M2L_PREC_TF32X3, M2L_PREC_BF16X3 = -1, 0, 1, 2, 3
 M2L_OUT_LOCALS, M2L_OUT_CHECK_POTENTIAL = 0, 1
+(M2L_WAIT_GATHER, M2L_WAIT_TMA, M2L_WAIT_ACC_FREE, M2L_WAIT_OPERANDS, M2L_WAIT_ACC_READY,
+ M2L_WAIT_SELFTEST) = range(1, 7)
 (M2L_Q_N, M2L_Q_RANK, M2L_Q_BOXES, M2L_Q_PAIRS, M2L_Q_GRID, M2L_Q_FREQS, M2L_Q_PINV_RANK, M2L_Q_ROWS,
  M2L_Q_FORM, M2L_Q_PRECISION, M2L_Q_LAUNCHES, M2L_Q_DEVICE_STATUS) = range(1, 13)
 
@@ -67,6 +69,8 @@ _lib.m2l_apply_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int]
 _lib.m2l_apply_noalloc.restype = ctypes.c_int
 _lib.m2l_get_operator.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
 _lib.m2l_get_operator.restype = ctypes.c_int
+_lib.m2l_selftest_watchdog.argtypes = [_vp, ctypes.c_longlong]
+_lib.m2l_selftest_watchdog.restype = ctypes.c_int
 
 
 class M2LError(RuntimeError):
@@ -132,6 +136,21 @@ def m2l_query(plan, what: int, level: int = -1) -> int:
     out = ctypes.c_longlong(0)
     _check(_lib.m2l_query(plan, what, level, ctypes.byref(out)))
     return out.value
+
+
+def m2l_device_status(plan) -> int:
+    """The plan's device status word (0, or the M2L_WAIT_* code of a bounded wait that ran out),
+    read and cleared without raising; m2l_query(M2L_Q_DEVICE_STATUS) raises M2LError(M2L_ETIMEOUT)
+    for a nonzero word instead."""
+    out = ctypes.c_longlong(0)
+    rc = _lib.m2l_query(plan, M2L_Q_DEVICE_STATUS, -1, ctypes.byref(out))
+    if rc not in (M2L_OK, M2L_ETIMEOUT):
+        _check(rc)
+    return out.value
+
+
+def m2l_selftest_watchdog(plan, polls: int) -> None:
+    _check(_lib.m2l_selftest_watchdog(plan, polls))
 
 
 def m2l_stage_times(plan):

@@ -236,6 +236,43 @@ def test_tensor_core_sparse_multi_rhs_truncated(lib, precision):
         assert e < TC_TOL[precision], (precision, l, e)
 
 
+def test_watchdog_expiry_is_reported_and_the_context_survives(lib):
+    """A bounded wait that nothing completes (the self-test barrier) runs out, is reported as
+    M2L_ETIMEOUT with its site code, is cleared by the query, and the CUDA context keeps working:
+    the tensor-core contraction afterwards still matches the oracle."""
+    import ctypes
+
+    import torch
+    wl = W.small(depth=3, p=4, density="u11")
+    qs = _qs(wl)
+    plan = lib.Plan(3, 4, 0.0, form="blas", precision="tf32x3")
+    try:
+        plan.set_stream()
+        lib.m2l_selftest_watchdog(plan.handle, 1000)
+        out = ctypes.c_longlong(0)
+        rc = lib._lib.m2l_query(plan.handle, lib.M2L_Q_DEVICE_STATUS, -1, ctypes.byref(out))
+        assert rc == lib.M2L_ETIMEOUT and out.value == lib.M2L_WAIT_SELFTEST
+        assert "ran out" in lib.m2l_last_error()
+        assert _status(lib, plan.handle) == 0          # cleared by the query above
+        with pytest.raises(lib.M2LError):
+            lib.m2l_selftest_watchdog(plan.handle, 0)  # bad argument, nothing launched
+        q = torch.from_numpy(wl.all_multipoles()).float().cuda()
+        o = torch.empty_like(q)
+        plan.set(output="check")
+        plan.apply(q, o, -1, 1)
+        assert _status(lib, plan.handle) == 0
+        flat = o.double().cpu().numpy()
+        off = 0
+        for l in wl.levels:
+            B = wl.n_boxes(l)
+            got = flat[off:off + B * plan.n].reshape(B, 1, plan.n)
+            off += B * plan.n
+            _, phi_ref = oracle_level(4, l, qs[l])
+            assert M.rel_l2_error(phi_ref, got) < TC_TOL["tf32x3"], l
+    finally:
+        plan.close()
+
+
 def test_tensor_core_status_clear(lib):
     import torch
     wl = W.small(depth=3, p=4)
