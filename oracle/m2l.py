@@ -90,10 +90,12 @@ def m2l_dense(p: int, level: int, q: np.ndarray, keys=None, targets=None,
 
 def m2l_compressed(p: int, level: int, q: np.ndarray, ops: dict, keys=None, targets=None,
                    root_width: float = 1.0):
-    """BLAS-M2L of Sec. 3.2 (without the directional recompression of Eq. 15).
+    """BLAS-M2L of Sec. 3.2.
 
     ``ops`` comes from ``operators.compressed_operators(p, rank_tol, width)`` built at this
-    level's box width. Returns (locals, check potentials), shapes (T, R, n).
+    level's box width. When it also holds the directional factors of Eq. 15 (the entries of
+    ``operators.directional_operators`` merged in), step 4 applies them as the two products
+    xi = Vbar'_t^T q~ and phi~ += Ubar_t xi. Returns (locals, check potentials), shapes (T, R, n).
     """
     rows, boxes, offsets, src, srow = interaction_csr(level, keys, targets)
     U, S, C, tv = ops["U"], ops["S"], ops["C"], ops["tvecs"]
@@ -113,7 +115,11 @@ def m2l_compressed(p: int, level: int, q: np.ndarray, ops: dict, keys=None, targ
         if len(sel) == 0:
             continue
         gathered = qt[srow[sel]]                       # (N_t, R, k)
-        contrib = gathered @ C[ti].T
+        if "Ubar" in ops:
+            xi = gathered @ ops["Vbarp"][ti]              # (N_t, R, k_t)
+            contrib = xi @ ops["Ubar"][ti].T
+        else:
+            contrib = gathered @ C[ti].T
         np.add.at(phit, tgt_of_pair[sel], contrib)
     # Uncompress the check potentials, phi = U phi~, then recover the locals.
     phi = phit @ U.T

@@ -102,6 +102,25 @@ def compressed_operators(p: int, rank_tol: float, width: float = 1.0):
     return dict(U=U, S=S, C=C, k=k, tvecs=tv, s_fat=s_fat, s_thin=s_thin, K=Ks)
 
 
+def directional_operators(C: np.ndarray, dir_tol: float):
+    """Directional recompression of Eq. 15: C_t ~ Ubar_t Sigmabar_t Vbar_t^T = Ubar_t Vbar'_t^T.
+
+    For every transfer vector t the SVD of C_t keeps the k_t singular values with
+    s_i >= dir_tol * s_0(C_t); dir_tol <= 0 keeps all k. Vbar'_t = Vbar_t Sigmabar_t is formed
+    here, as Sec. 3.2 step 4 advises. Returns dict(Ubar: list of (k, k_t), Vbarp: list of
+    (k, k_t), kt: (316,) ints, s: (316, k) singular values).
+    """
+    Ubar, Vbarp, kts, svals = [], [], [], []
+    for Ct in C:
+        Uc, sc, Vct = np.linalg.svd(Ct)
+        kt = len(sc) if dir_tol is None or dir_tol <= 0 else int(np.sum(sc >= dir_tol * sc[0]))
+        Ubar.append(Uc[:, :kt].copy())
+        Vbarp.append((Vct[:kt].T * sc[:kt][None, :]).copy())
+        kts.append(kt)
+        svals.append(sc)
+    return dict(Ubar=Ubar, Vbarp=Vbarp, kt=np.array(kts), s=np.array(svals))
+
+
 def conv_grid_size(p: int) -> int:
     """Side of the convolution grid, 2P points (App. A.1)."""
     return 2 * p

@@ -198,6 +198,59 @@ def test_truncated_error_is_monotone(rng):
     assert ks[0] < ks[-1] <= n
 
 
+def _directional_spectral_errors(ops, d):
+    """||C_t - Ubar_t Vbar'_t^T||_2 for every t, by an independent 2-norm evaluation."""
+    return np.array([np.linalg.norm(C - Ub @ Vp.T, 2) for C, Ub, Vp in zip(ops["C"], d["Ubar"], d["Vbarp"])])
+
+
+def test_directional_recompression_full_rank_is_exact(rng):
+    """Eq. 15 with every singular value kept reproduces C_t, and the BLAS-M2L result with it."""
+    p, level = 4, 3
+    n = G.n_surface(p)
+    ops = O.compressed_operators(p, 1e-6, G.box_width(level))
+    d = O.directional_operators(ops["C"], 0.0)
+    assert np.all(d["kt"] == ops["k"])
+    scale = max(np.linalg.norm(C, 2) for C in ops["C"])
+    assert _directional_spectral_errors(ops, d).max() < 1e-13 * scale
+    q = rng.standard_normal((8 ** level, 2, n))
+    tg = np.arange(0, 512, 17)
+    _, phi_c = M.m2l_compressed(p, level, q, ops, targets=tg)
+    _, phi_d = M.m2l_compressed(p, level, q, {**ops, **d}, targets=tg)
+    assert M.rel_l2_error(phi_c, phi_d) < 1e-13
+
+
+def test_directional_truncation_is_the_best_rank_kt_approximation():
+    """Eckart-Young: the spectral-norm error of the rank-k_t truncation equals the first dropped
+    singular value, which the threshold keeps below dir_tol * s_0(C_t)."""
+    ops = O.compressed_operators(6, 1e-7)
+    for dir_tol in (1e-3, 1e-6):
+        d = O.directional_operators(ops["C"], dir_tol)
+        err = _directional_spectral_errors(ops, d)
+        s = d["s"]
+        dropped = np.array([s[t, d["kt"][t]] if d["kt"][t] < s.shape[1] else 0.0 for t in range(len(s))])
+        assert np.allclose(err, dropped, rtol=1e-6, atol=1e-14 * s[:, 0].max())
+        assert np.all(err < dir_tol * s[:, 0] * (1 + 1e-9))
+        assert np.all(s[np.arange(len(s)), d["kt"] - 1] >= dir_tol * s[:, 0])
+
+
+def test_directional_error_is_monotone(rng):
+    p, level = 5, 3
+    n = G.n_surface(p)
+    q = rng.standard_normal((8 ** level, 1, n))
+    tg = np.arange(0, 512, 13)
+    ops = O.compressed_operators(p, 1e-10, G.box_width(level))
+    _, phi_ref = M.m2l_compressed(p, level, q, ops, targets=tg)
+    errs, sizes = [], []
+    for dir_tol in (1e-2, 1e-4, 1e-6, 1e-8):
+        d = O.directional_operators(ops["C"], dir_tol)
+        _, phi = M.m2l_compressed(p, level, q, {**ops, **d}, targets=tg)
+        errs.append(M.rel_l2_error(phi_ref, phi))
+        sizes.append(int(d["kt"].sum()))
+    assert all(a >= b for a, b in zip(errs, errs[1:])), errs
+    assert all(a <= b for a, b in zip(sizes, sizes[1:]))
+    assert errs[0] > 1e-4 and errs[-1] < 1e-6
+
+
 def test_symmetric_kernel_fat_and_thin_share_singular_values():
     """Sec. 3.1: for the symmetric Laplace kernel with equal surfaces one SVD suffices."""
     ops = O.compressed_operators(4, 1e-6)

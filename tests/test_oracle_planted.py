@@ -105,3 +105,33 @@ def test_loose_pinv_threshold_is_caught(monkeypatch):
     s = np.linalg.svd(A, compute_uv=False)
     assert V.shape[1] != np.sum(s > max(A.shape) * np.finfo(float).eps * s[0])
     assert np.linalg.matrix_rank(linalg.pinv(A)) != V.shape[1]
+
+
+def _directional_worst_error(directional):
+    ops = O.compressed_operators(5, 1e-7)
+    d = directional(ops["C"], 1e-5)
+    return max(np.linalg.norm(C - Ub @ Vp.T, 2) / np.linalg.norm(C, 2)
+               for C, Ub, Vp in zip(ops["C"], d["Ubar"], d["Vbarp"]))
+
+
+def test_directional_reference_is_within_threshold():
+    assert _directional_worst_error(O.directional_operators) < 1e-5
+
+
+def test_directional_factor_without_sigma_is_caught():
+    """Vbar' formed without the singular values (Vbar instead of Vbar Sigmabar)."""
+    def bad(C, dir_tol):
+        d = O.directional_operators(C, dir_tol)
+        d["Vbarp"] = [Vp / np.linalg.norm(Vp, axis=0)[None, :] for Vp in d["Vbarp"]]
+        return d
+    assert not _directional_worst_error(bad) < 1e-5
+
+
+def test_directional_swapped_factors_are_caught():
+    """Ubar and Vbar' exchanged (C_t^T applied instead of C_t)."""
+    def bad(C, dir_tol):
+        d = O.directional_operators(C, dir_tol)
+        d["Ubar"], d["Vbarp"] = d["Vbarp"], d["Ubar"]
+        return d
+    assert not _directional_worst_error(bad) < 1e-5
+
