@@ -45,7 +45,7 @@ from paper_2408_07436_gb300 import workloads as W  # noqa: E402
 VARIANTS = ["blas-fp64", "blas-fp32", "blas-tf32x3", "blas-bf16x3", "fft-fp64", "fft-fp32"]
 METRIC = "M2L interactions/s and % roofline: mixed+batched vs FP64 GPU at stated rel err"
 UNIT = "interactions/s"
-WORKLOAD = ("laplace3d-m2l uniform-cube 1M points depth5 p6 1rhs blas(rank_tol 1e-7)+fft(grid 11^3) "
+WORKLOAD = ("laplace3d-m2l uniform-cube 1M points depth5 p6 1rhs blas(rank_tol 1e-7, directional 1e-8)+fft(grid 11^3) "
             "fp64+fp32+tf32x3+bf16x3")
 
 # Nominal per-GPU figures (GB300) used where no measured peak exists.
@@ -154,7 +154,7 @@ def algorithmic_work(plan, form, prec, R):
     if form == "blas":
         k = plan.query(lib.M2L_Q_RANK)
         r = plan.query(lib.M2L_Q_PINV_RANK)
-        return {"compress": 2.0 * n * k * rows, "contract": 2.0 * k * k * pairs * R,
+        return {"compress": 2.0 * n * k * rows, "contract": float(plan.query(lib.M2L_Q_CONTRACT_FLOPS, -1)) * R,
                 "expand": 2.0 * (r * k + n * r) * rows}
     F = plan.query(lib.M2L_Q_FREQS)
     g = plan.query(lib.M2L_Q_GRID)
@@ -173,7 +173,7 @@ def workload_spec(name, depth):
         return [W.c2(depth=depth)], VARIANTS, False, None, WORKLOAD
     if name == "c3":
         return ([W.c3()], ["blas-bf16x3", "blas-tf32x3", "blas-fp64", "fft-fp32", "fft-fp64"], False, None,
-                "laplace3d-m2l uniform-cube 8M points depth6 p8 1rhs blas(rank_tol 1e-7) bf16x3/tf32x3/fp64 + fft fp32/fp64")
+                "laplace3d-m2l uniform-cube 8M points depth6 p8 1rhs blas(rank_tol 1e-7, directional 1e-8) bf16x3/tf32x3/fp64 + fft fp32/fp64")
     if name == "c4":
         return ([W.c4()], ["blas-bf16x3", "blas-tf32x3", "fft-fp32"], False, None,
                 "laplace3d-m2l unit-sphere-surface 2M points depth6 p6 32rhs pruned boxes blas(rank_tol 1e-7) bf16x3/tf32x3 + fft fp32")
@@ -209,6 +209,8 @@ def run_ours(args, rank, world, local_rank):
             pl = lib.Plan(wl.depth, wl.p, tol, form=form, precision=prec).set(timing=0 if batched else 1)
             if form == "fft" and wl.fft_grid:
                 pl.set(fft_grid=wl.fft_grid)
+            if form == "blas" and wl.dir_tol:
+                pl.set(dir_tol=wl.dir_tol)
             if target_tol is not None:
                 pl.set(target_tol=target_tol)
             for l in wl.levels:

@@ -75,9 +75,14 @@ enum m2l_option_e {
                                 it, times them on the plan's boxes and keeps the fastest, per n_rhs. */
     M2L_OPT_FFT_GRID = 6,    /* convolution grid side: 0 = 2p (default), else 2p-1 <= g <= 2p */
     M2L_OPT_TIMING = 7,      /* 1: record CUDA events around every stage (see m2l_stage_times) */
-    M2L_OPT_TC_GROUP = 8     /* split tensor-core forms: transfer vectors summed in tensor memory before
+    M2L_OPT_TC_GROUP = 8,    /* split tensor-core forms: transfer vectors summed in tensor memory before
                                 each round-to-nearest FP32 drain, 1..189 (default 1). Larger is faster;
                                 the tensor cores' truncating accumulation grows with it */
+    M2L_OPT_DIR_TOL = 9      /* directional recompression of the BLAS operators (Sec. 3.1, Eq. 15):
+                                the bits of a double dir_tol >= 0; 0 (default) = off. With
+                                dir_tol > 0 each C_t is factored as Ubar_t Vbar'_t^T keeping its
+                                singular values >= dir_tol s_0(C_t), and the CUDA-core contraction
+                                (FP64, FP32) applies the two factors; the tensor-core forms keep C_t */
 };
 
 /* Stages of one application, as indexed by m2l_stage_times. */
@@ -120,10 +125,14 @@ enum m2l_query_e {
     M2L_Q_FORM = 9,       /* form the next apply with n_rhs = `level` (>= 1) will run; resolves AUTO */
     M2L_Q_PRECISION = 10, /* precision of that apply (so the caller knows the element type) */
     M2L_Q_LAUNCHES = 11,  /* kernels launched by the last apply */
-    M2L_Q_DEVICE_STATUS = 12 /* waits for the plan's stream, reads the device status word into *out
+    M2L_Q_DEVICE_STATUS = 12, /* waits for the plan's stream, reads the device status word into *out
                                 (0, or the m2l_wait_e code of the first bounded wait that ran out
                                 since the last query) and clears it; returns M2L_ETIMEOUT when it
                                 was nonzero: results written since the last query are invalid */
+    M2L_Q_CONTRACT_FLOPS = 13, /* algorithmic flops of the BLAS contraction for one right-hand side at
+                                  `level` (-1: all levels): 2 k^2 per pair, or 4 k k_t with
+                                  M2L_OPT_DIR_TOL (rounded to an integer) */
+    M2L_Q_DIR_RANK_SUM = 14    /* sum of k_t over the 316 transfer vectors (0 when M2L_OPT_DIR_TOL is 0) */
 };
 
 /* Where a bounded device wait ran out (the value of M2L_Q_DEVICE_STATUS). Every wait of a kernel

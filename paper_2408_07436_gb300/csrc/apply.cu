@@ -391,7 +391,12 @@ static int blas_group(std::vector<Run> &runs, int precision, Workspace &ws, cuda
     const int *tvl = (const int *)own->exec.tvl;
     if (!tc) {
         stage_begin(own, M2L_STAGE_CONTRACT);
-        M2L_TRY(launch_contract_simt<T>(lv, tl, ntiles, tvl, qt, (const T *)D.C, kp, total, phit, s));
+        int rc = M2L_EUNSUPPORTED;
+        if (own->dir_tol > 0 && D.Ub)
+            rc = launch_contract_simt_dir<T>(lv, tl, ntiles, tvl, qt, (const T *)D.Ub, (const T *)D.Vt,
+                                             (const int *)D.dir_meta, own->k, kp, own->dir_kt8_max, total, phit, s);
+        if (rc == M2L_EUNSUPPORTED) rc = launch_contract_simt<T>(lv, tl, ntiles, tvl, qt, (const T *)D.C, kp, total, phit, s);
+        M2L_TRY(rc);
         stage_end(own, 1);
     } else {
         if constexpr (sizeof(T) == 4) {
@@ -520,9 +525,10 @@ int apply_device(m2l_plan_t *pl, const void *q, void *L, int level, int R) {
 
 struct GroupKey {
     int p, form, precision, kp, g;
-    double rank_tol;
+    double rank_tol, dir_tol;
     bool operator==(const GroupKey &o) const {
-        return p == o.p && form == o.form && precision == o.precision && kp == o.kp && g == o.g && rank_tol == o.rank_tol;
+        return p == o.p && form == o.form && precision == o.precision && kp == o.kp && g == o.g && rank_tol == o.rank_tol &&
+               dir_tol == o.dir_tol;
     }
 };
 
@@ -539,7 +545,7 @@ int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void
         M2L_TRY(resolve_form(pl, R[i], &form, &prec));
         M2L_TRY(prepare_plan(pl, form, prec));
         GroupKey k{pl->p, form, prec, form == M2L_FORM_BLAS ? pl->kp : 0, form == M2L_FORM_FFT ? pl->g : 0,
-                   form == M2L_FORM_BLAS ? pl->rank_tol : 0.0};
+                   form == M2L_FORM_BLAS ? pl->rank_tol : 0.0, form == M2L_FORM_BLAS ? pl->dir_tol : 0.0};
         size_t gi = 0;
         while (gi < keys.size() && !(keys[gi] == k)) ++gi;
         if (gi == keys.size()) {
@@ -583,7 +589,8 @@ int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         for (const Run &r : groups[gi]) {
             const DevOps &D = r.pl->dev[precs[gi]];
-            for (const void *ptr : {lead->batch_ws.buf, lead->spec.buf, r.pl->exec.levels, r.pl->exec.tiles, r.pl->exec.tvl, D.C, D.C_hi, D.C_lo, D.Khat, D.A, D.V, D.Vlo})
+            for (const void *ptr : {lead->batch_ws.buf, lead->spec.buf, r.pl->exec.levels, r.pl->exec.tiles,
+                                    r.pl->exec.tvl, D.C, D.C_hi, D.C_lo, D.Ub, D.Vt, D.dir_meta, D.Khat, D.A, D.V, D.Vlo})
                 sig.push_back((long long)(uintptr_t)ptr);
             sig.push_back(r.pl->tc_group);
             sig.push_back(r.pl->fft_grid_opt);

@@ -149,6 +149,22 @@ int m2l_set_option(m2l_plan_t *pl, int key, long long value) {
                 }
             }
             return M2L_OK;
+        case M2L_OPT_DIR_TOL: {
+            double d;
+            std::memcpy(&d, &value, sizeof d);
+            if (!(d >= 0.0) || !std::isfinite(d) || d >= 1.0) break;
+            if (d != pl->dir_tol) {
+                pl->dir_tol = d;
+                pl->dir_ready = false;
+                for (auto &D : pl->dev) {
+                    for (void **pp : {&D.Ub, &D.Vt, &D.dir_meta}) {
+                        if (*pp) cudaFree(*pp);
+                        *pp = nullptr;
+                    }
+                }
+            }
+            return M2L_OK;
+        }
         default:
             set_error("unknown option key %d", key);
             return M2L_EINVAL;
@@ -338,6 +354,20 @@ int m2l_query(const m2l_plan_t *cpl, int what, int level, long long *out) {
             int l0 = level < 0 ? 2 : level, l1 = level < 0 ? pl->depth : level;
             for (int l = l0; l <= l1; ++l) s += what == M2L_Q_PAIRS ? pl->ldev[l].pairs : pl->ldev[l].nboxes;
             *out = s;
+            return M2L_OK;
+        }
+        case M2L_Q_CONTRACT_FLOPS: {
+            if (!(level == -1 || (level >= 2 && level <= pl->depth))) break;
+            double f = 0.0;
+            if ((rc = contract_flops(pl, level, &f))) return rc;
+            *out = (long long)(f + 0.5);
+            return M2L_OK;
+        }
+        case M2L_Q_DIR_RANK_SUM: {
+            *out = 0;
+            if (pl->dir_tol <= 0) return M2L_OK;
+            if ((rc = build_directional(pl))) return rc;
+            for (int v : pl->dir_kt) *out += v;
             return M2L_OK;
         }
         case M2L_Q_GRID:

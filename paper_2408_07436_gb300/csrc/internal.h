@@ -45,6 +45,9 @@ struct DevOps {
     void *Vlo = nullptr;         // [n][rp]     V_eps - fl32(V_eps) (single-precision plans)
     void *Uc = nullptr;          // [n][kp]     U (check-potential output)
     void *C_hi = nullptr, *C_lo = nullptr;  // split C_t for the tensor-core forms
+    void *Ub = nullptr, *Vt = nullptr;      // directional factors (Eq. 15): Ubar_t [k_pad][k_t8],
+                                            // Vbar'_t^T [k_t8][k_pad], concatenated over t
+    void *dir_meta = nullptr;               // [316] int4: Ub offset, Vt offset, k_t, k_t8
     alignas(64) unsigned char tmap[2][128] = {};  // TMA maps (CUtensorMap) of C_hi and C_lo
     // FFT form
     void *Khat = nullptr;        // [316+1][F] complex kernel spectra (last row zero)
@@ -119,6 +122,12 @@ struct m2l_plan_s {
     std::vector<double> Aop;                      // [r][k] = Uteps * U
     int r32 = 0;                                  // singular values kept with Eq. 10's alpha = 1e-9
     std::vector<double> Veps32, Uteps32, Aop32;   // the factors used by single-precision paths
+    double dir_tol = 0.0;                         // directional recompression threshold (0: off)
+    bool dir_ready = false;
+    std::vector<int> dir_kt;                      // [316] k_t
+    std::vector<double> dir_ub, dir_vt;           // packed as on the device (FP64)
+    std::vector<int> dir_meta;                    // [316][4]
+    int dir_kt8_max = 0;
     int g = 0, F = 0;
     std::vector<double> Khat;                     // [316][F][2]
     std::vector<double> twiddle;                  // [g][2]
@@ -150,6 +159,8 @@ namespace m2l {
 // plan.cpp
 int build_pinv(m2l_plan_t *pl);
 int build_blas_host(m2l_plan_t *pl);
+int build_directional(m2l_plan_t *pl);
+int contract_flops(m2l_plan_t *pl, int level, double *out);
 int build_fft_host(m2l_plan_t *pl);
 int build_level_tables(m2l_plan_t *pl);     // host tables and pair counts
 int upload_level_tables(m2l_plan_t *pl);    // device copies

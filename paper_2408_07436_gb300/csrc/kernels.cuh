@@ -58,6 +58,14 @@ template <class T>
 int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
                          const T *qt, const T *C, int kp, long long zero_row, T *phit, cudaStream_t s);
 
+// B2 with the directional factors (Eq. 15): Ub = Ubar_t [k_pad][k_t8], Vt = Vbar'_t^T [k_t8][k_pad]
+// concatenated over t, meta = [316] int4 (Ub offset, Vt offset, k_t, k_t8). M2L_EUNSUPPORTED
+// (nothing launched) when its shared-memory tiles do not fit.
+template <class T>
+int launch_contract_simt_dir(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
+                             const T *qt, const T *Ub, const T *Vt, const int *meta, int k, int kp, int kt8max,
+                             long long zero_row, T *phit, cudaStream_t s);
+
 // FFT form, one level at a time.
 template <class T>
 int launch_fft_forward(const LevelView &L, int R, int p, int n, int g, const int *lattice,

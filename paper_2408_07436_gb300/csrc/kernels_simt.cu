@@ -335,6 +335,180 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(const LevelView *__r
     }
 }
 
+// B2 with the directional factors of Eq. 15. Per transfer vector t the tile's gathered sources X
+// (64 rows x k) go through the two products of Sec. 3.2 step 4: xi = X Vbar'_t (64 x k_t) and
+// phit += xi Ubar_t^T, so a pair costs 4 k k_t flops instead of 2 k^2. Stage 1 streams X and
+// Vbar'_t^T through shared memory in chunks of 16 along k (as the plain kernel streams C_t) and
+// gives a thread rows 2 sy, 2 sy + 1 and columns sx + 8 m of xi; xi then waits in shared memory
+// for stage 2, which uses the 4 x TN tile of the plain kernel and Ubar_t in chunks of 16 along
+// k_t. About 75 KB of shared memory in FP64, so two CTAs share an SM and one computes while the
+// other gathers. Both stages map the same 8 rows to a warp: a warp whose rows have no source
+// skips the products of both.
+// One 16-deep chunk of stage 1 with exactly NM column groups per thread: guarding an unrolled
+// loop with a runtime count would leave predicated-off FMAs that still occupy the FP64 pipe.
+template <class T, int NM>
+__device__ __forceinline__ void dir_stage1_chunk(const T *Xs, const T *Vs, int sx, int sy, T (&y)[8][2]) {
+    constexpr int XP = 66, VP = 66;
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+        const T x0 = Xs[kk * XP + 2 * sy], x1 = Xs[kk * XP + 2 * sy + 1];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            const T w = Vs[kk * VP + sx + 8 * m];
+            y[m][0] = fma(x0, w, y[m][0]);
+            y[m][1] = fma(x1, w, y[m][1]);
+        }
+    }
+}
+
+template <class T, int TN>
+__global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView *__restrict__ levels,
+                                                                const ContractTile *__restrict__ tiles,
+                                                                const int *__restrict__ tvl, const T *__restrict__ qt,
+                                                                const T *__restrict__ Ub, const T *__restrict__ Vt,
+                                                                const int4 *__restrict__ meta, int k, int kp, int kt8max,
+                                                                long long zero_row, T *__restrict__ phit) {
+    constexpr int BM = 64, BN = 16 * TN, BK = 16, XP = BM + 2, YC = 64;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Ys = reinterpret_cast<T *>(smem_raw);  // [kt8max][XP]: xi transposed
+    T *Xs = Ys + (size_t)kt8max * XP;         // [BK][XP]: a chunk of X transposed
+    T *Vs = Xs + (size_t)BK * XP;             // [BK][YC + 2]: a chunk of Vbar'_t
+    T *Us = Vs + (size_t)BK * (YC + 2);       // [BK][BN + 4]: a chunk of Ubar_t
+    __shared__ long long src_row[BM];
+    __shared__ int tgt_b[BM], tgt_r[BM];
+    __shared__ uint32_t tgt_xyz[BM];
+    const ContractTile tile = tiles[blockIdx.x];
+    const LevelView &L = levels[tile.lev];
+    const int R = L.R;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, sx = tid & 7, sy = tid >> 3;
+    const int col0 = blockIdx.y * BN;
+    if (tid < BM) {
+        if (tid < tile.rows) {
+            long long j = (long long)tile.j0 + tid;
+            int b = L.perm[L.oct_start[tile.oct] + j / R];
+            tgt_b[tid] = b;
+            tgt_r[tid] = (int)(j % R);
+            tgt_xyz[tid] = L.xyz[b];
+        } else {
+            tgt_b[tid] = -1;
+            tgt_r[tid] = 0;
+            tgt_xyz[tid] = 0;
+        }
+    }
+    T a[4][TN];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) a[i][j] = T(0);
+    const int N = L.N;
+    for (int v = 0; v < tile.ntv; ++v) {
+        const int pk = tvl[tile.tv0 + v];
+        const int dx = (pk & 15) - 3, dy = ((pk >> 4) & 15) - 3, dz = ((pk >> 8) & 15) - 3;
+        const int4 md = meta[pk >> 12];  // Ubar_t offset, Vbar'_t^T offset, k_t, k_t rounded up to 8
+        __syncthreads();                 // previous transfer vector's shared memory fully consumed
+        if (tid < BM) {
+            long long sr = zero_row;
+            if (tgt_b[tid] >= 0) {
+                uint32_t p = tgt_xyz[tid];
+                int x = (int)(p & 1023) + dx, y = (int)((p >> 10) & 1023) + dy, z = (int)((p >> 20) & 1023) + dz;
+                if (x >= 0 && y >= 0 && z >= 0 && x < N && y < N && z < N) {
+                    int s = L.slot[((long long)z * N + y) * N + x];
+                    if (s >= 0) sr = L.row0 + (long long)s * R + tgt_r[tid];
+                }
+            }
+            src_row[tid] = sr;
+        }
+        __syncthreads();
+        bool mine = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mine |= src_row[ty * 4 + i] != zero_row;
+        const bool live = __any_sync(0xffffffffu, mine);
+        // stage 1: xi = X Vbar'_t, up to 64 columns of xi per pass
+        for (int jp0 = 0; jp0 < md.w; jp0 += YC) {
+            const int ncol = min(YC, md.w - jp0), nm = ncol / 8;
+            T y[8][2];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) y[m][0] = y[m][1] = T(0);
+            const T *V = Vt + md.y + (size_t)jp0 * kp;
+            for (int k0 = 0; k0 < k; k0 += BK) {
+                if (k0) __syncthreads();  // previous chunk consumed
+                for (int e = tid; e < BM * BK; e += 256) {
+                    const int r = e / BK, kk = e % BK;
+                    Xs[kk * XP + r] = k0 + kk < kp ? qt[src_row[r] * kp + k0 + kk] : T(0);
+                }
+                for (int e = tid; e < ncol * BK; e += 256) {
+                    const int j = e / BK, kk = e % BK;
+                    Vs[kk * (YC + 2) + j] = k0 + kk < kp ? V[(size_t)j * kp + k0 + kk] : T(0);
+                }
+                __syncthreads();
+                if (live) {
+                    switch (nm) {
+                        case 1: dir_stage1_chunk<T, 1>(Xs, Vs, sx, sy, y); break;
+                        case 2: dir_stage1_chunk<T, 2>(Xs, Vs, sx, sy, y); break;
+                        case 3: dir_stage1_chunk<T, 3>(Xs, Vs, sx, sy, y); break;
+                        case 4: dir_stage1_chunk<T, 4>(Xs, Vs, sx, sy, y); break;
+                        case 5: dir_stage1_chunk<T, 5>(Xs, Vs, sx, sy, y); break;
+                        case 6: dir_stage1_chunk<T, 6>(Xs, Vs, sx, sy, y); break;
+                        case 7: dir_stage1_chunk<T, 7>(Xs, Vs, sx, sy, y); break;
+                        default: dir_stage1_chunk<T, 8>(Xs, Vs, sx, sy, y); break;
+                    }
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                if (m < nm) {
+                    Ys[(size_t)(jp0 + sx + 8 * m) * XP + 2 * sy] = y[m][0];
+                    Ys[(size_t)(jp0 + sx + 8 * m) * XP + 2 * sy + 1] = y[m][1];
+                }
+            }
+            __syncthreads();  // the next pass reuses Xs and Vs; stage 2 reads Ys
+        }
+        // stage 2: phit += xi Ubar_t^T over the k_t columns of xi
+        const T *Ut = Ub + md.x;  // [kp][k_t8]
+        for (int j0 = 0; j0 < md.z; j0 += BK) {
+            if (j0) __syncthreads();  // previous chunk of Ubar_t consumed
+            for (int e = tid; e < BN * BK; e += 256) {
+                const int c = e / BK, kk = e % BK, gc = col0 + c;
+                Us[(size_t)kk * (BN + 4) + c] = (gc < kp && j0 + kk < md.w) ? Ut[(size_t)gc * md.w + j0 + kk] : T(0);
+            }
+            __syncthreads();
+            if (live) {
+                const int jn = min(BK, md.z - j0);
+                // a full chunk unrolled; the last, partial one with an exact trip count
+                auto step = [&](int kk) {
+                    T xa[4], wb[TN];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) xa[i] = Ys[(size_t)(j0 + kk) * XP + ty * 4 + i];
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) wb[j] = Us[(size_t)kk * (BN + 4) + tx * TN + j];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < TN; ++j) a[i][j] = fma(xa[i], wb[j], a[i][j]);
+                };
+                if (jn == BK) {
+#pragma unroll
+                    for (int kk = 0; kk < BK; ++kk) step(kk);
+                } else {
+#pragma unroll 1
+                    for (int kk = 0; kk < jn; ++kk) step(kk);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int r = ty * 4 + i;
+        if (r >= tile.rows) continue;
+        long long orow = L.row0 + (long long)tgt_b[r] * R + tgt_r[r];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            int c = col0 + tx * TN + j;
+            if (c < kp) phit[orow * kp + c] = a[i][j];
+        }
+    }
+}
+
 // Columns per thread for a rank: the fewest column blocks of at most 16 * max_tn columns, then
 // the narrowest blocks that still cover k_pad.
 inline int contract_tn(int kp, int max_tn) {
@@ -368,6 +542,44 @@ int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, lon
             return M2L_EINVAL;
     }
     return check_launch("contract");
+}
+
+template <class T, int TN>
+static int launch_contract_dir_tn(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
+                                  const T *qt, const T *Ub, const T *Vt, const int *meta, int k, int kp, int kt8max,
+                                  long long zero_row, T *phit, cudaStream_t s) {
+    constexpr int BN = 16 * TN;
+    const size_t smem = sizeof(T) * ((size_t)kt8max * 66 + (size_t)16 * 66 + (size_t)16 * 66 + (size_t)16 * (BN + 4));
+    if (smem > 200 * 1024) return M2L_EUNSUPPORTED;
+    if (cudaFuncSetAttribute(contract_simt_dir_kernel<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return M2L_EUNSUPPORTED;
+    }
+    dim3 grid((unsigned)ntiles, (unsigned)((kp + BN - 1) / BN));
+    contract_simt_dir_kernel<T, TN><<<grid, 256, smem, s>>>(levels, tiles, tvl, qt, Ub, Vt,
+                                                             reinterpret_cast<const int4 *>(meta), k, kp, kt8max,
+                                                             zero_row, phit);
+    return check_launch("contract_dir");
+}
+
+// Returns M2L_EUNSUPPORTED (nothing launched) when the shared-memory tiles do not fit; the caller
+// then applies C_t unfactored.
+template <class T>
+int launch_contract_simt_dir(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
+                             const T *qt, const T *Ub, const T *Vt, const int *meta, int k, int kp, int kt8max,
+                             long long zero_row, T *phit, cudaStream_t s) {
+    if (ntiles <= 0) return M2L_OK;
+    const int tn = contract_tn(kp, 12);  // one column block where possible: stage 1 is per block
+    switch (tn) {
+#define M2L_TN(n) \
+    case n: return launch_contract_dir_tn<T, n>(levels, tiles, ntiles, tvl, qt, Ub, Vt, meta, k, kp, kt8max, zero_row, phit, s);
+        M2L_TN(1) M2L_TN(2) M2L_TN(3) M2L_TN(4) M2L_TN(5) M2L_TN(6)
+        M2L_TN(7) M2L_TN(8) M2L_TN(9) M2L_TN(10) M2L_TN(11) M2L_TN(12)
+#undef M2L_TN
+        default:
+            return M2L_EUNSUPPORTED;
+    }
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -856,6 +1068,9 @@ size_t fft_smem_bytes(int p, int g, int elt) {
 #define M2L_INSTANTIATE(T)                                                                              \
     template int launch_gemm_xwt<T>(const T *, long long, const T *, long long, T *, long long, long long, \
                                     int, int, int, cudaStream_t);                                       \
+    template int launch_contract_simt_dir<T>(const LevelView *, const ContractTile *, long long, const int *,   \
+                                             const T *, const T *, const T *, const int *, int, int, int, long long, \
+                                             T *, cudaStream_t);                                             \
     template int launch_contract_simt<T>(const LevelView *, const ContractTile *, long long, const int *,       \
                                          const T *, const T *, int, long long, T *, cudaStream_t);      \
     template int launch_fft_forward<T>(const LevelView &, int, int, int, int, const int *, const T *,   \

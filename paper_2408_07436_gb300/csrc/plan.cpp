@@ -228,6 +228,98 @@ int build_blas_host(m2l_plan_t *pl) {
     return M2L_OK;
 }
 
+// Directional recompression (Eq. 15): C_t ~ Ubar_t Sigmabar_t Vbar_t^T = Ubar_t Vbar'_t^T with the
+// k_t singular values of C_t at or above dir_tol s_0(C_t). Packed as the contraction reads them:
+// Ubar_t as [k_pad][k_t8] (one row per output component) and Vbar'_t^T as [k_t8][k_pad], k_t
+// rounded up to 8 with zero padding.
+int build_directional(m2l_plan_t *pl) {
+    if (pl->dir_ready) return M2L_OK;
+    int rc = build_blas_host(pl);
+    if (rc) return rc;
+    const int k = pl->k, kp = pl->kp;
+    std::vector<int> kt(kNumTransfer);
+    std::vector<std::vector<double>> ub(kNumTransfer), vt(kNumTransfer);
+#pragma omp parallel for schedule(dynamic, 2)
+    for (int t = 0; t < kNumTransfer; ++t) {
+        // C_t is row-major [a][c]; the SVD routine takes column-major
+        std::vector<double> A((size_t)k * k), U, sv, V;
+        const double *C = &pl->C[(size_t)t * k * k];
+        for (int a = 0; a < k; ++a)
+            for (int c = 0; c < k; ++c) A[(size_t)c * k + a] = C[(size_t)a * k + c];
+        jacobi_svd(A, k, k, U, sv, V);
+        int m = 0;
+        while (m < k && sv[m] >= pl->dir_tol * sv[0]) ++m;
+        if (m < 1) m = 1;
+        const int m8 = round_up(m, 8);
+        kt[t] = m;
+        ub[t].assign((size_t)kp * m8, 0.0);
+        vt[t].assign((size_t)m8 * kp, 0.0);
+        for (int j = 0; j < m; ++j)
+            for (int a = 0; a < k; ++a) {
+                ub[t][(size_t)a * m8 + j] = U[(size_t)j * k + a];          // Ubar_t[a][j]
+                vt[t][(size_t)j * kp + a] = sv[j] * V[(size_t)j * k + a];  // Vbar'_t^T[j][c] = s_j V[c][j]
+            }
+    }
+    pl->dir_kt = kt;
+    pl->dir_ub.clear();
+    pl->dir_vt.clear();
+    pl->dir_meta.assign((size_t)kNumTransfer * 4, 0);
+    pl->dir_kt8_max = 0;
+    for (int t = 0; t < kNumTransfer; ++t) {
+        const int m8 = round_up(kt[t], 8);
+        pl->dir_meta[4 * t + 0] = (int)pl->dir_ub.size();
+        pl->dir_meta[4 * t + 1] = (int)pl->dir_vt.size();
+        pl->dir_meta[4 * t + 2] = kt[t];
+        pl->dir_meta[4 * t + 3] = m8;
+        pl->dir_kt8_max = std::max(pl->dir_kt8_max, m8);
+        pl->dir_ub.insert(pl->dir_ub.end(), ub[t].begin(), ub[t].end());
+        pl->dir_vt.insert(pl->dir_vt.end(), vt[t].begin(), vt[t].end());
+    }
+    pl->dir_ready = true;
+    return M2L_OK;
+}
+
+// Algorithmic flops of the BLAS contraction for one right-hand side at `level` (-1: levels
+// 2..depth): 2 k^2 per (target, source) pair, or 4 k k_t for a pair with transfer vector t when
+// the directional factors are used (the two products of Sec. 3.2 step 4).
+int contract_flops(m2l_plan_t *pl, int level, double *out) {
+    int rc = build_level_tables(pl);
+    if (!rc) rc = build_blas_host(pl);
+    if (!rc && pl->dir_tol > 0) rc = build_directional(pl);
+    if (rc) return rc;
+    double w[kNumTransfer];
+    for (int t = 0; t < kNumTransfer; ++t)
+        w[t] = pl->dir_tol > 0 ? 4.0 * pl->k * pl->dir_kt[t] : 2.0 * pl->k * pl->k;
+    double total = 0.0;
+    const int l0 = level < 0 ? 2 : level, l1 = level < 0 ? pl->depth : level;
+    for (int l = l0; l <= l1; ++l) {
+        const LevelDev &L = pl->ldev[l];
+        const long long N = 1LL << l;
+        double sum = 0.0;
+#pragma omp parallel for reduction(+ : sum) schedule(static)
+        for (long long b = 0; b < L.nboxes; ++b) {
+            const uint32_t p = L.h_xyz[b];
+            const int x = p & 1023, y = (p >> 10) & 1023, z = (p >> 20) & 1023;
+            for (int tx = -3; tx <= 3; ++tx)
+                for (int ty = -3; ty <= 3; ++ty)
+                    for (int tz = -3; tz <= 3; ++tz) {
+                        const int ti = transfer_index(tx, ty, tz);
+                        if (ti < 0) continue;
+                        const int sx = x + tx, sy = y + ty, sz = z + tz;
+                        // the source must lie in the target's interaction list: parents adjacent
+                        if ((sx >> 1) - (x >> 1) < -1 || (sx >> 1) - (x >> 1) > 1 || (sy >> 1) - (y >> 1) < -1 ||
+                            (sy >> 1) - (y >> 1) > 1 || (sz >> 1) - (z >> 1) < -1 || (sz >> 1) - (z >> 1) > 1)
+                            continue;
+                        if (sx < 0 || sy < 0 || sz < 0 || sx >= N || sy >= N || sz >= N) continue;
+                        if (L.h_slot[((size_t)sz * N + sy) * N + sx] >= 0) sum += w[ti];
+                    }
+        }
+        total += sum;
+    }
+    *out = total;
+    return M2L_OK;
+}
+
 // Kernel spectra (App. A.1 step 1): for each transfer vector the kernel sequence
 // G_t(m) = K(-t + h m), h = alpha_inner / (p - 1), m in [-(p-1), p-1]^3, placed at m mod g on the
 // g^3 grid, then its 3D real DFT keeping kz in [0, g/2] (f = (kx g + ky)(g/2+1) + kz).
@@ -473,6 +565,17 @@ static int upload_vec(void *&dst, const std::vector<T> &v) {
 
 int split_tc_operators(m2l_plan_t *pl, int precision);  // kernels_tc.cu
 
+// The directional factors, when the plan asks for them and they are not on the device yet.
+template <class T>
+static int upload_directional(m2l_plan_t *pl, DevOps &D) {
+    if (pl->dir_tol <= 0 || D.Ub) return M2L_OK;
+    int rc = build_directional(pl);
+    if (rc) return rc;
+    std::vector<T> ub(pl->dir_ub.begin(), pl->dir_ub.end()), vt(pl->dir_vt.begin(), pl->dir_vt.end());
+    if ((rc = upload_vec(D.Ub, ub)) || (rc = upload_vec(D.Vt, vt)) || (rc = upload_vec(D.dir_meta, pl->dir_meta))) return rc;
+    return M2L_OK;
+}
+
 template <class T>
 static int upload_typed(m2l_plan_t *pl, DevOps &D, int form) {
     // single-precision paths take the pseudo-inverse truncated with alpha = 1e-9 (build_pinv)
@@ -496,6 +599,7 @@ static int upload_typed(m2l_plan_t *pl, DevOps &D, int form) {
         if ((rc = upload_vec(D.C, Cp))) return rc;
         if ((rc = upload_vec(D.A, pad2<T>(Aop, r, k, rp, kp)))) return rc;
         if ((rc = upload_vec(D.Uc, pad2<T>(pl->U, n, k, n, kp)))) return rc;
+        if ((rc = upload_directional<T>(pl, D))) return rc;
     } else {
         int F = pl->F;
         std::vector<T> K((size_t)(kNumTransfer + 1) * F * 2, T(0));
@@ -525,7 +629,10 @@ int upload_ops(m2l_plan_t *pl, int precision, int form) {
     DevOps &D = pl->dev[precision];
     // one DevOps per precision holds both forms; track readiness per form with the pointers
     bool have = form == M2L_FORM_BLAS ? (D.C != nullptr) : (D.Khat != nullptr);
-    if (have) return M2L_OK;
+    if (have) {
+        if (form != M2L_FORM_BLAS || pl->dir_tol <= 0 || D.Ub) return M2L_OK;
+        return precision == M2L_PREC_FP64 ? upload_directional<double>(pl, D) : upload_directional<float>(pl, D);
+    }
     int rc = form == M2L_FORM_BLAS ? build_blas_host(pl) : build_fft_host(pl);
     if (rc) return rc;
     if (precision == M2L_PREC_FP64) {
@@ -543,7 +650,8 @@ int upload_ops(m2l_plan_t *pl, int precision, int form) {
 
 void free_device(m2l_plan_t *pl) {
     for (auto &D : pl->dev) {
-        void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Vlo, &D.Uc, &D.C_hi, &D.C_lo, &D.Khat, &D.Ut, &D.tw};
+        void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Vlo, &D.Uc, &D.C_hi, &D.C_lo, &D.Ub, &D.Vt, &D.dir_meta,
+                         &D.Khat, &D.Ut, &D.tw};
         for (void **pp : ptrs) {
             if (*pp) cudaFree(*pp);
             *pp = nullptr;

@@ -29,6 +29,8 @@ M2L_OK, M2L_EINVAL, M2L_ENOMEM, M2L_ECUDA, M2L_ETIMEOUT, M2L_EUNSUPPORTED = 0, -
 M2L_OPT_FORM, M2L_OPT_PRECISION, M2L_OPT_ACCUMULATE, M2L_OPT_OUTPUT, M2L_OPT_TARGET_TOL, M2L_OPT_FFT_GRID = 1, 2, 3, 4, 5, 6
 M2L_OPT_TIMING = 7
 M2L_OPT_TC_GROUP = 8
+M2L_OPT_DIR_TOL = 9
+M2L_Q_CONTRACT_FLOPS, M2L_Q_DIR_RANK_SUM = 13, 14
 STAGES = ["compress", "contract", "expand", "fft_forward", "hadamard", "fft_inverse", "pinv"]
 M2L_NUM_STAGES = 7
 M2L_FORM_AUTO, M2L_FORM_BLAS, M2L_FORM_FFT = 0, 1, 2
@@ -110,7 +112,7 @@ def m2l_destroy(plan) -> None:
 
 
 def m2l_set_option(plan, key: int, value) -> int:
-    if key == M2L_OPT_TARGET_TOL:
+    if key in (M2L_OPT_TARGET_TOL, M2L_OPT_DIR_TOL):
         value = struct.unpack("<q", struct.pack("<d", float(value)))[0]
     return _lib.m2l_set_option(plan, key, int(value))
 
@@ -179,7 +181,7 @@ class Plan:
         self.set(form=form, precision=precision)
 
     def set(self, form=None, precision=None, accumulate=None, output=None, target_tol=None, fft_grid=None,
-            timing=None, tc_group=None):
+            timing=None, tc_group=None, dir_tol=None):
         if form is not None:
             _check(m2l_set_option(self.handle, M2L_OPT_FORM, FORMS[form]))
         if precision is not None:
@@ -197,6 +199,8 @@ class Plan:
             _check(m2l_set_option(self.handle, M2L_OPT_TIMING, int(bool(timing))))
         if tc_group is not None:
             _check(m2l_set_option(self.handle, M2L_OPT_TC_GROUP, int(tc_group)))
+        if dir_tol is not None:
+            _check(m2l_set_option(self.handle, M2L_OPT_DIR_TOL, float(dir_tol)))
         return self
 
     def stage_times(self):

@@ -58,6 +58,7 @@ class Workload:
     keys: dict                         # level -> sorted uint64 Morton keys, or None for a full level
     n_points: int = 0
     fft_grid: int | None = None        # convolution grid side of the FFT form (None: 2p)
+    dir_tol: float | None = None       # directional recompression threshold of the BLAS form (None: off)
 
     @property
     def levels(self):
@@ -132,11 +133,16 @@ def c2(rank_tol: float = 1e-7, depth: int = 5) -> Workload:
     the padding zero, still free of aliasing (App. A.1)."""
     wl = uniform_cube("c2", 2, 1_000_000, depth, 6, 1, rank_tol, "u11")
     wl.fft_grid = 2 * wl.p - 1
+    # Eq. 15 at a tenth of the rank threshold: a directional cut adds about ten times its
+    # threshold to the compressed check potential, which then stays below the rank truncation's
+    wl.dir_tol = rank_tol / 10 if rank_tol > 0 else None
     return wl
 
 
 def c3(bin_points: bool = True) -> Workload:
-    return uniform_cube("c3", 3, 8_000_000, 6, 8, 1, 1e-7, "u01", bin_points)
+    wl = uniform_cube("c3", 3, 8_000_000, 6, 8, 1, 1e-7, "u01", bin_points)
+    wl.dir_tol = wl.rank_tol / 10  # as for the 1M-point workload
+    return wl
 
 
 def c4() -> Workload:

@@ -22,7 +22,7 @@ def split(flat, sizes, levels, R, n):
 
 
 def run_gpu(lib, depth, p, qs, keys=None, rank_tol=0.0, form="blas", precision="fp64", output="locals",
-            level=-1, R=1, fft_grid=None, accumulate=False, init=None, host=False):
+            level=-1, R=1, fft_grid=None, accumulate=False, init=None, host=False, dir_tol=None):
     """Apply through the C ABI on cuda:0. qs: {level: (B, R, n) float64}. Returns {level: array}."""
     import torch
     keys = keys or {}
@@ -30,6 +30,8 @@ def run_gpu(lib, depth, p, qs, keys=None, rank_tol=0.0, form="blas", precision="
     plan.set(output=output, accumulate=accumulate)
     if fft_grid is not None:
         plan.set(fft_grid=fft_grid)
+    if dir_tol is not None:
+        plan.set(dir_tol=dir_tol)
     for l, k in keys.items():
         if k is not None:
             plan.set_boxes(l, np.asarray(k, dtype=np.uint64))

@@ -127,6 +127,35 @@ def test_plan_compression_matches_oracle(lib, p, tol):
         lib.m2l_destroy(h)
 
 
+@pytest.mark.parametrize("p,tol,dir_tol", [(5, 1e-8, 1e-5), (6, 1e-7, 1e-8)])
+def test_directional_ranks_and_flops_match_oracle(lib, p, tol, dir_tol):
+    """Eq. 15 on the host: the plan keeps, per transfer vector, as many singular values of C_t as
+    the oracle's own SVDs (the singular values do not depend on the bases of U and S), and the
+    contraction flop count is 2 k^2 per pair without the factors and 4 k k_t with them."""
+    h = lib.m2l_plan(3, p, 0, tol)
+    try:
+        k = lib.m2l_query(h, lib.M2L_Q_RANK)
+        pairs = lib.m2l_query(h, lib.M2L_Q_PAIRS, -1)
+        assert lib.m2l_query(h, lib.M2L_Q_CONTRACT_FLOPS, -1) == 2 * k * k * pairs
+        assert lib.m2l_query(h, lib.M2L_Q_DIR_RANK_SUM) == 0
+        lib.m2l_set_option(h, lib.M2L_OPT_DIR_TOL, dir_tol)
+        ops = O.compressed_operators(p, tol, 1.0)
+        d = O.directional_operators(ops["C"], dir_tol)
+        assert lib.m2l_query(h, lib.M2L_Q_DIR_RANK_SUM) == int(d["kt"].sum())
+        # per-transfer-vector pair counts of the full levels 2..3, by brute force on the oracle's lists
+        tindex = {tuple(v): i for i, v in enumerate(G.transfer_vectors())}
+        flops = 0
+        for level in (2, 3):
+            rows, boxes, offsets, src, srow = M.interaction_csr(level)
+            tgt = np.repeat(np.arange(len(rows)), np.diff(offsets))
+            for v in src - boxes[rows][tgt]:
+                flops += 4 * k * d["kt"][tindex[tuple(v)]]
+        assert lib.m2l_query(h, lib.M2L_Q_CONTRACT_FLOPS, -1) == flops
+        assert np.all(d["kt"] <= k) and d["kt"].sum() < 316 * k
+    finally:
+        lib.m2l_destroy(h)
+
+
 def test_full_rank_operators_are_exact(lib):
     p = 4
     h = lib.m2l_plan(3, p, 0, 0.0)

@@ -199,6 +199,58 @@ def test_c2_full_size_sampled(lib, form, precision):
         assert M.rel_l2_error(phi_ref, chk[l][sample]) < bound * (10 if form == "blas" else 1), (l,)
 
 
+# Directional recompression (Eq. 15). Where the plan and the oracle keep the same k_t (checked on
+# the host, test_capi_host), the rank-k_t truncation of C_t is unique, so the two agree to
+# rounding although their SVD bases differ.
+def _directional_ref(p, level, q, rank_tol, dir_tol, keys=None, targets=None):
+    ops = O.compressed_operators(p, rank_tol, 1.0)
+    d = O.directional_operators(ops["C"], dir_tol)
+    return M.m2l_compressed(p, level, q, {**ops, **d}, keys=keys, targets=targets)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_directional_contraction_matches_oracle(lib, precision):
+    wl = W.small(depth=3, p=5, density="u11", rank_tol=1e-8)
+    qs = _qs(wl)
+    chk = run_gpu(lib, 3, 5, qs, rank_tol=1e-8, precision=precision, output="check", dir_tol=1e-5)
+    for l in wl.levels:
+        L_ref, phi_ref = _directional_ref(5, l, qs[l], 1e-8, 1e-5)
+        e = M.rel_l2_error(phi_ref, chk[l])
+        assert e < (1e-10 if precision == "fp64" else FP32_TOL), (precision, l, e)
+        # and the factorisation stays close to the unfactored operators (about 10 dir_tol)
+        _, phi_dense = oracle_level(5, l, qs[l])
+        assert M.rel_l2_error(phi_dense, chk[l]) < 1e-3
+
+
+def test_directional_sparse_multi_rhs(lib):
+    wl = W.small(depth=4, p=4, n_rhs=3, n_points=500, density="normal", rank_tol=1e-6)
+    qs = _qs(wl)
+    keys = {l: wl.keys[l] for l in wl.levels}
+    chk = run_gpu(lib, wl.depth, wl.p, qs, keys=keys, rank_tol=1e-6, output="check", R=3, dir_tol=1e-4)
+    loc = run_gpu(lib, wl.depth, wl.p, qs, keys=keys, rank_tol=1e-6, output="locals", R=3, dir_tol=1e-4)
+    for l in wl.levels:
+        k = None if keys[l] is None else keys[l].astype(np.int64)
+        L_ref, phi_ref = _directional_ref(wl.p, l, qs[l], 1e-6, 1e-4, keys=k)
+        assert M.rel_l2_error(phi_ref, chk[l]) < 1e-10, l
+        # locals through the unit-width pseudo-inverse of the oracle's check potentials
+        assert M.check_norm_error(wl.p, 0, M.locals_from_check(wl.p, 0, phi_ref), loc[l]) < 1e-9, l
+
+
+def test_c2_full_size_sampled_directional(lib):
+    """The 1M-point workload's FP64 BLAS configuration with the directional factors at 1e-8."""
+    wl = W.c2()
+    qs = _qs(wl)
+    chk = run_gpu(lib, wl.depth, wl.p, qs, rank_tol=wl.rank_tol, output="check", dir_tol=wl.rank_tol / 10)
+    rng = np.random.default_rng(8)
+    for l in wl.levels:
+        B = wl.n_boxes(l)
+        sample = np.sort(rng.choice(B, size=min(B, 32), replace=False))
+        _, phi_ref = _directional_ref(wl.p, l, qs[l], wl.rank_tol, wl.rank_tol / 10, targets=sample)
+        assert M.rel_l2_error(phi_ref, chk[l][sample]) < 1e-10, l
+        _, phi_dense = oracle_level(wl.p, l, qs[l], targets=sample)
+        assert M.rel_l2_error(phi_dense, chk[l][sample]) < 2e-6, l
+
+
 # Split tensor-core precisions (tcgen05): bounds on check potentials. TF32x3 pieces carry 22
 # mantissa bits, so the result sits at FP32 rounding (measured 4e-7 to 1.6e-6 for p = 4..10);
 # BF16x3 pieces carry about 17 (measured 3e-7 to 9.5e-6, largest for densities of both signs).
