@@ -209,8 +209,8 @@ def run_ours(args, rank, world, local_rank):
             pl = lib.Plan(wl.depth, wl.p, tol, form=form, precision=prec).set(timing=0 if batched else 1)
             if form == "fft" and wl.fft_grid:
                 pl.set(fft_grid=wl.fft_grid)
-            if form == "blas" and wl.dir_tol:
-                pl.set(dir_tol=wl.dir_tol)
+            if form == "blas" and prec in ("fp64", "fp32") and wl.dir_tol:
+                pl.set(dir_tol=wl.dir_tol)  # the CUDA-core contraction applies Eq. 15's factors
             if target_tol is not None:
                 pl.set(target_tol=target_tol)
             for l in wl.levels:

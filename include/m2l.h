@@ -131,7 +131,8 @@ enum m2l_query_e {
                                 was nonzero: results written since the last query are invalid */
     M2L_Q_CONTRACT_FLOPS = 13, /* algorithmic flops of the BLAS contraction for one right-hand side at
                                   `level` (-1: all levels): 2 k^2 per pair, or 4 k k_t with
-                                  M2L_OPT_DIR_TOL (rounded to an integer) */
+                                  M2L_OPT_DIR_TOL in a precision that applies the factors (FP64,
+                                  FP32, AUTO), rounded to an integer */
     M2L_Q_DIR_RANK_SUM = 14    /* sum of k_t over the 316 transfer vectors (0 when M2L_OPT_DIR_TOL is 0) */
 };
 

@@ -281,15 +281,16 @@ int build_directional(m2l_plan_t *pl) {
 
 // Algorithmic flops of the BLAS contraction for one right-hand side at `level` (-1: levels
 // 2..depth): 2 k^2 per (target, source) pair, or 4 k k_t for a pair with transfer vector t when
-// the directional factors are used (the two products of Sec. 3.2 step 4).
+// the directional factors are used (the two products of Sec. 3.2 step 4): with M2L_OPT_DIR_TOL
+// set and a precision whose contraction applies them (FP64, FP32, or AUTO).
 int contract_flops(m2l_plan_t *pl, int level, double *out) {
+    const bool dir = pl->dir_tol > 0 && pl->precision != M2L_PREC_TF32X3 && pl->precision != M2L_PREC_BF16X3;
     int rc = build_level_tables(pl);
     if (!rc) rc = build_blas_host(pl);
-    if (!rc && pl->dir_tol > 0) rc = build_directional(pl);
+    if (!rc && dir) rc = build_directional(pl);
     if (rc) return rc;
     double w[kNumTransfer];
-    for (int t = 0; t < kNumTransfer; ++t)
-        w[t] = pl->dir_tol > 0 ? 4.0 * pl->k * pl->dir_kt[t] : 2.0 * pl->k * pl->k;
+    for (int t = 0; t < kNumTransfer; ++t) w[t] = dir ? 4.0 * pl->k * pl->dir_kt[t] : 2.0 * pl->k * pl->k;
     double total = 0.0;
     const int l0 = level < 0 ? 2 : level, l1 = level < 0 ? pl->depth : level;
     for (int l = l0; l <= l1; ++l) {
