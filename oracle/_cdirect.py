@@ -34,7 +34,7 @@ def lib():
         _lib = ctypes.CDLL(build())
         d = ctypes.POINTER(ctypes.c_double)
         ll = ctypes.POINTER(ctypes.c_longlong)
-        _lib.oracle_check_potential.argtypes = [ctypes.c_int, d, d, ctypes.c_longlong, d, ll, d, ll, d,
+        _lib.oracle_check_potential.argtypes = [ctypes.c_int, ctypes.c_int, d, d, ctypes.c_longlong, d, ll, d, ll, d,
                                                 ctypes.c_int, d]
         _lib.oracle_check_potential.restype = None
         _lib.oracle_direct_potential.argtypes = [ctypes.c_longlong, d, ctypes.c_longlong, d, d, d]
@@ -51,7 +51,10 @@ def _lp(a):
 
 
 def check_potential(x_off, y_off, t_centre, offsets, s_centre, s_row, q, R):
+    """phi[t, r, i] = sum over the sources e of target t of sum_j K(t_centre + x_off_i,
+    s_centre_e + y_off_j) q[s_row_e, r, j]; x_off and y_off may have different lengths."""
     n = x_off.shape[0]
+    ny = y_off.shape[0]
     x_off = np.ascontiguousarray(x_off, dtype=np.float64)
     y_off = np.ascontiguousarray(y_off, dtype=np.float64)
     t_centre = np.ascontiguousarray(t_centre, dtype=np.float64)
@@ -62,7 +65,7 @@ def check_potential(x_off, y_off, t_centre, offsets, s_centre, s_row, q, R):
     T = t_centre.shape[0]
     phi = np.zeros((T, R, n), dtype=np.float64)
     if T:
-        lib().oracle_check_potential(n, _dp(x_off), _dp(y_off), T, _dp(t_centre), _lp(offsets),
+        lib().oracle_check_potential(n, ny, _dp(x_off), _dp(y_off), T, _dp(t_centre), _lp(offsets),
                                      _dp(s_centre), _lp(s_row), _dp(q), R, _dp(phi))
     return phi
 

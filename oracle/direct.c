@@ -27,7 +27,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-void oracle_check_potential(int n, const double *x_off, const double *y_off,
+void oracle_check_potential(int nx, int ny, const double *x_off, const double *y_off,
                             long long n_targets, const double *t_centre,
                             const long long *offsets, const double *s_centre,
                             const long long *s_row, const double *q, int R, double *phi)
@@ -35,21 +35,21 @@ void oracle_check_potential(int n, const double *x_off, const double *y_off,
     const double four_pi = 4.0 * 3.14159265358979323846;
 #pragma omp parallel for schedule(dynamic, 4)
     for (long long t = 0; t < n_targets; ++t) {
-        double *out = phi + (size_t)t * R * n;
-        memset(out, 0, sizeof(double) * (size_t)R * n);
+        double *out = phi + (size_t)t * R * nx;
+        memset(out, 0, sizeof(double) * (size_t)R * nx);
         for (long long e = offsets[t]; e < offsets[t + 1]; ++e) {
-            const double *qs = q + (size_t)s_row[e] * R * n;
-            for (int i = 0; i < n; ++i) {
+            const double *qs = q + (size_t)s_row[e] * R * ny;
+            for (int i = 0; i < nx; ++i) {
                 double xi0 = t_centre[3 * t + 0] + x_off[3 * i + 0];
                 double xi1 = t_centre[3 * t + 1] + x_off[3 * i + 1];
                 double xi2 = t_centre[3 * t + 2] + x_off[3 * i + 2];
-                for (int j = 0; j < n; ++j) {
+                for (int j = 0; j < ny; ++j) {
                     double d0 = xi0 - (s_centre[3 * e + 0] + y_off[3 * j + 0]);
                     double d1 = xi1 - (s_centre[3 * e + 1] + y_off[3 * j + 1]);
                     double d2 = xi2 - (s_centre[3 * e + 2] + y_off[3 * j + 2]);
                     double k = 1.0 / (four_pi * sqrt(d0 * d0 + d1 * d1 + d2 * d2));
                     for (int r = 0; r < R; ++r)
-                        out[(size_t)r * n + i] += k * qs[(size_t)r * n + j];
+                        out[(size_t)r * nx + i] += k * qs[(size_t)r * ny + j];
                 }
             }
         }

@@ -30,21 +30,23 @@ def direct(points: np.ndarray, charges: np.ndarray) -> np.ndarray:
     return _cdirect.direct_potential(points, points, charges)
 
 
-def upward(points, charges, depth, p, root_origin=(0.0, 0.0, 0.0), root_width=1.0):
-    """P2M at the leaves and M2M up to level 2. Returns {level: (keys, q (B, 1, n))}."""
+def upward(points, charges, depth, p, root_origin=(0.0, 0.0, 0.0), root_width=1.0, p_c=None):
+    """P2M at the leaves and M2M up to level 2. Returns {level: (keys, q (B, 1, n))}.
+    ``p_c`` is the order of every check surface (default p)."""
+    pc = p if p_c is None else p_c
     leaf = _leaf_index(points, depth, root_origin, root_width)
     lkeys = G.morton_encode(leaf, depth)
     keys = np.unique(lkeys)
     n = G.n_surface(p)
     out = {}
     # P2M: upward check potential from the points, then the upward pseudo-inverse.
-    fac = O.up_pinv(p, depth, root_width)
+    fac = O.up_pinv(p, depth, root_width, p_c=pc)
     w = G.box_width(depth, root_width)
     q = np.zeros((len(keys), 1, n))
     for b, key in enumerate(keys):
         sel = lkeys == key
         c = G.box_centre(G.morton_decode(key, depth), depth, root_origin, root_width)
-        x = G.surface_points(p, c, w, G.ALPHA_OUTER)
+        x = G.surface_points(pc, c, w, G.ALPHA_OUTER)
         phi = O.laplace(x, points[sel]) @ charges[sel]
         q[b, 0] = O.pinv_apply(fac, phi)
     out[depth] = (keys, q)
@@ -52,14 +54,14 @@ def upward(points, charges, depth, p, root_origin=(0.0, 0.0, 0.0), root_width=1.
     for level in range(depth - 1, 1, -1):
         ckeys, cq = out[level + 1]
         pkeys = np.unique(ckeys >> 3)
-        fac = O.up_pinv(p, level, root_width)
+        fac = O.up_pinv(p, level, root_width, p_c=pc)
         w = G.box_width(level, root_width)
         wc = G.box_width(level + 1, root_width)
         q = np.zeros((len(pkeys), 1, n))
         for b, key in enumerate(pkeys):
             c = G.box_centre(G.morton_decode(key, level), level, root_origin, root_width)
-            x = G.surface_points(p, c, w, G.ALPHA_OUTER)
-            phi = np.zeros(n)
+            x = G.surface_points(pc, c, w, G.ALPHA_OUTER)
+            phi = np.zeros(len(x))
             for ci in np.nonzero((ckeys >> 3) == key)[0]:
                 cc = G.box_centre(G.morton_decode(ckeys[ci], level + 1), level + 1, root_origin, root_width)
                 y = G.surface_points(p, cc, wc, G.ALPHA_INNER)
@@ -69,7 +71,7 @@ def upward(points, charges, depth, p, root_origin=(0.0, 0.0, 0.0), root_width=1.
     return out
 
 
-def fmm(points, charges, depth, p, root_origin=(0.0, 0.0, 0.0), root_width=1.0, m2l=None):
+def fmm(points, charges, depth, p, root_origin=(0.0, 0.0, 0.0), root_width=1.0, m2l=None, p_c=None):
     """Potentials at every point from the full FMM.
 
     ``m2l(p, level, q, keys)`` may replace the M2L check-potential evaluation (it must return
@@ -77,13 +79,14 @@ def fmm(points, charges, depth, p, root_origin=(0.0, 0.0, 0.0), root_width=1.0, 
     """
     if depth < 2:
         raise ValueError("depth must be >= 2")
-    up = upward(points, charges, depth, p, root_origin, root_width)
+    up = upward(points, charges, depth, p, root_origin, root_width, p_c)
+    pc = p if p_c is None else p_c
     n = G.n_surface(p)
     down = {}
     for level in range(2, depth + 1):
         keys, q = up[level]
         if m2l is None:
-            phi = M.check_potentials(p, level, q, keys, None, root_origin, root_width)
+            phi = M.check_potentials(p, level, q, keys, None, root_origin, root_width, p_c)
         else:
             phi = m2l(p, level, q, keys)
         if level > 2:
@@ -94,11 +97,11 @@ def fmm(points, charges, depth, p, root_origin=(0.0, 0.0, 0.0), root_width=1.0, 
             for b, key in enumerate(keys):
                 pi = int(np.searchsorted(pkeys, key >> 3))
                 c = G.box_centre(G.morton_decode(key, level), level, root_origin, root_width)
-                pc = G.box_centre(G.morton_decode(pkeys[pi], level - 1), level - 1, root_origin, root_width)
-                x = G.surface_points(p, c, w, G.ALPHA_INNER)
-                y = G.surface_points(p, pc, wp, G.ALPHA_OUTER)
+                pcen = G.box_centre(G.morton_decode(pkeys[pi], level - 1), level - 1, root_origin, root_width)
+                x = G.surface_points(pc, c, w, G.ALPHA_INNER)
+                y = G.surface_points(p, pcen, wp, G.ALPHA_OUTER)
                 phi[b, 0] += O.laplace(x, y) @ pL[pi, 0]
-        down[level] = (keys, M.locals_from_check(p, level, phi, root_width))
+        down[level] = (keys, M.locals_from_check(p, level, phi, root_width, p_c))
     # L2P and P2P at the leaves.
     keys, L = down[depth]
     leaf = _leaf_index(points, depth, root_origin, root_width)

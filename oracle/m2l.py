@@ -54,42 +54,43 @@ def interaction_csr(level: int, keys=None, targets=None):
     return rows, boxes, offsets, src, srow
 
 
-def m2l_surfaces(p: int, width: float):
-    """Offsets from the box centre of the target's downward-check points and the source's
-    upward-equivalent points (Sec. 2.2); both lie on the inner radius."""
-    x_off = G.surface_points(p, np.zeros(3), width, G.ALPHA_INNER)
+def m2l_surfaces(p: int, width: float, p_c: int | None = None):
+    """Offsets from the box centre of the target's downward-check points (order p_c, default p)
+    and the source's upward-equivalent points (Sec. 2.2); both lie on the inner radius."""
+    x_off = G.surface_points(p if p_c is None else p_c, np.zeros(3), width, G.ALPHA_INNER)
     y_off = G.surface_points(p, np.zeros(3), width, G.ALPHA_INNER)
     return x_off, y_off
 
 
 def check_potentials(p: int, level: int, q: np.ndarray, keys=None, targets=None,
-                     root_origin=(0.0, 0.0, 0.0), root_width: float = 1.0) -> np.ndarray:
-    """phi_tau = sum_{sigma in I_tau} K_{sigma,tau} q^sigma (the sum in Eq. 11), shape (T, R, n)."""
+                     root_origin=(0.0, 0.0, 0.0), root_width: float = 1.0, p_c: int | None = None) -> np.ndarray:
+    """phi_tau = sum_{sigma in I_tau} K_{sigma,tau} q^sigma (the sum in Eq. 11), shape (T, R, n_c)."""
     rows, boxes, offsets, src, srow = interaction_csr(level, keys, targets)
     w = G.box_width(level, root_width)
-    x_off, y_off = m2l_surfaces(p, w)
+    x_off, y_off = m2l_surfaces(p, w, p_c)
     t_centre = G.box_centre(boxes[rows], level, root_origin, root_width)
     s_centre = G.box_centre(src, level, root_origin, root_width)
     return _cdirect.check_potential(x_off, y_off, t_centre, offsets, s_centre, srow, q, q.shape[1])
 
 
-def locals_from_check(p: int, level: int, phi: np.ndarray, root_width: float = 1.0) -> np.ndarray:
-    """q^tau = (K_tau)^+ phi_tau with the two-factor pseudo-inverse (Eqs. 7-10)."""
-    fac = O.down_pinv(p, level, root_width)
-    T, R, n = phi.shape
-    cols = phi.reshape(T * R, n).T
-    return O.pinv_apply(fac, cols).T.reshape(T, R, n)
+def locals_from_check(p: int, level: int, phi: np.ndarray, root_width: float = 1.0,
+                      p_c: int | None = None) -> np.ndarray:
+    """q^tau = (K_tau)^+ phi_tau with the two-factor pseudo-inverse (Eqs. 7-10); phi (T, R, n_c)."""
+    fac = O.down_pinv(p, level, root_width, p_c=p_c)
+    T, R, nc = phi.shape
+    cols = phi.reshape(T * R, nc).T
+    return O.pinv_apply(fac, cols).T.reshape(T, R, -1)
 
 
 def m2l_dense(p: int, level: int, q: np.ndarray, keys=None, targets=None,
-              root_origin=(0.0, 0.0, 0.0), root_width: float = 1.0):
-    """Eq. 11 at one level. Returns (locals (T,R,n), check potentials (T,R,n))."""
-    phi = check_potentials(p, level, q, keys, targets, root_origin, root_width)
-    return locals_from_check(p, level, phi, root_width), phi
+              root_origin=(0.0, 0.0, 0.0), root_width: float = 1.0, p_c: int | None = None):
+    """Eq. 11 at one level. Returns (locals (T,R,n), check potentials (T,R,n_c))."""
+    phi = check_potentials(p, level, q, keys, targets, root_origin, root_width, p_c)
+    return locals_from_check(p, level, phi, root_width, p_c), phi
 
 
 def m2l_compressed(p: int, level: int, q: np.ndarray, ops: dict, keys=None, targets=None,
-                   root_width: float = 1.0):
+                   root_width: float = 1.0, p_c: int | None = None):
     """BLAS-M2L of Sec. 3.2.
 
     ``ops`` comes from ``operators.compressed_operators(p, rank_tol, width)`` built at this
@@ -100,7 +101,7 @@ def m2l_compressed(p: int, level: int, q: np.ndarray, ops: dict, keys=None, targ
     rows, boxes, offsets, src, srow = interaction_csr(level, keys, targets)
     U, S, C, tv = ops["U"], ops["S"], ops["C"], ops["tvecs"]
     B, R, n = q.shape
-    k = ops["k"]
+    kc = ops.get("kc", ops["k"])
     # Step 1: map every (target, source) pair to its transfer vector t = idx(sigma) - idx(tau).
     tgt_of_pair = np.repeat(np.arange(len(rows)), np.diff(offsets))
     tvec = src - boxes[rows][tgt_of_pair]
@@ -109,7 +110,7 @@ def m2l_compressed(p: int, level: int, q: np.ndarray, ops: dict, keys=None, targ
     # Step 2: compressed multipoles of every source box, q~ = S^T q.
     qt = q @ S
     # Steps 3-5: per transfer vector, gather its sources, apply C_t, accumulate into targets.
-    phit = np.zeros((len(rows), R, k))
+    phit = np.zeros((len(rows), R, kc))
     for ti in range(len(tv)):
         sel = np.nonzero(t_of_pair == ti)[0]
         if len(sel) == 0:
@@ -123,7 +124,7 @@ def m2l_compressed(p: int, level: int, q: np.ndarray, ops: dict, keys=None, targ
         np.add.at(phit, tgt_of_pair[sel], contrib)
     # Uncompress the check potentials, phi = U phi~, then recover the locals.
     phi = phit @ U.T
-    return locals_from_check(p, level, phi, root_width), phi
+    return locals_from_check(p, level, phi, root_width, p_c), phi
 
 
 def kernel_spectra(p: int, width: float, g: int | None = None) -> dict:
@@ -165,7 +166,8 @@ def rel_l2_error(ref: np.ndarray, approx: np.ndarray) -> float:
     return float(np.sqrt(num / den)) if den > 0 else float(np.sqrt(num))
 
 
-def check_norm_error(p: int, level: int, L_ref: np.ndarray, L_test: np.ndarray, root_width: float = 1.0) -> float:
+def check_norm_error(p: int, level: int, L_ref: np.ndarray, L_test: np.ndarray, root_width: float = 1.0,
+                     p_c: int | None = None) -> float:
     """Eq. 16 applied to the check potentials K_tau q^tau that two sets of locals reproduce.
 
     The locals solve an ill-conditioned least-squares problem (Sec. 2.1.1), so rounding in the
@@ -174,7 +176,7 @@ def check_norm_error(p: int, level: int, L_ref: np.ndarray, L_test: np.ndarray, 
     Comparing K_tau q^tau measures agreement in the quantity the FMM uses downstream.
     """
     w = G.box_width(level, root_width)
-    x = G.surface_points(p, np.zeros(3), w, G.ALPHA_INNER)
+    x = G.surface_points(p if p_c is None else p_c, np.zeros(3), w, G.ALPHA_INNER)
     y = G.surface_points(p, np.zeros(3), w, G.ALPHA_OUTER)
     K = O.laplace(x, y)
     a = np.einsum("ij,brj->bri", K, np.asarray(L_ref, dtype=np.float64))

@@ -40,47 +40,51 @@ def pinv_apply(factors, phi: np.ndarray) -> np.ndarray:
     return V_eps @ (Ut_eps @ phi)
 
 
-def down_pinv(p: int, level: int, root_width: float = 1.0, centre=None):
+def down_pinv(p: int, level: int, root_width: float = 1.0, centre=None, p_c: int | None = None):
     """Factors of (K_tau)^+ for the downward check -> downward equivalent map at ``level``.
 
     Built from the actual surfaces of one box of that level (Sec. 2.2 notes this matrix is the
-    same for every box of a level).
+    same for every box of a level). ``p_c`` is the check surface's order (default p): with
+    p_c > p the least-squares problem of Eq. 6 has more check than equivalent points.
     """
     w = G.box_width(level, root_width)
     c = np.zeros(3) if centre is None else np.asarray(centre, dtype=np.float64)
-    x = G.surface_points(p, c, w, G.ALPHA_INNER)   # downward check
+    x = G.surface_points(p if p_c is None else p_c, c, w, G.ALPHA_INNER)   # downward check
     y = G.surface_points(p, c, w, G.ALPHA_OUTER)   # downward equivalent
     return pinv_factors(laplace(x, y))
 
 
-def up_pinv(p: int, level: int, root_width: float = 1.0, centre=None):
+def up_pinv(p: int, level: int, root_width: float = 1.0, centre=None, p_c: int | None = None):
     """Factors of the upward check -> upward equivalent pseudo-inverse (Eq. 6 solved by Eq. 9)."""
     w = G.box_width(level, root_width)
     c = np.zeros(3) if centre is None else np.asarray(centre, dtype=np.float64)
-    x = G.surface_points(p, c, w, G.ALPHA_OUTER)   # upward check
+    x = G.surface_points(p if p_c is None else p_c, c, w, G.ALPHA_OUTER)   # upward check
     y = G.surface_points(p, c, w, G.ALPHA_INNER)   # upward equivalent
     return pinv_factors(laplace(x, y))
 
 
-def m2l_matrix(p: int, t, width: float = 1.0) -> np.ndarray:
+def m2l_matrix(p: int, t, width: float = 1.0, p_c: int | None = None) -> np.ndarray:
     """K_t: downward check of a target at the origin vs upward equivalent of the source at t*width (Sec. 2.2)."""
     t = np.asarray(t, dtype=np.float64)
-    x = G.surface_points(p, np.zeros(3), width, G.ALPHA_INNER)
+    x = G.surface_points(p if p_c is None else p_c, np.zeros(3), width, G.ALPHA_INNER)
     y = G.surface_points(p, t * width, width, G.ALPHA_INNER)
     return laplace(x, y)
 
 
-def compressed_operators(p: int, rank_tol: float, width: float = 1.0):
+def compressed_operators(p: int, rank_tol: float, width: float = 1.0, p_c: int | None = None):
     """SVD compression of Sec. 3.1 (Eqs. 12-14) over all 316 transfer vectors.
 
     K_fat = [K_1 ... K_316] ~ U Sigma V~^T and K_thin = [K_1; ...; K_316] ~ R~ Lambda S^T.
     The rank k keeps the singular values with s_i / s_0 >= rank_tol in either SVD (the larger
-    of the two counts); rank_tol <= 0 keeps full rank (k = n).
+    of the two counts); rank_tol <= 0 keeps full rank (k = n). With a check order p_c > p the
+    K_t are n_c x n and the two bases get their own ranks: U is n_c x k_c (K_fat's count, up to
+    n_c), S is n x k (K_thin's, up to n) and C_t is k_c x k. ("k" is the equivalent-side rank,
+    "kc" the check-side one; they are equal when p_c = p.)
     Returns dict(U (n,k), S (n,k), C (316,k,k), k, tvecs, s_fat, s_thin).
     """
     tv = G.transfer_vectors()
-    Ks = np.stack([m2l_matrix(p, t, width) for t in tv])  # (316, n, n)
-    n = Ks.shape[1]
+    Ks = np.stack([m2l_matrix(p, t, width, p_c) for t in tv])  # (316, n_c, n)
+    n = Ks.shape[2]
     K_fat = np.concatenate(list(Ks), axis=1)               # n x 316 n
     K_thin = np.concatenate(list(Ks), axis=0)              # 316 n x n
     # Singular values and the n-dimensional singular vectors of the two stacked matrices.
@@ -90,16 +94,20 @@ def compressed_operators(p: int, rank_tol: float, width: float = 1.0):
     _, s_fat, Ut_full = np.linalg.svd(np.linalg.qr(K_fat.T, mode="r"))
     U_full = Ut_full.T
     _, s_thin, St_full = np.linalg.svd(np.linalg.qr(K_thin, mode="r"))
+    nc = Ks.shape[1]
     if rank_tol is None or rank_tol <= 0:
-        k = n
+        kc, ke = nc, n
     else:
         k_fat = int(np.sum(s_fat / s_fat[0] >= rank_tol))
         k_thin = int(np.sum(s_thin / s_thin[0] >= rank_tol))
-        k = max(k_fat, k_thin)
-    U = U_full[:, :k]
-    S = St_full[:k].T
-    C = np.matmul(np.matmul(U.T[None], Ks), S[None])  # C_t = U^T K_t S
-    return dict(U=U, S=S, C=C, k=k, tvecs=tv, s_fat=s_fat, s_thin=s_thin, K=Ks)
+        if nc == n:
+            kc = ke = max(k_fat, k_thin)   # equal orders: one k for both bases (Sec. 3.1)
+        else:
+            kc, ke = k_fat, k_thin         # check and equivalent spaces of different sizes
+    U = U_full[:, :kc]
+    S = St_full[:ke].T
+    C = np.matmul(np.matmul(U.T[None], Ks), S[None])  # C_t = U^T K_t S  (kc x ke)
+    return dict(U=U, S=S, C=C, k=ke, kc=kc, tvecs=tv, s_fat=s_fat, s_thin=s_thin, K=Ks)
 
 
 def directional_operators(C: np.ndarray, dir_tol: float):

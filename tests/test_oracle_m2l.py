@@ -251,6 +251,81 @@ def test_directional_error_is_monotone(rng):
     assert errs[0] > 1e-4 and errs[-1] < 1e-6
 
 
+# Check order above the equivalent order (P_c > P_e; Sec. 5 and the optimal parameters of the
+# BLAS tables): rectangular check-to-equivalent maps.
+
+def test_check_potential_with_higher_check_order_matches_brute_force(rng):
+    """n_c check points of order p + 1 against n equivalent points of order p, explicit sum."""
+    p, pc, level = 3, 4, 2
+    n, nc = G.n_surface(p), G.n_surface(pc)
+    q = rng.standard_normal((64, 1, n))
+    phi = M.check_potentials(p, level, q, p_c=pc)
+    assert phi.shape == (64, 1, nc)
+    w = G.box_width(level)
+    boxes = G.all_boxes(level)
+    for ti in (0, 27, 63):
+        tau = boxes[ti]
+        x = G.surface_points(pc, G.box_centre(tau, level), w, G.ALPHA_INNER)
+        ref = np.zeros(nc)
+        for si, s in enumerate(boxes):
+            if np.max(np.abs(s - tau)) >= 2:
+                y = G.surface_points(p, G.box_centre(s, level), w, G.ALPHA_INNER)
+                for i in range(nc):
+                    ref[i] += np.sum(q[si, 0] / (4 * np.pi * np.linalg.norm(x[i] - y, axis=1)))
+        assert np.allclose(phi[ti, 0], ref, rtol=1e-13, atol=0)
+
+
+def test_rectangular_pinv_penrose_identities():
+    """The downward check-to-equivalent map with n_c > n rows is a least-squares problem; its
+    pseudo-inverse still satisfies the four Penrose conditions to max(M,N) eps cond."""
+    for p, pc in ((3, 4), (4, 6)):
+        V, Ut = O.down_pinv(p, 0, p_c=pc)
+        x = G.surface_points(pc, np.zeros(3), 1.0, G.ALPHA_INNER)
+        y = G.surface_points(p, np.zeros(3), 1.0, G.ALPHA_OUTER)
+        A = O.laplace(x, y)
+        assert A.shape == (G.n_surface(pc), G.n_surface(p)) and V.shape[0] == G.n_surface(p)
+        Ap = V @ Ut
+        sv = np.linalg.svd(A, compute_uv=False)
+        tol = 10 * max(A.shape) * np.finfo(float).eps * sv[0] / sv[V.shape[1] - 1]
+        assert np.linalg.norm(A @ Ap @ A - A, 2) <= tol * np.linalg.norm(A, 2)
+        assert np.linalg.norm(Ap @ A @ Ap - Ap, 2) <= tol * np.linalg.norm(Ap, 2)
+        assert np.linalg.norm(A @ Ap - (A @ Ap).T, 2) <= tol
+        assert np.linalg.norm(Ap @ A - (Ap @ A).T, 2) <= tol
+
+
+def test_compressed_with_higher_check_order(rng):
+    """With n_c > n the two bases get their own ranks (the column space of K_fat has more than n
+    significant directions: its (n+1)-th singular value is still 4e-5 of the largest at p = 4,
+    p_c = 5). At full rank the compressed form is exact; truncated, its error is of the order of
+    the threshold."""
+    p, pc, level = 4, 5, 3
+    n, nc = G.n_surface(p), G.n_surface(pc)
+    q = rng.standard_normal((8 ** level, 1, n))
+    tg = np.arange(0, 512, 19)
+    _, phi_d = M.m2l_dense(p, level, q, targets=tg, p_c=pc)
+    full = O.compressed_operators(p, 0.0, G.box_width(level), p_c=pc)
+    assert (full["kc"], full["k"]) == (nc, n) and full["C"].shape == (316, nc, n)
+    _, phi_c = M.m2l_compressed(p, level, q, full, targets=tg, p_c=pc)
+    assert M.rel_l2_error(phi_d, phi_c) < 1e-12
+    assert full["s_fat"][n] / full["s_fat"][0] > 1e-5   # a k <= n check basis could not be exact
+    cut = O.compressed_operators(p, 1e-6, G.box_width(level), p_c=pc)
+    assert n < cut["kc"] < nc
+    _, phi_t = M.m2l_compressed(p, level, q, cut, targets=tg, p_c=pc)
+    assert 1e-8 < M.rel_l2_error(phi_d, phi_t) < 1e-5
+
+
+def test_fmm_error_falls_with_check_order():
+    """More check than equivalent points: the tiny FMM's error falls as P_c rises above P_e at
+    every order tried (the effect behind the BLAS tables' P_c > P_e)."""
+    rng = np.random.default_rng(1)
+    pts = rng.random((800, 3))
+    q = rng.random(800)
+    ref = fmm.direct(pts, q)
+    for p in (3, 4, 5):
+        e = [M.rel_l2_error(ref, fmm.fmm(pts, q, 3, p, p_c=pc)) for pc in (p, p + 1, p + 2)]
+        assert e[0] > e[1] > e[2], (p, e)
+
+
 def test_symmetric_kernel_fat_and_thin_share_singular_values():
     """Sec. 3.1: for the symmetric Laplace kernel with equal surfaces one SVD suffices."""
     ops = O.compressed_operators(4, 1e-6)

@@ -21,7 +21,7 @@ def test_reference_fmm_error_is_small():
 
 def test_source_on_wrong_surface_is_caught(monkeypatch):
     """M2L source taken on the outer (upward check) radius instead of its equivalent surface."""
-    def bad(p, width):
+    def bad(p, width, p_c=None):
         return (G.surface_points(p, np.zeros(3), width, G.ALPHA_INNER),
                 G.surface_points(p, np.zeros(3), width, G.ALPHA_OUTER))
     monkeypatch.setattr(M, "m2l_surfaces", bad)
@@ -30,7 +30,7 @@ def test_source_on_wrong_surface_is_caught(monkeypatch):
 
 def test_wrong_check_radius_is_caught(monkeypatch):
     """Target check points moved off the inner radius."""
-    def bad(p, width):
+    def bad(p, width, p_c=None):
         return (G.surface_points(p, np.zeros(3), width, 1.5),
                 G.surface_points(p, np.zeros(3), width, G.ALPHA_INNER))
     monkeypatch.setattr(M, "m2l_surfaces", bad)
@@ -49,7 +49,7 @@ def test_flipped_transfer_vector_is_caught(rng, monkeypatch):
     tg = np.arange(0, 512, 31)
     _, phi_d = M.m2l_dense(p, level, q, targets=tg)
     orig = O.m2l_matrix
-    monkeypatch.setattr(O, "m2l_matrix", lambda p, t, width=1.0: orig(p, -np.asarray(t), width))
+    monkeypatch.setattr(O, "m2l_matrix", lambda p, t, width=1.0, p_c=None: orig(p, -np.asarray(t), width, p_c))
     ops = O.compressed_operators(p, 0.0, G.box_width(level))
     _, phi_c = M.m2l_compressed(p, level, q, ops, targets=tg)
     assert M.rel_l2_error(phi_d, phi_c) > 1e-6
@@ -61,7 +61,7 @@ def test_transposed_operator_is_caught(rng, monkeypatch):
     tg = np.arange(0, 512, 31)
     _, phi_d = M.m2l_dense(p, level, q, targets=tg)
     orig = O.m2l_matrix
-    monkeypatch.setattr(O, "m2l_matrix", lambda p, t, width=1.0: orig(p, t, width).T)
+    monkeypatch.setattr(O, "m2l_matrix", lambda p, t, width=1.0, p_c=None: orig(p, t, width, p_c).T)
     ops = O.compressed_operators(p, 0.0, G.box_width(level))
     _, phi_c = M.m2l_compressed(p, level, q, ops, targets=tg)
     assert M.rel_l2_error(phi_d, phi_c) > 1e-6
