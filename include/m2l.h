@@ -78,11 +78,18 @@ enum m2l_option_e {
     M2L_OPT_TC_GROUP = 8,    /* split tensor-core forms: transfer vectors summed in tensor memory before
                                 each round-to-nearest FP32 drain, 1..189 (default 1). Larger is faster;
                                 the tensor cores' truncating accumulation grows with it */
-    M2L_OPT_DIR_TOL = 9      /* directional recompression of the BLAS operators (Sec. 3.1, Eq. 15):
+    M2L_OPT_DIR_TOL = 9,     /* directional recompression of the BLAS operators (Sec. 3.1, Eq. 15):
                                 the bits of a double dir_tol >= 0; 0 (default) = off. With
                                 dir_tol > 0 each C_t is factored as Ubar_t Vbar'_t^T keeping its
                                 singular values >= dir_tol s_0(C_t), and the CUDA-core contraction
                                 (FP64, FP32) applies the two factors; the tensor-core forms keep C_t */
+    M2L_OPT_CHECK_ORDER = 10 /* order p_c of the downward check surface, p <= p_c <= 16 (0: p, the
+                                default). p_c > p gives n_c = 6(p_c-1)^2+2 check points for the n
+                                equivalent points (the BLAS tables' P_c > P_e): K_t and the
+                                pseudo-inverse become n_c x n, U is n_c x k_c, C_t is k_c x k.
+                                BLAS form in FP64 or FP32 only (the FFT form needs one grid, the
+                                tensor-core contraction a square C_t); check potentials written
+                                with M2L_OUT_CHECK_POTENTIAL then have n_c values per row */
 };
 
 /* Stages of one application, as indexed by m2l_stage_times. */
@@ -133,7 +140,9 @@ enum m2l_query_e {
                                   `level` (-1: all levels): 2 k^2 per pair, or 4 k k_t with
                                   M2L_OPT_DIR_TOL in a precision that applies the factors (FP64,
                                   FP32, AUTO), rounded to an integer */
-    M2L_Q_DIR_RANK_SUM = 14    /* sum of k_t over the 316 transfer vectors (0 when M2L_OPT_DIR_TOL is 0) */
+    M2L_Q_DIR_RANK_SUM = 14,   /* sum of k_t over the 316 transfer vectors (0 when M2L_OPT_DIR_TOL is 0) */
+    M2L_Q_NC = 15,             /* check points per box, n_c (n unless M2L_OPT_CHECK_ORDER > p) */
+    M2L_Q_RANK_CHECK = 16      /* rank k_c of the check-side basis U (k unless M2L_OPT_CHECK_ORDER > p) */
 };
 
 /* Where a bounded device wait ran out (the value of M2L_Q_DEVICE_STATUS). Every wait of a kernel
@@ -241,8 +250,9 @@ int m2l_apply_noalloc(m2l_plan_t *plan, const double *multipoles, double *locals
 int m2l_selftest_watchdog(m2l_plan_t *plan, long long polls);
 
 /* Copy a plan operator to host memory (FP64), for tests and inspection:
- * which = 0: U (n x k), 1: S (n x k), 2: C_t (316 x k x k), 3: singular values of K_fat (n),
- *         4: pseudo-inverse factor V_eps (n x r), 5: Ut_eps = Sigma_eps^-1 U_eps^T (r x n).
+ * which = 0: U (n_c x k_c), 1: S (n x k), 2: C_t (316 x k_c x k), 3: singular values of K_fat
+ *         (n_c), 4: pseudo-inverse factor V_eps (n x r), 5: Ut_eps = Sigma_eps^-1 U_eps^T (r x n_c).
+ * (n_c = n and k_c = k unless M2L_OPT_CHECK_ORDER > p.)
  * *count receives the number of doubles; dst may be NULL to query the size. */
 int m2l_get_operator(m2l_plan_t *plan, int which, double *dst, long long *count);
 

@@ -98,6 +98,15 @@ int prepare_plan(m2l_plan_t *pl, int form, int precision) {
         set_error("the FFT form runs in FP64 or FP32; split tensor-core precisions apply to the BLAS form");
         return M2L_EUNSUPPORTED;
     }
+    if (pl->pc != pl->p && form == M2L_FORM_FFT) {
+        // the convolution needs the check and equivalent surfaces on one grid (Sec. 3.3)
+        set_error("the FFT form needs equal check and equivalent orders (check order %d, order %d)", pl->pc, pl->p);
+        return M2L_EUNSUPPORTED;
+    }
+    if (pl->pc != pl->p && (precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3)) {
+        set_error("the tensor-core contraction needs equal check and equivalent orders; use FP64 or FP32");
+        return M2L_EUNSUPPORTED;
+    }
     M2L_TRY(upload_ops(pl, precision, form));
     if (form == M2L_FORM_FFT) M2L_TRY(ensure_lattice(pl));
     if (!pl->dev_status) {
@@ -295,7 +304,7 @@ static BlasLayout blas_layout(const m2l_plan_t *pl, long long total_rows, int pr
     const size_t e = precision == M2L_PREC_FP64 ? 8 : 4;
     BlasLayout b;
     b.qt_b = (size_t)(total_rows + 1) * pl->kp * e;
-    b.ph_b = (size_t)total_rows * pl->kp * e;
+    b.ph_b = (size_t)total_rows * pl->kcp * e;
     b.z_b = (size_t)total_rows * pl->rp * e;
     b.split_b = tc ? (size_t)(total_rows + 1) * pl->kp * (precision == M2L_PREC_TF32X3 ? 4 : 2) : 0;
     return b;
@@ -335,7 +344,7 @@ size_t workspace_estimate(const m2l_plan_t *pl, int form, int precision, int R) 
         const bool tc = precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3;
         const size_t e = precision == M2L_PREC_FP64 ? 8 : 4;
         const size_t rows = (size_t)pl->total_rows * R + 1;
-        size_t b = rows * (2 * (size_t)pl->kp + pl->rp) * e;
+        size_t b = rows * ((size_t)pl->kp + pl->kcp + pl->rp) * e;
         if (tc) b += 2 * rows * pl->kp * (precision == M2L_PREC_TF32X3 ? 4 : 2);
         return b;
     }
@@ -367,7 +376,7 @@ template <class T>
 static int blas_group(std::vector<Run> &runs, int precision, Workspace &ws, cudaStream_t s) {
     m2l_plan_t *own = runs[0].pl;
     const DevOps &D = own->dev[precision];
-    const int n = own->n, kp = own->kp, rp = own->rp;
+    const int n = own->n, nc = own->nc, kp = own->kp, kcp = own->kcp, rp = own->rp;
     const bool tc = precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3;
     long long ntiles = 0, total = 0;
     M2L_TRY(ensure_exec(own, runs, tc ? 128 : 64, &ntiles, &total));
@@ -394,8 +403,9 @@ static int blas_group(std::vector<Run> &runs, int precision, Workspace &ws, cuda
         int rc = M2L_EUNSUPPORTED;
         if (own->dir_tol > 0 && D.Ub)
             rc = launch_contract_simt_dir<T>(lv, tl, ntiles, tvl, qt, (const T *)D.Ub, (const T *)D.Vt,
-                                             (const int *)D.dir_meta, own->k, kp, own->dir_kt8_max, total, phit, s);
-        if (rc == M2L_EUNSUPPORTED) rc = launch_contract_simt<T>(lv, tl, ntiles, tvl, qt, (const T *)D.C, kp, total, phit, s);
+                                             (const int *)D.dir_meta, own->k, kp, kcp, own->dir_kt8_max, total, phit, s);
+        if (rc == M2L_EUNSUPPORTED)
+            rc = launch_contract_simt<T>(lv, tl, ntiles, tvl, qt, (const T *)D.C, kp, kcp, total, phit, s);
         M2L_TRY(rc);
         stage_end(own, 1);
     } else {
@@ -415,13 +425,13 @@ static int blas_group(std::vector<Run> &runs, int precision, Workspace &ws, cuda
     stage_begin(own, M2L_STAGE_EXPAND);
     long long nl = 0;
     for (const Run &r : runs) {
-        const T *ph = phit + r.row_off * kp;
+        const T *ph = phit + r.row_off * kcp;
         if (r.pl->output == M2L_OUT_LOCALS) {
-            M2L_TRY(launch_gemm_xwt<T>(ph, kp, (const T *)D.A, kp, Z + r.row_off * rp, rp, r.rows, rp, kp, 0, s));
+            M2L_TRY(launch_gemm_xwt<T>(ph, kcp, (const T *)D.A, kcp, Z + r.row_off * rp, rp, r.rows, rp, kcp, 0, s));
             M2L_TRY(apply_veps<T>(own, D, Z + r.row_off * rp, (T *)r.L, r.rows, r.pl->accumulate, false, s));
             nl += 2;
         } else {
-            M2L_TRY(launch_gemm_xwt<T>(ph, kp, (const T *)D.Uc, kp, (T *)r.L, n, r.rows, n, kp, r.pl->accumulate, s));
+            M2L_TRY(launch_gemm_xwt<T>(ph, kcp, (const T *)D.Uc, kcp, (T *)r.L, nc, r.rows, nc, kcp, r.pl->accumulate, s));
             nl += 1;
         }
     }
@@ -524,10 +534,11 @@ int apply_device(m2l_plan_t *pl, const void *q, void *L, int level, int R) {
 // Batches of independent instances (device buffers, every level of each).
 
 struct GroupKey {
-    int p, form, precision, kp, g;
+    int p, pc, form, precision, kp, g;
     double rank_tol, dir_tol;
     bool operator==(const GroupKey &o) const {
-        return p == o.p && form == o.form && precision == o.precision && kp == o.kp && g == o.g && rank_tol == o.rank_tol &&
+        return p == o.p && pc == o.pc && form == o.form && precision == o.precision && kp == o.kp && g == o.g &&
+               rank_tol == o.rank_tol &&
                dir_tol == o.dir_tol;
     }
 };
@@ -544,7 +555,7 @@ int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void
         int form, prec;
         M2L_TRY(resolve_form(pl, R[i], &form, &prec));
         M2L_TRY(prepare_plan(pl, form, prec));
-        GroupKey k{pl->p, form, prec, form == M2L_FORM_BLAS ? pl->kp : 0, form == M2L_FORM_FFT ? pl->g : 0,
+        GroupKey k{pl->p, pl->pc, form, prec, form == M2L_FORM_BLAS ? pl->kp : 0, form == M2L_FORM_FFT ? pl->g : 0,
                    form == M2L_FORM_BLAS ? pl->rank_tol : 0.0, form == M2L_FORM_BLAS ? pl->dir_tol : 0.0};
         size_t gi = 0;
         while (gi < keys.size() && !(keys[gi] == k)) ++gi;

@@ -43,6 +43,8 @@ double stated_bound(int form, int precision, int p) {
 
 static bool eligible(const m2l_plan_t *pl, int form, int prec) {
     if (form == M2L_FORM_FFT && (prec == M2L_PREC_TF32X3 || prec == M2L_PREC_BF16X3)) return false;
+    // a check order above p: BLAS form on CUDA cores only
+    if (pl->pc != pl->p && (form == M2L_FORM_FFT || prec == M2L_PREC_TF32X3 || prec == M2L_PREC_BF16X3)) return false;
     double bound = stated_bound(form, prec, pl->p);
     if (form == M2L_FORM_BLAS && pl->rank_tol > 0) bound = std::max(bound, pl->rank_tol);
     if (bound > pl->target_tol) return false;
@@ -97,7 +99,7 @@ static int time_candidate(m2l_plan_t *pl, int form, int prec, int R, float *ms) 
     return rc;
 }
 
-using TuneKey = std::tuple<int, int, int, double, double, int, int, int>;
+using TuneKey = std::tuple<int, int, int, double, double, int, int, int, int, double>;
 static std::map<TuneKey, std::pair<int, int>> g_decisions;
 static std::mutex g_decisions_mu;
 
@@ -143,7 +145,7 @@ static int tune_on(m2l_plan_t *pl, const m2l_plan_t *real, int R, int *form, int
 static int tune(m2l_plan_t *pl, int R, int *form, int *prec) {
     // box counts enter through the memory check, so the decision is shared per tree size too
     const TuneKey key{pl->device, pl->p * 1000 + pl->depth, R, pl->rank_tol, pl->target_tol, pl->form, pl->precision,
-                      pl->fft_grid_opt};
+                      pl->fft_grid_opt, pl->pc, pl->dir_tol};
     {
         std::lock_guard<std::mutex> g(g_decisions_mu);
         auto it = g_decisions.find(key);
@@ -160,6 +162,8 @@ static int tune(m2l_plan_t *pl, int R, int *form, int *prec) {
     proxy->target_tol = pl->target_tol;
     proxy->fft_grid_opt = pl->fft_grid_opt;
     proxy->tc_group = pl->tc_group;
+    proxy->dir_tol = pl->dir_tol;
+    if (pl->pc != pl->p) m2l_set_option(proxy, M2L_OPT_CHECK_ORDER, pl->pc);
     proxy->stream = pl->stream;
     if (build_level_tables(pl) || build_pinv(pl)) return M2L_ECUDA;
     if (pl->rank_tol > 0 || pl->form != M2L_FORM_FFT) build_blas_host(pl);

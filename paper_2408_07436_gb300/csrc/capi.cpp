@@ -73,6 +73,9 @@ m2l_plan_t *m2l_plan(int depth, int p, int kernel, double rank_tol) {
                 }
     pl->n = (int)pl->lattice.size() / 3;
     pl->np_ = pl->n;
+    pl->pc = p;
+    pl->nc = pl->n;
+    pl->lattice_c = pl->lattice;
     for (int l = 2; l <= depth; ++l) {
         pl->levels[l].dense = true;
         pl->levels[l].nboxes = 1LL << (3 * l);
@@ -149,6 +152,28 @@ int m2l_set_option(m2l_plan_t *pl, int key, long long value) {
                 }
             }
             return M2L_OK;
+        case M2L_OPT_CHECK_ORDER: {
+            const int pc = value == 0 ? pl->p : (int)value;
+            if (pc < pl->p || pc > 16) break;
+            if (pc != pl->pc) {
+                pl->pc = pc;
+                pl->lattice_c.clear();
+                for (int a = 0; a < pc; ++a)
+                    for (int b = 0; b < pc; ++b)
+                        for (int c = 0; c < pc; ++c)
+                            if (a == 0 || a == pc - 1 || b == 0 || b == pc - 1 || c == 0 || c == pc - 1) {
+                                pl->lattice_c.push_back(a);
+                                pl->lattice_c.push_back(b);
+                                pl->lattice_c.push_back(c);
+                            }
+                pl->nc = (int)pl->lattice_c.size() / 3;
+                // every operator that touches the check surface is rebuilt on next use
+                pl->pinv_ready = pl->blas_host_ready = pl->dir_ready = false;
+                pl->tuned.clear();
+                release_operators(pl);
+            }
+            return M2L_OK;
+        }
         case M2L_OPT_DIR_TOL: {
             double d;
             std::memcpy(&d, &value, sizeof d);
@@ -246,9 +271,12 @@ int m2l_apply(m2l_plan_t *pl, const void *q, void *L, int level, int n_rhs) {
     int rc = m2l::resolve_form(pl, n_rhs, &form, &prec);
     if (rc) return rc;
     size_t elt = prec == M2L_PREC_FP64 ? 8 : 4;
-    size_t bytes = (size_t)rows_of(pl, level) * n_rhs * pl->n * elt;
+    size_t bytes = (size_t)rows_of(pl, level) * n_rhs * pl->n * elt;  // multipoles; locals alike
+    const size_t out_bytes = pl->output == M2L_OUT_CHECK_POTENTIAL && form == M2L_FORM_BLAS
+                                 ? (size_t)rows_of(pl, level) * n_rhs * pl->nc * elt  // check potentials: nc per row
+                                 : bytes;
     const char *qa = (const char *)q, *la = (const char *)L;
-    if (qa < la + bytes && la < qa + bytes) {
+    if (qa < la + out_bytes && la < qa + bytes) {
         set_error("multipoles and locals overlap");
         return M2L_EINVAL;
     }
@@ -274,21 +302,21 @@ int m2l_apply(m2l_plan_t *pl, const void *q, void *L, int level, int n_rhs) {
             dq = pl->stage_in.buf;
         }
         if (!ldev) {
-            if (!pl->stage_out.buf || pl->stage_out.bytes < bytes) {
+            if (!pl->stage_out.buf || pl->stage_out.bytes < out_bytes) {
                 if (pl->stage_out.buf) cudaFree(pl->stage_out.buf);
                 pl->stage_out = {};
-                if (cudaMalloc(&pl->stage_out.buf, bytes) != cudaSuccess) {
+                if (cudaMalloc(&pl->stage_out.buf, out_bytes) != cudaSuccess) {
                     cudaGetLastError();
                     set_error("staging allocation failed");
                     return M2L_ENOMEM;
                 }
-                pl->stage_out.bytes = bytes;
+                pl->stage_out.bytes = out_bytes;
             }
-            if (pl->accumulate) cudaMemcpyAsync(pl->stage_out.buf, L, bytes, cudaMemcpyHostToDevice, pl->stream);
+            if (pl->accumulate) cudaMemcpyAsync(pl->stage_out.buf, L, out_bytes, cudaMemcpyHostToDevice, pl->stream);
             dl = pl->stage_out.buf;
         }
         rc = apply_device(pl, dq, dl, level, n_rhs);
-        if (rc == M2L_OK && !ldev) cudaMemcpyAsync(L, dl, bytes, cudaMemcpyDeviceToHost, pl->stream);
+        if (rc == M2L_OK && !ldev) cudaMemcpyAsync(L, dl, out_bytes, cudaMemcpyDeviceToHost, pl->stream);
         if (rc == M2L_OK && cudaStreamSynchronize(pl->stream) != cudaSuccess) {
             set_error("stream synchronisation failed: %s", cudaGetErrorString(cudaGetLastError()));
             rc = M2L_ECUDA;
@@ -363,6 +391,13 @@ int m2l_query(const m2l_plan_t *cpl, int what, int level, long long *out) {
             *out = (long long)(f + 0.5);
             return M2L_OK;
         }
+        case M2L_Q_NC:
+            *out = pl->nc;
+            return M2L_OK;
+        case M2L_Q_RANK_CHECK:
+            if ((rc = build_blas_host(pl))) return rc;
+            *out = pl->kc;
+            return M2L_OK;
         case M2L_Q_DIR_RANK_SUM: {
             *out = 0;
             if (pl->dir_tol <= 0) return M2L_OK;

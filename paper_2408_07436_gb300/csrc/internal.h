@@ -111,13 +111,16 @@ struct m2l_plan_s {
     int device = 0;
     int num_sms = 148;
     // geometry
-    std::vector<int> lattice;                 // n x 3
+    std::vector<int> lattice;                 // n x 3: equivalent surfaces, order p
+    int pc = 0, nc = 0;                       // check surface order (M2L_OPT_CHECK_ORDER) and points
+    std::vector<int> lattice_c;               // nc x 3: the downward check surface
     int *lattice_dev = nullptr;               // packed a << 16 | b << 8 | c
     m2l::LevelSet levels[m2l::kMaxDepth + 1];
     // host operators (FP64)
     bool blas_host_ready = false, fft_host_ready = false, pinv_ready = false;
-    int k = 0, kp = 0, r = 0, rp = 0, np_ = 0;
-    std::vector<double> U, S, C, s_fat, s_thin;   // U, S: n x k (row-major [n][k]); C: 316 x k x k
+    int k = 0, kp = 0, r = 0, rp = 0, np_ = 0;    // k: rank of the equivalent side (S), padded kp
+    int kc = 0, kcp = 0;                          // rank of the check side (U), padded; k unless pc > p
+    std::vector<double> U, S, C, s_fat, s_thin;   // U: nc x kc, S: n x k (row-major); C: 316 x kc x k
     std::vector<double> Veps, Uteps;              // [n][r], [r][n]   threshold n eps_64 s_0
     std::vector<double> Aop;                      // [r][k] = Uteps * U
     int r32 = 0;                                  // singular values kept with Eq. 10's alpha = 1e-9
@@ -160,6 +163,7 @@ namespace m2l {
 int build_pinv(m2l_plan_t *pl);
 int build_blas_host(m2l_plan_t *pl);
 int build_directional(m2l_plan_t *pl);
+void release_operators(m2l_plan_t *pl);
 int contract_flops(m2l_plan_t *pl, int level, double *out);
 int build_fft_host(m2l_plan_t *pl);
 int build_level_tables(m2l_plan_t *pl);     // host tables and pair counts

@@ -52,19 +52,21 @@ int launch_gemm_xwt_ff(const float *X, long long ldx, const float *Wh, const flo
                        long long ldy, long long rows, int O, int K, int acc, cudaStream_t s);
 
 // B2 on CUDA cores: phit[row0 + b R + r][:] = sum_t C_t qt[row0 + src R + r][:] over the tiles,
+// qt rows of kp values, C_t [kcp][kp], phit rows of kcp values (kcp = kp unless the check order
+// exceeds the equivalent order),
 // `levels` a device array of LevelView indexed by ContractTile::lev, `tvl` the tiles' transfer
 // vector lists.
 template <class T>
 int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
-                         const T *qt, const T *C, int kp, long long zero_row, T *phit, cudaStream_t s);
+                         const T *qt, const T *C, int kp, int kcp, long long zero_row, T *phit, cudaStream_t s);
 
-// B2 with the directional factors (Eq. 15): Ub = Ubar_t [k_pad][k_t8], Vt = Vbar'_t^T [k_t8][k_pad]
+// B2 with the directional factors (Eq. 15): Ub = Ubar_t [kc_pad][k_t8], Vt = Vbar'_t^T [k_t8][k_pad]
 // concatenated over t, meta = [316] int4 (Ub offset, Vt offset, k_t, k_t8). M2L_EUNSUPPORTED
 // (nothing launched) when its shared-memory tiles do not fit.
 template <class T>
 int launch_contract_simt_dir(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
-                             const T *qt, const T *Ub, const T *Vt, const int *meta, int k, int kp, int kt8max,
-                             long long zero_row, T *phit, cudaStream_t s);
+                             const T *qt, const T *Ub, const T *Vt, const int *meta, int k, int kp, int kcp,
+                             int kt8max, long long zero_row, T *phit, cudaStream_t s);
 
 // FFT form, one level at a time.
 template <class T>

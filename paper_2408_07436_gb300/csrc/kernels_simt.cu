@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(const LevelView *__r
                                                             const ContractTile *__restrict__ tiles,
                                                             const int *__restrict__ tvl,
                                                             const T *__restrict__ qt, const T *__restrict__ C, int kp,
-                                                            long long zero_row, T *__restrict__ phit) {
+                                                            int kcp, long long zero_row, T *__restrict__ phit) {
     constexpr int BM = 64, BN = 16 * TN, BK = 16;
     __shared__ T Xs[BK][BM + 4];
     __shared__ T Ws[BK][BN + 4];
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(const LevelView *__r
 #pragma unroll
         for (int i = 0; i < 4; ++i) mine |= src_row[ty * 4 + i] != zero_row;
         const bool live = __any_sync(0xffffffffu, mine);
-        const T *Ct = C + (long long)ti * kp * kp;
+        const T *Ct = C + (long long)ti * kcp * kp;  // [kcp][kp]
         for (int k0 = 0; k0 < kp; k0 += BK) {
             for (int e = tid; e < BM * BK; e += 256) {
                 const int r = e / BK, kk = e % BK;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(const LevelView *__r
             }
             for (int e = tid; e < BN * BK; e += 256) {
                 const int c = e / BK, kk = e % BK, gc = col0 + c;
-                Ws[kk][c] = gc < kp ? Ct[(long long)gc * kp + k0 + kk] : T(0);
+                Ws[kk][c] = gc < kcp ? Ct[(long long)gc * kp + k0 + kk] : T(0);
             }
             __syncthreads();
             if (live) {
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(const LevelView *__r
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
             int c = col0 + tx * TN + j;
-            if (c < kp) phit[orow * kp + c] = a[i][j];
+            if (c < kcp) phit[orow * kcp + c] = a[i][j];
         }
     }
 }
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView 
                                                                 const ContractTile *__restrict__ tiles,
                                                                 const int *__restrict__ tvl, const T *__restrict__ qt,
                                                                 const T *__restrict__ Ub, const T *__restrict__ Vt,
-                                                                const int4 *__restrict__ meta, int k, int kp, int kt8max,
+                                                                const int4 *__restrict__ meta, int k, int kp, int kcp, int kt8max,
                                                                 long long zero_row, T *__restrict__ phit) {
     constexpr int BM = 64, BN = 16 * TN, BK = 16, XP = BM + 2, YC = 64;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -464,12 +464,12 @@ __global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView 
             __syncthreads();  // the next pass reuses Xs and Vs; stage 2 reads Ys
         }
         // stage 2: phit += xi Ubar_t^T over the k_t columns of xi
-        const T *Ut = Ub + md.x;  // [kp][k_t8]
+        const T *Ut = Ub + md.x;  // [kcp][k_t8]
         for (int j0 = 0; j0 < md.z; j0 += BK) {
             if (j0) __syncthreads();  // previous chunk of Ubar_t consumed
             for (int e = tid; e < BN * BK; e += 256) {
                 const int c = e / BK, kk = e % BK, gc = col0 + c;
-                Us[(size_t)kk * (BN + 4) + c] = (gc < kp && j0 + kk < md.w) ? Ut[(size_t)gc * md.w + j0 + kk] : T(0);
+                Us[(size_t)kk * (BN + 4) + c] = (gc < kcp && j0 + kk < md.w) ? Ut[(size_t)gc * md.w + j0 + kk] : T(0);
             }
             __syncthreads();
             if (live) {
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView 
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
             int c = col0 + tx * TN + j;
-            if (c < kp) phit[orow * kp + c] = a[i][j];
+            if (c < kcp) phit[orow * kcp + c] = a[i][j];
         }
     }
 }
@@ -519,21 +519,21 @@ inline int contract_tn(int kp, int max_tn) {
 
 template <class T, int TN>
 static void launch_contract_tn(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
-                               const T *qt, const T *C, int kp, long long zero_row, T *phit, cudaStream_t s) {
-    dim3 grid((unsigned)ntiles, (unsigned)((kp + 16 * TN - 1) / (16 * TN)));
-    contract_simt_kernel<T, TN><<<grid, 256, 0, s>>>(levels, tiles, tvl, qt, C, kp, zero_row, phit);
+                               const T *qt, const T *C, int kp, int kcp, long long zero_row, T *phit, cudaStream_t s) {
+    dim3 grid((unsigned)ntiles, (unsigned)((kcp + 16 * TN - 1) / (16 * TN)));
+    contract_simt_kernel<T, TN><<<grid, 256, 0, s>>>(levels, tiles, tvl, qt, C, kp, kcp, zero_row, phit);
 }
 
 template <class T>
 int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
-                         const T *qt, const T *C, int kp, long long zero_row, T *phit, cudaStream_t s) {
+                         const T *qt, const T *C, int kp, int kcp, long long zero_row, T *phit, cudaStream_t s) {
     if (ntiles <= 0) return M2L_OK;
     // FP64: one block of up to 192 columns keeps the FP64 units fed from registers; FP32 keeps
     // more warps resident with narrower blocks
-    const int tn = contract_tn(kp, sizeof(T) == 8 ? 12 : 8);
+    const int tn = contract_tn(kcp, sizeof(T) == 8 ? 12 : 8);
     switch (tn) {
 #define M2L_TN(n) \
-    case n: launch_contract_tn<T, n>(levels, tiles, ntiles, tvl, qt, C, kp, zero_row, phit, s); break;
+    case n: launch_contract_tn<T, n>(levels, tiles, ntiles, tvl, qt, C, kp, kcp, zero_row, phit, s); break;
         M2L_TN(1) M2L_TN(2) M2L_TN(3) M2L_TN(4) M2L_TN(5) M2L_TN(6)
         M2L_TN(7) M2L_TN(8) M2L_TN(9) M2L_TN(10) M2L_TN(11) M2L_TN(12)
 #undef M2L_TN
@@ -546,8 +546,8 @@ int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, lon
 
 template <class T, int TN>
 static int launch_contract_dir_tn(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
-                                  const T *qt, const T *Ub, const T *Vt, const int *meta, int k, int kp, int kt8max,
-                                  long long zero_row, T *phit, cudaStream_t s) {
+                                  const T *qt, const T *Ub, const T *Vt, const int *meta, int k, int kp, int kcp,
+                                  int kt8max, long long zero_row, T *phit, cudaStream_t s) {
     constexpr int BN = 16 * TN;
     const size_t smem = sizeof(T) * ((size_t)kt8max * 66 + (size_t)16 * 66 + (size_t)16 * 66 + (size_t)16 * (BN + 4));
     if (smem > 200 * 1024) return M2L_EUNSUPPORTED;
@@ -556,9 +556,9 @@ static int launch_contract_dir_tn(const LevelView *levels, const ContractTile *t
         cudaGetLastError();
         return M2L_EUNSUPPORTED;
     }
-    dim3 grid((unsigned)ntiles, (unsigned)((kp + BN - 1) / BN));
+    dim3 grid((unsigned)ntiles, (unsigned)((kcp + BN - 1) / BN));
     contract_simt_dir_kernel<T, TN><<<grid, 256, smem, s>>>(levels, tiles, tvl, qt, Ub, Vt,
-                                                             reinterpret_cast<const int4 *>(meta), k, kp, kt8max,
+                                                             reinterpret_cast<const int4 *>(meta), k, kp, kcp, kt8max,
                                                              zero_row, phit);
     return check_launch("contract_dir");
 }
@@ -567,13 +567,15 @@ static int launch_contract_dir_tn(const LevelView *levels, const ContractTile *t
 // then applies C_t unfactored.
 template <class T>
 int launch_contract_simt_dir(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
-                             const T *qt, const T *Ub, const T *Vt, const int *meta, int k, int kp, int kt8max,
-                             long long zero_row, T *phit, cudaStream_t s) {
+                             const T *qt, const T *Ub, const T *Vt, const int *meta, int k, int kp, int kcp,
+                             int kt8max, long long zero_row, T *phit, cudaStream_t s) {
     if (ntiles <= 0) return M2L_OK;
-    const int tn = contract_tn(kp, 12);  // one column block where possible: stage 1 is per block
+    const int tn = contract_tn(kcp, 12);  // one column block where possible: stage 1 is per block
     switch (tn) {
 #define M2L_TN(n) \
-    case n: return launch_contract_dir_tn<T, n>(levels, tiles, ntiles, tvl, qt, Ub, Vt, meta, k, kp, kt8max, zero_row, phit, s);
+    case n:                                                                                                    \
+        return launch_contract_dir_tn<T, n>(levels, tiles, ntiles, tvl, qt, Ub, Vt, meta, k, kp, kcp, kt8max, zero_row, \
+                                            phit, s);
         M2L_TN(1) M2L_TN(2) M2L_TN(3) M2L_TN(4) M2L_TN(5) M2L_TN(6)
         M2L_TN(7) M2L_TN(8) M2L_TN(9) M2L_TN(10) M2L_TN(11) M2L_TN(12)
 #undef M2L_TN
@@ -1069,10 +1071,10 @@ size_t fft_smem_bytes(int p, int g, int elt) {
     template int launch_gemm_xwt<T>(const T *, long long, const T *, long long, T *, long long, long long, \
                                     int, int, int, cudaStream_t);                                       \
     template int launch_contract_simt_dir<T>(const LevelView *, const ContractTile *, long long, const int *,   \
-                                             const T *, const T *, const T *, const int *, int, int, int, long long, \
-                                             T *, cudaStream_t);                                             \
+                                             const T *, const T *, const T *, const int *, int, int, int, int,  \
+                                             long long, T *, cudaStream_t);                                  \
     template int launch_contract_simt<T>(const LevelView *, const ContractTile *, long long, const int *,       \
-                                         const T *, const T *, int, long long, T *, cudaStream_t);      \
+                                         const T *, const T *, int, int, long long, T *, cudaStream_t); \
     template int launch_fft_forward<T>(const LevelView &, int, int, int, int, const int *, const T *,   \
                                        const T *, T *, cudaStream_t);                                   \
     template int launch_hadamard<T>(const LevelView &, int, int, const T *, const T *, T *, cudaStream_t); \

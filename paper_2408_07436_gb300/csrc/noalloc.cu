@@ -181,6 +181,10 @@ extern "C" int m2l_apply_noalloc(m2l_plan_t *pl, const double *multipoles, doubl
     }
     const DevOps &D = pl->dev[M2L_PREC_FP64];
     const LevelDev &LD = pl->ldev[level];
+    if (pl->pc != pl->p) {
+        set_error("m2l_apply_noalloc needs equal check and equivalent orders");
+        return M2L_EINVAL;
+    }
     if (D.C == nullptr || D.St == nullptr || D.A == nullptr || D.V == nullptr || D.Uc == nullptr ||
         pl->levels_dirty || !LD.on_device) {
         set_error("plan not prepared: its FP64 BLAS operators and box tables are not on the device yet "

@@ -62,14 +62,17 @@ void transfer_vector(int idx, int &x, int &y, int &z) {
 
 // ---------------------------------------------------------------------------------------------
 // Surfaces (Sec. 2.1.1; App. A.3 point count): boundary points of the p^3 lattice, x slowest.
+// `check` selects the downward check surface, of order pc (M2L_OPT_CHECK_ORDER); every other
+// surface has order p.
 static void surface(const m2l_plan_t *pl, double cx, double cy, double cz, double alpha,
-                    std::vector<double> &pts) {
-    int n = pl->n, p = pl->p;
+                    std::vector<double> &pts, bool check = false) {
+    const std::vector<int> &lat = check ? pl->lattice_c : pl->lattice;
+    const int n = (int)lat.size() / 3, p = check ? pl->pc : pl->p;
     pts.resize((size_t)3 * n);
     for (int i = 0; i < n; ++i) {
         for (int a = 0; a < 3; ++a) {
             double c = a == 0 ? cx : (a == 1 ? cy : cz);
-            pts[3 * i + a] = c + alpha * 0.5 * (-1.0 + 2.0 * pl->lattice[3 * i + a] / (p - 1));
+            pts[3 * i + a] = c + alpha * 0.5 * (-1.0 + 2.0 * lat[3 * i + a] / (p - 1));
         }
     }
 }
@@ -79,17 +82,17 @@ static inline double laplace(const double *x, const double *y) {
     return 1.0 / (4.0 * M_PI * std::sqrt(d0 * d0 + d1 * d1 + d2 * d2));
 }
 
-// K_t (n x n, row-major [i][j]): downward-check of the unit target at the origin against the
+// K_t (nc x n, row-major [i][j]): downward-check of the unit target at the origin against the
 // upward-equivalent points of the unit source at t (Sec. 2.2).
 static void m2l_matrix(const m2l_plan_t *pl, int t, std::vector<double> &K) {
     int x, y, z;
     transfer_vector(t, x, y, z);
     std::vector<double> xs, ys;
-    surface(pl, 0, 0, 0, kAlphaInner, xs);
+    surface(pl, 0, 0, 0, kAlphaInner, xs, true);
     surface(pl, x, y, z, kAlphaInner, ys);
-    int n = pl->n;
-    K.resize((size_t)n * n);
-    for (int i = 0; i < n; ++i)
+    const int n = pl->n, nc = pl->nc;
+    K.resize((size_t)nc * n);
+    for (int i = 0; i < nc; ++i)
         for (int j = 0; j < n; ++j) K[(size_t)i * n + j] = laplace(&xs[3 * i], &ys[3 * j]);
 }
 
@@ -107,34 +110,35 @@ static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 //                 rounding level of their check potential for p = 4..10.
 static constexpr double kPinvAlphaSingle = 1e-9;
 
-static void pinv_truncation(int n, const std::vector<double> &U, const std::vector<double> &s,
+// For the m x n (m >= n) matrix A = U diag(s) V^T (column-major factors): Veps [n][r] and
+// Uteps [r][m] of the singular values above (alpha + max(m, n) eps_mach) s_0.
+static void pinv_truncation(int m, int n, const std::vector<double> &U, const std::vector<double> &s,
                             const std::vector<double> &V, double alpha, int &r, std::vector<double> &Veps,
                             std::vector<double> &Uteps) {
-    const double thresh = (alpha + n * 2.220446049250313e-16) * s[0];
+    const double thresh = (alpha + std::max(m, n) * 2.220446049250313e-16) * s[0];
     r = 0;
     while (r < n && s[r] > thresh) ++r;
     Veps.assign((size_t)n * r, 0.0);
-    Uteps.assign((size_t)r * n, 0.0);
-    for (int a = 0; a < r; ++a)
-        for (int i = 0; i < n; ++i) {
-            Veps[(size_t)i * r + a] = V[(size_t)a * n + i];
-            Uteps[(size_t)a * n + i] = U[(size_t)a * n + i] / s[a];
-        }
+    Uteps.assign((size_t)r * m, 0.0);
+    for (int a = 0; a < r; ++a) {
+        for (int i = 0; i < n; ++i) Veps[(size_t)i * r + a] = V[(size_t)a * n + i];
+        for (int i = 0; i < m; ++i) Uteps[(size_t)a * m + i] = U[(size_t)a * m + i] / s[a];
+    }
 }
 
 int build_pinv(m2l_plan_t *pl) {
     if (pl->pinv_ready) return M2L_OK;
-    int n = pl->n;
+    const int n = pl->n, nc = pl->nc;
     std::vector<double> xs, ys;
-    surface(pl, 0, 0, 0, kAlphaInner, xs);   // downward check
-    surface(pl, 0, 0, 0, kAlphaOuter, ys);   // downward equivalent
-    std::vector<double> K((size_t)n * n);    // column-major
+    surface(pl, 0, 0, 0, kAlphaInner, xs, true);   // downward check (order pc)
+    surface(pl, 0, 0, 0, kAlphaOuter, ys);         // downward equivalent
+    std::vector<double> K((size_t)nc * n);         // column-major, nc x n (nc >= n)
     for (int j = 0; j < n; ++j)
-        for (int i = 0; i < n; ++i) K[(size_t)j * n + i] = laplace(&xs[3 * i], &ys[3 * j]);
+        for (int i = 0; i < nc; ++i) K[(size_t)j * nc + i] = laplace(&xs[3 * i], &ys[3 * j]);
     std::vector<double> U, s, V;
-    jacobi_svd(K, n, n, U, s, V);
-    pinv_truncation(n, U, s, V, 0.0, pl->r, pl->Veps, pl->Uteps);
-    pinv_truncation(n, U, s, V, kPinvAlphaSingle, pl->r32, pl->Veps32, pl->Uteps32);
+    jacobi_svd(K, nc, n, U, s, V);
+    pinv_truncation(nc, n, U, s, V, 0.0, pl->r, pl->Veps, pl->Uteps);
+    pinv_truncation(nc, n, U, s, V, kPinvAlphaSingle, pl->r32, pl->Veps32, pl->Uteps32);
     pl->rp = round_up(pl->r, 16);
     pl->pinv_ready = true;
     return M2L_OK;
@@ -146,80 +150,87 @@ int build_blas_host(m2l_plan_t *pl) {
     if (pl->blas_host_ready) return M2L_OK;
     int rc = build_pinv(pl);
     if (rc) return rc;
-    int n = pl->n;
+    const int n = pl->n, nc = pl->nc;
     std::vector<std::vector<double>> Ks(kNumTransfer);
 #pragma omp parallel for schedule(dynamic, 4)
     for (int t = 0; t < kNumTransfer; ++t) m2l_matrix(pl, t, Ks[t]);
-    int k;
+    int k, kc;
     if (pl->rank_tol <= 0) {
         k = n;
-        pl->U.assign((size_t)n * k, 0.0);
-        for (int i = 0; i < n; ++i) pl->U[(size_t)i * k + i] = 1.0;
-        pl->S = pl->U;
+        kc = nc;
+        pl->U.assign((size_t)nc * kc, 0.0);
+        for (int i = 0; i < nc; ++i) pl->U[(size_t)i * kc + i] = 1.0;
+        pl->S.assign((size_t)n * k, 0.0);
+        for (int i = 0; i < n; ++i) pl->S[(size_t)i * k + i] = 1.0;
         pl->s_fat.clear();
         pl->s_thin.clear();
     } else {
-        // K_thin = [K_1; ...; K_316]: stack the column-major K_t. K_fat^T = [K_1^T; ...]:
-        // a row-major K_t read as column-major is K_t^T.
+        // K_thin = [K_1; ...; K_316] (316 nc x n): stack the column-major K_t. K_fat^T =
+        // [K_1^T; ...] (316 n x nc): a row-major K_t read as column-major is K_t^T.
         std::vector<std::vector<double>> thin(kNumTransfer), fatT(kNumTransfer);
         for (int t = 0; t < kNumTransfer; ++t) {
             fatT[t] = Ks[t];
-            thin[t].resize((size_t)n * n);
-            for (int i = 0; i < n; ++i)
-                for (int j = 0; j < n; ++j) thin[t][(size_t)j * n + i] = Ks[t][(size_t)i * n + j];
+            thin[t].resize((size_t)nc * n);
+            for (int i = 0; i < nc; ++i)
+                for (int j = 0; j < n; ++j) thin[t][(size_t)j * nc + i] = Ks[t][(size_t)i * n + j];
         }
-        std::vector<double> Rf = stacked_r_factor(std::move(fatT), n);
+        std::vector<double> Rf = stacked_r_factor(std::move(fatT), nc);
         std::vector<double> Rt = stacked_r_factor(std::move(thin), n);
         std::vector<double> Uf, Vf, Ut_, Vt_;
-        jacobi_svd(Rf, n, n, Uf, pl->s_fat, Vf);
+        jacobi_svd(Rf, nc, nc, Uf, pl->s_fat, Vf);
         jacobi_svd(Rt, n, n, Ut_, pl->s_thin, Vt_);
         int kf = 0, kt = 0;
-        while (kf < n && pl->s_fat[kf] / pl->s_fat[0] >= pl->rank_tol) ++kf;
+        while (kf < nc && pl->s_fat[kf] / pl->s_fat[0] >= pl->rank_tol) ++kf;
         while (kt < n && pl->s_thin[kt] / pl->s_thin[0] >= pl->rank_tol) ++kt;
-        k = std::max(kf, kt);
-        if (k < 1) k = 1;
+        if (nc == n) {
+            k = kc = std::max(std::max(kf, kt), 1);  // equal orders: one k (Sec. 3.1)
+        } else {
+            kc = std::max(kf, 1);                    // check and equivalent spaces of different sizes
+            k = std::max(kt, 1);
+        }
         // U: left singular vectors of K_fat = right singular vectors of K_fat^T (and of Rf).
-        pl->U.assign((size_t)n * k, 0.0);
+        pl->U.assign((size_t)nc * kc, 0.0);
         pl->S.assign((size_t)n * k, 0.0);
+        for (int c = 0; c < kc; ++c)
+            for (int i = 0; i < nc; ++i) pl->U[(size_t)i * kc + c] = Vf[(size_t)c * nc + i];
         for (int c = 0; c < k; ++c)
-            for (int i = 0; i < n; ++i) {
-                pl->U[(size_t)i * k + c] = Vf[(size_t)c * n + i];
-                pl->S[(size_t)i * k + c] = Vt_[(size_t)c * n + i];
-            }
+            for (int i = 0; i < n; ++i) pl->S[(size_t)i * k + c] = Vt_[(size_t)c * n + i];
     }
     pl->k = k;
     pl->kp = round_up(k, 16);
-    // C_t = U^T K_t S  (k x k, row-major)
-    pl->C.assign((size_t)kNumTransfer * k * k, 0.0);
+    pl->kc = kc;
+    pl->kcp = round_up(kc, 16);
+    // C_t = U^T K_t S  (kc x k, row-major)
+    pl->C.assign((size_t)kNumTransfer * kc * k, 0.0);
 #pragma omp parallel for schedule(dynamic, 2)
     for (int t = 0; t < kNumTransfer; ++t) {
-        std::vector<double> KS((size_t)n * k, 0.0);
+        std::vector<double> KS((size_t)nc * k, 0.0);
         const double *K = Ks[t].data();
-        for (int i = 0; i < n; ++i)
+        for (int i = 0; i < nc; ++i)
             for (int j = 0; j < n; ++j) {
                 double kij = K[(size_t)i * n + j];
                 const double *srow = &pl->S[(size_t)j * k];
                 double *dst = &KS[(size_t)i * k];
                 for (int c = 0; c < k; ++c) dst[c] += kij * srow[c];
             }
-        double *C = &pl->C[(size_t)t * k * k];
-        for (int i = 0; i < n; ++i) {
-            const double *urow = &pl->U[(size_t)i * k];
+        double *C = &pl->C[(size_t)t * kc * k];
+        for (int i = 0; i < nc; ++i) {
+            const double *urow = &pl->U[(size_t)i * kc];
             const double *ks = &KS[(size_t)i * k];
-            for (int a = 0; a < k; ++a) {
+            for (int a = 0; a < kc; ++a) {
                 double u = urow[a];
                 if (u == 0.0) continue;
                 for (int c = 0; c < k; ++c) C[(size_t)a * k + c] += u * ks[c];
             }
         }
     }
-    // A = Ut_eps U  (r x k): the scaled factor of the pseudo-inverse times the uncompression.
+    // A = Ut_eps U  (r x kc): the scaled factor of the pseudo-inverse times the uncompression.
     auto fold = [&](const std::vector<double> &Ut, int r, std::vector<double> &A) {
-        A.assign((size_t)r * k, 0.0);
+        A.assign((size_t)r * kc, 0.0);
         for (int a = 0; a < r; ++a)
-            for (int i = 0; i < n; ++i) {
-                double u = Ut[(size_t)a * n + i];
-                for (int c = 0; c < k; ++c) A[(size_t)a * k + c] += u * pl->U[(size_t)i * k + c];
+            for (int i = 0; i < nc; ++i) {
+                double u = Ut[(size_t)a * nc + i];
+                for (int c = 0; c < kc; ++c) A[(size_t)a * kc + c] += u * pl->U[(size_t)i * kc + c];
             }
     };
     fold(pl->Uteps, pl->r, pl->Aop);
@@ -230,35 +241,45 @@ int build_blas_host(m2l_plan_t *pl) {
 
 // Directional recompression (Eq. 15): C_t ~ Ubar_t Sigmabar_t Vbar_t^T = Ubar_t Vbar'_t^T with the
 // k_t singular values of C_t at or above dir_tol s_0(C_t). Packed as the contraction reads them:
-// Ubar_t as [k_pad][k_t8] (one row per output component) and Vbar'_t^T as [k_t8][k_pad], k_t
+// Ubar_t as [kc_pad][k_t8] (one row per output component) and Vbar'_t^T as [k_t8][k_pad], k_t
 // rounded up to 8 with zero padding.
 int build_directional(m2l_plan_t *pl) {
     if (pl->dir_ready) return M2L_OK;
     int rc = build_blas_host(pl);
     if (rc) return rc;
-    const int k = pl->k, kp = pl->kp;
+    const int k = pl->k, kp = pl->kp, kc = pl->kc, kcp = pl->kcp;
     std::vector<int> kt(kNumTransfer);
     std::vector<std::vector<double>> ub(kNumTransfer), vt(kNumTransfer);
 #pragma omp parallel for schedule(dynamic, 2)
     for (int t = 0; t < kNumTransfer; ++t) {
-        // C_t is row-major [a][c]; the SVD routine takes column-major
-        std::vector<double> A((size_t)k * k), U, sv, V;
-        const double *C = &pl->C[(size_t)t * k * k];
-        for (int a = 0; a < k; ++a)
-            for (int c = 0; c < k; ++c) A[(size_t)c * k + a] = C[(size_t)a * k + c];
-        jacobi_svd(A, k, k, U, sv, V);
-        int m = 0;
-        while (m < k && sv[m] >= pl->dir_tol * sv[0]) ++m;
-        if (m < 1) m = 1;
-        const int m8 = round_up(m, 8);
-        kt[t] = m;
-        ub[t].assign((size_t)kp * m8, 0.0);
-        vt[t].assign((size_t)m8 * kp, 0.0);
-        for (int j = 0; j < m; ++j)
-            for (int a = 0; a < k; ++a) {
-                ub[t][(size_t)a * m8 + j] = U[(size_t)j * k + a];          // Ubar_t[a][j]
-                vt[t][(size_t)j * kp + a] = sv[j] * V[(size_t)j * k + a];  // Vbar'_t^T[j][c] = s_j V[c][j]
+        // C_t is row-major kc x k; the SVD routine takes a column-major matrix with at least as
+        // many rows as columns, so a wide C_t is factored through its transpose
+        const double *C = &pl->C[(size_t)t * kc * k];
+        const bool tall = kc >= k;
+        const int m = tall ? kc : k, nn = tall ? k : kc;
+        std::vector<double> A((size_t)m * nn), U, sv, V;
+        for (int a = 0; a < kc; ++a)
+            for (int c = 0; c < k; ++c) {
+                if (tall)
+                    A[(size_t)c * kc + a] = C[(size_t)a * k + c];
+                else
+                    A[(size_t)a * k + c] = C[(size_t)a * k + c];
             }
+        jacobi_svd(A, m, nn, U, sv, V);
+        // left (check side, kc) and right (equivalent side, k) singular vectors of C_t
+        auto left = [&](int j, int a) { return tall ? U[(size_t)j * kc + a] : V[(size_t)j * kc + a]; };
+        auto right = [&](int j, int c) { return tall ? V[(size_t)j * k + c] : U[(size_t)j * k + c]; };
+        int r = 0;
+        while (r < nn && sv[r] >= pl->dir_tol * sv[0]) ++r;
+        if (r < 1) r = 1;
+        const int r8 = round_up(r, 8);
+        kt[t] = r;
+        ub[t].assign((size_t)kcp * r8, 0.0);
+        vt[t].assign((size_t)r8 * kp, 0.0);
+        for (int j = 0; j < r; ++j) {
+            for (int a = 0; a < kc; ++a) ub[t][(size_t)a * r8 + j] = left(j, a);             // Ubar_t[a][j]
+            for (int c = 0; c < k; ++c) vt[t][(size_t)j * kp + c] = sv[j] * right(j, c);    // Vbar'_t^T[j][c]
+        }
     }
     pl->dir_kt = kt;
     pl->dir_ub.clear();
@@ -280,7 +301,7 @@ int build_directional(m2l_plan_t *pl) {
 }
 
 // Algorithmic flops of the BLAS contraction for one right-hand side at `level` (-1: levels
-// 2..depth): 2 k^2 per (target, source) pair, or 4 k k_t for a pair with transfer vector t when
+// 2..depth): 2 kc k per (target, source) pair, or 2 k_t (kc + k) for a pair with transfer vector t when
 // the directional factors are used (the two products of Sec. 3.2 step 4): with M2L_OPT_DIR_TOL
 // set and a precision whose contraction applies them (FP64, FP32, or AUTO).
 int contract_flops(m2l_plan_t *pl, int level, double *out) {
@@ -290,7 +311,8 @@ int contract_flops(m2l_plan_t *pl, int level, double *out) {
     if (!rc && dir) rc = build_directional(pl);
     if (rc) return rc;
     double w[kNumTransfer];
-    for (int t = 0; t < kNumTransfer; ++t) w[t] = dir ? 4.0 * pl->k * pl->dir_kt[t] : 2.0 * pl->k * pl->k;
+    for (int t = 0; t < kNumTransfer; ++t)
+        w[t] = dir ? 2.0 * pl->dir_kt[t] * (pl->kc + pl->k) : 2.0 * pl->kc * pl->k;
     double total = 0.0;
     const int l0 = level < 0 ? 2 : level, l1 = level < 0 ? pl->depth : level;
     for (int l = l0; l <= l1; ++l) {
@@ -582,6 +604,7 @@ static int upload_typed(m2l_plan_t *pl, DevOps &D, int form) {
     // single-precision paths take the pseudo-inverse truncated with alpha = 1e-9 (build_pinv)
     const bool single = sizeof(T) == 4;
     const int n = pl->n, k = pl->k, kp = pl->kp, r = single ? pl->r32 : pl->r, rp = pl->rp;
+    const int nc = pl->nc, kc = pl->kc, kcp = pl->kcp;
     const std::vector<double> &Veps = single ? pl->Veps32 : pl->Veps;
     const std::vector<double> &Uteps = single ? pl->Uteps32 : pl->Uteps;
     const std::vector<double> &Aop = single ? pl->Aop32 : pl->Aop;
@@ -591,15 +614,16 @@ static int upload_typed(m2l_plan_t *pl, DevOps &D, int form) {
         std::vector<double> St((size_t)k * n);
         for (int c = 0; c < k; ++c)
             for (int i = 0; i < n; ++i) St[(size_t)c * n + i] = pl->S[(size_t)i * k + c];
-        std::vector<T> Cp((size_t)kNumTransfer * kp * kp, T(0));
+        // C_t  [316][kcp][kp]
+        std::vector<T> Cp((size_t)kNumTransfer * kcp * kp, T(0));
         for (int t = 0; t < kNumTransfer; ++t)
-            for (int a = 0; a < k; ++a)
+            for (int a = 0; a < kc; ++a)
                 for (int c = 0; c < k; ++c)
-                    Cp[((size_t)t * kp + a) * kp + c] = (T)pl->C[((size_t)t * k + a) * k + c];
+                    Cp[((size_t)t * kcp + a) * kp + c] = (T)pl->C[((size_t)t * kc + a) * k + c];
         if ((rc = upload_vec(D.St, pad2<T>(St, k, n, kp, n)))) return rc;
         if ((rc = upload_vec(D.C, Cp))) return rc;
-        if ((rc = upload_vec(D.A, pad2<T>(Aop, r, k, rp, kp)))) return rc;
-        if ((rc = upload_vec(D.Uc, pad2<T>(pl->U, n, k, n, kp)))) return rc;
+        if ((rc = upload_vec(D.A, pad2<T>(Aop, r, kc, rp, kcp)))) return rc;
+        if ((rc = upload_vec(D.Uc, pad2<T>(pl->U, nc, kc, nc, kcp)))) return rc;
         if ((rc = upload_directional<T>(pl, D))) return rc;
     } else {
         int F = pl->F;
@@ -647,6 +671,19 @@ int upload_ops(m2l_plan_t *pl, int precision, int form) {
     }
     D.ready = rc == M2L_OK;
     return rc;
+}
+
+// Device copies of the operators (every precision), for options that change them.
+void release_operators(m2l_plan_t *pl) {
+    for (auto &D : pl->dev) {
+        void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Vlo, &D.Uc, &D.C_hi, &D.C_lo, &D.Ub, &D.Vt, &D.dir_meta,
+                         &D.Khat, &D.Ut, &D.tw};
+        for (void **pp : ptrs) {
+            if (*pp) cudaFree(*pp);
+            *pp = nullptr;
+        }
+        D.ready = false;
+    }
 }
 
 void free_device(m2l_plan_t *pl) {

@@ -30,7 +30,8 @@ M2L_OPT_FORM, M2L_OPT_PRECISION, M2L_OPT_ACCUMULATE, M2L_OPT_OUTPUT, M2L_OPT_TAR
 M2L_OPT_TIMING = 7
 M2L_OPT_TC_GROUP = 8
 M2L_OPT_DIR_TOL = 9
-M2L_Q_CONTRACT_FLOPS, M2L_Q_DIR_RANK_SUM = 13, 14
+M2L_OPT_CHECK_ORDER = 10
+M2L_Q_CONTRACT_FLOPS, M2L_Q_DIR_RANK_SUM, M2L_Q_NC, M2L_Q_RANK_CHECK = 13, 14, 15, 16
 STAGES = ["compress", "contract", "expand", "fft_forward", "hadamard", "fft_inverse", "pinv"]
 M2L_NUM_STAGES = 7
 M2L_FORM_AUTO, M2L_FORM_BLAS, M2L_FORM_FFT = 0, 1, 2
@@ -181,7 +182,7 @@ class Plan:
         self.set(form=form, precision=precision)
 
     def set(self, form=None, precision=None, accumulate=None, output=None, target_tol=None, fft_grid=None,
-            timing=None, tc_group=None, dir_tol=None):
+            timing=None, tc_group=None, dir_tol=None, check_order=None):
         if form is not None:
             _check(m2l_set_option(self.handle, M2L_OPT_FORM, FORMS[form]))
         if precision is not None:
@@ -201,6 +202,8 @@ class Plan:
             _check(m2l_set_option(self.handle, M2L_OPT_TC_GROUP, int(tc_group)))
         if dir_tol is not None:
             _check(m2l_set_option(self.handle, M2L_OPT_DIR_TOL, float(dir_tol)))
+        if check_order is not None:
+            _check(m2l_set_option(self.handle, M2L_OPT_CHECK_ORDER, int(check_order)))
         return self
 
     def stage_times(self):
@@ -226,6 +229,10 @@ class Plan:
     @property
     def n(self) -> int:
         return self.query(M2L_Q_N)
+
+    @property
+    def nc(self) -> int:
+        return self.query(M2L_Q_NC)
 
     def rows(self, level: int = -1) -> int:
         return self.query(M2L_Q_ROWS, level)

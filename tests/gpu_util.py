@@ -22,7 +22,7 @@ def split(flat, sizes, levels, R, n):
 
 
 def run_gpu(lib, depth, p, qs, keys=None, rank_tol=0.0, form="blas", precision="fp64", output="locals",
-            level=-1, R=1, fft_grid=None, accumulate=False, init=None, host=False, dir_tol=None):
+            level=-1, R=1, fft_grid=None, accumulate=False, init=None, host=False, dir_tol=None, check_order=None):
     """Apply through the C ABI on cuda:0. qs: {level: (B, R, n) float64}. Returns {level: array}."""
     import torch
     keys = keys or {}
@@ -32,14 +32,20 @@ def run_gpu(lib, depth, p, qs, keys=None, rank_tol=0.0, form="blas", precision="
         plan.set(fft_grid=fft_grid)
     if dir_tol is not None:
         plan.set(dir_tol=dir_tol)
+    if check_order is not None:
+        plan.set(check_order=check_order)
     for l, k in keys.items():
         if k is not None:
             plan.set_boxes(l, np.asarray(k, dtype=np.uint64))
     levels = levels_of(depth) if level == -1 else [level]
     n = plan.n
+    n_out = plan.nc if output == "check" else n  # check potentials have n_c values per row
     dt = torch.float64 if precision == "fp64" else torch.float32
     q = torch.from_numpy(concat(qs, levels)).to(dt)
-    out0 = torch.zeros_like(q) if init is None else torch.from_numpy(concat(init, levels)).to(dt)
+    sizes = {l: qs[l].shape[0] for l in levels}
+    rows = sum(sizes.values()) * R
+    out0 = (torch.zeros(rows * n_out, dtype=dt) if init is None
+            else torch.from_numpy(concat(init, levels)).to(dt))
     if host:
         qd, od = q.contiguous(), out0.clone()
     else:
@@ -48,8 +54,7 @@ def run_gpu(lib, depth, p, qs, keys=None, rank_tol=0.0, form="blas", precision="
     plan.apply(qd, od, level=level, n_rhs=R)
     torch.cuda.synchronize()
     flat = od.cpu().double().numpy()
-    sizes = {l: qs[l].shape[0] for l in levels}
-    res = split(flat, sizes, levels, R, n)
+    res = split(flat, sizes, levels, R, n_out)
     plan.close()
     return res
 

@@ -156,6 +156,47 @@ def test_directional_ranks_and_flops_match_oracle(lib, p, tol, dir_tol):
         lib.m2l_destroy(h)
 
 
+@pytest.mark.parametrize("p,pc,tol", [(4, 5, 1e-6), (3, 5, 0.0), (5, 6, 1e-8)])
+def test_check_order_operators_match_oracle(lib, p, pc, tol):
+    """M2L_OPT_CHECK_ORDER: the plan's rectangular operators against the oracle's, basis free
+    (U C_t S^T) and rank by rank, and its pseudo-inverse of the n_c x n check-to-equivalent map."""
+    h = lib.m2l_plan(3, p, 0, tol)
+    try:
+        lib.m2l_set_option(h, lib.M2L_OPT_CHECK_ORDER, pc)
+        n, nc = G.n_surface(p), G.n_surface(pc)
+        assert lib.m2l_query(h, lib.M2L_Q_N) == n and lib.m2l_query(h, lib.M2L_Q_NC) == nc
+        k = lib.m2l_query(h, lib.M2L_Q_RANK)
+        kc = lib.m2l_query(h, lib.M2L_Q_RANK_CHECK)
+        ops = O.compressed_operators(p, tol, 1.0, p_c=pc)
+        assert (kc, k) == (ops["kc"], ops["k"])
+        U = lib.m2l_get_operator(h, 0).reshape(nc, kc)
+        S = lib.m2l_get_operator(h, 1).reshape(n, k)
+        C = lib.m2l_get_operator(h, 2).reshape(316, kc, k)
+        for t in (0, 99, 315):
+            mine = U @ C[t] @ S.T
+            ref = ops["U"] @ ops["C"][t] @ ops["S"].T
+            assert np.linalg.norm(mine - ref) <= 1e-11 * np.linalg.norm(ops["K"][t])
+        V = lib.m2l_get_operator(h, 4)
+        Ut = lib.m2l_get_operator(h, 5)
+        r = V.size // n
+        V, Ut = V.reshape(n, r), Ut.reshape(r, nc)
+        Vo, Uto = O.down_pinv(p, 0, p_c=pc)
+        assert r == Vo.shape[1]
+        x = G.surface_points(pc, np.zeros(3), 1.0, G.ALPHA_INNER)
+        y = G.surface_points(p, np.zeros(3), 1.0, G.ALPHA_OUTER)
+        sv = np.linalg.svd(O.laplace(x, y), compute_uv=False)
+        kappa = sv[0] / sv[r - 1]
+        ref = Vo @ Uto
+        assert np.linalg.norm(V @ Ut - ref) <= nc * np.finfo(float).eps * kappa * np.linalg.norm(ref)
+        # the option is validated: below p or above 16 is refused, 0 restores p
+        assert lib.m2l_set_option(h, lib.M2L_OPT_CHECK_ORDER, p - 1) == lib.M2L_EINVAL
+        assert lib.m2l_set_option(h, lib.M2L_OPT_CHECK_ORDER, 17) == lib.M2L_EINVAL
+        assert lib.m2l_set_option(h, lib.M2L_OPT_CHECK_ORDER, 0) == lib.M2L_OK
+        assert lib.m2l_query(h, lib.M2L_Q_NC) == n
+    finally:
+        lib.m2l_destroy(h)
+
+
 def test_full_rank_operators_are_exact(lib):
     p = 4
     h = lib.m2l_plan(3, p, 0, 0.0)

@@ -251,6 +251,49 @@ def test_c2_full_size_sampled_directional(lib):
         assert M.rel_l2_error(phi_dense, chk[l][sample]) < 2e-6, l
 
 
+# Check order above the equivalent order (M2L_OPT_CHECK_ORDER; the BLAS tables' P_c > P_e).
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_check_order_full_rank_matches_dense(lib, precision):
+    wl = W.small(depth=3, p=4, density="u11")
+    qs = _qs(wl)
+    chk = run_gpu(lib, 3, 4, qs, precision=precision, output="check", check_order=5)
+    loc = run_gpu(lib, 3, 4, qs, precision=precision, output="locals", check_order=5)
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    for l in wl.levels:
+        L_ref, phi_ref = M.m2l_dense(4, l, qs[l], p_c=5)
+        assert chk[l].shape[2] == G.n_surface(5)
+        assert M.rel_l2_error(phi_ref / 2.0 ** l, chk[l]) < tol, (precision, l)
+        assert M.check_norm_error(4, l, L_ref, loc[l], p_c=5) < tol, (precision, l)
+
+
+def test_check_order_truncated_directional_sparse(lib):
+    wl = W.small(depth=4, p=5, n_rhs=3, n_points=500, density="normal", rank_tol=1e-8)
+    qs = _qs(wl)
+    keys = {l: wl.keys[l] for l in wl.levels}
+    kw = dict(keys=keys, rank_tol=1e-8, R=3, check_order=6, dir_tol=1e-5)
+    chk = run_gpu(lib, wl.depth, wl.p, qs, output="check", **kw)
+    loc = run_gpu(lib, wl.depth, wl.p, qs, output="locals", **kw)
+    ops = O.compressed_operators(5, 1e-8, 1.0, p_c=6)
+    d = O.directional_operators(ops["C"], 1e-5)
+    for l in wl.levels:
+        k = None if keys[l] is None else keys[l].astype(np.int64)
+        _, phi_ref = M.m2l_compressed(5, l, qs[l], {**ops, **d}, keys=k, p_c=6)
+        assert M.rel_l2_error(phi_ref, chk[l]) < 1e-10, l
+        L_ref = M.locals_from_check(5, 0, phi_ref, p_c=6)
+        assert M.check_norm_error(5, 0, L_ref, loc[l], p_c=6) < 1e-9, l
+        _, phi_dense = M.m2l_dense(5, l, qs[l], keys=k, p_c=6)
+        assert M.rel_l2_error(phi_dense / 2.0 ** l, chk[l]) < 1e-3, l
+
+
+def test_check_order_refuses_fft_and_tensor_cores(lib):
+    wl = W.small(depth=2, p=4)
+    qs = _qs(wl)
+    for form, precision in (("fft", "fp64"), ("blas", "tf32x3"), ("blas", "bf16x3")):
+        with pytest.raises(lib.M2LError) as e:
+            run_gpu(lib, 2, 4, qs, form=form, precision=precision, check_order=5)
+        assert e.value.code == lib.M2L_EUNSUPPORTED, (form, precision)
+
+
 # Split tensor-core precisions (tcgen05): bounds on check potentials. TF32x3 pieces carry 22
 # mantissa bits, so the result sits at FP32 rounding (measured 4e-7 to 1.6e-6 for p = 4..10);
 # BF16x3 pieces carry about 17 (measured 3e-7 to 9.5e-6, largest for densities of both signs).
