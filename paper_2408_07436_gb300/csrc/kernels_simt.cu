@@ -77,45 +77,56 @@ static int check_launch(const char *what) {
 }
 
 // ----------------------------------------------------------------------------------------------
-// Y = X W^T (+ Y): 64 x 64 output tile per CTA, 4 x 4 per thread, K in steps of 16 (one type
-// for X, W and accumulation, written as TY).
-template <class TX, class TW, class TY>
+// Columns per thread for a rank: the fewest column blocks of at most 16 * max_tn columns, then
+// the narrowest blocks that still cover k_pad.
+inline int contract_tn(int kp, int max_tn) {
+    const int units = (kp + 15) / 16;
+    const int blocks = (units + max_tn - 1) / max_tn;
+    return (units + blocks - 1) / blocks;
+}
+
+// Y = X W^T (+ Y): 64 rows x 16 TN columns per CTA, 4 x TN per thread, K in steps of 16 (one
+// type for X, W and accumulation, written as TY). TN is picked per output width so the column
+// blocks cover it with little padding (as in the contraction).
+template <class TX, class TW, class TY, int TN>
 __global__ void __launch_bounds__(256) gemm_xwt_kernel(const TX *__restrict__ X, long long ldx,
                                                        const TW *__restrict__ W, long long ldw,
                                                        TY *__restrict__ Y, long long ldy, long long rows,
                                                        int O, int K, int acc) {
-    constexpr int BM = 64, BN = 64, BK = 16;
+    constexpr int BM = 64, BN = 16 * TN, BK = 16;
     __shared__ TW Xs[BK][BM + 4];
     __shared__ TW Ws[BK][BN + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const long long row0 = (long long)blockIdx.x * BM;
     const int col0 = blockIdx.y * BN;
-    TW a[4][4];
+    TW a[4][TN];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) a[i][j] = TW(0);
+        for (int j = 0; j < TN; ++j) a[i][j] = TW(0);
     for (int k0 = 0; k0 < K; k0 += BK) {
         for (int e = tid; e < BM * BK; e += 256) {
-            int r = e / BK, kk = e % BK;
-            long long gr = row0 + r;
-            int gk = k0 + kk, gc = col0 + r;
+            const int r = e / BK, kk = e % BK;
+            const long long gr = row0 + r;
+            const int gk = k0 + kk;
             Xs[kk][r] = (gr < rows && gk < K) ? (TW)X[gr * ldx + gk] : TW(0);
-            Ws[kk][r] = (gc < O && gk < K) ? W[(long long)gc * ldw + gk] : TW(0);
+        }
+        for (int e = tid; e < BN * BK; e += 256) {
+            const int c = e / BK, kk = e % BK, gc = col0 + c, gk = k0 + kk;
+            Ws[kk][c] = (gc < O && gk < K) ? W[(long long)gc * ldw + gk] : TW(0);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            TW xa[4], wb[4];
+            TW xa[4], wb[TN];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                xa[i] = Xs[kk][ty * 4 + i];
-                wb[i] = Ws[kk][tx * 4 + i];
-            }
+            for (int i = 0; i < 4; ++i) xa[i] = Xs[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) wb[j] = Ws[kk][tx * TN + j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) a[i][j] = fma(xa[i], wb[j], a[i][j]);
+                for (int j = 0; j < TN; ++j) a[i][j] = fma(xa[i], wb[j], a[i][j]);
         }
         __syncthreads();
     }
@@ -124,8 +135,8 @@ __global__ void __launch_bounds__(256) gemm_xwt_kernel(const TX *__restrict__ X,
         long long r = row0 + ty * 4 + i;
         if (r >= rows) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int c = col0 + tx * 4 + j;
+        for (int j = 0; j < TN; ++j) {
+            int c = col0 + tx * TN + j;
             if (c < O) {
                 TW v = a[i][j];
                 if (acc) v += (TW)Y[r * ldy + c];
@@ -133,6 +144,13 @@ __global__ void __launch_bounds__(256) gemm_xwt_kernel(const TX *__restrict__ X,
             }
         }
     }
+}
+
+template <class T, int TN>
+static void launch_gemm_tn(const T *X, long long ldx, const T *W, long long ldw, T *Y, long long ldy, long long rows,
+                           int O, int K, int acc, cudaStream_t s) {
+    dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((O + 16 * TN - 1) / (16 * TN)));
+    gemm_xwt_kernel<T, T, T, TN><<<grid, 256, 0, s>>>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc);
 }
 
 // Y = X (W_hi + W_lo)^T (+ Y) for FP32 data with about twice FP32's precision in the sum: every
@@ -221,8 +239,20 @@ template <class T>
 int launch_gemm_xwt(const T *X, long long ldx, const T *W, long long ldw, T *Y, long long ldy,
                     long long rows, int O, int K, int acc, cudaStream_t s) {
     if (rows <= 0 || O <= 0) return M2L_OK;
-    dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((O + 63) / 64));
-    gemm_xwt_kernel<T, T, T><<<grid, 256, 0, s>>>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc);
+    switch (contract_tn(O, sizeof(T) == 8 ? 12 : 8)) {
+        case 1: launch_gemm_tn<T, 1>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
+        case 2: launch_gemm_tn<T, 2>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
+        case 3: launch_gemm_tn<T, 3>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
+        case 4: launch_gemm_tn<T, 4>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
+        case 5: launch_gemm_tn<T, 5>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
+        case 6: launch_gemm_tn<T, 6>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
+        case 7: launch_gemm_tn<T, 7>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
+        case 8: launch_gemm_tn<T, 8>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
+        case 9: launch_gemm_tn<T, 9>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
+        case 10: launch_gemm_tn<T, 10>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
+        case 11: launch_gemm_tn<T, 11>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
+        default: launch_gemm_tn<T, 12>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
+    }
     return check_launch("gemm");
 }
 
@@ -509,13 +539,6 @@ __global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView 
     }
 }
 
-// Columns per thread for a rank: the fewest column blocks of at most 16 * max_tn columns, then
-// the narrowest blocks that still cover k_pad.
-inline int contract_tn(int kp, int max_tn) {
-    const int units = (kp + 15) / 16;
-    const int blocks = (units + max_tn - 1) / max_tn;
-    return (units + blocks - 1) / blocks;
-}
 
 template <class T, int TN>
 static void launch_contract_tn(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
