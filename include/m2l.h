@@ -249,6 +249,38 @@ int m2l_apply_noalloc(m2l_plan_t *plan, const double *multipoles, double *locals
  * Returns M2L_OK, M2L_EINVAL (no GPU plan, polls < 1) or M2L_ECUDA. */
 int m2l_selftest_watchdog(m2l_plan_t *plan, long long polls);
 
+/* ---------------------------------------------------------------------------------------------
+ * A whole FMM around the M2L plan: the other stages of the kiFMM (Sec. 2.1-2.2, Fig. 2), namely
+ * P2M, M2M, L2L, L2P and the near-field P2P, on the GPU, with M2L through an m2l plan on the
+ * occupied boxes of every level. It turns M2L into potentials that can be compared with direct
+ * summation (Eq. 16). FP64, one charge vector; check and equivalent orders equal. The upward and
+ * downward operators use the surfaces and the pseudo-inverse rule of M2L; like M2L they are
+ * scale free (Laplace kernel of degree -1) and built once at unit width.
+ */
+typedef struct m2l_fmm_s m2l_fmm_t;
+
+/* points: HOST pointer, n_points x 3 (x, y, z) inside [origin, origin + width)^3 (origin: 3
+ * doubles, NULL for 0). depth in [2, 8] (leaves are the boxes of that level), p in [2, 16],
+ * rank_tol as for m2l_plan. Sorts the points into leaves and builds the box lists, neighbour
+ * lists, operators and the inner M2L plan. NULL on error (m2l_last_error). */
+m2l_fmm_t *m2l_fmm_plan(const double *points, long long n_points, int depth, int p, double rank_tol,
+                        const double *origin, double width);
+
+/* Set an option of the inner M2L plan (M2L_OPT_FORM, M2L_OPT_DIR_TOL, M2L_OPT_TC_GROUP ...).
+ * M2L_OPT_PRECISION other than FP64 and M2L_OPT_CHECK_ORDER are refused (M2L_EINVAL). */
+int m2l_fmm_set_m2l_option(m2l_fmm_t *fmm, int key, long long value);
+
+/* potentials[i] = sum over j != i of charges[j] / (4 pi |x_i - x_j|), by the FMM: P2M at the
+ * leaves, M2M up to level 2, M2L at levels 2..depth, L2L down, L2P and P2P at the leaves.
+ * charges, potentials: n_points doubles each, HOST or DEVICE pointers, in the order the points
+ * were given. Synchronous. Returns M2L_OK, M2L_EINVAL, M2L_ENOMEM or M2L_ECUDA. */
+int m2l_fmm_evaluate(m2l_fmm_t *fmm, const double *charges, double *potentials);
+
+/* The inner M2L plan (owned by the FMM; valid until m2l_fmm_destroy), for queries. */
+m2l_plan_t *m2l_fmm_m2l_plan(m2l_fmm_t *fmm);
+
+void m2l_fmm_destroy(m2l_fmm_t *fmm); /* NULL-safe */
+
 /* Copy a plan operator to host memory (FP64), for tests and inspection:
  * which = 0: U (n_c x k_c), 1: S (n x k), 2: C_t (316 x k_c x k), 3: singular values of K_fat
  *         (n_c), 4: pseudo-inverse factor V_eps (n x r), 5: Ut_eps = Sigma_eps^-1 U_eps^T (r x n_c).

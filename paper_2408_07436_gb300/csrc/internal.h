@@ -164,6 +164,11 @@ int build_pinv(m2l_plan_t *pl);
 int build_blas_host(m2l_plan_t *pl);
 int build_directional(m2l_plan_t *pl);
 void release_operators(m2l_plan_t *pl);
+// Pseudo-inverse factors of Eq. 10 from the SVD of an m x n (m >= n) matrix, U, V column-major:
+// Veps [n][r], Uteps [r][m] with the singular values above (alpha + max(m, n) eps) s_0.
+void pinv_truncation(int m, int n, const std::vector<double> &U, const std::vector<double> &s,
+                     const std::vector<double> &V, double alpha, int &r, std::vector<double> &Veps,
+                     std::vector<double> &Uteps);
 int contract_flops(m2l_plan_t *pl, int level, double *out);
 int build_fft_host(m2l_plan_t *pl);
 int build_level_tables(m2l_plan_t *pl);     // host tables and pair counts

@@ -112,7 +112,7 @@ static constexpr double kPinvAlphaSingle = 1e-9;
 
 // For the m x n (m >= n) matrix A = U diag(s) V^T (column-major factors): Veps [n][r] and
 // Uteps [r][m] of the singular values above (alpha + max(m, n) eps_mach) s_0.
-static void pinv_truncation(int m, int n, const std::vector<double> &U, const std::vector<double> &s,
+void pinv_truncation(int m, int n, const std::vector<double> &U, const std::vector<double> &s,
                             const std::vector<double> &V, double alpha, int &r, std::vector<double> &Veps,
                             std::vector<double> &Uteps) {
     const double thresh = (alpha + std::max(m, n) * 2.220446049250313e-16) * s[0];

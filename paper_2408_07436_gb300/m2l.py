@@ -74,6 +74,17 @@ _lib.m2l_get_operator.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_dou
 _lib.m2l_get_operator.restype = ctypes.c_int
 _lib.m2l_selftest_watchdog.argtypes = [_vp, ctypes.c_longlong]
 _lib.m2l_selftest_watchdog.restype = ctypes.c_int
+_dpp = ctypes.POINTER(ctypes.c_double)
+_lib.m2l_fmm_plan.argtypes = [_dpp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dpp, ctypes.c_double]
+_lib.m2l_fmm_plan.restype = _vp
+_lib.m2l_fmm_set_m2l_option.argtypes = [_vp, ctypes.c_int, ctypes.c_longlong]
+_lib.m2l_fmm_set_m2l_option.restype = ctypes.c_int
+_lib.m2l_fmm_evaluate.argtypes = [_vp, _vp, _vp]
+_lib.m2l_fmm_evaluate.restype = ctypes.c_int
+_lib.m2l_fmm_m2l_plan.argtypes = [_vp]
+_lib.m2l_fmm_m2l_plan.restype = _vp
+_lib.m2l_fmm_destroy.argtypes = [_vp]
+_lib.m2l_fmm_destroy.restype = None
 
 
 class M2LError(RuntimeError):
@@ -256,3 +267,55 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class FMM:
+    """A whole FMM (P2M, M2M, M2L, L2L, L2P, P2P on the GPU, FP64) over points fixed at plan time."""
+
+    def __init__(self, points, depth: int, p: int, rank_tol: float = 0.0, origin=None, width: float = 1.0):
+        import numpy as np
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        if pts.ndim != 2 or pts.shape[1] != 3:
+            raise ValueError("points must be (N, 3)")
+        self.n_points = pts.shape[0]
+        org = None if origin is None else np.ascontiguousarray(origin, dtype=np.float64)
+        self.handle = _lib.m2l_fmm_plan(pts.ctypes.data_as(_dpp), self.n_points, depth, p, rank_tol,
+                                        None if org is None else org.ctypes.data_as(_dpp), width)
+        if not self.handle:
+            raise M2LError(M2L_EINVAL, m2l_last_error())
+
+    def set_m2l(self, form=None, dir_tol=None, tc_group=None):
+        if form is not None:
+            _check(_lib.m2l_fmm_set_m2l_option(self.handle, M2L_OPT_FORM, FORMS[form]))
+        if dir_tol is not None:
+            bits = struct.unpack("<q", struct.pack("<d", float(dir_tol)))[0]
+            _check(_lib.m2l_fmm_set_m2l_option(self.handle, M2L_OPT_DIR_TOL, bits))
+        return self
+
+    def m2l_query(self, what: int, level: int = -1) -> int:
+        return m2l_query(_lib.m2l_fmm_m2l_plan(self.handle), what, level)
+
+    def evaluate(self, charges, out=None):
+        """Potentials at the points (numpy arrays on the host, or torch tensors on either side)."""
+        import numpy as np
+        if hasattr(charges, "data_ptr"):
+            if out is None:
+                out = charges.new_empty(charges.shape)
+            _check(_lib.m2l_fmm_evaluate(self.handle, charges.data_ptr(), out.data_ptr()))
+            return out
+        q = np.ascontiguousarray(charges, dtype=np.float64)
+        res = np.empty_like(q) if out is None else out
+        _check(_lib.m2l_fmm_evaluate(self.handle, q.ctypes.data, res.ctypes.data))
+        return res
+
+    def close(self):
+        if self.handle:
+            _lib.m2l_fmm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
