@@ -561,14 +561,59 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_fmm(args):
+    """The whole FMM (P2M, M2M, M2L, L2L, L2P, P2P; FP64) on the 1M-point cloud of the default
+    workload (depth 5, p = 6, M2L in the BLAS form at rank 1e-7 with directional factors at 1e-8,
+    or the FFT form with --variants fft). Charges resident on the device; the plan (tree,
+    operators) is built before the timed region. Accuracy: Eq. 16 against direct summation on a
+    seeded sample of 1,000 targets (the oracle's direct sum on this host)."""
+    import torch
+    from oracle import _cdirect
+    from paper_2408_07436_gb300 import m2l as lib
+    wl = W.c2(depth=args.depth)
+    rng = np.random.default_rng(W.SEED_BASE + 2)
+    pts = rng.random((wl.n_points, 3))
+    q = rng.uniform(-1.0, 1.0, wl.n_points)
+    form = (args.variants or "blas").split(",")[0].split("-")[0]
+    fmm = lib.FMM(pts, depth=wl.depth, p=wl.p, rank_tol=wl.rank_tol if form == "blas" else 0.0)
+    fmm.set_m2l(form=form, dir_tol=wl.dir_tol if form == "blas" else None)
+    qd = torch.from_numpy(q).cuda()
+    out = torch.empty_like(qd)
+    for _ in range(args.warmup):
+        fmm.evaluate(qd, out)
+    torch.cuda.synchronize()
+    sampler = ClockSampler()
+    sampler.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fmm.evaluate(qd, out)  # synchronous
+    el = (time.perf_counter() - t0) / args.steps
+    clocks = sampler.stop()
+    pot = out.cpu().numpy()
+    sample = np.sort(rng.choice(wl.n_points, 1000, replace=False))
+    ref = _cdirect.direct_potential(pts[sample], pts, q)
+    err = float(np.linalg.norm(pot[sample] - ref) / np.linalg.norm(ref))
+    pairs = fmm.m2l_query(lib.M2L_Q_PAIRS, -1)
+    fmm.close()
+    return {"metric": "whole FMM potentials/s (FP64)", "value": wl.n_points / el, "unit": "points/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"laplace3d whole FMM uniform-cube {wl.n_points} points depth{wl.depth} p{wl.p} "
+                                   f"m2l {form}" + (f"(rank_tol {wl.rank_tol:g}, directional {wl.dir_tol:g})"
+                                                     if form == "blas" else "(grid 12^3)"),
+                       "m2l_pairs": int(pairs), "timing": "wall clock around synchronous evaluations"},
+            "rel_err_vs_direct_1000_targets": err, "clocks": clocks}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
-                    help="c2 (default): the 1M-point workload; c3/c4/c5: precision, RHS-batching and instance-batching studies")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "fmm"],
+                    help="c2 (default): the 1M-point workload; c3/c4/c5: precision, RHS-batching and instance-batching "
+                         "studies; fmm: the whole FMM around M2L on the 1M-point cloud")
     ap.add_argument("--variants", default=None, help="comma list of form-precision (default: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -582,6 +627,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)))
+        return
+    if args.workload == "fmm":
+        if rank == 0:
+            print(json.dumps(run_fmm(args)))
         return
     if world > 1:
         import torch
