@@ -128,6 +128,7 @@ static LevelView view_of(const LevelDev &D) {
     v.cslot = D.cslot;
     v.cxyz = D.cxyz;
     v.cchild = D.cchild;
+    v.cperm = D.cperm;
     v.base = D.base;
     v.cbase = D.cbase;
     v.nboxes = D.nboxes;

@@ -66,9 +66,10 @@ struct LevelDev {
     int *cslot = nullptr;               // [8^(l-1)] parent grid -> cluster or -1
     uint32_t *cxyz = nullptr;           // [nclusters] packed parent coordinates
     int *cchild = nullptr;              // [nclusters][8] compact child box or -1
+    int *cperm = nullptr;               // [nclusters] clusters by domain-boundary class, Morton inside
     long long pairs = 0;                // M2L (target, source) pairs
     // host copies (built without a GPU; uploaded on first use)
-    std::vector<int> h_slot, h_perm, h_cslot, h_cchild;
+    std::vector<int> h_slot, h_perm, h_cslot, h_cchild, h_cperm;
     std::vector<uint32_t> h_xyz, h_cxyz;
     bool on_device = false;
 };

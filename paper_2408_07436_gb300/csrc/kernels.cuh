@@ -15,6 +15,7 @@ struct LevelView {
     const int *cslot;       // [(N/2)^3] parent grid -> cluster or -1
     const uint32_t *cxyz;   // [nclusters] packed parent coordinates
     const int *cchild;      // [nclusters][8] compact child box or -1
+    const int *cperm;       // [nclusters] clusters grouped by domain-boundary class
     long long base;         // first global box row of the level
     long long cbase;        // first global cluster of the level
     long long nboxes, nclusters;

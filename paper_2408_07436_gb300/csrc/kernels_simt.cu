@@ -3,6 +3,7 @@
 // transfer vectors of each target octant, and the three stages of the FFT form.
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "internal.h"
 #include "kernels.cuh"
@@ -20,10 +21,13 @@ __constant__ short c_tidx[7][7][7];
 __constant__ short c_clu[26][64];
 __constant__ signed char c_dir[26][3];
 
+static void cache_launch_shapes();
+
 int ensure_constants(int device) {
     static bool done[64] = {false};
     if (device < 0 || device >= 64) return M2L_EINVAL;
     if (done[device]) return M2L_OK;
+    cache_launch_shapes();  // before any launch, so never inside a stream capture
     short tidx[7][7][7];
     for (int x = -3; x <= 3; ++x)
         for (int y = -3; y <= 3; ++y)
@@ -368,25 +372,28 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(const LevelView *__r
 // B2 with the directional factors of Eq. 15. Per transfer vector t the tile's gathered sources X
 // (64 rows x k) go through the two products of Sec. 3.2 step 4: xi = X Vbar'_t (64 x k_t) and
 // phit += xi Ubar_t^T, so a pair costs 4 k k_t flops instead of 2 k^2. Stage 1 streams X and
-// Vbar'_t^T through shared memory in chunks of 16 along k (as the plain kernel streams C_t) and
-// gives a thread rows 2 sy, 2 sy + 1 and columns sx + 8 m of xi; xi then waits in shared memory
-// for stage 2, which uses the 4 x TN tile of the plain kernel and Ubar_t in chunks of 16 along
-// k_t. About 75 KB of shared memory in FP64, so two CTAs share an SM and one computes while the
-// other gathers. Both stages map the same 8 rows to a warp: a warp whose rows have no source
-// skips the products of both.
-// One 16-deep chunk of stage 1 with exactly NM column groups per thread: guarding an unrolled
-// loop with a runtime count would leave predicated-off FMAs that still occupy the FP64 pipe.
+// Vbar'_t^T through shared memory in chunks of 16 along k (as the plain kernel streams C_t). The
+// k_t columns of xi (up to 64 per pass) are cut into 8 contiguous groups of floor or ceil(k_t / 8)
+// columns, one per warp, and a lane holds rows 2 l, 2 l + 1 of its warp's group: the column
+// count is exact (no rounding of k_t up to a multiple of 8), a warp's trip count is uniform and
+// its column loads are broadcasts. xi then waits in shared memory for stage 2, which uses the
+// 4 x TN tile of the plain kernel and Ubar_t in chunks of 16 along k_t. About 75 KB of shared
+// memory in FP64, so two CTAs share an SM and one computes while the other gathers. Stage 1 is
+// skipped when no row of the tile has a source for t, stage 2 per warp of 8 rows.
+// One 16-deep chunk of stage 1 with exactly NM columns per lane: guarding an unrolled loop with a
+// runtime count would leave predicated-off FMAs that still occupy the FP64 pipe.
 template <class T, int NM>
-__device__ __forceinline__ void dir_stage1_chunk(const T *Xs, const T *Vs, int sx, int sy, T (&y)[8][2]) {
+__device__ __forceinline__ void dir_stage1_chunk(const T *Xs, const T *Vs, int c0, int lane, T (&y)[8][2]) {
     constexpr int XP = 66, VP = 66;
+    using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-        const T x0 = Xs[kk * XP + 2 * sy], x1 = Xs[kk * XP + 2 * sy + 1];
+        const T2 x = *reinterpret_cast<const T2 *>(Xs + kk * XP + 2 * lane);  // rows 2 l, 2 l + 1
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
-            const T w = Vs[kk * VP + sx + 8 * m];
-            y[m][0] = fma(x0, w, y[m][0]);
-            y[m][1] = fma(x1, w, y[m][1]);
+            const T w = Vs[kk * VP + c0 + m];
+            y[m][0] = fma(x.x, w, y[m][0]);
+            y[m][1] = fma(x.y, w, y[m][1]);
         }
     }
 }
@@ -410,7 +417,7 @@ __global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView 
     const ContractTile tile = tiles[blockIdx.x];
     const LevelView &L = levels[tile.lev];
     const int R = L.R;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, sx = tid & 7, sy = tid >> 3;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31, warp = tid >> 5;
     const int col0 = blockIdx.y * BN;
     if (tid < BM) {
         if (tid < tile.rows) {
@@ -453,9 +460,12 @@ __global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView 
 #pragma unroll
         for (int i = 0; i < 4; ++i) mine |= src_row[ty * 4 + i] != zero_row;
         const bool live = __any_sync(0xffffffffu, mine);
+        const bool live1 =
+            __any_sync(0xffffffffu, src_row[2 * lane] != zero_row || src_row[2 * lane + 1] != zero_row);
         // stage 1: xi = X Vbar'_t, up to 64 columns of xi per pass
-        for (int jp0 = 0; jp0 < md.w; jp0 += YC) {
-            const int ncol = min(YC, md.w - jp0), nm = ncol / 8;
+        for (int jp0 = 0; jp0 < md.z; jp0 += YC) {
+            const int ncol = min(YC, md.z - jp0), q = ncol >> 3, rm = ncol & 7;
+            const int nm = q + (warp < rm ? 1 : 0), c0 = warp * q + min(warp, rm);
             T y[8][2];
 #pragma unroll
             for (int m = 0; m < 8; ++m) y[m][0] = y[m][1] = T(0);
@@ -471,24 +481,25 @@ __global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView 
                     Vs[kk * (YC + 2) + j] = k0 + kk < kp ? V[(size_t)j * kp + k0 + kk] : T(0);
                 }
                 __syncthreads();
-                if (live) {
+                if (live1) {
                     switch (nm) {
-                        case 1: dir_stage1_chunk<T, 1>(Xs, Vs, sx, sy, y); break;
-                        case 2: dir_stage1_chunk<T, 2>(Xs, Vs, sx, sy, y); break;
-                        case 3: dir_stage1_chunk<T, 3>(Xs, Vs, sx, sy, y); break;
-                        case 4: dir_stage1_chunk<T, 4>(Xs, Vs, sx, sy, y); break;
-                        case 5: dir_stage1_chunk<T, 5>(Xs, Vs, sx, sy, y); break;
-                        case 6: dir_stage1_chunk<T, 6>(Xs, Vs, sx, sy, y); break;
-                        case 7: dir_stage1_chunk<T, 7>(Xs, Vs, sx, sy, y); break;
-                        default: dir_stage1_chunk<T, 8>(Xs, Vs, sx, sy, y); break;
+                        case 0: break;
+                        case 1: dir_stage1_chunk<T, 1>(Xs, Vs, c0, lane, y); break;
+                        case 2: dir_stage1_chunk<T, 2>(Xs, Vs, c0, lane, y); break;
+                        case 3: dir_stage1_chunk<T, 3>(Xs, Vs, c0, lane, y); break;
+                        case 4: dir_stage1_chunk<T, 4>(Xs, Vs, c0, lane, y); break;
+                        case 5: dir_stage1_chunk<T, 5>(Xs, Vs, c0, lane, y); break;
+                        case 6: dir_stage1_chunk<T, 6>(Xs, Vs, c0, lane, y); break;
+                        case 7: dir_stage1_chunk<T, 7>(Xs, Vs, c0, lane, y); break;
+                        default: dir_stage1_chunk<T, 8>(Xs, Vs, c0, lane, y); break;
                     }
                 }
             }
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
                 if (m < nm) {
-                    Ys[(size_t)(jp0 + sx + 8 * m) * XP + 2 * sy] = y[m][0];
-                    Ys[(size_t)(jp0 + sx + 8 * m) * XP + 2 * sy + 1] = y[m][1];
+                    Ys[(size_t)(jp0 + c0 + m) * XP + 2 * lane] = y[m][0];
+                    Ys[(size_t)(jp0 + c0 + m) * XP + 2 * lane + 1] = y[m][1];
                 }
             }
             __syncthreads();  // the next pass reuses Xs and Vs; stage 2 reads Ys
@@ -782,7 +793,7 @@ __global__ void __launch_bounds__(256) hadamard_kernel(LevelView L, int R, int F
             row[b] = -1;
             px[b] = py[b] = pz[b] = rr[b] = 0;
             if (it < items) {
-                const long long tc = it / R;
+                const long long tc = L.cperm[it / R];
                 rr[b] = (int)(it % R);
                 row[b] = (L.cbase + tc) * R + rr[b];
                 const uint32_t pc = L.cxyz[tc];
@@ -958,6 +969,28 @@ static int launch_hadamard_warp(const LevelView &L, int R, int F, const T *Khat,
     return check_launch("hadamard");
 }
 
+// Resident CTAs of hadamard_kernel on the device (occupancy query, cached on first use).
+template <class T>
+static int hadamard_resident() {
+    constexpr int FB = 128 / (2 * (int)sizeof(T)), IB = sizeof(T) == 4 ? 2 : 1;
+    static int resident = 0;
+    if (!resident) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hadamard_kernel<T, FB, IB>, 256, 0) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        resident = per_sm * sm_count();
+    }
+    return resident;
+}
+
+static void cache_launch_shapes() {
+    hadamard_resident<float>();
+    hadamard_resident<double>();
+}
+
 template <class T>
 int launch_hadamard(const LevelView &L, int R, int F, const T *Khat, const T *qhat, T *phihat, cudaStream_t s) {
     constexpr int FB = 128 / (2 * (int)sizeof(T)), TC = 256 / FB;  // one 128-byte line of complex values
@@ -974,9 +1007,20 @@ int launch_hadamard(const LevelView &L, int R, int F, const T *Khat, const T *qh
     // FP64 is bound by the FP64 units and keeps one
     constexpr int IB = sizeof(T) == 4 ? 2 : 1;
     const unsigned gy = (unsigned)((F + FB - 1) / FB);
-    // up to 8 item groups per thread, fewer when a level is too small to fill four waves of CTAs
-    const long long waves4 = 4LL * sm_count() * 2 * TC * IB;
-    const long long ipt = std::max(1LL, std::min(8LL, items * (long long)gy / waves4));
+    // Item groups per thread (ipt): the CTAs of a launch all do ipt iterations, so the launch takes
+    // about ceil(CTAs / resident CTAs) x ipt iteration times; take the ipt in 1..16 that makes
+    // this smallest (a partial last wave costs as much as a full one), the larger ipt on ties
+    // (fewer CTAs load the spectra block).
+    const int resident = hadamard_resident<T>();
+    long long ipt = 1, best = -1;
+    for (long long c = 1; c <= 16; ++c) {
+        const long long ctas = (items + TC * IB * c - 1) / (TC * IB * c) * (long long)gy;
+        const long long cost = (ctas + resident - 1) / resident * c;
+        if (best < 0 || cost <= best) {
+            best = cost;
+            ipt = c;
+        }
+    }
     long long gx = (items + TC * IB * ipt - 1) / (TC * IB * ipt);
     if (gx < 1) gx = 1;
     if (gx > (1LL << 30)) gx = 1LL << 30;

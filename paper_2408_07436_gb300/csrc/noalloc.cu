@@ -220,6 +220,7 @@ extern "C" int m2l_apply_noalloc(m2l_plan_t *pl, const double *multipoles, doubl
     L.perm = LD.perm;
     L.cslot = LD.cslot;
     L.cxyz = LD.cxyz;
+    L.cperm = LD.cperm;
     L.cchild = LD.cchild;
     L.base = 0;
     L.cbase = 0;

@@ -459,11 +459,11 @@ static int dev_upload(T *&dst, const std::vector<T> &src) {
 }
 
 static void free_level(LevelDev &L) {
-    void *ptrs[] = {L.slot, L.xyz, L.perm, L.cslot, L.cxyz, L.cchild};
+    void *ptrs[] = {L.slot, L.xyz, L.perm, L.cslot, L.cxyz, L.cchild, L.cperm};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     L.slot = nullptr; L.xyz = nullptr; L.perm = nullptr;
-    L.cslot = nullptr; L.cxyz = nullptr; L.cchild = nullptr;
+    L.cslot = nullptr; L.cxyz = nullptr; L.cchild = nullptr; L.cperm = nullptr;
 }
 
 int build_level_tables(m2l_plan_t *pl) {
@@ -488,7 +488,20 @@ int build_level_tables(m2l_plan_t *pl) {
             xyz[b] = x | (y << 10) | (z << 20);
             slot[((size_t)z * N + y) * N + x] = (int)b;
         }
-        // targets grouped by octant (the low three bits of the key), Morton order inside
+        // targets grouped by octant (the low three bits of the key); inside an octant by the
+        // domain-boundary class of the parent (per axis: first plane, last plane, neither), Morton
+        // order inside a class. A target's interaction list loses the transfer vectors that leave
+        // the domain exactly by its class, so contraction tiles cut from this order hold targets
+        // with the same live vectors and rows without a source stay rare.
+        const uint32_t Np = N / 2;
+        auto boundary_class = [&](long long b) {
+            int c = 0;
+            for (int a = 0; a < 3; ++a) {
+                const uint32_t pv = ((xyz[b] >> (10 * a)) & 1023) >> 1;
+                c |= ((pv == 0 ? 1 : 0) | (pv == Np - 1 ? 2 : 0)) << (2 * a);
+            }
+            return c;
+        };
         std::vector<int> &perm = L.h_perm;
         perm.clear();
         perm.reserve(B);
@@ -496,13 +509,14 @@ int build_level_tables(m2l_plan_t *pl) {
             L.oct_start[c] = (long long)perm.size();
             for (long long b = 0; b < B; ++b)
                 if ((int)(keys[b] & 7) == c) perm.push_back((int)b);
+            std::stable_sort(perm.begin() + L.oct_start[c], perm.end(),
+                             [&](int x, int y) { return boundary_class(x) < boundary_class(y); });
         }
         L.oct_start[8] = (long long)perm.size();
         // clusters: non-empty parents (App. A.1), Morton order
         std::vector<uint64_t> pk;
         for (long long b = 0; b < B; ++b)
             if (pk.empty() || pk.back() != (keys[b] >> 3)) pk.push_back(keys[b] >> 3);
-        uint32_t Np = N / 2;
         std::vector<int> &cslot = L.h_cslot, &cchild = L.h_cchild;
         std::vector<uint32_t> &cxyz = L.h_cxyz;
         cslot.assign((size_t)Np * Np * Np, -1);
@@ -520,6 +534,20 @@ int build_level_tables(m2l_plan_t *pl) {
                 cchild[c * 8 + (keys[b] & 7)] = (int)b;
             }
         }
+        // clusters in the same grouping as the targets above: the Hadamard product works on a few
+        // consecutive clusters per warp, which then miss the same neighbour directions
+        std::vector<int> &cperm = L.h_cperm;
+        cperm.resize(pk.size());
+        std::iota(cperm.begin(), cperm.end(), 0);
+        auto cluster_class = [&](int c) {
+            int k = 0;
+            for (int a = 0; a < 3; ++a) {
+                const uint32_t v = (cxyz[c] >> (10 * a)) & 1023;
+                k |= ((v == 0 ? 1 : 0) | (v == Np - 1 ? 2 : 0)) << (2 * a);
+            }
+            return k;
+        };
+        std::stable_sort(cperm.begin(), cperm.end(), [&](int x, int y) { return cluster_class(x) < cluster_class(y); });
         // pairs: targets x sources that exist, over the 189 transfer vectors of each octant
         long long pairs = 0;
 #pragma omp parallel for reduction(+ : pairs) schedule(static)
@@ -559,7 +587,8 @@ int upload_level_tables(m2l_plan_t *pl) {
         if (L.on_device) continue;
         if ((rc = dev_upload(L.slot, L.h_slot)) || (rc = dev_upload(L.xyz, L.h_xyz)) ||
             (rc = dev_upload(L.perm, L.h_perm)) || (rc = dev_upload(L.cslot, L.h_cslot)) ||
-            (rc = dev_upload(L.cxyz, L.h_cxyz)) || (rc = dev_upload(L.cchild, L.h_cchild)))
+            (rc = dev_upload(L.cxyz, L.h_cxyz)) || (rc = dev_upload(L.cchild, L.h_cchild)) ||
+            (rc = dev_upload(L.cperm, L.h_cperm)))
             return rc;
         L.on_device = true;
     }
