@@ -373,6 +373,14 @@ static int apply_veps(const m2l_plan_t *pl, const DevOps &D, const T *Z, T *out,
     return launch_gemm_xwt<T>(Z, rp, (const T *)D.V, rp, out, n, rows, n, rp, acc, s);
 }
 
+// Rows per contraction tile: 128 for the tensor-core kernel (one MMA tile), kDirTileRows for the
+// directional CUDA-core kernel, 64 for the plain one (which also runs on shorter tiles).
+static int contract_tile_rows(const m2l_plan_t *own, int precision) {
+    if (precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3) return 128;
+    if (own->dir_tol > 0) return precision == M2L_PREC_FP64 ? kDirTileRows<double> : kDirTileRows<float>;
+    return 64;
+}
+
 template <class T>
 static int blas_group(std::vector<Run> &runs, int precision, Workspace &ws, cudaStream_t s) {
     m2l_plan_t *own = runs[0].pl;
@@ -380,7 +388,7 @@ static int blas_group(std::vector<Run> &runs, int precision, Workspace &ws, cuda
     const int n = own->n, nc = own->nc, kp = own->kp, kcp = own->kcp, rp = own->rp;
     const bool tc = precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3;
     long long ntiles = 0, total = 0;
-    M2L_TRY(ensure_exec(own, runs, tc ? 128 : 64, &ntiles, &total));
+    M2L_TRY(ensure_exec(own, runs, contract_tile_rows(own, precision), &ntiles, &total));
     const BlasLayout lay = blas_layout(own, total, precision);
     M2L_TRY(ensure_buffer(ws, lay.total()));
     char *w = (char *)ws.buf;
@@ -578,9 +586,8 @@ int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         m2l_plan_t *own = groups[gi][0].pl;
         if (forms[gi] == M2L_FORM_BLAS) {
-            const bool tc = precs[gi] == M2L_PREC_TF32X3 || precs[gi] == M2L_PREC_BF16X3;
             long long nt = 0, total = 0;
-            M2L_TRY(ensure_exec(own, groups[gi], tc ? 128 : 64, &nt, &total));
+            M2L_TRY(ensure_exec(own, groups[gi], contract_tile_rows(own, precs[gi]), &nt, &total));
             ws_need = std::max(ws_need, blas_layout(own, total, precs[gi]).total());
         } else {
             for (const Run &r : groups[gi]) {

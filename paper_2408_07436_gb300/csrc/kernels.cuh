@@ -62,8 +62,13 @@ int launch_contract_simt(const LevelView *levels, const ContractTile *tiles, lon
                          const T *qt, const T *C, int kp, int kcp, long long zero_row, T *phit, cudaStream_t s);
 
 // B2 with the directional factors (Eq. 15): Ub = Ubar_t [kc_pad][k_t8], Vt = Vbar'_t^T [k_t8][k_pad]
-// concatenated over t, meta = [316] int4 (Ub offset, Vt offset, k_t, k_t8). M2L_EUNSUPPORTED
-// (nothing launched) when its shared-memory tiles do not fit.
+// concatenated over t, meta = [316] int4 (Ub offset, Vt offset, k_t, k_t8). Its tiles hold at most
+// kDirTileRows<T> rows: 32 in FP64, where the kernel is bound by the FP64 units and finer tiles
+// shorten the tail after the last wave of CTAs; 64 in FP32, where the taller register tile's reuse
+// of each shared-memory load matters more. M2L_EUNSUPPORTED (nothing launched) when its
+// shared-memory tiles do not fit.
+template <class T>
+constexpr int kDirTileRows = sizeof(T) == 8 ? 32 : 64;
 template <class T>
 int launch_contract_simt_dir(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
                              const T *qt, const T *Ub, const T *Vt, const int *meta, int k, int kp, int kcp,

@@ -370,42 +370,51 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(const LevelView *__r
 }
 
 // B2 with the directional factors of Eq. 15. Per transfer vector t the tile's gathered sources X
-// (64 rows x k) go through the two products of Sec. 3.2 step 4: xi = X Vbar'_t (64 x k_t) and
+// (BM rows x k) go through the two products of Sec. 3.2 step 4: xi = X Vbar'_t (BM x k_t) and
 // phit += xi Ubar_t^T, so a pair costs 4 k k_t flops instead of 2 k^2. Stage 1 streams X and
 // Vbar'_t^T through shared memory in chunks of 16 along k (as the plain kernel streams C_t). The
 // k_t columns of xi (up to 64 per pass) are cut into 8 contiguous groups of floor or ceil(k_t / 8)
-// columns, one per warp, and a lane holds rows 2 l, 2 l + 1 of its warp's group: the column
+// columns, one per warp, and a lane holds BM / 32 consecutive rows of its warp's group: the column
 // count is exact (no rounding of k_t up to a multiple of 8), a warp's trip count is uniform and
-// its column loads are broadcasts. xi then waits in shared memory for stage 2, which uses the
-// 4 x TN tile of the plain kernel and Ubar_t in chunks of 16 along k_t. About 75 KB of shared
-// memory in FP64, so two CTAs share an SM and one computes while the other gathers. Stage 1 is
-// skipped when no row of the tile has a source for t, stage 2 per warp of 8 rows.
+// its column loads are broadcasts. xi then waits in shared memory for stage 2, which gives a
+// thread BM / 16 rows x TN columns and takes Ubar_t in chunks of 16 along k_t. Stage 1 is skipped
+// when no row of the tile has a source for t, stage 2 per warp of BM / 8 rows. In FP64, tiles of
+// 32 rows (1,176 on the 1M-point workload against 592 of 64) leave a shorter tail of idle SMs
+// after the last wave; two CTAs share an SM.
 // One 16-deep chunk of stage 1 with exactly NM columns per lane: guarding an unrolled loop with a
 // runtime count would leave predicated-off FMAs that still occupy the FP64 pipe.
-template <class T, int NM>
-__device__ __forceinline__ void dir_stage1_chunk(const T *Xs, const T *Vs, int c0, int lane, T (&y)[8][2]) {
-    constexpr int XP = 66, VP = 66;
-    using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+template <class T, int NM, int RPL, int XP>
+__device__ __forceinline__ void dir_stage1_chunk(const T *Xs, const T *Vs, int c0, int lane, T (&y)[8][RPL]) {
+    constexpr int VP = 66;
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-        const T2 x = *reinterpret_cast<const T2 *>(Xs + kk * XP + 2 * lane);  // rows 2 l, 2 l + 1
+        T x[RPL];
+        if constexpr (RPL == 2) {
+            using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+            const T2 x2 = *reinterpret_cast<const T2 *>(Xs + kk * XP + 2 * lane);  // rows 2 l, 2 l + 1
+            x[0] = x2.x;
+            x[1] = x2.y;
+        } else {
+            x[0] = Xs[kk * XP + lane];
+        }
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
             const T w = Vs[kk * VP + c0 + m];
-            y[m][0] = fma(x.x, w, y[m][0]);
-            y[m][1] = fma(x.y, w, y[m][1]);
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) y[m][r] = fma(x[r], w, y[m][r]);
         }
     }
 }
 
-template <class T, int TN>
+template <class T, int TN, int BM>
 __global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView *__restrict__ levels,
                                                                 const ContractTile *__restrict__ tiles,
                                                                 const int *__restrict__ tvl, const T *__restrict__ qt,
                                                                 const T *__restrict__ Ub, const T *__restrict__ Vt,
                                                                 const int4 *__restrict__ meta, int k, int kp, int kcp, int kt8max,
                                                                 long long zero_row, T *__restrict__ phit) {
-    constexpr int BM = 64, BN = 16 * TN, BK = 16, XP = BM + 2, YC = 64;
+    static_assert(BM == 32 || BM == 64, "tile heights of 32 or 64 rows");
+    constexpr int BN = 16 * TN, BK = 16, XP = BM + 2, YC = 64, RPL = BM / 32, RPT = BM / 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Ys = reinterpret_cast<T *>(smem_raw);  // [kt8max][XP]: xi transposed
     T *Xs = Ys + (size_t)kt8max * XP;         // [BK][XP]: a chunk of X transposed
@@ -432,9 +441,9 @@ __global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView 
             tgt_xyz[tid] = 0;
         }
     }
-    T a[4][TN];
+    T a[RPT][TN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RPT; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) a[i][j] = T(0);
     const int N = L.N;
@@ -456,19 +465,22 @@ __global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView 
             src_row[tid] = sr;
         }
         __syncthreads();
-        bool mine = false;
+        bool mine = false, mine1 = false;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) mine |= src_row[ty * 4 + i] != zero_row;
+        for (int i = 0; i < RPT; ++i) mine |= src_row[ty * RPT + i] != zero_row;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) mine1 |= src_row[RPL * lane + r] != zero_row;
         const bool live = __any_sync(0xffffffffu, mine);
-        const bool live1 =
-            __any_sync(0xffffffffu, src_row[2 * lane] != zero_row || src_row[2 * lane + 1] != zero_row);
+        const bool live1 = __any_sync(0xffffffffu, mine1);
         // stage 1: xi = X Vbar'_t, up to 64 columns of xi per pass
         for (int jp0 = 0; jp0 < md.z; jp0 += YC) {
             const int ncol = min(YC, md.z - jp0), q = ncol >> 3, rm = ncol & 7;
             const int nm = q + (warp < rm ? 1 : 0), c0 = warp * q + min(warp, rm);
-            T y[8][2];
+            T y[8][RPL];
 #pragma unroll
-            for (int m = 0; m < 8; ++m) y[m][0] = y[m][1] = T(0);
+            for (int m = 0; m < 8; ++m)
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) y[m][r] = T(0);
             const T *V = Vt + md.y + (size_t)jp0 * kp;
             for (int k0 = 0; k0 < k; k0 += BK) {
                 if (k0) __syncthreads();  // previous chunk consumed
@@ -484,22 +496,22 @@ __global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView 
                 if (live1) {
                     switch (nm) {
                         case 0: break;
-                        case 1: dir_stage1_chunk<T, 1>(Xs, Vs, c0, lane, y); break;
-                        case 2: dir_stage1_chunk<T, 2>(Xs, Vs, c0, lane, y); break;
-                        case 3: dir_stage1_chunk<T, 3>(Xs, Vs, c0, lane, y); break;
-                        case 4: dir_stage1_chunk<T, 4>(Xs, Vs, c0, lane, y); break;
-                        case 5: dir_stage1_chunk<T, 5>(Xs, Vs, c0, lane, y); break;
-                        case 6: dir_stage1_chunk<T, 6>(Xs, Vs, c0, lane, y); break;
-                        case 7: dir_stage1_chunk<T, 7>(Xs, Vs, c0, lane, y); break;
-                        default: dir_stage1_chunk<T, 8>(Xs, Vs, c0, lane, y); break;
+                        case 1: dir_stage1_chunk<T, 1, RPL, XP>(Xs, Vs, c0, lane, y); break;
+                        case 2: dir_stage1_chunk<T, 2, RPL, XP>(Xs, Vs, c0, lane, y); break;
+                        case 3: dir_stage1_chunk<T, 3, RPL, XP>(Xs, Vs, c0, lane, y); break;
+                        case 4: dir_stage1_chunk<T, 4, RPL, XP>(Xs, Vs, c0, lane, y); break;
+                        case 5: dir_stage1_chunk<T, 5, RPL, XP>(Xs, Vs, c0, lane, y); break;
+                        case 6: dir_stage1_chunk<T, 6, RPL, XP>(Xs, Vs, c0, lane, y); break;
+                        case 7: dir_stage1_chunk<T, 7, RPL, XP>(Xs, Vs, c0, lane, y); break;
+                        default: dir_stage1_chunk<T, 8, RPL, XP>(Xs, Vs, c0, lane, y); break;
                     }
                 }
             }
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
                 if (m < nm) {
-                    Ys[(size_t)(jp0 + c0 + m) * XP + 2 * lane] = y[m][0];
-                    Ys[(size_t)(jp0 + c0 + m) * XP + 2 * lane + 1] = y[m][1];
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r) Ys[(size_t)(jp0 + c0 + m) * XP + RPL * lane + r] = y[m][r];
                 }
             }
             __syncthreads();  // the next pass reuses Xs and Vs; stage 2 reads Ys
@@ -517,13 +529,13 @@ __global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView 
                 const int jn = min(BK, md.z - j0);
                 // a full chunk unrolled; the last, partial one with an exact trip count
                 auto step = [&](int kk) {
-                    T xa[4], wb[TN];
+                    T xa[RPT], wb[TN];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) xa[i] = Ys[(size_t)(j0 + kk) * XP + ty * 4 + i];
+                    for (int i = 0; i < RPT; ++i) xa[i] = Ys[(size_t)(j0 + kk) * XP + ty * RPT + i];
 #pragma unroll
                     for (int j = 0; j < TN; ++j) wb[j] = Us[(size_t)kk * (BN + 4) + tx * TN + j];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < RPT; ++i)
 #pragma unroll
                         for (int j = 0; j < TN; ++j) a[i][j] = fma(xa[i], wb[j], a[i][j]);
                 };
@@ -538,8 +550,8 @@ __global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView 
         }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int r = ty * 4 + i;
+    for (int i = 0; i < RPT; ++i) {
+        int r = ty * RPT + i;
         if (r >= tile.rows) continue;
         long long orow = L.row0 + (long long)tgt_b[r] * R + tgt_r[r];
 #pragma unroll
@@ -582,16 +594,16 @@ template <class T, int TN>
 static int launch_contract_dir_tn(const LevelView *levels, const ContractTile *tiles, long long ntiles, const int *tvl,
                                   const T *qt, const T *Ub, const T *Vt, const int *meta, int k, int kp, int kcp,
                                   int kt8max, long long zero_row, T *phit, cudaStream_t s) {
-    constexpr int BN = 16 * TN;
-    const size_t smem = sizeof(T) * ((size_t)kt8max * 66 + (size_t)16 * 66 + (size_t)16 * 66 + (size_t)16 * (BN + 4));
+    constexpr int BN = 16 * TN, BM = kDirTileRows<T>, XP = BM + 2;
+    const size_t smem = sizeof(T) * ((size_t)kt8max * XP + (size_t)16 * XP + (size_t)16 * 66 + (size_t)16 * (BN + 4));
     if (smem > 200 * 1024) return M2L_EUNSUPPORTED;
-    if (cudaFuncSetAttribute(contract_simt_dir_kernel<T, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
+    if (cudaFuncSetAttribute(contract_simt_dir_kernel<T, TN, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return M2L_EUNSUPPORTED;
     }
     dim3 grid((unsigned)ntiles, (unsigned)((kcp + BN - 1) / BN));
-    contract_simt_dir_kernel<T, TN><<<grid, 256, smem, s>>>(levels, tiles, tvl, qt, Ub, Vt,
+    contract_simt_dir_kernel<T, TN, BM><<<grid, 256, smem, s>>>(levels, tiles, tvl, qt, Ub, Vt,
                                                              reinterpret_cast<const int4 *>(meta), k, kp, kcp, kt8max,
                                                              zero_row, phit);
     return check_launch("contract_dir");
