@@ -406,8 +406,10 @@ __device__ __forceinline__ void dir_stage1_chunk(const T *Xs, const T *Vs, int c
     }
 }
 
+// FP32 asks for three resident CTAs per SM (80 registers, no spills): its FMAs are cheap, and
+// shared-load latency needs more warps to hide. FP64 is bound by its FP64 units at two.
 template <class T, int TN, int BM>
-__global__ void __launch_bounds__(256) contract_simt_dir_kernel(const LevelView *__restrict__ levels,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) contract_simt_dir_kernel(const LevelView *__restrict__ levels,
                                                                 const ContractTile *__restrict__ tiles,
                                                                 const int *__restrict__ tvl, const T *__restrict__ qt,
                                                                 const T *__restrict__ Ub, const T *__restrict__ Vt,
