@@ -420,3 +420,53 @@ def test_single_precision_bounds_over_orders(lib, p):
             tg, L_ref, phi_ref = refs[l]
             assert M.rel_l2_error(phi_ref, chk[l][tg]) < bound, (form, prec, p, l)
             assert M.check_norm_error(p, l, L_ref, loc[l][tg]) < bound, (form, prec, p, l)
+
+
+def test_c3_full_size_sampled(lib):
+    """The 8M-point, depth-6, p = 8 workload at full size, sampled targets checked one by one:
+    BF16x3 against the oracle's compressed form, the FP64 BLAS form with the directional factors
+    against the oracle's directional form and the dense definition, and FP64 FFT against the
+    dense definition."""
+    wl = W.c3()
+    qs = _qs(wl)
+    rng = np.random.default_rng(9)
+    samples = {l: np.sort(rng.choice(wl.n_boxes(l), size=min(wl.n_boxes(l), 24), replace=False)) for l in wl.levels}
+    dense = {l: oracle_level(wl.p, l, qs[l], targets=samples[l])[1] for l in wl.levels}
+    ops = O.compressed_operators(wl.p, wl.rank_tol, 1.0)
+    chk = run_gpu(lib, wl.depth, wl.p, qs, rank_tol=wl.rank_tol, precision="bf16x3", output="check")
+    for l in wl.levels:
+        _, ref = M.m2l_compressed(wl.p, l, qs[l], ops, targets=samples[l])
+        assert M.rel_l2_error(ref, chk[l][samples[l]]) < TC_TOL["bf16x3"], ("bf16x3", l)
+    chk = run_gpu(lib, wl.depth, wl.p, qs, rank_tol=wl.rank_tol, output="check", dir_tol=wl.dir_tol)
+    d = O.directional_operators(ops["C"], wl.dir_tol)
+    for l in wl.levels:
+        _, ref = M.m2l_compressed(wl.p, l, qs[l], {**ops, **d}, targets=samples[l])
+        assert M.rel_l2_error(ref, chk[l][samples[l]]) < 1e-10, ("fp64 directional", l)
+        # the truncation at 1e-7 and the directional cut at 1e-8 against the dense definition
+        assert M.rel_l2_error(dense[l], chk[l][samples[l]]) < 2e-8, ("fp64 directional vs dense", l)
+    chk = run_gpu(lib, wl.depth, wl.p, qs, form="fft", output="check")
+    for l in wl.levels:
+        assert M.rel_l2_error(dense[l], chk[l][samples[l]]) < FP64_TOL, ("fft fp64", l)
+
+
+def test_c4_full_size_sampled(lib):
+    """The sphere-surface workload (2M points, depth 6, p = 6, 32 right-hand sides, empty boxes
+    pruned) at full size, sampled targets checked one by one: the split tensor-core forms against
+    the oracle's compressed form and FP32 FFT against the dense definition."""
+    wl = W.c4()
+    qs = _qs(wl)
+    keys = {l: wl.keys[l] for l in wl.levels}
+    okeys = {l: None if keys[l] is None else keys[l].astype(np.int64) for l in wl.levels}
+    rng = np.random.default_rng(10)
+    samples = {l: np.sort(rng.choice(wl.n_boxes(l), size=min(wl.n_boxes(l), 16), replace=False)) for l in wl.levels}
+    ops = O.compressed_operators(wl.p, wl.rank_tol, 1.0)
+    for prec in ("bf16x3", "tf32x3"):
+        chk = run_gpu(lib, wl.depth, wl.p, qs, keys=keys, rank_tol=wl.rank_tol, precision=prec, output="check",
+                      R=wl.n_rhs)
+        for l in wl.levels:
+            _, ref = M.m2l_compressed(wl.p, l, qs[l], ops, keys=okeys[l], targets=samples[l])
+            assert M.rel_l2_error(ref, chk[l][samples[l]]) < TC_TOL[prec], (prec, l)
+    chk = run_gpu(lib, wl.depth, wl.p, qs, keys=keys, form="fft", precision="fp32", output="check", R=wl.n_rhs)
+    for l in wl.levels:
+        _, ref = oracle_level(wl.p, l, qs[l], keys=okeys[l], targets=samples[l])
+        assert M.rel_l2_error(ref, chk[l][samples[l]]) < SINGLE_BOUND[("fft", "fp32")], ("fft fp32", l)
