@@ -50,7 +50,7 @@ static bool eligible(const m2l_plan_t *pl, int form, int prec) {
     if (bound > pl->target_tol) return false;
     if (form == M2L_FORM_BLAS && (prec == M2L_PREC_TF32X3 || prec == M2L_PREC_BF16X3)) {
         // the tensor-core contraction holds k_pad <= 256 columns
-        if (((const_cast<m2l_plan_t *>(pl)->blas_host_ready ? pl->kp : 0) > 256)) return false;
+        if ((pl->blas ? pl->kp : 0) > 256) return false;
     }
     return true;
 }

@@ -143,7 +143,7 @@ int m2l_set_option(m2l_plan_t *pl, int key, long long value) {
             if (value != 0 && (value < 2 * pl->p - 1 || value > 2 * pl->p)) break;
             if ((int)value != pl->fft_grid_opt) {
                 pl->fft_grid_opt = (int)value;
-                pl->fft_host_ready = false;
+                pl->fft.reset();
                 for (auto &D : pl->dev) {
                     if (D.Khat) cudaFree(D.Khat);
                     if (D.tw) cudaFree(D.tw);
@@ -168,7 +168,9 @@ int m2l_set_option(m2l_plan_t *pl, int key, long long value) {
                             }
                 pl->nc = (int)pl->lattice_c.size() / 3;
                 // every operator that touches the check surface is rebuilt on next use
-                pl->pinv_ready = pl->blas_host_ready = pl->dir_ready = false;
+                pl->pinv.reset();
+                pl->blas.reset();
+                pl->dirop.reset();
                 pl->tuned.clear();
                 release_operators(pl);
             }
@@ -180,7 +182,7 @@ int m2l_set_option(m2l_plan_t *pl, int key, long long value) {
             if (!(d >= 0.0) || !std::isfinite(d) || d >= 1.0) break;
             if (d != pl->dir_tol) {
                 pl->dir_tol = d;
-                pl->dir_ready = false;
+                pl->dirop.reset();
                 for (auto &D : pl->dev) {
                     for (void **pp : {&D.Ub, &D.Vt, &D.dir_meta}) {
                         if (*pp) cudaFree(*pp);
@@ -402,7 +404,7 @@ int m2l_query(const m2l_plan_t *cpl, int what, int level, long long *out) {
             *out = 0;
             if (pl->dir_tol <= 0) return M2L_OK;
             if ((rc = build_directional(pl))) return rc;
-            for (int v : pl->dir_kt) *out += v;
+            for (int v : pl->dirop->kt) *out += v;
             return M2L_OK;
         }
         case M2L_Q_GRID:
@@ -481,12 +483,12 @@ int m2l_get_operator(m2l_plan_t *pl, int which, double *dst, long long *count) {
     if (rc) return rc;
     const std::vector<double> *src = nullptr;
     switch (which) {
-        case 0: src = &pl->U; break;
-        case 1: src = &pl->S; break;
-        case 2: src = &pl->C; break;
-        case 3: src = &pl->s_fat; break;
-        case 4: src = &pl->Veps; break;
-        case 5: src = &pl->Uteps; break;
+        case 0: src = &pl->blas->U; break;
+        case 1: src = &pl->blas->S; break;
+        case 2: src = &pl->blas->C; break;
+        case 3: src = &pl->blas->s_fat; break;
+        case 4: src = &pl->pinv->Veps; break;
+        case 5: src = &pl->pinv->Uteps; break;
         default:
             set_error("unknown operator %d", which);
             return M2L_EINVAL;

@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -26,6 +27,31 @@ void clear_error();
 // Index of transfer vector (x, y, z) in [-3,3]^3 \ [-1,1]^3, enumerated x slowest then y, z.
 int transfer_index(int x, int y, int z);
 void transfer_vector(int idx, int &x, int &y, int &z);
+
+// Host operators (FP64). They depend on the kernel, the orders and the thresholds, never on the
+// tree, so plans alive at the same time with the same parameters (the instances of a batch, the
+// autotuner's proxy plans) share one read-only build (see plan.cpp).
+struct PinvOps {                              // Eqs. 7-10, two-factor storage
+    int r = 0, r32 = 0;                       // kept singular values: alpha = 0 and alpha = 1e-9
+    std::vector<double> Veps, Uteps;          // [n][r], [r][nc]
+    std::vector<double> Veps32, Uteps32;      // the factors used by single-precision paths
+};
+struct BlasOps {                              // Sec. 3.1-3.2 compression
+    int k = 0, kc = 0;                        // ranks of the equivalent (S) and check (U) sides
+    std::vector<double> U, S, C, s_fat, s_thin;  // U: nc x kc, S: n x k (row-major); C: 316 x kc x k
+    std::vector<double> Aop, Aop32;           // [r][kc] = Uteps * U (and with the alpha = 1e-9 factor)
+};
+struct DirOps {                               // Eq. 15 factors, packed as on the device
+    std::vector<int> kt;                      // [316] k_t
+    std::vector<double> ub, vt;
+    std::vector<int> meta;                    // [316][4]
+    int kt8_max = 0;
+};
+struct FftOps {                               // App. A.1 kernel spectra
+    int g = 0, F = 0;
+    std::vector<double> Khat;                 // [316][F][2]
+    std::vector<double> twiddle;              // [g][2]
+};
 
 struct LevelSet {
     bool dense = true;
@@ -117,24 +143,18 @@ struct m2l_plan_s {
     std::vector<int> lattice_c;               // nc x 3: the downward check surface
     int *lattice_dev = nullptr;               // packed a << 16 | b << 8 | c
     m2l::LevelSet levels[m2l::kMaxDepth + 1];
-    // host operators (FP64)
-    bool blas_host_ready = false, fft_host_ready = false, pinv_ready = false;
+    // host operators (FP64), shared read-only with other plans of the same parameters; null until
+    // built, reset by the options that change them
+    std::shared_ptr<const m2l::PinvOps> pinv;
+    std::shared_ptr<const m2l::BlasOps> blas;
+    std::shared_ptr<const m2l::DirOps> dirop;
+    std::shared_ptr<const m2l::FftOps> fft;
     int k = 0, kp = 0, r = 0, rp = 0, np_ = 0;    // k: rank of the equivalent side (S), padded kp
     int kc = 0, kcp = 0;                          // rank of the check side (U), padded; k unless pc > p
-    std::vector<double> U, S, C, s_fat, s_thin;   // U: nc x kc, S: n x k (row-major); C: 316 x kc x k
-    std::vector<double> Veps, Uteps;              // [n][r], [r][n]   threshold n eps_64 s_0
-    std::vector<double> Aop;                      // [r][k] = Uteps * U
     int r32 = 0;                                  // singular values kept with Eq. 10's alpha = 1e-9
-    std::vector<double> Veps32, Uteps32, Aop32;   // the factors used by single-precision paths
     double dir_tol = 0.0;                         // directional recompression threshold (0: off)
-    bool dir_ready = false;
-    std::vector<int> dir_kt;                      // [316] k_t
-    std::vector<double> dir_ub, dir_vt;           // packed as on the device (FP64)
-    std::vector<int> dir_meta;                    // [316][4]
     int dir_kt8_max = 0;
     int g = 0, F = 0;
-    std::vector<double> Khat;                     // [316][F][2]
-    std::vector<double> twiddle;                  // [g][2]
     // device
     m2l::DevOps dev[4];                           // by precision (FP64, FP32, TF32X3, BF16X3 share FP32 data)
     bool levels_dirty = true;

@@ -512,7 +512,7 @@ int split_tc_operators(m2l_plan_t *pl, int precision) {
     for (int t = 0; t < kNumTransfer; ++t)
         for (int a = 0; a < k; ++a)
             for (int c = 0; c < k; ++c) {
-                const double v = pl->C[((size_t)t * k + a) * k + c];
+                const double v = pl->blas->C[((size_t)t * k + a) * k + c];
                 const size_t i = ((size_t)t * kp + a) * kp + c;
                 if (kind == 0) {
                     float h = tf32_round((float)v);

@@ -5,7 +5,10 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <tuple>
 
 #include "internal.h"
 #include "linalg.h"
@@ -126,116 +129,166 @@ void pinv_truncation(int m, int n, const std::vector<double> &U, const std::vect
     }
 }
 
+// Process-wide table of the host operators by their parameters. It holds weak references: an
+// entry lives while a plan uses it, so plans alive together share one build (64 uneven instances
+// of four orders build four operator sets, not 64) and memory goes with the last plan. Two plans
+// that miss at the same time both build; the first to publish wins.
+template <class Ops, class Key>
+class OpCache {
+  public:
+    std::shared_ptr<const Ops> find(const Key &key) {
+        std::lock_guard<std::mutex> lock(mu_);
+        auto it = map_.find(key);
+        if (it == map_.end()) return nullptr;
+        std::shared_ptr<const Ops> sp = it->second.lock();
+        if (!sp) map_.erase(it);
+        return sp;
+    }
+    std::shared_ptr<const Ops> publish(const Key &key, std::shared_ptr<const Ops> ops) {
+        std::lock_guard<std::mutex> lock(mu_);
+        std::weak_ptr<const Ops> &slot = map_[key];
+        if (std::shared_ptr<const Ops> sp = slot.lock()) return sp;
+        slot = ops;
+        return ops;
+    }
+
+  private:
+    std::mutex mu_;
+    std::map<Key, std::weak_ptr<const Ops>> map_;
+};
+
+// keys: (kernel, p, p_c[, rank_tol[, dir_tol]]) and (kernel, p, grid)
+static OpCache<PinvOps, std::tuple<int, int, int>> g_pinv_cache;
+static OpCache<BlasOps, std::tuple<int, int, int, double>> g_blas_cache;
+static OpCache<DirOps, std::tuple<int, int, int, double, double>> g_dir_cache;
+static OpCache<FftOps, std::tuple<int, int, int>> g_fft_cache;
+
+static double rank_key(double rank_tol) { return rank_tol > 0 ? rank_tol : 0.0; }
+
 int build_pinv(m2l_plan_t *pl) {
-    if (pl->pinv_ready) return M2L_OK;
-    const int n = pl->n, nc = pl->nc;
-    std::vector<double> xs, ys;
-    surface(pl, 0, 0, 0, kAlphaInner, xs, true);   // downward check (order pc)
-    surface(pl, 0, 0, 0, kAlphaOuter, ys);         // downward equivalent
-    std::vector<double> K((size_t)nc * n);         // column-major, nc x n (nc >= n)
-    for (int j = 0; j < n; ++j)
-        for (int i = 0; i < nc; ++i) K[(size_t)j * nc + i] = laplace(&xs[3 * i], &ys[3 * j]);
-    std::vector<double> U, s, V;
-    jacobi_svd(K, nc, n, U, s, V);
-    pinv_truncation(nc, n, U, s, V, 0.0, pl->r, pl->Veps, pl->Uteps);
-    pinv_truncation(nc, n, U, s, V, kPinvAlphaSingle, pl->r32, pl->Veps32, pl->Uteps32);
+    if (pl->pinv) return M2L_OK;
+    const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc);
+    std::shared_ptr<const PinvOps> ops = g_pinv_cache.find(key);
+    if (!ops) {
+        auto o = std::make_shared<PinvOps>();
+        const int n = pl->n, nc = pl->nc;
+        std::vector<double> xs, ys;
+        surface(pl, 0, 0, 0, kAlphaInner, xs, true);   // downward check (order pc)
+        surface(pl, 0, 0, 0, kAlphaOuter, ys);         // downward equivalent
+        std::vector<double> K((size_t)nc * n);         // column-major, nc x n (nc >= n)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < nc; ++i) K[(size_t)j * nc + i] = laplace(&xs[3 * i], &ys[3 * j]);
+        std::vector<double> U, sv, V;
+        jacobi_svd(K, nc, n, U, sv, V);
+        pinv_truncation(nc, n, U, sv, V, 0.0, o->r, o->Veps, o->Uteps);
+        pinv_truncation(nc, n, U, sv, V, kPinvAlphaSingle, o->r32, o->Veps32, o->Uteps32);
+        ops = g_pinv_cache.publish(key, std::move(o));
+    }
+    pl->pinv = ops;
+    pl->r = ops->r;
+    pl->r32 = ops->r32;
     pl->rp = round_up(pl->r, 16);
-    pl->pinv_ready = true;
     return M2L_OK;
 }
 
 // SVD compression of Sec. 3.1 (Eqs. 12-14). Full rank (rank_tol <= 0) uses U = S = I: the
 // compressed form is then exact for any orthonormal bases, so no SVD is needed.
 int build_blas_host(m2l_plan_t *pl) {
-    if (pl->blas_host_ready) return M2L_OK;
+    if (pl->blas) return M2L_OK;
     int rc = build_pinv(pl);
     if (rc) return rc;
-    const int n = pl->n, nc = pl->nc;
-    std::vector<std::vector<double>> Ks(kNumTransfer);
+    const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc, rank_key(pl->rank_tol));
+    std::shared_ptr<const BlasOps> ops = g_blas_cache.find(key);
+    if (!ops) {
+        auto o = std::make_shared<BlasOps>();
+        const int n = pl->n, nc = pl->nc;
+        std::vector<std::vector<double>> Ks(kNumTransfer);
 #pragma omp parallel for schedule(dynamic, 4)
-    for (int t = 0; t < kNumTransfer; ++t) m2l_matrix(pl, t, Ks[t]);
-    int k, kc;
-    if (pl->rank_tol <= 0) {
-        k = n;
-        kc = nc;
-        pl->U.assign((size_t)nc * kc, 0.0);
-        for (int i = 0; i < nc; ++i) pl->U[(size_t)i * kc + i] = 1.0;
-        pl->S.assign((size_t)n * k, 0.0);
-        for (int i = 0; i < n; ++i) pl->S[(size_t)i * k + i] = 1.0;
-        pl->s_fat.clear();
-        pl->s_thin.clear();
-    } else {
-        // K_thin = [K_1; ...; K_316] (316 nc x n): stack the column-major K_t. K_fat^T =
-        // [K_1^T; ...] (316 n x nc): a row-major K_t read as column-major is K_t^T.
-        std::vector<std::vector<double>> thin(kNumTransfer), fatT(kNumTransfer);
-        for (int t = 0; t < kNumTransfer; ++t) {
-            fatT[t] = Ks[t];
-            thin[t].resize((size_t)nc * n);
-            for (int i = 0; i < nc; ++i)
-                for (int j = 0; j < n; ++j) thin[t][(size_t)j * nc + i] = Ks[t][(size_t)i * n + j];
-        }
-        std::vector<double> Rf = stacked_r_factor(std::move(fatT), nc);
-        std::vector<double> Rt = stacked_r_factor(std::move(thin), n);
-        std::vector<double> Uf, Vf, Ut_, Vt_;
-        jacobi_svd(Rf, nc, nc, Uf, pl->s_fat, Vf);
-        jacobi_svd(Rt, n, n, Ut_, pl->s_thin, Vt_);
-        int kf = 0, kt = 0;
-        while (kf < nc && pl->s_fat[kf] / pl->s_fat[0] >= pl->rank_tol) ++kf;
-        while (kt < n && pl->s_thin[kt] / pl->s_thin[0] >= pl->rank_tol) ++kt;
-        if (nc == n) {
-            k = kc = std::max(std::max(kf, kt), 1);  // equal orders: one k (Sec. 3.1)
+        for (int t = 0; t < kNumTransfer; ++t) m2l_matrix(pl, t, Ks[t]);
+        int k, kc;
+        if (pl->rank_tol <= 0) {
+            k = n;
+            kc = nc;
+            o->U.assign((size_t)nc * kc, 0.0);
+            for (int i = 0; i < nc; ++i) o->U[(size_t)i * kc + i] = 1.0;
+            o->S.assign((size_t)n * k, 0.0);
+            for (int i = 0; i < n; ++i) o->S[(size_t)i * k + i] = 1.0;
         } else {
-            kc = std::max(kf, 1);                    // check and equivalent spaces of different sizes
-            k = std::max(kt, 1);
+            // K_thin = [K_1; ...; K_316] (316 nc x n): stack the column-major K_t. K_fat^T =
+            // [K_1^T; ...] (316 n x nc): a row-major K_t read as column-major is K_t^T.
+            std::vector<std::vector<double>> thin(kNumTransfer), fatT(kNumTransfer);
+            for (int t = 0; t < kNumTransfer; ++t) {
+                fatT[t] = Ks[t];
+                thin[t].resize((size_t)nc * n);
+                for (int i = 0; i < nc; ++i)
+                    for (int j = 0; j < n; ++j) thin[t][(size_t)j * nc + i] = Ks[t][(size_t)i * n + j];
+            }
+            std::vector<double> Rf = stacked_r_factor(std::move(fatT), nc);
+            std::vector<double> Rt = stacked_r_factor(std::move(thin), n);
+            std::vector<double> Uf, Vf, Ut_, Vt_;
+            jacobi_svd(Rf, nc, nc, Uf, o->s_fat, Vf);
+            jacobi_svd(Rt, n, n, Ut_, o->s_thin, Vt_);
+            int kf = 0, kt = 0;
+            while (kf < nc && o->s_fat[kf] / o->s_fat[0] >= pl->rank_tol) ++kf;
+            while (kt < n && o->s_thin[kt] / o->s_thin[0] >= pl->rank_tol) ++kt;
+            if (nc == n) {
+                k = kc = std::max(std::max(kf, kt), 1);  // equal orders: one k (Sec. 3.1)
+            } else {
+                kc = std::max(kf, 1);                    // check and equivalent spaces of different sizes
+                k = std::max(kt, 1);
+            }
+            // U: left singular vectors of K_fat = right singular vectors of K_fat^T (and of Rf).
+            o->U.assign((size_t)nc * kc, 0.0);
+            o->S.assign((size_t)n * k, 0.0);
+            for (int c = 0; c < kc; ++c)
+                for (int i = 0; i < nc; ++i) o->U[(size_t)i * kc + c] = Vf[(size_t)c * nc + i];
+            for (int c = 0; c < k; ++c)
+                for (int i = 0; i < n; ++i) o->S[(size_t)i * k + c] = Vt_[(size_t)c * n + i];
         }
-        // U: left singular vectors of K_fat = right singular vectors of K_fat^T (and of Rf).
-        pl->U.assign((size_t)nc * kc, 0.0);
-        pl->S.assign((size_t)n * k, 0.0);
-        for (int c = 0; c < kc; ++c)
-            for (int i = 0; i < nc; ++i) pl->U[(size_t)i * kc + c] = Vf[(size_t)c * nc + i];
-        for (int c = 0; c < k; ++c)
-            for (int i = 0; i < n; ++i) pl->S[(size_t)i * k + c] = Vt_[(size_t)c * n + i];
-    }
-    pl->k = k;
-    pl->kp = round_up(k, 16);
-    pl->kc = kc;
-    pl->kcp = round_up(kc, 16);
-    // C_t = U^T K_t S  (kc x k, row-major)
-    pl->C.assign((size_t)kNumTransfer * kc * k, 0.0);
+        o->k = k;
+        o->kc = kc;
+        // C_t = U^T K_t S  (kc x k, row-major)
+        o->C.assign((size_t)kNumTransfer * kc * k, 0.0);
 #pragma omp parallel for schedule(dynamic, 2)
-    for (int t = 0; t < kNumTransfer; ++t) {
-        std::vector<double> KS((size_t)nc * k, 0.0);
-        const double *K = Ks[t].data();
-        for (int i = 0; i < nc; ++i)
-            for (int j = 0; j < n; ++j) {
-                double kij = K[(size_t)i * n + j];
-                const double *srow = &pl->S[(size_t)j * k];
-                double *dst = &KS[(size_t)i * k];
-                for (int c = 0; c < k; ++c) dst[c] += kij * srow[c];
-            }
-        double *C = &pl->C[(size_t)t * kc * k];
-        for (int i = 0; i < nc; ++i) {
-            const double *urow = &pl->U[(size_t)i * kc];
-            const double *ks = &KS[(size_t)i * k];
-            for (int a = 0; a < kc; ++a) {
-                double u = urow[a];
-                if (u == 0.0) continue;
-                for (int c = 0; c < k; ++c) C[(size_t)a * k + c] += u * ks[c];
+        for (int t = 0; t < kNumTransfer; ++t) {
+            std::vector<double> KS((size_t)nc * k, 0.0);
+            const double *K = Ks[t].data();
+            for (int i = 0; i < nc; ++i)
+                for (int j = 0; j < n; ++j) {
+                    double kij = K[(size_t)i * n + j];
+                    const double *srow = &o->S[(size_t)j * k];
+                    double *dst = &KS[(size_t)i * k];
+                    for (int c = 0; c < k; ++c) dst[c] += kij * srow[c];
+                }
+            double *C = &o->C[(size_t)t * kc * k];
+            for (int i = 0; i < nc; ++i) {
+                const double *urow = &o->U[(size_t)i * kc];
+                const double *ks = &KS[(size_t)i * k];
+                for (int a = 0; a < kc; ++a) {
+                    double u = urow[a];
+                    if (u == 0.0) continue;
+                    for (int c = 0; c < k; ++c) C[(size_t)a * k + c] += u * ks[c];
+                }
             }
         }
+        // A = Ut_eps U  (r x kc): the scaled factor of the pseudo-inverse times the uncompression.
+        auto fold = [&](const std::vector<double> &Ut, int r, std::vector<double> &A) {
+            A.assign((size_t)r * kc, 0.0);
+            for (int a = 0; a < r; ++a)
+                for (int i = 0; i < nc; ++i) {
+                    double u = Ut[(size_t)a * nc + i];
+                    for (int c = 0; c < kc; ++c) A[(size_t)a * kc + c] += u * o->U[(size_t)i * kc + c];
+                }
+        };
+        fold(pl->pinv->Uteps, pl->pinv->r, o->Aop);
+        fold(pl->pinv->Uteps32, pl->pinv->r32, o->Aop32);
+        ops = g_blas_cache.publish(key, std::move(o));
     }
-    // A = Ut_eps U  (r x kc): the scaled factor of the pseudo-inverse times the uncompression.
-    auto fold = [&](const std::vector<double> &Ut, int r, std::vector<double> &A) {
-        A.assign((size_t)r * kc, 0.0);
-        for (int a = 0; a < r; ++a)
-            for (int i = 0; i < nc; ++i) {
-                double u = Ut[(size_t)a * nc + i];
-                for (int c = 0; c < kc; ++c) A[(size_t)a * kc + c] += u * pl->U[(size_t)i * kc + c];
-            }
-    };
-    fold(pl->Uteps, pl->r, pl->Aop);
-    fold(pl->Uteps32, pl->r32, pl->Aop32);
-    pl->blas_host_ready = true;
+    pl->blas = ops;
+    pl->k = ops->k;
+    pl->kp = round_up(ops->k, 16);
+    pl->kc = ops->kc;
+    pl->kcp = round_up(ops->kc, 16);
     return M2L_OK;
 }
 
@@ -244,59 +297,64 @@ int build_blas_host(m2l_plan_t *pl) {
 // Ubar_t as [kc_pad][k_t8] (one row per output component) and Vbar'_t^T as [k_t8][k_pad], k_t
 // rounded up to 8 with zero padding.
 int build_directional(m2l_plan_t *pl) {
-    if (pl->dir_ready) return M2L_OK;
+    if (pl->dirop) return M2L_OK;
     int rc = build_blas_host(pl);
     if (rc) return rc;
-    const int k = pl->k, kp = pl->kp, kc = pl->kc, kcp = pl->kcp;
-    std::vector<int> kt(kNumTransfer);
-    std::vector<std::vector<double>> ub(kNumTransfer), vt(kNumTransfer);
+    const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc, rank_key(pl->rank_tol), pl->dir_tol);
+    std::shared_ptr<const DirOps> ops = g_dir_cache.find(key);
+    if (!ops) {
+        auto o = std::make_shared<DirOps>();
+        const int k = pl->k, kp = pl->kp, kc = pl->kc, kcp = pl->kcp;
+        const std::vector<double> &Call = pl->blas->C;
+        std::vector<int> kt(kNumTransfer);
+        std::vector<std::vector<double>> ub(kNumTransfer), vt(kNumTransfer);
 #pragma omp parallel for schedule(dynamic, 2)
-    for (int t = 0; t < kNumTransfer; ++t) {
-        // C_t is row-major kc x k; the SVD routine takes a column-major matrix with at least as
-        // many rows as columns, so a wide C_t is factored through its transpose
-        const double *C = &pl->C[(size_t)t * kc * k];
-        const bool tall = kc >= k;
-        const int m = tall ? kc : k, nn = tall ? k : kc;
-        std::vector<double> A((size_t)m * nn), U, sv, V;
-        for (int a = 0; a < kc; ++a)
-            for (int c = 0; c < k; ++c) {
-                if (tall)
-                    A[(size_t)c * kc + a] = C[(size_t)a * k + c];
-                else
-                    A[(size_t)a * k + c] = C[(size_t)a * k + c];
+        for (int t = 0; t < kNumTransfer; ++t) {
+            // C_t is row-major kc x k; the SVD routine takes a column-major matrix with at least as
+            // many rows as columns, so a wide C_t is factored through its transpose
+            const double *C = &Call[(size_t)t * kc * k];
+            const bool tall = kc >= k;
+            const int m = tall ? kc : k, nn = tall ? k : kc;
+            std::vector<double> A((size_t)m * nn), U, sv, V;
+            for (int a = 0; a < kc; ++a)
+                for (int c = 0; c < k; ++c) {
+                    if (tall)
+                        A[(size_t)c * kc + a] = C[(size_t)a * k + c];
+                    else
+                        A[(size_t)a * k + c] = C[(size_t)a * k + c];
+                }
+            jacobi_svd(A, m, nn, U, sv, V);
+            // left (check side, kc) and right (equivalent side, k) singular vectors of C_t
+            auto left = [&](int j, int a) { return tall ? U[(size_t)j * kc + a] : V[(size_t)j * kc + a]; };
+            auto right = [&](int j, int c) { return tall ? V[(size_t)j * k + c] : U[(size_t)j * k + c]; };
+            int r = 0;
+            while (r < nn && sv[r] >= pl->dir_tol * sv[0]) ++r;
+            if (r < 1) r = 1;
+            const int r8 = round_up(r, 8);
+            kt[t] = r;
+            ub[t].assign((size_t)kcp * r8, 0.0);
+            vt[t].assign((size_t)r8 * kp, 0.0);
+            for (int j = 0; j < r; ++j) {
+                for (int a = 0; a < kc; ++a) ub[t][(size_t)a * r8 + j] = left(j, a);             // Ubar_t[a][j]
+                for (int c = 0; c < k; ++c) vt[t][(size_t)j * kp + c] = sv[j] * right(j, c);    // Vbar'_t^T[j][c]
             }
-        jacobi_svd(A, m, nn, U, sv, V);
-        // left (check side, kc) and right (equivalent side, k) singular vectors of C_t
-        auto left = [&](int j, int a) { return tall ? U[(size_t)j * kc + a] : V[(size_t)j * kc + a]; };
-        auto right = [&](int j, int c) { return tall ? V[(size_t)j * k + c] : U[(size_t)j * k + c]; };
-        int r = 0;
-        while (r < nn && sv[r] >= pl->dir_tol * sv[0]) ++r;
-        if (r < 1) r = 1;
-        const int r8 = round_up(r, 8);
-        kt[t] = r;
-        ub[t].assign((size_t)kcp * r8, 0.0);
-        vt[t].assign((size_t)r8 * kp, 0.0);
-        for (int j = 0; j < r; ++j) {
-            for (int a = 0; a < kc; ++a) ub[t][(size_t)a * r8 + j] = left(j, a);             // Ubar_t[a][j]
-            for (int c = 0; c < k; ++c) vt[t][(size_t)j * kp + c] = sv[j] * right(j, c);    // Vbar'_t^T[j][c]
         }
+        o->kt = kt;
+        o->meta.assign((size_t)kNumTransfer * 4, 0);
+        for (int t = 0; t < kNumTransfer; ++t) {
+            const int m8 = round_up(kt[t], 8);
+            o->meta[4 * t + 0] = (int)o->ub.size();
+            o->meta[4 * t + 1] = (int)o->vt.size();
+            o->meta[4 * t + 2] = kt[t];
+            o->meta[4 * t + 3] = m8;
+            o->kt8_max = std::max(o->kt8_max, m8);
+            o->ub.insert(o->ub.end(), ub[t].begin(), ub[t].end());
+            o->vt.insert(o->vt.end(), vt[t].begin(), vt[t].end());
+        }
+        ops = g_dir_cache.publish(key, std::move(o));
     }
-    pl->dir_kt = kt;
-    pl->dir_ub.clear();
-    pl->dir_vt.clear();
-    pl->dir_meta.assign((size_t)kNumTransfer * 4, 0);
-    pl->dir_kt8_max = 0;
-    for (int t = 0; t < kNumTransfer; ++t) {
-        const int m8 = round_up(kt[t], 8);
-        pl->dir_meta[4 * t + 0] = (int)pl->dir_ub.size();
-        pl->dir_meta[4 * t + 1] = (int)pl->dir_vt.size();
-        pl->dir_meta[4 * t + 2] = kt[t];
-        pl->dir_meta[4 * t + 3] = m8;
-        pl->dir_kt8_max = std::max(pl->dir_kt8_max, m8);
-        pl->dir_ub.insert(pl->dir_ub.end(), ub[t].begin(), ub[t].end());
-        pl->dir_vt.insert(pl->dir_vt.end(), vt[t].begin(), vt[t].end());
-    }
-    pl->dir_ready = true;
+    pl->dirop = ops;
+    pl->dir_kt8_max = ops->kt8_max;
     return M2L_OK;
 }
 
@@ -312,7 +370,7 @@ int contract_flops(m2l_plan_t *pl, int level, double *out) {
     if (rc) return rc;
     double w[kNumTransfer];
     for (int t = 0; t < kNumTransfer; ++t)
-        w[t] = dir ? 2.0 * pl->dir_kt[t] * (pl->kc + pl->k) : 2.0 * pl->kc * pl->k;
+        w[t] = dir ? 2.0 * pl->dirop->kt[t] * (pl->kc + pl->k) : 2.0 * pl->kc * pl->k;
     double total = 0.0;
     const int l0 = level < 0 ? 2 : level, l1 = level < 0 ? pl->depth : level;
     for (int l = l0; l <= l1; ++l) {
@@ -347,22 +405,31 @@ int contract_flops(m2l_plan_t *pl, int level, double *out) {
 // G_t(m) = K(-t + h m), h = alpha_inner / (p - 1), m in [-(p-1), p-1]^3, placed at m mod g on the
 // g^3 grid, then its 3D real DFT keeping kz in [0, g/2] (f = (kx g + ky)(g/2+1) + kz).
 int build_fft_host(m2l_plan_t *pl) {
-    if (pl->fft_host_ready) return M2L_OK;
+    if (pl->fft) return M2L_OK;
     int rc = build_pinv(pl);
     if (rc) return rc;
     int p = pl->p;
     int g = pl->fft_grid_opt ? pl->fft_grid_opt : 2 * p;
+    const auto key = std::make_tuple(pl->kernel, p, g);
+    std::shared_ptr<const FftOps> ops = g_fft_cache.find(key);
+    if (ops) {
+        pl->fft = ops;
+        pl->g = ops->g;
+        pl->F = ops->F;
+        return M2L_OK;
+    }
+    auto o = std::make_shared<FftOps>();
     int H = g / 2 + 1;
-    pl->g = g;
-    pl->F = g * g * H;
-    pl->twiddle.resize((size_t)2 * g);
+    o->g = g;
+    o->F = g * g * H;
+    o->twiddle.resize((size_t)2 * g);
     for (int m = 0; m < g; ++m) {
-        pl->twiddle[2 * m] = std::cos(2.0 * M_PI * m / g);
-        pl->twiddle[2 * m + 1] = -std::sin(2.0 * M_PI * m / g);
+        o->twiddle[2 * m] = std::cos(2.0 * M_PI * m / g);
+        o->twiddle[2 * m + 1] = -std::sin(2.0 * M_PI * m / g);
     }
     const double h = kAlphaInner / (p - 1);
-    pl->Khat.assign((size_t)kNumTransfer * pl->F * 2, 0.0);
-    const double *w = pl->twiddle.data();
+    o->Khat.assign((size_t)kNumTransfer * o->F * 2, 0.0);
+    const double *w = o->twiddle.data();
 #pragma omp parallel for schedule(dynamic, 2)
     for (int t = 0; t < kNumTransfer; ++t) {
         int tx, ty, tz;
@@ -408,7 +475,7 @@ int build_fft_host(m2l_plan_t *pl) {
                     Y2[o] = re; Y2[o + 1] = im;
                 }
         // along x
-        double *out = &pl->Khat[(size_t)t * pl->F * 2];
+        double *out = &o->Khat[(size_t)t * o->F * 2];
         for (int kx = 0; kx < g; ++kx)
             for (int ky = 0; ky < g; ++ky)
                 for (int kz = 0; kz < H; ++kz) {
@@ -424,7 +491,10 @@ int build_fft_host(m2l_plan_t *pl) {
                     out[2 * f] = re; out[2 * f + 1] = im;
                 }
     }
-    pl->fft_host_ready = true;
+    ops = g_fft_cache.publish(key, std::move(o));
+    pl->fft = ops;
+    pl->g = ops->g;
+    pl->F = ops->F;
     return M2L_OK;
 }
 
@@ -623,8 +693,9 @@ static int upload_directional(m2l_plan_t *pl, DevOps &D) {
     if (pl->dir_tol <= 0 || D.Ub) return M2L_OK;
     int rc = build_directional(pl);
     if (rc) return rc;
-    std::vector<T> ub(pl->dir_ub.begin(), pl->dir_ub.end()), vt(pl->dir_vt.begin(), pl->dir_vt.end());
-    if ((rc = upload_vec(D.Ub, ub)) || (rc = upload_vec(D.Vt, vt)) || (rc = upload_vec(D.dir_meta, pl->dir_meta))) return rc;
+    const DirOps &dop = *pl->dirop;
+    std::vector<T> ub(dop.ub.begin(), dop.ub.end()), vt(dop.vt.begin(), dop.vt.end());
+    if ((rc = upload_vec(D.Ub, ub)) || (rc = upload_vec(D.Vt, vt)) || (rc = upload_vec(D.dir_meta, dop.meta))) return rc;
     return M2L_OK;
 }
 
@@ -634,32 +705,34 @@ static int upload_typed(m2l_plan_t *pl, DevOps &D, int form) {
     const bool single = sizeof(T) == 4;
     const int n = pl->n, k = pl->k, kp = pl->kp, r = single ? pl->r32 : pl->r, rp = pl->rp;
     const int nc = pl->nc, kc = pl->kc, kcp = pl->kcp;
-    const std::vector<double> &Veps = single ? pl->Veps32 : pl->Veps;
-    const std::vector<double> &Uteps = single ? pl->Uteps32 : pl->Uteps;
-    const std::vector<double> &Aop = single ? pl->Aop32 : pl->Aop;
+    const std::vector<double> &Veps = single ? pl->pinv->Veps32 : pl->pinv->Veps;
+    const std::vector<double> &Uteps = single ? pl->pinv->Uteps32 : pl->pinv->Uteps;
     int rc = M2L_OK;
     if (form == M2L_FORM_BLAS) {
+        const BlasOps &B = *pl->blas;
+        const std::vector<double> &Aop = single ? B.Aop32 : B.Aop;
         // S^T  [kp][n]
         std::vector<double> St((size_t)k * n);
         for (int c = 0; c < k; ++c)
-            for (int i = 0; i < n; ++i) St[(size_t)c * n + i] = pl->S[(size_t)i * k + c];
+            for (int i = 0; i < n; ++i) St[(size_t)c * n + i] = B.S[(size_t)i * k + c];
         // C_t  [316][kcp][kp]
         std::vector<T> Cp((size_t)kNumTransfer * kcp * kp, T(0));
         for (int t = 0; t < kNumTransfer; ++t)
             for (int a = 0; a < kc; ++a)
                 for (int c = 0; c < k; ++c)
-                    Cp[((size_t)t * kcp + a) * kp + c] = (T)pl->C[((size_t)t * kc + a) * k + c];
+                    Cp[((size_t)t * kcp + a) * kp + c] = (T)B.C[((size_t)t * kc + a) * k + c];
         if ((rc = upload_vec(D.St, pad2<T>(St, k, n, kp, n)))) return rc;
         if ((rc = upload_vec(D.C, Cp))) return rc;
         if ((rc = upload_vec(D.A, pad2<T>(Aop, r, kc, rp, kcp)))) return rc;
-        if ((rc = upload_vec(D.Uc, pad2<T>(pl->U, nc, kc, nc, kcp)))) return rc;
+        if ((rc = upload_vec(D.Uc, pad2<T>(B.U, nc, kc, nc, kcp)))) return rc;
         if ((rc = upload_directional<T>(pl, D))) return rc;
     } else {
-        int F = pl->F;
+        const FftOps &Fo = *pl->fft;
+        int F = Fo.F;
         std::vector<T> K((size_t)(kNumTransfer + 1) * F * 2, T(0));
-        for (size_t i = 0; i < (size_t)kNumTransfer * F * 2; ++i) K[i] = (T)pl->Khat[i];
-        std::vector<T> tw(pl->twiddle.size());
-        for (size_t i = 0; i < tw.size(); ++i) tw[i] = (T)pl->twiddle[i];
+        for (size_t i = 0; i < (size_t)kNumTransfer * F * 2; ++i) K[i] = (T)Fo.Khat[i];
+        std::vector<T> tw(Fo.twiddle.size());
+        for (size_t i = 0; i < tw.size(); ++i) tw[i] = (T)Fo.twiddle[i];
         if ((rc = upload_vec(D.Khat, K))) return rc;
         if ((rc = upload_vec(D.tw, tw))) return rc;
         if ((rc = upload_vec(D.Ut, pad2<T>(Uteps, r, n, rp, n)))) return rc;

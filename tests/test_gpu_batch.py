@@ -183,3 +183,44 @@ def test_autotuner_at_1e6_stays_in_single_precision(lib, p):
                 assert M.check_norm_error(p, l, L_ref, got[tg, r:r + 1]) < 1e-6, (p, l, r)
     finally:
         plan.close()
+
+
+def test_c5_full_size_batch_sampled(lib):
+    """The 64 uneven instances (1e4..2e6 points, depth 3-6, p in {4, 6, 8, 10}, 1-8 right-hand
+    sides) in one autotuned batch at a target of 1e-6, as the bench runs them: two sampled
+    targets per level of every instance against the dense definition, within the target."""
+    import torch
+    insts = W.c5()
+    made = []
+    try:
+        for wl in insts:
+            pl = lib.Plan(wl.depth, wl.p, wl.rank_tol, form="auto", precision="auto")
+            pl.set(output="check", target_tol=1e-6)
+            for l in wl.levels:
+                if wl.keys[l] is not None:
+                    pl.set_boxes(l, wl.keys[l])
+            pl.set_stream()
+            prec = pl.query(lib.M2L_Q_PRECISION, wl.n_rhs)
+            dt = torch.float64 if prec == lib.M2L_PREC_FP64 else torch.float32
+            q = torch.from_numpy(wl.all_multipoles()).to(dt).cuda()
+            made.append((wl, pl, q, torch.empty_like(q)))
+        _batch(lib, [m[1] for m in made], [m[2] for m in made], [m[3] for m in made], [wl.n_rhs for wl in insts])
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(12)
+        for i, (wl, pl, q, out) in enumerate(made):
+            n, R = W.n_surface(wl.p), wl.n_rhs
+            off = 0
+            for l in wl.levels:
+                B = wl.n_boxes(l)
+                tg = np.sort(rng.choice(B, size=min(B, 2), replace=False))
+                idx = torch.from_numpy((off + tg[:, None] * R * n + np.arange(R * n)[None, :]).reshape(-1)).cuda()
+                got = out[idx].double().cpu().numpy().reshape(len(tg), R, n)
+                # the oracle takes the densities the kernels saw (rounded to the plan's precision)
+                ql = q[off:off + B * R * n].cpu().double().numpy().reshape(B, R, n)
+                off += B * R * n
+                keys = None if wl.keys[l] is None else wl.keys[l].astype(np.int64)
+                _, ref = oracle_level(wl.p, l, ql, keys=keys, targets=tg)
+                assert M.rel_l2_error(ref, got) < 1e-6, (i, wl.p, wl.depth, R, l)
+    finally:
+        for m in made:
+            m[1].close()
