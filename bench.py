@@ -525,11 +525,35 @@ def cpu_baseline(insts, q64, plans, bufs, dtypes, seconds, run_variant):
                 errs[v]["check_potential_rel_err_per_level"].append(M.rel_l2_error(np.concatenate(res[l][1]), c[tg]))
                 errs[v]["locals_rel_err_per_level"].append(
                     M.check_norm_error(wl.p, l, np.concatenate(res[l][2]), lo[tg], root_width=wl_root_width(wl)))
-    return {"value": inter / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": inter / el, "unit": UNIT, "cores": cores, "cpu": host_cpu(), "kind": "oracle",
             "sample": f"{batches} batches of up to 16 random target boxes per level of the "
                       f"{len(order)} largest instance(s), dense FP64 definition (per-pair kernel evaluation "
                       f"+ pseudo-inverse), {el:.1f} s",
             "rel_err_vs_oracle": errs}
+
+
+def host_cpu():
+    """Architecture and CPU model of this host, for the CPU legs' records."""
+    import platform
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return f"{platform.machine()} {model}".strip()
 
 
 def wl_root_width(wl):
@@ -555,7 +579,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "levels": wl.levels},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu": host_cpu(), "kind": "oracle",
                              "sample": f"per step about {per_step:.0f} s of random target boxes (16 per level "
                                        f"per batch) of the same workload, dense FP64 definition"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
