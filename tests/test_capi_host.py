@@ -261,3 +261,34 @@ def test_plans_alive_together_share_host_operators(lib):
         for h in (a, b, c):
             if h is not None:
                 lib.m2l_destroy(h)
+
+
+def test_plans_built_from_several_threads_get_one_operator_set(lib):
+    """Plans of the same parameters built concurrently (the C ABI is called without the GIL):
+    whichever build publishes first, every plan ends up with the same operators."""
+    import threading
+    handles, ranks, errors = [None] * 6, [None] * 6, []
+
+    def work(i):
+        try:
+            h = lib.m2l_plan(3, 5, 0, 1e-8)
+            handles[i] = h
+            ranks[i] = lib.m2l_query(h, lib.M2L_Q_RANK)
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(6)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    try:
+        assert not errors, errors
+        assert len(set(ranks)) == 1
+        C0 = lib.m2l_get_operator(handles[0], 2)
+        for h in handles[1:]:
+            assert np.array_equal(lib.m2l_get_operator(h, 2), C0)
+    finally:
+        for h in handles:
+            if h is not None:
+                lib.m2l_destroy(h)
