@@ -29,38 +29,43 @@ void clear_error() { g_err.clear(); }
 const char *last_error() { return g_err.c_str(); }
 
 // ---------------------------------------------------------------------------------------------
-// Transfer vectors: [-3,3]^3 minus [-1,1]^3, x slowest (Sec. 3.1).
-static int g_tidx[7][7][7];
-static int g_tvec[kNumTransfer][3];
-static bool g_tready = false;
-
-static void init_transfer() {
-    if (g_tready) return;
-    int k = 0;
-    for (int x = -3; x <= 3; ++x)
-        for (int y = -3; y <= 3; ++y)
-            for (int z = -3; z <= 3; ++z) {
-                int m = std::max(std::abs(x), std::max(std::abs(y), std::abs(z)));
-                if (m >= 2) {
-                    g_tidx[x + 3][y + 3][z + 3] = k;
-                    g_tvec[k][0] = x; g_tvec[k][1] = y; g_tvec[k][2] = z;
-                    ++k;
-                } else {
-                    g_tidx[x + 3][y + 3][z + 3] = -1;
+// Transfer vectors: [-3,3]^3 minus [-1,1]^3, x slowest (Sec. 3.1). Built once, on first use from
+// any thread (a function-local static is initialised exactly once, with the other threads
+// waiting for it).
+namespace {
+struct TransferTables {
+    int idx[7][7][7];
+    int vec[kNumTransfer][3];
+    TransferTables() {
+        int k = 0;
+        for (int x = -3; x <= 3; ++x)
+            for (int y = -3; y <= 3; ++y)
+                for (int z = -3; z <= 3; ++z) {
+                    int m = std::max(std::abs(x), std::max(std::abs(y), std::abs(z)));
+                    if (m >= 2) {
+                        idx[x + 3][y + 3][z + 3] = k;
+                        vec[k][0] = x; vec[k][1] = y; vec[k][2] = z;
+                        ++k;
+                    } else {
+                        idx[x + 3][y + 3][z + 3] = -1;
+                    }
                 }
-            }
-    g_tready = true;
+    }
+};
+const TransferTables &transfer_tables() {
+    static const TransferTables t;
+    return t;
 }
+}  // namespace
 
 int transfer_index(int x, int y, int z) {
-    init_transfer();
     if (x < -3 || x > 3 || y < -3 || y > 3 || z < -3 || z > 3) return -1;
-    return g_tidx[x + 3][y + 3][z + 3];
+    return transfer_tables().idx[x + 3][y + 3][z + 3];
 }
 
 void transfer_vector(int idx, int &x, int &y, int &z) {
-    init_transfer();
-    x = g_tvec[idx][0]; y = g_tvec[idx][1]; z = g_tvec[idx][2];
+    const TransferTables &t = transfer_tables();
+    x = t.vec[idx][0]; y = t.vec[idx][1]; z = t.vec[idx][2];
 }
 
 // ---------------------------------------------------------------------------------------------
