@@ -229,14 +229,15 @@ def test_plans_alive_together_share_host_operators(lib):
     equal. An option that changes one plan's operators leaves the other plan's untouched, and
     another threshold builds its own."""
     import time
-    a = lib.m2l_plan(3, 6, 0, 1e-7)
+    # a parameter set no other test uses, so the first build is a real one
+    a = lib.m2l_plan(3, 7, 0, 3e-7)
     b = c = None
     try:
         t0 = time.perf_counter()
         ka = lib.m2l_query(a, lib.M2L_Q_RANK)
         ta = time.perf_counter() - t0
         Ca = lib.m2l_get_operator(a, 2).copy()
-        b = lib.m2l_plan(4, 6, 0, 1e-7)  # another depth: the operators do not depend on the tree
+        b = lib.m2l_plan(4, 7, 0, 3e-7)  # another depth: the operators do not depend on the tree
         t0 = time.perf_counter()
         kb = lib.m2l_query(b, lib.M2L_Q_RANK)
         tb = time.perf_counter() - t0
@@ -245,15 +246,15 @@ def test_plans_alive_together_share_host_operators(lib):
         assert np.array_equal(lib.m2l_get_operator(b, 4), lib.m2l_get_operator(a, 4))
         assert tb < 0.2 * ta, (ta, tb)
         # a check order above p rebuilds a's operators and leaves b's alone
-        lib.m2l_set_option(a, lib.M2L_OPT_CHECK_ORDER, 7)
-        assert lib.m2l_query(a, lib.M2L_Q_NC) == G.n_surface(7)
-        assert lib.m2l_query(b, lib.M2L_Q_NC) == G.n_surface(6)
+        lib.m2l_set_option(a, lib.M2L_OPT_CHECK_ORDER, 8)
+        assert lib.m2l_query(a, lib.M2L_Q_NC) == G.n_surface(8)
+        assert lib.m2l_query(b, lib.M2L_Q_NC) == G.n_surface(7)
         assert lib.m2l_get_operator(a, 2).size != Ca.size or not np.array_equal(lib.m2l_get_operator(a, 2), Ca)
         assert np.array_equal(lib.m2l_get_operator(b, 2), Ca)
         # directional factors are keyed by their threshold as well
         lib.m2l_set_option(b, lib.M2L_OPT_DIR_TOL, 1e-8)
         s8 = lib.m2l_query(b, lib.M2L_Q_DIR_RANK_SUM)
-        c = lib.m2l_plan(3, 6, 0, 1e-7)
+        c = lib.m2l_plan(3, 7, 0, 3e-7)
         lib.m2l_set_option(c, lib.M2L_OPT_DIR_TOL, 1e-6)
         assert 0 < lib.m2l_query(c, lib.M2L_Q_DIR_RANK_SUM) < s8
         assert lib.m2l_query(c, lib.M2L_Q_RANK) == ka
