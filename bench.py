@@ -316,7 +316,7 @@ def run_ours(args, rank, world, local_rank):
                 a[0] += ms
                 a[1] += nl
             probe_work = algorithmic_work(probe, fname, pname, wl.n_rhs)
-            stage_acc[v]["_work"] = probe_work
+            stage_acc[v]["_algorithmic"] = probe_work
             stage_acc[v]["_prec"] = pname
             probe.close()
         steps_for_stages = 1
@@ -339,7 +339,7 @@ def run_ours(args, rank, world, local_rank):
     for v in variants:
         # algorithmic work per stage, summed over instances (each resolved to its own precision);
         # for a batch, the stage times and work are those of its largest instance
-        probe_work = stage_acc[v].pop("_work", None)
+        probe_work = stage_acc[v].pop("_algorithmic", None)
         probe_prec = stage_acc[v].pop("_prec", None)
         work, prec_of = {}, None
         for i, (pl, wl) in enumerate(zip(plans[v], insts)):
