@@ -90,30 +90,6 @@ def test_truncated_blas_matches_compressed_oracle(lib):
         assert M.rel_l2_error(phi_d, chk[l]) < 1e-6      # the truncation itself
 
 
-@pytest.mark.parametrize("precision,bound", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
-def test_truncated_blas_with_the_plans_own_operators(lib, precision, bound):
-    """The truncated BLAS form with the oracle applying the plan's exported U, S and C_t (data,
-    not code): the rank truncation cancels, and what is left is the GPU's arithmetic, held to the
-    bound of its precision."""
-    p, tol, depth = 6, 1e-7, 3
-    wl = W.small(depth=depth, p=p, density="u11", rank_tol=tol)
-    qs = _qs(wl)
-    chk = run_gpu(lib, depth, p, qs, rank_tol=tol, precision=precision, output="check")
-    h = lib.m2l_plan(depth, p, 0, tol)
-    try:
-        n = lib.m2l_query(h, lib.M2L_Q_N)
-        k = lib.m2l_query(h, lib.M2L_Q_RANK)
-        kc = lib.m2l_query(h, lib.M2L_Q_RANK_CHECK)
-        ops = {"U": lib.m2l_get_operator(h, 0).reshape(n, kc), "S": lib.m2l_get_operator(h, 1).reshape(n, k),
-               "C": lib.m2l_get_operator(h, 2).reshape(316, kc, k), "k": k, "kc": kc,
-               "tvecs": G.transfer_vectors()}
-    finally:
-        lib.m2l_destroy(h)
-    for l in wl.levels:
-        _, phi = M.m2l_compressed(p, l, qs[l], ops)
-        assert M.rel_l2_error(phi, chk[l]) < bound, (precision, l)
-
-
 @pytest.mark.parametrize("form", ["blas", "fft"])
 @pytest.mark.parametrize("R", [1, 3])
 def test_sparse_boxes_and_multiple_rhs(lib, form, R):
