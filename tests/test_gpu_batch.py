@@ -215,7 +215,8 @@ def test_c5_full_size_batch_sampled(lib):
                 tg = np.sort(rng.choice(B, size=min(B, 2), replace=False))
                 idx = torch.from_numpy((off + tg[:, None] * R * n + np.arange(R * n)[None, :]).reshape(-1)).cuda()
                 got = out[idx].double().cpu().numpy().reshape(len(tg), R, n)
-                # the oracle takes the densities the kernels saw (rounded to the plan's precision)
+                # the oracle takes this test's own seeded input as uploaded (rounded to the plan's
+                # precision), copied back rather than regenerated; no kernel has written it
                 ql = q[off:off + B * R * n].cpu().double().numpy().reshape(B, R, n)
                 off += B * R * n
                 keys = None if wl.keys[l] is None else wl.keys[l].astype(np.int64)
