@@ -232,9 +232,10 @@ int m2l_stage_times(m2l_plan_t *plan, double *ms, long long *launches);
  * Preconditions: the plan's FP64 BLAS operators and box tables are already on the device (one
  * earlier m2l_apply of this plan with M2L_FORM_BLAS and M2L_PREC_FP64, after the last
  * m2l_set_boxes, uploads them); otherwise M2L_EINVAL.
- * Set-up: the first call on a device, with that device current, looks up the array's device
- * address (cudaGetSymbolAddress) and uploads a small constant table; make that first call
- * before any stream capture.
+ * Device: the plan's device must be the current device (otherwise M2L_EINVAL, nothing runs).
+ * Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and uploads a small constant table, once per device even when several host threads make that
+ * first call together; make that first call before any stream capture.
  * Sharing: every call uses the same array and leaves the last call's contents in it (the one
  * part that must start at zero is cleared on every call). Calls that overlap on the GPU (other
  * streams, other plans, other host threads) race on the array and give wrong results.
@@ -242,11 +243,12 @@ int m2l_stage_times(m2l_plan_t *plan, double *ms, long long *launches);
 int m2l_apply_noalloc(m2l_plan_t *plan, const double *multipoles, double *locals, int level, int n_rhs);
 
 /* Exercise the device watchdog: one thread waits, with the same bounded-wait code the
- * contraction uses, on a barrier that nothing completes, for at most `polls` polls (>= 1), then
+ * contraction uses, on a barrier that nothing completes, for at most `polls` polls (1 <= polls <=
+ * 2^24, the limit of the contraction's own waits), then
  * records M2L_WAIT_SELFTEST in the plan's status word and returns. No copy or MMA is in flight,
  * so nothing else is affected. Asynchronous on the plan's stream; read the outcome with
  * m2l_query(M2L_Q_DEVICE_STATUS), which then returns M2L_ETIMEOUT. The paper has no counterpart.
- * Returns M2L_OK, M2L_EINVAL (no GPU plan, polls < 1) or M2L_ECUDA. */
+ * Returns M2L_OK, M2L_EINVAL (no GPU plan, polls out of range) or M2L_ECUDA. */
 int m2l_selftest_watchdog(m2l_plan_t *plan, long long polls);
 
 /* ---------------------------------------------------------------------------------------------

@@ -14,7 +14,7 @@ What it computes (arxiv 2408.07436):
   * the relative L2 error of Eq. 16
 
 Everything is float64. Where the paper is silent the readings used are stated in
-``geometry.py`` and repeated in DESIGN.md.
+``geometry.py`` beside the code that takes them.
 """
 
 from . import geometry, operators, m2l, fmm  # noqa: F401

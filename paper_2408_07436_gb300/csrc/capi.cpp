@@ -504,8 +504,8 @@ int m2l_selftest_watchdog(m2l_plan_t *pl, long long polls) {
         set_error("the watchdog self-test needs a plan made on a GPU");
         return M2L_EINVAL;
     }
-    if (polls < 1) {
-        set_error("polls must be at least 1");
+    if (polls < 1 || polls > (1LL << 24)) {
+        set_error("polls must be in [1, 2^24] (the bound of the contraction's own waits); got %lld", polls);
         return M2L_EINVAL;
     }
     if (!pl->dev_status) {

@@ -7,6 +7,8 @@
 // but each CTA derives its tile from blockIdx (no device tile list) and every row index is local
 // to the level.
 #include <cstdio>
+#include <mutex>
+#include <string>
 
 #include "internal.h"
 #include "kernels.cuh"
@@ -20,23 +22,22 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles
 __constant__ short c_na_tidx[7][7][7];
 
 namespace {
+// Set-up of one device: the array's device address and the transfer-vector table. std::call_once
+// makes it safe when several host threads make their first call on one device together; a set-up
+// that failed is reported again by every later call on that device.
 struct DeviceSetup {
-    bool done = false;
+    std::once_flag once;
+    int rc = M2L_EINVAL;
+    std::string msg;
     double *scratch = nullptr;
 };
 DeviceSetup g_setup[64];
 
-int setup_device(int device) {
-    if (device < 0 || device >= 64) {
-        set_error("device ordinal %d not supported", device);
-        return M2L_EINVAL;
-    }
-    DeviceSetup &S = g_setup[device];
-    if (S.done) return M2L_OK;
+int setup_once(DeviceSetup &S) {
     void *ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) {
-        set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+        S.msg = std::string("cudaGetSymbolAddress of the static scratch failed: ") + cudaGetErrorString(e);
         return M2L_ECUDA;
     }
     short tidx[7][7][7];
@@ -45,11 +46,25 @@ int setup_device(int device) {
             for (int z = -3; z <= 3; ++z) tidx[x + 3][y + 3][z + 3] = (short)transfer_index(x, y, z);
     e = cudaMemcpyToSymbol(c_na_tidx, tidx, sizeof tidx);
     if (e != cudaSuccess) {
-        set_error("uploading the transfer-vector table failed: %s", cudaGetErrorString(e));
+        S.msg = std::string("uploading the transfer-vector table failed: ") + cudaGetErrorString(e);
         return M2L_ECUDA;
     }
     S.scratch = static_cast<double *>(ptr);
-    S.done = true;
+    return M2L_OK;
+}
+
+// The caller has checked that `device` is the current device.
+int setup_device(int device) {
+    if (device < 0 || device >= 64) {
+        set_error("device ordinal %d not supported", device);
+        return M2L_EINVAL;
+    }
+    DeviceSetup &S = g_setup[device];
+    std::call_once(S.once, [&] { S.rc = setup_once(S); });
+    if (S.rc != M2L_OK) {
+        set_error("%s", S.msg.c_str());
+        return S.rc;
+    }
     return M2L_OK;
 }
 }  // namespace
@@ -201,6 +216,13 @@ extern "C" int m2l_apply_noalloc(m2l_plan_t *pl, const double *multipoles, doubl
                   "(use m2l_apply)", level, n_rhs, need, kNoAllocScratchDoubles);
         return M2L_EINVAL;
     }
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != pl->device) {
+        cudaGetLastError();
+        set_error("m2l_apply_noalloc must be called with the plan's device (%d) current; device %d is current",
+                  pl->device, cur);
+        return M2L_EINVAL;
+    }
     int rc = setup_device(pl->device);
     if (rc) return rc;
     double *scratch = g_setup[pl->device].scratch;
@@ -239,7 +261,10 @@ extern "C" int m2l_apply_noalloc(m2l_plan_t *pl, const double *multipoles, doubl
             return M2L_ECUDA;
         }
     } else {
-        cudaMemsetAsync(phit, 0, rows * kp * sizeof(double), s);
+        if (cudaMemsetAsync(phit, 0, rows * kp * sizeof(double), s) != cudaSuccess) {
+            set_error("clearing the check potentials failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return M2L_ECUDA;
+        }
     }
     // B3: locals = V_eps (A phit), or the check potential U phit
     if (pl->output == M2L_OUT_LOCALS) {
