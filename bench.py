@@ -1,26 +1,33 @@
 #!/usr/bin/env python
 """M2L interactions/s on GB300 for the 3D Laplace kiFMM (arxiv 2408.07436).
 
-One step = one pass of the whole M2L hot path over the 1M-point workload (uniform cube,
-depth 5, p = 6, 1 RHS; levels 2..5, 6,039,504 target/source pairs) in every precision the
-library offers for it: BLAS-M2L (SVD truncated at 1e-7) in FP64, FP32 and the split tensor-core
-forms TF32x3 and BF16x3, and FFT-M2L in FP64 and FP32. Each variant is one m2l_apply over all
-levels (one launch per stage covers every level) through the C ABI.
+Default workload: 8M points uniform in the unit cube, depth 6 (262,144 leaves), p = 8 (296 surface
+points), 1 RHS: M2L at levels 2..6, 52,337,880 target/source pairs per pass.
 
-  value      whole-job M2L interactions/s (pairs x RHS x variants per step / device time per
-             step), inputs resident in HBM, L2 flushed between timed steps, CUDA events on the
-             launching stream, max over ranks.
-  e2e        the same through m2l_apply with pinned HOST buffers (H2D and D2H inside the call).
-  roofline   the dominant kernel (longest stage) with its algorithmic work per launch divided
-             by its live event-timed launch duration.
-  variants   interactions/s, ms and stage times of each variant; the relative error of each
-             variant against the FP64 oracle (Eq. 16) is measured in the CPU-baseline leg.
-  cpu_baseline  the FP64 oracle (dense definition of Eq. 11 + pseudo-inverse) on a bounded sample
-             of target boxes, on this host's cores.
+One step = one m2l_apply over all levels (every stage of the chosen form) through the C ABI, in
+the form and precision the library's autotuner picks among the reduced-precision forms whose
+stated relative error bound (p-dependent, Eq. 16 on the check potential) and rank truncation
+are within the target (default 1e-6). Nothing else runs in the timed region.
 
---impl reference times the oracle itself (the CPU program the ratio is taken against).
-Multi-GPU (torchrun): every rank runs its own independent instance (weak scaling, no
-collective on the data path).
+  value          interactions/s of that one form: pairs x RHS / device time per step (CUDA events
+                 on the launching stream), inputs resident in HBM, L2 flushed between steps.
+  fp64_same_target  the FP64 form the autotuner picks at the same target, timed the same way;
+                 mixed_vs_fp64 = value / its rate.
+  variants       every explicit (form, precision) of the workload, timed alone (not in `value`).
+  batched        (default workload) the 64 uneven instances in one graph-replayed, autotuned
+                 m2l_apply_batch at the same target.
+  e2e            the headline form through m2l_apply with pinned HOST buffers (H2D and D2H
+                 inside the call).
+  roofline       the dominant kernel of the headline form: algorithmic work per launch divided
+                 by its event-timed launch duration, against the measured peak of its pipe
+                 (CUDA-core peaks from the FMA probe run at the start of this bench).
+  cpu_baseline   the FP64 oracle (dense Eq. 11 + pseudo-inverse) on a bounded sample of target
+                 boxes on this host's cores; the same leg measures the relative error of every
+                 timed form against it (per level, check potentials and locals).
+
+--impl reference times the oracle itself (the CPU program the driver's ratio is taken against).
+Multi-GPU (torchrun): every rank runs its own independent instance (weak scaling, no collective on
+the data path).
 """
 
 from __future__ import annotations
@@ -42,27 +49,15 @@ sys.path.insert(0, ROOT)
 
 from paper_2408_07436_gb300 import workloads as W  # noqa: E402
 
-VARIANTS = ["blas-fp64", "blas-fp32", "blas-tf32x3", "blas-bf16x3", "fft-fp64", "fft-fp32"]
 METRIC = "M2L interactions/s and % roofline: mixed+batched vs FP64 GPU at stated rel err"
 UNIT = "interactions/s"
-WORKLOAD = ("laplace3d-m2l uniform-cube 1M points depth5 p6 1rhs blas(rank_tol 1e-7, directional 1e-8)+fft(grid 11^3) "
-            "fp64+fp32+tf32x3+bf16x3")
+DEFAULT_TARGET = 1e-6
 
-# Nominal per-GPU figures (GB300) used where no measured peak exists.
-NOMINAL_FP64_TFLOPS = 1.25       # FP64 (vector and tensor) dense
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
-
-
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a workload's dominant
-# kernel from one ncu capture, with the SHA-256 of the source file the kernel was built from; the
-# summary and command are in profiles/. A source that has changed since reports null.
-TRAFFIC = {
-    ("c2", 5, "blas-fp64:contract"): {"bytes": 139138560 + 33806592,
-                                        "source": "paper_2408_07436_gb300/csrc/kernels_simt.cu",
-                                        "sha256": "50642335be9d49633f0d86f1977242f8d8c5ed997eb7bda25b42405aba4c86d0"},
-}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a dominant kernel from
+# one ncu capture, keyed by (workload, depth, kernel), with the SHA-256 of the source file the
+# kernel was built from; the summary and the command are in profiles/. A source that has changed
+# since the capture reports null.
+TRAFFIC = {}
 
 
 def measured_traffic(workload, depth, kernel):
@@ -78,16 +73,22 @@ def measured_traffic(workload, depth, kernel):
     return t["bytes"]
 
 
-def fp32_alu_peak_tflops(mhz=SM_MAX_MHZ):
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-
-
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)
     except Exception:
         return {}
+
+
+def alu_peaks():
+    """FP64 and FP32 FMA throughput of this GPU (TFLOP/s), measured now by the FMA probe."""
+    from paper_2408_07436_gb300 import peaks
+    out = {}
+    for name, fp64, iters in (("fp64", True, 24_000), ("fp32", False, 1_200_000)):
+        best, med, ms = peaks.m2l_fma_peak(fp64, iters, reps=5)
+        out[name] = {"best_tflops": best, "median_tflops": med, "launch_ms": ms}
+    return out
 
 
 # ---------------------------------------------------------------------------------------------
@@ -139,14 +140,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def log(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 # ---------------------------------------------------------------------------------------------
-def variant_parts(v):
-    form, prec = v.split("-")
-    return form, prec
+def form_name(lib, f):
+    return {lib.M2L_FORM_BLAS: "blas", lib.M2L_FORM_FFT: "fft"}[f]
 
 
-def algorithmic_work(plan, form, prec, R):
-    """Per-stage algorithmic flops of one application (for the roofline of that stage)."""
+def prec_name(lib, pr):
+    return {lib.M2L_PREC_FP64: "fp64", lib.M2L_PREC_FP32: "fp32", lib.M2L_PREC_TF32X3: "tf32x3",
+            lib.M2L_PREC_BF16X3: "bf16x3"}[pr]
+
+
+def resolved(lib, pl, R):
+    """(form, precision) names the plan's next apply with R right-hand sides runs."""
+    return form_name(lib, pl.query(lib.M2L_Q_FORM, R)), prec_name(lib, pl.query(lib.M2L_Q_PRECISION, R))
+
+
+def algorithmic_work(plan, form, R):
+    """Per-stage algorithmic flops of one application (for the roofline of that stage). `plan` has
+    an explicit form and precision."""
     from paper_2408_07436_gb300 import m2l as lib
     n = plan.n
     pairs = plan.pairs(-1)
@@ -167,25 +182,122 @@ def algorithmic_work(plan, form, prec, R):
             "pinv": 2.0 * 2 * n * r * rows}
 
 
+DESC = {
+    "c2": "laplace3d-m2l uniform-cube 1M points depth5 p6 1rhs (blas rank_tol 1e-7; fft grid 11^3)",
+    "c3": "laplace3d-m2l uniform-cube 8M points depth6 p8 1rhs (blas rank_tol 1e-7; fft grid 16^3)",
+    "c4": "laplace3d-m2l unit-sphere-surface 2M points depth6 p6 32rhs, empty boxes pruned (blas rank_tol 1e-7)",
+    "c5": "laplace3d-m2l 64 uneven instances (1e4..2e6 points, depth 3-6, p 4/6/8/10, 1-8 rhs), one batched "
+          "graph-replayed pass",
+}
+
+
 def workload_spec(name, depth):
-    """(instances, variants, batched, target_tol, description) of a named workload."""
+    """(instances, explicit variants timed beside the headline, batched) of a named workload."""
     if name == "c2":
-        return [W.c2(depth=depth)], VARIANTS, False, None, WORKLOAD
+        return [W.c2(depth=depth)], ["blas-fp64", "blas-fp32", "blas-tf32x3", "blas-bf16x3", "fft-fp64",
+                                     "fft-fp32"], False
     if name == "c3":
-        return ([W.c3()], ["blas-bf16x3", "blas-tf32x3", "blas-fp64", "fft-fp32", "fft-fp64"], False, None,
-                "laplace3d-m2l uniform-cube 8M points depth6 p8 1rhs blas(rank_tol 1e-7, directional 1e-8) bf16x3/tf32x3/fp64 + fft fp32/fp64")
+        return [W.c3()], ["blas-bf16x3", "blas-tf32x3", "blas-fp32", "blas-fp64", "fft-fp32", "fft-fp64"], False
     if name == "c4":
-        return ([W.c4()], ["blas-bf16x3", "blas-tf32x3", "fft-fp32"], False, None,
-                "laplace3d-m2l unit-sphere-surface 2M points depth6 p6 32rhs pruned boxes blas(rank_tol 1e-7) bf16x3/tf32x3 + fft fp32")
+        return [W.c4()], ["blas-bf16x3", "blas-tf32x3", "fft-fp32"], False
     if name == "c5":
-        return (W.c5(), ["auto-auto"], True, 1e-6,
-                "laplace3d-m2l 64 uneven instances (1e4..2e6 points, depth 3-6, p 4/6/8/10, 1-8 rhs) one batched "
-                "graph-replayed pass, autotuned form/precision at 1e-6")
+        return W.c5(), [], True
     raise ValueError(name)
 
 
-def log(msg):
-    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+def make_plan(lib, wl, form, prec, target=None, timing=True):
+    """A plan of one instance with the workload's options, on the current torch stream."""
+    tol = wl.rank_tol if form in ("blas", "auto") else 0.0
+    pl = lib.Plan(wl.depth, wl.p, tol, form=form, precision=prec).set(timing=int(timing))
+    if form in ("fft", "auto") and wl.fft_grid:
+        pl.set(fft_grid=wl.fft_grid)
+    if form in ("blas", "auto") and prec in ("fp64", "fp32", "auto") and wl.dir_tol:
+        pl.set(dir_tol=wl.dir_tol)  # the CUDA-core contraction applies Eq. 15's factors
+    if target is not None:
+        pl.set(target_tol=target)
+    for l in wl.levels:
+        if wl.keys[l] is not None:
+            pl.set_boxes(l, wl.keys[l])
+    pl.set_stream()
+    return pl
+
+
+class Timed:
+    """Device time per step of `run` (CUDA events on the current stream, L2 flushed before each
+    step outside the timed interval), with the stage times and launches of the plans it reports."""
+
+    def __init__(self, torch, flush):
+        self.torch, self.flush = torch, flush
+
+    def __call__(self, run, steps, warmup, plans=(), sampler=None, barrier=None):
+        torch = self.torch
+        for _ in range(warmup):
+            run()
+        torch.cuda.synchronize()
+        if barrier:
+            barrier()
+        if sampler:
+            sampler.start()
+        stream = torch.cuda.current_stream()
+        ms, stages, launches = [], {}, 0
+        for _ in range(steps):
+            self.flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+            for pl in plans:
+                st = pl.stage_times()
+                for name, (sms, nl) in st.items():
+                    acc = stages.setdefault(name, [0.0, 0])
+                    acc[0] += sms
+                    acc[1] += nl
+                launches += pl.query(pl_launches_key())
+        clocks = sampler.stop() if sampler else None
+        if barrier:
+            barrier()
+        return ms, stages, launches, clocks
+
+
+def pl_launches_key():
+    from paper_2408_07436_gb300 import m2l as lib
+    return lib.M2L_Q_LAUNCHES
+
+
+def roofline_of(lib, wl, form, prec, stages, steps, peaks, alu, args):
+    """Roofline of the dominant stage (longest device time) of one explicit (form, precision)."""
+    if not stages:
+        return None
+    acct = make_plan(lib, wl, form, prec, timing=False)   # host-side queries only (operators shared)
+    work = algorithmic_work(acct, form, wl.n_rhs)
+    acct.close()
+    name = max(stages, key=lambda n: stages[n][0])
+    ms_tot, nl = stages[name]
+    per_launch_ms = ms_tot / nl
+    ach = work.get(name, 0.0) * steps / nl / (per_launch_ms / 1e3) / 1e12
+    bf = peaks.get("bf16_tflops_sustained")
+    if prec in ("fp64", "fp32"):
+        pk = alu[prec]["best_tflops"]
+        bound, src = "alu", f"measured: {prec.upper()} FMA probe of this run (best of 5 launches of " \
+                            f"{alu[prec]['launch_ms']:.0f} ms)"
+    elif bf is None:
+        pk, bound, src = (1700.0 / 3 if prec == "bf16x3" else 1700.0 / 6), "tensor", \
+            "of fallback: 1.7 PFLOP/s bf16 sustained / 3 MMAs per useful product" + (" / 2 (tf32)" if prec == "tf32x3" else "")
+    elif prec == "bf16x3":
+        pk, bound, src = bf / 3.0, "tensor", "of measured: bf16 sustained / 3 (each useful product is 3 MMAs)"
+    else:
+        pk, bound, src = bf / 6.0, "tensor", "of measured: bf16 sustained / 2 (nominal tf32 ratio) / 3 (3 MMAs per product)"
+    return {"bound": bound, "kernel": f"{form}-{prec}:{name}", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+            "frac": ach / pk, "traffic": measured_traffic(args.workload, wl.depth, f"{form}-{prec}:{name}"),
+            "peak_source": src, "algorithmic_flops_per_launch": work.get(name, 0.0) * steps / nl,
+            "launch_ms": per_launch_ms}
+
+
+def stage_summary(stages, steps):
+    return {name: {"ms_per_step": ms / steps, "launches_per_step": nl / steps} for name, (ms, nl) in stages.items()
+            if nl}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -194,258 +306,217 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    insts, variants, batched, target_tol, desc = workload_spec(args.workload, args.depth)
-    if args.variants:
-        variants = args.variants.split(",")
+    target = args.target
+    insts, variants, batched = workload_spec(args.workload, args.depth)
+    if args.variants is not None:
+        variants = [v for v in args.variants.split(",") if v]
+    alu = alu_peaks()
+    log(f"FMA probe: fp64 {alu['fp64']['best_tflops']:.3f} TFLOP/s, fp32 {alu['fp32']['best_tflops']:.1f} TFLOP/s")
+    peaks = measured_peaks()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    timed = Timed(torch, flush)
+    barrier = None
+    if world > 1:
+        import torch.distributed as dist
+        barrier = dist.barrier
     # every rank draws its own independent instances of the workload
     q64 = [np.concatenate([wl.multipoles(l, rng_offset=rank).reshape(-1) for l in wl.levels]) for wl in insts]
-    plans = {v: [] for v in variants}
-    bufs = {}       # (instance, dtype) -> (q, out)
-    dtypes = {}     # (variant, instance) -> dtype
-    for v in variants:
-        form, prec = variant_parts(v)
-        for i, wl in enumerate(insts):
-            tol = wl.rank_tol if form in ("blas", "auto") else 0.0
-            pl = lib.Plan(wl.depth, wl.p, tol, form=form, precision=prec).set(timing=0 if batched else 1)
-            if form == "fft" and wl.fft_grid:
-                pl.set(fft_grid=wl.fft_grid)
-            if form == "blas" and prec in ("fp64", "fp32") and wl.dir_tol:
-                pl.set(dir_tol=wl.dir_tol)  # the CUDA-core contraction applies Eq. 15's factors
-            if target_tol is not None:
-                pl.set(target_tol=target_tol)
-            for l in wl.levels:
-                if wl.keys[l] is not None:
-                    pl.set_boxes(l, wl.keys[l])
-            pl.set_stream()
-            plans[v].append(pl)
-            pr = pl.query(lib.M2L_Q_PRECISION, wl.n_rhs)
-            dt = torch.float64 if pr == lib.M2L_PREC_FP64 else torch.float32
-            dtypes[(v, i)] = dt
-            if (i, dt) not in bufs:
-                bufs[(i, dt)] = (torch.from_numpy(q64[i]).to(dt).to(dev), torch.empty(len(q64[i]), dtype=dt, device=dev))
-    log(f"{len(insts)} instance(s), {len(variants)} variant(s): plans ready")
-    pairs = [plans[variants[0]][i].pairs(-1) for i in range(len(insts))]
-    inter_variant = sum(pairs[i] * insts[i].n_rhs for i in range(len(insts)))
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    dbufs = {}
 
-    def run_variant(v):
+    def buf(i, dt):
+        if (i, dt) not in dbufs:
+            dbufs[(i, dt)] = (torch.from_numpy(q64[i]).to(dt).to(dev), torch.empty(len(q64[i]), dtype=dt, device=dev))
+        return dbufs[(i, dt)]
+
+    def dtype_of(pl, wl):
+        return torch.float64 if pl.query(lib.M2L_Q_PRECISION, wl.n_rhs) == lib.M2L_PREC_FP64 else torch.float32
+
+    def runner(plans):
+        """One pass over every instance with `plans` (a batch when the workload is batched)."""
         if batched:
-            qs = [bufs[(i, dtypes[(v, i)])][0] for i in range(len(insts))]
-            os_ = [bufs[(i, dtypes[(v, i)])][1] for i in range(len(insts))]
-            rc = lib.m2l_apply_batch([pl.handle for pl in plans[v]], [q.data_ptr() for q in qs],
-                                     [o.data_ptr() for o in os_], [wl.n_rhs for wl in insts])
-            if rc != lib.M2L_OK:
-                raise lib.M2LError(rc, lib.m2l_last_error())
-        else:
-            for i, wl in enumerate(insts):
-                qd, od = bufs[(i, dtypes[(v, i)])]
-                plans[v][i].apply(qd, od, -1, wl.n_rhs)
+            qs = [buf(i, dtype_of(pl, wl))[0] for i, (pl, wl) in enumerate(zip(plans, insts))]
+            os_ = [buf(i, dtype_of(pl, wl))[1] for i, (pl, wl) in enumerate(zip(plans, insts))]
+            hs, qp, op, rs = ([pl.handle for pl in plans], [q.data_ptr() for q in qs], [o.data_ptr() for o in os_],
+                              [wl.n_rhs for wl in insts])
 
-    for _ in range(args.warmup):
-        for v in variants:
-            run_variant(v)
-    torch.cuda.synchronize()
-    log("warm-up done")
-    stream = torch.cuda.current_stream()
-    stage_acc = {v: {} for v in variants}
-    var_ms = {v: 0.0 for v in variants}
-    launches = 0
-    sampler = ClockSampler()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    total_ms = 0.0
-    for _ in range(args.steps):
-        flush.zero_()  # L2 flush, outside the timed interval
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(variants) + 1)]
-        evs[0].record(stream)
-        for j, v in enumerate(variants):
-            run_variant(v)
-            evs[j + 1].record(stream)
-        torch.cuda.synchronize()
-        total_ms += evs[0].elapsed_time(evs[-1])
-        for j, v in enumerate(variants):
-            var_ms[v] += evs[j].elapsed_time(evs[j + 1])
-            if batched:
-                launches += plans[v][0].query(lib.M2L_Q_LAUNCHES)
-                continue
-            for pl in plans[v]:
-                for name, (ms, nl) in pl.stage_times().items():
-                    a = stage_acc[v].setdefault(name, [0.0, 0])
-                    a[0] += ms
-                    a[1] += nl
-                    launches += nl
-    torch.cuda.synchronize()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    clocks = sampler.stop()
-    log(f"timed steps done: {total_ms / args.steps:.1f} ms per step")
-    ms_step = total_ms / args.steps
+            def run():
+                rc = lib.m2l_apply_batch(hs, qp, op, rs)
+                if rc != lib.M2L_OK:
+                    raise lib.M2LError(rc, lib.m2l_last_error())
+            return run
+        bs = [buf(i, dtype_of(pl, wl)) for i, (pl, wl) in enumerate(zip(plans, insts))]
+
+        def run():
+            for (qd, od), pl, wl in zip(bs, plans, insts):
+                pl.apply(qd, od, -1, wl.n_rhs)
+        return run
+
+    pairs = [make_plan(lib, wl, "fft", "fp64", timing=False) for wl in insts]
+    inter = sum(p_.pairs(-1) * wl.n_rhs for p_, wl in zip(pairs, insts))
+    for p_ in pairs:
+        p_.close()
+
+    # ---- headline: the autotuned reduced-precision form at the target ----
+    head = [make_plan(lib, wl, "auto", "auto", target=target, timing=not batched) for wl in insts]
+    forms = [resolved(lib, pl, wl.n_rhs) for pl, wl in zip(head, insts)]
+    log(f"headline forms at {target:g}: {sorted(set(forms))}")
+    run_head = runner(head)
+    ms, stages, launches, clocks = timed(run_head, args.steps, args.warmup, plans=[] if batched else head,
+                                         sampler=ClockSampler(), barrier=barrier)
+    ms_step = sum(ms) / len(ms)
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
-    inter_step = inter_variant * len(variants)
-    value = world * inter_step / (ms_step / 1e3)
-    steps_for_stages = args.steps
     if batched:
-        # stage times of a batch: one separate, untimed apply of the largest instance on a fresh plan
-        big = max(range(len(insts)), key=lambda i: pairs[i] * insts[i].n_rhs)
-        wl = insts[big]
-        for v in variants:
-            src = plans[v][big]
-            f = src.query(lib.M2L_Q_FORM, wl.n_rhs)
-            pr = src.query(lib.M2L_Q_PRECISION, wl.n_rhs)
-            fname = "blas" if f == lib.M2L_FORM_BLAS else "fft"
-            pname = {lib.M2L_PREC_FP64: "fp64", lib.M2L_PREC_FP32: "fp32", lib.M2L_PREC_TF32X3: "tf32x3",
-                     lib.M2L_PREC_BF16X3: "bf16x3"}[pr]
-            probe = lib.Plan(wl.depth, wl.p, wl.rank_tol if fname == "blas" else 0.0, form=fname,
-                             precision=pname).set(timing=1)
-            for l in wl.levels:
-                if wl.keys[l] is not None:
-                    probe.set_boxes(l, wl.keys[l])
-            probe.set_stream()
-            qd, od = bufs[(big, dtypes[(v, big)])]
-            probe.apply(qd, od, -1, wl.n_rhs)
-            for name, (ms, nl) in probe.stage_times().items():
-                a = stage_acc[v].setdefault(name, [0.0, 0])
-                a[0] += ms
-                a[1] += nl
-            probe_work = algorithmic_work(probe, fname, pname, wl.n_rhs)
-            stage_acc[v]["_algorithmic"] = probe_work
-            stage_acc[v]["_prec"] = pname
-            probe.close()
-        steps_for_stages = 1
+        launches = head[0].query(lib.M2L_Q_LAUNCHES) * args.steps
+    value = world * inter / (ms_step / 1e3)
+    log(f"headline: {ms_step:.2f} ms per step, {value:.3e} interactions/s")
+    head_form, head_prec = forms[0] if len(set(forms)) == 1 else ("mixed", "mixed")
+    roofline = None
+    if not batched:
+        roofline = roofline_of(lib, insts[0], head_form, head_prec, stages, args.steps, peaks, alu, args)
 
-    # roofline of the dominant kernel of each variant and of the step
-    peaks = measured_peaks()
+    # ---- the FP64 form the autotuner picks at the same target ----
+    fp64_out, fp64_plans = None, None
+    if not args.no_fp64:
+        fp64_plans = [make_plan(lib, wl, "auto", "fp64", target=target, timing=not batched) for wl in insts]
+        f64 = [resolved(lib, pl, wl.n_rhs) for pl, wl in zip(fp64_plans, insts)]
+        k = max(1, min(args.steps, 3))
+        ms64, st64, _, _ = timed(runner(fp64_plans), k, 2, plans=[] if batched else fp64_plans, barrier=barrier)
+        m64 = sum(ms64) / len(ms64)
+        fp64_out = {"interactions_per_s": world * inter / (m64 / 1e3), "ms": m64, "steps": k,
+                    "forms": sorted(set(f"{a}-{b}" for a, b in f64)), "stages": stage_summary(st64, k)}
+        if not batched:
+            fp64_out["roofline"] = roofline_of(lib, insts[0], f64[0][0], f64[0][1], st64, k, peaks, alu, args)
+        log(f"fp64 at {target:g}: {fp64_out['forms']} {m64:.1f} ms")
 
-    def peak_for(prec):
-        if prec == "fp64":
-            return NOMINAL_FP64_TFLOPS, "alu", "nominal GB300 FP64 1.25 TFLOP/s"
-        if prec == "fp32":
-            return fp32_alu_peak_tflops(), "alu", "152 SM x 128 FP32 lanes x 2 flops x 2070 MHz"
-        bf = peaks.get("bf16_tflops_sustained", 1700.0)
-        if prec == "bf16x3":
-            return bf / 3.0, "tensor", "of measured: bf16 sustained / 3 (each useful product is 3 MMAs)"
-        return bf / 2.0 / 3.0, "tensor", "of measured: bf16 sustained / 2 (nominal tf32 ratio) / 3 (3 MMAs per product)"
-
-    var_out = {}
-    best = None
+    # ---- every explicit variant of the workload, alone ----
+    var_out, var_plans = {}, {}
     for v in variants:
-        # algorithmic work per stage, summed over instances (each resolved to its own precision);
-        # for a batch, the stage times and work are those of its largest instance
-        probe_work = stage_acc[v].pop("_algorithmic", None)
-        probe_prec = stage_acc[v].pop("_prec", None)
-        work, prec_of = {}, None
-        for i, (pl, wl) in enumerate(zip(plans[v], insts)):
-            f = pl.query(lib.M2L_Q_FORM, wl.n_rhs)
-            pr = pl.query(lib.M2L_Q_PRECISION, wl.n_rhs)
-            fname = "blas" if f == lib.M2L_FORM_BLAS else "fft"
-            pname = {lib.M2L_PREC_FP64: "fp64", lib.M2L_PREC_FP32: "fp32", lib.M2L_PREC_TF32X3: "tf32x3",
-                     lib.M2L_PREC_BF16X3: "bf16x3"}[pr]
-            prec_of = pname if prec_of in (None, pname) else "mixed"
-            for k, w in algorithmic_work(pl, fname, pname, wl.n_rhs).items():
-                work[k] = work.get(k, 0.0) + w
-        prec_all = prec_of
-        if probe_work is not None:
-            work, prec_of = probe_work, probe_prec
-        stages = {}
-        for name, (ms, nl) in stage_acc[v].items():
-            if nl == 0:
-                continue
-            per_launch_ms = ms / nl
-            flops_launch = work.get(name, 0.0) * steps_for_stages / nl
-            stages[name] = {"ms_per_step": ms / steps_for_stages, "launches_per_step": nl / steps_for_stages,
-                            "gflops": flops_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None}
-        var_out[v] = {"interactions_per_s": inter_variant / (var_ms[v] / args.steps / 1e3), "ms": var_ms[v] / args.steps,
-                      "stages": stages, "precision": prec_all}
-        if probe_work is not None:
-            var_out[v]["stages_of"] = "largest instance, separate apply"
-        if insts and variant_parts(v)[0] == "blas":
-            var_out[v]["rank"] = [pl.query(lib.M2L_Q_RANK) for pl in plans[v]][:4]
-        if stages and prec_of != "mixed":
-            name = max(stages, key=lambda n: stages[n]["ms_per_step"])
-            ms_tot, nl = stage_acc[v][name]
-            pk, bound, note = peak_for(prec_of)
-            per_launch_ms = ms_tot / nl
-            ach = work.get(name, 0.0) * steps_for_stages / nl / (per_launch_ms / 1e3) / 1e12
-            rf = {"bound": bound, "kernel": f"{v}:{name}", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                  "frac": ach / pk, "traffic": measured_traffic(args.workload, args.depth, f"{v}:{name}"),
-                  "peak_source": note}
-            var_out[v]["roofline"] = rf
-            if best is None or ms_tot > best[0]:
-                best = (ms_tot, rf)
-    roofline = best[1] if best else None
+        form, prec = v.split("-")
+        pls = [make_plan(lib, wl, form, prec, timing=True) for wl in insts]
+        try:
+            mv, sv, _, _ = timed(runner(pls), 2, 1, plans=pls)
+        except lib.M2LError as e:
+            var_out[v] = {"unavailable": str(e)}
+            for pl in pls:
+                pl.close()
+            continue
+        m = sum(mv) / len(mv)
+        var_out[v] = {"interactions_per_s": world * inter / (m / 1e3), "ms": m, "steps": 2,
+                      "stages": stage_summary(sv, 2),
+                      "roofline": roofline_of(lib, insts[0], form, prec, sv, 2, peaks, alu, args)}
+        if form == "blas":
+            var_out[v]["rank"] = pls[0].query(lib.M2L_Q_RANK)
+        var_plans[v] = pls
+        log(f"variant {v}: {m:.2f} ms")
 
-    # end to end through the C ABI with pinned host buffers
+    # ---- the 64 uneven instances in one batched pass (extra key of the default workload) ----
+    batch_out = None
+    if args.workload == "c3" and not args.no_batch:
+        batch_out = run_batched_key(lib, torch, timed, dev, target, rank)
+        log(f"batched: {batch_out['ms']:.1f} ms per pass")
+
+    # ---- end to end through the C ABI with pinned host buffers ----
     e2e = None
     if not args.no_e2e:
-        hq = {k: bufs[k][0].cpu().pin_memory() for k in bufs}
-        ho = {k: torch.empty_like(hq[k]).pin_memory() for k in bufs}
+        hq, ho = {}, {}
+        for i, (pl, wl) in enumerate(zip(head, insts)):
+            dt = dtype_of(pl, wl)
+            hq[i] = torch.from_numpy(q64[i]).to(dt).pin_memory()
+            ho[i] = torch.empty_like(hq[i]).pin_memory()
 
         def e2e_pass():
-            for v in variants:
-                if batched:
-                    for i in range(len(insts)):
-                        k = (i, dtypes[(v, i)])
-                        bufs[k][0].copy_(hq[k], non_blocking=True)
-                    run_variant(v)
-                    for i in range(len(insts)):
-                        k = (i, dtypes[(v, i)])
-                        ho[k].copy_(bufs[k][1], non_blocking=True)
-                    torch.cuda.synchronize()
-                else:
-                    for i, wl in enumerate(insts):
-                        k = (i, dtypes[(v, i)])
-                        plans[v][i].apply(hq[k], ho[k], -1, wl.n_rhs)
+            if batched:
+                for i, (pl, wl) in enumerate(zip(head, insts)):
+                    buf(i, dtype_of(pl, wl))[0].copy_(hq[i], non_blocking=True)
+                run_head()
+                for i, (pl, wl) in enumerate(zip(head, insts)):
+                    ho[i].copy_(buf(i, dtype_of(pl, wl))[1], non_blocking=True)
+                torch.cuda.synchronize()
+            else:
+                for i, (pl, wl) in enumerate(zip(head, insts)):
+                    pl.apply(hq[i], ho[i], -1, wl.n_rhs)   # host pointers: staged inside the call
 
-        e2e_pass()  # warm the staging buffers
+        e2e_pass()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             e2e_pass()
         el = time.perf_counter() - t0
-        h2d = sum(hq[(i, dtypes[(v, i)])].numel() * hq[(i, dtypes[(v, i)])].element_size()
-                  for v in variants for i in range(len(insts)))
         if world > 1:
             import torch.distributed as dist
             t = torch.tensor([el], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             el = float(t.item())
-        e2e = {"value": world * inter_step * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": h2d}
+        nbytes = sum(hq[i].numel() * hq[i].element_size() for i in hq)
+        e2e = {"value": world * inter * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+        log("e2e done")
 
-    mixed = [v for v in variants if var_out[v].get("precision") in ("tf32x3", "bf16x3", "fp32")]
-    fp64 = [v for v in variants if var_out[v].get("precision") == "fp64"]
-    headline = None
-    if mixed and fp64:
-        bm = max(mixed, key=lambda v: var_out[v]["interactions_per_s"])
-        bf = max(fp64, key=lambda v: var_out[v]["interactions_per_s"])
-        headline = {"fastest_reduced_precision": bm, "fastest_fp64": bf,
-                    "speedup": var_out[bm]["interactions_per_s"] / var_out[bf]["interactions_per_s"]}
-    precs = sorted({var_out[v].get("precision") or "?" for v in variants})
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "+".join(precs), "data": "synthetic",
-           "config": {"workload": desc, "instances": len(insts), "pairs_per_variant": int(sum(pairs)),
-                      "interactions_per_variant": int(inter_variant), "variants": variants,
-                      "batched": batched, "target_tol": target_tol,
-                      "l2": "flushed between timed steps (512 MB write)",
+           "vs_baseline": None, "dtype": head_prec, "data": "synthetic",
+           "config": {"workload": DESC[args.workload] if args.depth == 5 or args.workload != "c2"
+                      else DESC["c2"].replace("depth5", f"depth{args.depth}"),
+                      "instances": len(insts), "pairs_x_rhs": int(inter), "target_rel_err": target,
+                      "form": head_form, "precision": head_prec,
+                      "choice": "autotuned among forms whose stated bound and rank truncation are within the target",
+                      "batched": batched, "l2": "flushed between timed steps (512 MB write)",
                       "ranks": "one independent set of instances per rank"},
-           "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e, "variants": var_out,
-           "mixed_vs_fp64": headline}
-    log("e2e done")
+           "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
+           "stages": stage_summary(stages, args.steps) if stages else None,
+           "fp64_same_target": fp64_out,
+           "mixed_vs_fp64": (value / fp64_out["interactions_per_s"]) if fp64_out else None,
+           "variants": var_out, "batched": batch_out,
+           "alu_peaks_measured": alu}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(insts, q64, plans, bufs, dtypes, args.cpu_seconds, run_variant)
+        sets = {"headline": head}
+        if fp64_plans:
+            sets["fp64_same_target"] = fp64_plans
+        sets.update(var_plans)
+        out["cpu_baseline"] = cpu_baseline(insts, q64, sets, runner, buf, dtype_of, args.cpu_seconds)
         log("cpu baseline done")
-    for v in variants:
-        for pl in plans[v]:
+    for pls in [head] + ([fp64_plans] if fp64_plans else []) + list(var_plans.values()):
+        for pl in pls:
             pl.close()
+    return out
+
+
+def run_batched_key(lib, torch, timed, dev, target, rank):
+    """The 64 uneven instances (1e4..2e6 points, depth 3-6, p 4/6/8/10, 1-8 RHS) in one
+    m2l_apply_batch, autotuned at `target`, graph-captured on the first call and replayed."""
+    insts = W.c5()
+    plans = [make_plan(lib, wl, "auto", "auto", target=target, timing=False) for wl in insts]
+    qs, os_ = [], []
+    for pl, wl in zip(plans, insts):
+        dt = torch.float64 if pl.query(lib.M2L_Q_PRECISION, wl.n_rhs) == lib.M2L_PREC_FP64 else torch.float32
+        q = np.concatenate([wl.multipoles(l, rng_offset=rank).reshape(-1) for l in wl.levels])
+        qs.append(torch.from_numpy(q).to(dt).to(dev))
+        os_.append(torch.empty_like(qs[-1]))
+    hs, qp, op, rs = [pl.handle for pl in plans], [q.data_ptr() for q in qs], [o.data_ptr() for o in os_], \
+        [wl.n_rhs for wl in insts]
+
+    def run():
+        rc = lib.m2l_apply_batch(hs, qp, op, rs)
+        if rc != lib.M2L_OK:
+            raise lib.M2LError(rc, lib.m2l_last_error())
+
+    ms, _, _, _ = timed(run, 2, 3)
+    m = sum(ms) / len(ms)
+    inter = sum(pl.pairs(-1) * wl.n_rhs for pl, wl in zip(plans, insts))
+    hist = {}
+    for pl, wl in zip(plans, insts):
+        f, p_ = resolved(lib, pl, wl.n_rhs)
+        key = f"{f}-{p_}"
+        hist[key] = hist.get(key, 0) + 1
+    out = {"workload": DESC["c5"], "target_rel_err": target, "interactions_per_s": inter / (m / 1e3), "ms": m,
+           "steps": 2, "warmup": 3, "pairs_x_rhs": int(inter), "forms": hist,
+           "launches_per_pass": plans[0].query(lib.M2L_Q_LAUNCHES)}
+    for pl in plans:
+        pl.close()
     return out
 
 
@@ -482,11 +553,10 @@ def _oracle_sample(wl, q64, seconds, seed=11):
     return done_pairs * R, el, results, batches
 
 
-def cpu_baseline(insts, q64, plans, bufs, dtypes, seconds, run_variant):
+def cpu_baseline(insts, q64, sets, runner, buf, dtype_of, seconds):
     """The FP64 oracle on this host's cores, on a bounded sample of the workload's instances; also
-    the error of each variant on the sampled targets (Eq. 16). Each variant is re-run the way the
-    timed loop runs it (`run_variant`: one batch call for a batched workload), once with check
-    potentials and once with locals as output."""
+    the error (Eq. 16) of every timed set of plans on the sampled targets: each set is re-run the
+    way the timed loop runs it, once with check potentials and once with locals as output."""
     import torch
     from oracle import m2l as M
     cores = os.cpu_count()
@@ -500,16 +570,20 @@ def cpu_baseline(insts, q64, plans, bufs, dtypes, seconds, run_variant):
         el += e_
         batches += b_
         samples[i] = res
-    errs = {v: {"check_potential_rel_err_per_level": [], "locals_rel_err_per_level": []} for v in plans}
-    for v in plans:
+    errs = {}
+    for name, plans in sets.items():
+        e = {"check_potential_rel_err_per_level": [], "locals_rel_err_per_level": [],
+             "check_potential_max_target_rel_err": 0.0}
         outs = {i: {} for i in order}
         for mode in ("check", "locals"):
-            for pl in plans[v]:
+            for pl in plans:
                 pl.set(output=mode)
-            run_variant(v)
+            runner(plans)()
             torch.cuda.synchronize()
             for i in order:
-                outs[i][mode] = bufs[(i, dtypes[(v, i)])][1].double().cpu().numpy()
+                outs[i][mode] = buf(i, dtype_of(plans[i], insts[i]))[1].double().cpu().numpy()
+        for pl in plans:
+            pl.set(output="locals")
         for i in order:
             wl, res = insts[i], samples[i]
             n, R = W.n_surface(wl.p), wl.n_rhs
@@ -522,9 +596,13 @@ def cpu_baseline(insts, q64, plans, bufs, dtypes, seconds, run_variant):
                 tg = np.concatenate(res[l][0])
                 if len(tg) == 0:
                     continue
-                errs[v]["check_potential_rel_err_per_level"].append(M.rel_l2_error(np.concatenate(res[l][1]), c[tg]))
-                errs[v]["locals_rel_err_per_level"].append(
+                ref = np.concatenate(res[l][1])
+                e["check_potential_rel_err_per_level"].append(M.rel_l2_error(ref, c[tg]))
+                e["check_potential_max_target_rel_err"] = max(e["check_potential_max_target_rel_err"],
+                                                              M.max_target_rel_error(ref, c[tg]))
+                e["locals_rel_err_per_level"].append(
                     M.check_norm_error(wl.p, l, np.concatenate(res[l][2]), lo[tg], root_width=wl_root_width(wl)))
+        errs[name] = e
     return {"value": inter / el, "unit": UNIT, "cores": cores, "cpu": host_cpu(), "kind": "oracle",
             "sample": f"{batches} batches of up to 16 random target boxes per level of the "
                       f"{len(order)} largest instance(s), dense FP64 definition (per-pair kernel evaluation "
@@ -562,7 +640,7 @@ def wl_root_width(wl):
 
 def run_reference(args):
     """The oracle (FP64, this host's cores) timed on bounded samples of the same workload."""
-    insts, _, _, _, desc = workload_spec(args.workload, args.depth)
+    insts, _, _ = workload_spec(args.workload, args.depth)
     wl = max(insts, key=lambda w: w.n_boxes(w.depth))
     q64 = np.concatenate([wl.multipoles(l).reshape(-1) for l in wl.levels])
     per_step = args.ref_seconds
@@ -578,7 +656,7 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "levels": wl.levels},
+            "config": {"workload": DESC[args.workload], "levels": wl.levels, "target_rel_err": 0.0},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu": host_cpu(), "kind": "oracle",
                              "sample": f"per step about {per_step:.0f} s of random target boxes (16 per level "
                                        f"per batch) of the same workload, dense FP64 definition"},
@@ -586,11 +664,11 @@ def run_reference(args):
 
 
 def run_fmm(args):
-    """The whole FMM (P2M, M2M, M2L, L2L, L2P, P2P; FP64) on the 1M-point cloud of the default
-    workload (depth 5, p = 6, M2L in the BLAS form at rank 1e-7 with directional factors at 1e-8,
-    or the FFT form with --variants fft). Charges resident on the device; the plan (tree,
-    operators) is built before the timed region. Accuracy: Eq. 16 against direct summation on a
-    seeded sample of 1,000 targets (the oracle's direct sum on this host)."""
+    """The whole FMM (P2M, M2M, M2L, L2L, L2P, P2P; FP64) on the 1M-point cloud (depth 5, p = 6,
+    M2L in the BLAS form at rank 1e-7 with directional factors at 1e-8, or the FFT form with
+    --variants fft). Charges resident on the device; the plan (tree, operators) is built before
+    the timed region. Accuracy: Eq. 16 against direct summation on a seeded sample of 1,000
+    targets (the oracle's direct sum on this host)."""
     import torch
     from oracle import _cdirect
     from paper_2408_07436_gb300 import m2l as lib
@@ -632,18 +710,23 @@ def run_fmm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "fmm"],
-                    help="c2 (default): the 1M-point workload; c3/c4/c5: precision, RHS-batching and instance-batching "
-                         "studies; fmm: the whole FMM around M2L on the 1M-point cloud")
-    ap.add_argument("--variants", default=None, help="comma list of form-precision (default: the workload's)")
+    ap.add_argument("--workload", default="c3", choices=["c2", "c3", "c4", "c5", "fmm"],
+                    help="c3 (default): the 8M-point, p = 8 workload; c2: 1M points, p = 6; c4: sphere surface, "
+                         "32 RHS; c5: 64 uneven instances batched; fmm: the whole FMM on the 1M-point cloud")
+    ap.add_argument("--target", type=float, default=DEFAULT_TARGET,
+                    help="relative error (Eq. 16) the headline and the FP64 comparison must meet")
+    ap.add_argument("--variants", default=None, help="comma list of form-precision timed beside the headline "
+                                                     "(default: the workload's; empty: none)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison at the same target")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-instance key")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=6.0)
-    ap.add_argument("--depth", type=int, default=5, help="tree depth (5 is the workload; smaller for profiling)")
+    ap.add_argument("--depth", type=int, default=5, help="tree depth of the 1M-point workload (c2, fmm)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

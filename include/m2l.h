@@ -285,7 +285,8 @@ void m2l_fmm_destroy(m2l_fmm_t *fmm); /* NULL-safe */
 
 /* Copy a plan operator to host memory (FP64), for tests and inspection:
  * which = 0: U (n_c x k_c), 1: S (n x k), 2: C_t (316 x k_c x k), 3: singular values of K_fat
- *         (n_c), 4: pseudo-inverse factor V_eps (n x r), 5: Ut_eps = Sigma_eps^-1 U_eps^T (r x n_c).
+ *         (n_c), 4: pseudo-inverse factor V_eps (n x r), 5: Ut_eps = Sigma_eps^-1 U_eps^T (r x n_c),
+ *         6: the directional products Ubar_t Vbar'_t^T (316 x k_c x k; needs M2L_OPT_DIR_TOL > 0).
  * (n_c = n and k_c = k unless M2L_OPT_CHECK_ORDER > p.)
  * *count receives the number of doubles; dst may be NULL to query the size. */
 int m2l_get_operator(m2l_plan_t *plan, int which, double *dst, long long *count);

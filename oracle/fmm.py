@@ -43,8 +43,11 @@ def upward(points, charges, depth, p, root_origin=(0.0, 0.0, 0.0), root_width=1.
     fac = O.up_pinv(p, depth, root_width, p_c=pc)
     w = G.box_width(depth, root_width)
     q = np.zeros((len(keys), 1, n))
+    order = np.argsort(lkeys, kind="stable")          # the points of one leaf are one slice
+    bounds = np.searchsorted(lkeys[order], keys, side="left")
+    ends = np.searchsorted(lkeys[order], keys, side="right")
     for b, key in enumerate(keys):
-        sel = lkeys == key
+        sel = order[bounds[b]:ends[b]]
         c = G.box_centre(G.morton_decode(key, depth), depth, root_origin, root_width)
         x = G.surface_points(pc, c, w, G.ALPHA_OUTER)
         phi = O.laplace(x, points[sel]) @ charges[sel]
@@ -62,7 +65,8 @@ def upward(points, charges, depth, p, root_origin=(0.0, 0.0, 0.0), root_width=1.
             c = G.box_centre(G.morton_decode(key, level), level, root_origin, root_width)
             x = G.surface_points(pc, c, w, G.ALPHA_OUTER)
             phi = np.zeros(len(x))
-            for ci in np.nonzero((ckeys >> 3) == key)[0]:
+            lo, hi = np.searchsorted(ckeys, [key << 3, (key << 3) + 8])   # ckeys is sorted
+            for ci in range(lo, hi):
                 cc = G.box_centre(G.morton_decode(ckeys[ci], level + 1), level + 1, root_origin, root_width)
                 y = G.surface_points(p, cc, wc, G.ALPHA_INNER)
                 phi += O.laplace(x, y) @ cq[ci, 0]

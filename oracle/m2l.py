@@ -166,6 +166,28 @@ def rel_l2_error(ref: np.ndarray, approx: np.ndarray) -> float:
     return float(np.sqrt(num / den)) if den > 0 else float(np.sqrt(num))
 
 
+def max_target_rel_error(ref: np.ndarray, approx: np.ndarray) -> float:
+    """Largest relative L2 error of one target's values: max over (box, rhs) of
+    ||ref[b, r] - approx[b, r]|| / ||ref[b, r]|| (Eq. 16 per target box and right-hand side).
+    A single wrong box among many barely moves the level-wide error of Eq. 16; here it is the
+    maximum."""
+    ref = np.asarray(ref, dtype=np.float64)
+    approx = np.asarray(approx, dtype=np.float64)
+    num = np.sqrt(np.sum((ref - approx) ** 2, axis=-1))
+    den = np.sqrt(np.sum(ref ** 2, axis=-1))
+    rel = np.where(den > 0, num / np.where(den > 0, den, 1.0), num)
+    return float(rel.max()) if rel.size else 0.0
+
+
+def down_check_matrix(p: int, level: int, root_width: float = 1.0, p_c: int | None = None) -> np.ndarray:
+    """K_tau: the downward-equivalent surface of a box of ``level`` seen from its own downward
+    check surface (the matrix of Eq. 6 that the locals solve with, Sec. 2.2)."""
+    w = G.box_width(level, root_width)
+    x = G.surface_points(p if p_c is None else p_c, np.zeros(3), w, G.ALPHA_INNER)
+    y = G.surface_points(p, np.zeros(3), w, G.ALPHA_OUTER)
+    return O.laplace(x, y)
+
+
 def check_norm_error(p: int, level: int, L_ref: np.ndarray, L_test: np.ndarray, root_width: float = 1.0,
                      p_c: int | None = None) -> float:
     """Eq. 16 applied to the check potentials K_tau q^tau that two sets of locals reproduce.
@@ -175,13 +197,30 @@ def check_norm_error(p: int, level: int, L_ref: np.ndarray, L_test: np.ndarray, 
     again whenever the locals are used to evaluate a potential (the footnote of Sec. 2.1.1).
     Comparing K_tau q^tau measures agreement in the quantity the FMM uses downstream.
     """
-    w = G.box_width(level, root_width)
-    x = G.surface_points(p if p_c is None else p_c, np.zeros(3), w, G.ALPHA_INNER)
-    y = G.surface_points(p, np.zeros(3), w, G.ALPHA_OUTER)
-    K = O.laplace(x, y)
+    K = down_check_matrix(p, level, root_width, p_c)
     a = np.einsum("ij,brj->bri", K, np.asarray(L_ref, dtype=np.float64))
     b = np.einsum("ij,brj->bri", K, np.asarray(L_test, dtype=np.float64))
     return rel_l2_error(a, b)
+
+
+def locals_backward_bound(p: int, level: int, L: np.ndarray, root_width: float = 1.0,
+                          p_c: int | None = None) -> float:
+    """How far two correct sets of FP64 locals may sit apart in the check norm of
+    ``check_norm_error``: b = n_c eps ||K_tau||_2 ||L|| / ||K_tau L|| (norms over every box and
+    right-hand side of ``L``).
+
+    The locals solve K_tau q = phi through the two factors of the pseudo-inverse (Eqs. 7-10 and
+    the footnote of Sec. 2.1.1). A normwise backward-stable solve returns the exact solution of a
+    matrix within n_c eps ||K_tau|| of K_tau, so its check potential K_tau q differs from another
+    such solve's by up to about n_c eps ||K_tau|| ||q||: small against ||phi|| when the locals
+    are smooth, large when they oscillate (p >= 8, where cond(K_tau) reaches 1e12)."""
+    K = down_check_matrix(p, level, root_width, p_c)
+    L = np.asarray(L, dtype=np.float64)
+    KL = np.einsum("ij,brj->bri", K, L)
+    den = np.linalg.norm(KL)
+    if den == 0:
+        return 0.0
+    return float(K.shape[0] * np.finfo(np.float64).eps * np.linalg.norm(K, 2) * np.linalg.norm(L) / den)
 
 
 def pair_count(level: int, keys=None) -> int:

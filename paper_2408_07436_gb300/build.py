@@ -1,4 +1,5 @@
-"""Compile the CUDA library for sm_103a, in tree (``paper_2408_07436_gb300/libm2l_gb300.so``).
+"""Compile the CUDA library for sm_103a, in tree (``paper_2408_07436_gb300/libm2l_gb300.so``), and
+the FMA-throughput probe the bench takes its CUDA-core peaks from (``libm2l_peaks.so``).
 
 Each translation unit is compiled by nvcc in parallel, then linked into one shared library.
 No CMake; the same command works on the x86 build container and on the Arm GPU host.
@@ -18,6 +19,8 @@ LIB = os.path.join(HERE, "libm2l_gb300.so")
 SOURCES = ["plan.cpp", "linalg.cpp", "capi.cpp", "autotune.cpp", "apply.cu", "kernels_simt.cu", "kernels_tc.cu", "noalloc.cu",
            "fmm.cpp", "fmm_kernels.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
+PEAKS_SOURCES = ["peaks.cu"]
+PEAKS_LIB = os.path.join(HERE, "libm2l_peaks.so")
 
 
 def nvcc() -> str:
@@ -43,20 +46,27 @@ def _compile(src: str) -> str:
     return obj
 
 
-def build(verbose: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(SOURCES))) as ex:
-        objs = list(ex.map(_compile, SOURCES))
-    if os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(o) for o in objs):
-        return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), "-shared", "-o", tmp] + objs + GENCODE + ["-Xcompiler", "-fopenmp", "-lgomp", "-lcudart"]
+def _link(lib: str, objs) -> None:
+    if os.path.exists(lib) and all(os.path.getmtime(lib) >= os.path.getmtime(o) for o in objs):
+        return
+    tmp = lib + f".{os.getpid()}.tmp"
+    cmd = [nvcc(), "-shared", "-o", tmp] + list(objs) + GENCODE + ["-Xcompiler", "-fopenmp", "-lgomp", "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
+
+
+def build(verbose: bool = False) -> str:
+    os.makedirs(OUT, exist_ok=True)
+    srcs = SOURCES + PEAKS_SOURCES
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+        objs = list(ex.map(_compile, srcs))
+    _link(LIB, objs[:len(SOURCES)])
+    _link(PEAKS_LIB, objs[len(SOURCES):])
     if verbose:
         print(LIB)
+        print(PEAKS_LIB)
     return LIB
 
 

@@ -479,10 +479,33 @@ int m2l_get_operator(m2l_plan_t *pl, int which, double *dst, long long *count) {
         set_error("NULL plan or count");
         return M2L_EINVAL;
     }
-    int rc = which <= 3 ? build_blas_host(pl) : build_pinv(pl);
+    int rc = which <= 3 ? build_blas_host(pl) : which == 6 ? build_directional(pl) : build_pinv(pl);
     if (rc) return rc;
     const std::vector<double> *src = nullptr;
+    std::vector<double> prod;
     switch (which) {
+        case 6: {
+            if (pl->dir_tol <= 0) {
+                set_error("operator 6 (directional products) needs M2L_OPT_DIR_TOL > 0");
+                return M2L_EINVAL;
+            }
+            // Ubar_t Vbar'_t^T (kc x k) from the packed factors, for every t
+            const DirOps &d = *pl->dirop;
+            const int k = pl->k, kc = pl->kc, kp = pl->kp;
+            prod.assign((size_t)kNumTransfer * kc * k, 0.0);
+            for (int t = 0; t < kNumTransfer; ++t) {
+                const double *ub = &d.ub[d.meta[4 * t]], *vt = &d.vt[d.meta[4 * t + 1]];
+                const int kt = d.meta[4 * t + 2], kt8 = d.meta[4 * t + 3];
+                double *P = &prod[(size_t)t * kc * k];
+                for (int a = 0; a < kc; ++a)
+                    for (int j = 0; j < kt; ++j) {
+                        const double u = ub[(size_t)a * kt8 + j];
+                        for (int c = 0; c < k; ++c) P[(size_t)a * k + c] += u * vt[(size_t)j * kp + c];
+                    }
+            }
+            src = &prod;
+            break;
+        }
         case 0: src = &pl->blas->U; break;
         case 1: src = &pl->blas->S; break;
         case 2: src = &pl->blas->C; break;

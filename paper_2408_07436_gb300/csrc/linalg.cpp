@@ -153,4 +153,22 @@ void jacobi_svd(const std::vector<double> &A, int m, int n, std::vector<double> 
     V.swap(Vs);
 }
 
+void orthonormalize_columns(double *M, int rows, int cols) {
+    for (int c = 0; c < cols; ++c) {
+        double *vc = M + (size_t)c * rows;
+        for (int pass = 0; pass < 2; ++pass)
+            for (int b = 0; b < c; ++b) {
+                const double *vb = M + (size_t)b * rows;
+                double d = 0.0;
+                for (int r = 0; r < rows; ++r) d += vb[r] * vc[r];
+                for (int r = 0; r < rows; ++r) vc[r] -= d * vb[r];
+            }
+        double nr = 0.0;
+        for (int r = 0; r < rows; ++r) nr += vc[r] * vc[r];
+        nr = std::sqrt(nr);
+        if (nr > 0)
+            for (int r = 0; r < rows; ++r) vc[r] /= nr;
+    }
+}
+
 }  // namespace m2l

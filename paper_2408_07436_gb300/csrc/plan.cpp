@@ -243,6 +243,10 @@ int build_blas_host(m2l_plan_t *pl) {
                 k = std::max(kt, 1);
             }
             // U: left singular vectors of K_fat = right singular vectors of K_fat^T (and of Rf).
+            // The kept columns of both bases are re-orthonormalised, so that U_k U_k^T and
+            // S_k S_k^T are projectors to rounding.
+            orthonormalize_columns(Vf.data(), nc, kc);
+            orthonormalize_columns(Vt_.data(), n, k);
             o->U.assign((size_t)nc * kc, 0.0);
             o->S.assign((size_t)n * k, 0.0);
             for (int c = 0; c < kc; ++c)
@@ -329,19 +333,30 @@ int build_directional(m2l_plan_t *pl) {
                         A[(size_t)a * k + c] = C[(size_t)a * k + c];
                 }
             jacobi_svd(A, m, nn, U, sv, V);
-            // left (check side, kc) and right (equivalent side, k) singular vectors of C_t
+            // left singular vectors of C_t (check side, kc values)
             auto left = [&](int j, int a) { return tall ? U[(size_t)j * kc + a] : V[(size_t)j * kc + a]; };
-            auto right = [&](int j, int c) { return tall ? V[(size_t)j * k + c] : U[(size_t)j * k + c]; };
             int r = 0;
             while (r < nn && sv[r] >= pl->dir_tol * sv[0]) ++r;
             if (r < 1) r = 1;
             const int r8 = round_up(r, 8);
             kt[t] = r;
+            // Ubar_t: the r leading left singular vectors, re-orthonormalised; Vbar'_t^T =
+            // Ubar_t^T C_t, so that Ubar_t Vbar'_t^T is the projection of C_t onto that subspace
+            // (the same product as Ubar_t Sigmabar_t Vbar_t^T, without the drift of accumulated
+            // rotations)
+            std::vector<double> Ub((size_t)kc * r);
+            for (int j = 0; j < r; ++j)
+                for (int a = 0; a < kc; ++a) Ub[(size_t)j * kc + a] = left(j, a);
+            orthonormalize_columns(Ub.data(), kc, r);
             ub[t].assign((size_t)kcp * r8, 0.0);
             vt[t].assign((size_t)r8 * kp, 0.0);
             for (int j = 0; j < r; ++j) {
-                for (int a = 0; a < kc; ++a) ub[t][(size_t)a * r8 + j] = left(j, a);             // Ubar_t[a][j]
-                for (int c = 0; c < k; ++c) vt[t][(size_t)j * kp + c] = sv[j] * right(j, c);    // Vbar'_t^T[j][c]
+                for (int a = 0; a < kc; ++a) ub[t][(size_t)a * r8 + j] = Ub[(size_t)j * kc + a];  // Ubar_t[a][j]
+                for (int c = 0; c < k; ++c) {
+                    double v = 0.0;
+                    for (int a = 0; a < kc; ++a) v += Ub[(size_t)j * kc + a] * C[(size_t)a * k + c];
+                    vt[t][(size_t)j * kp + c] = v;                                               // Vbar'_t^T[j][c]
+                }
             }
         }
         o->kt = kt;

@@ -222,6 +222,7 @@ def test_c5_full_size_batch_sampled(lib):
                 keys = None if wl.keys[l] is None else wl.keys[l].astype(np.int64)
                 _, ref = oracle_level(wl.p, l, ql, keys=keys, targets=tg)
                 assert M.rel_l2_error(ref, got) < 1e-6, (i, wl.p, wl.depth, R, l)
+                assert M.max_target_rel_error(ref, got) < 1e-5, (i, wl.p, wl.depth, R, l)
     finally:
         for m in made:
             m[1].close()

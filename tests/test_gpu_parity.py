@@ -5,8 +5,17 @@ potential they reproduce (oracle.m2l.check_norm_error): the pseudo-inverse ampli
 by up to cond(K_tau) (1e5 at p = 4, 1e9 at p = 6), and the FMM only ever uses the locals
 through potentials they generate (the footnote of Sec. 2.1.1).
 
-Tolerances: FP64 paths 1e-12 (the benchmark spec's bound). FP32 paths: the relative rounding of a
+Tolerances: FP64 paths 1e-12 (the benchmark spec's bound) on check potentials, truncated and
+directional forms included: the plan's compressed and directional operators equal the oracle's
+own to 1e-13 of ||K_t|| (tests/test_capi_host.py), so they add at most a few 1e-14. FP64 locals:
+1e-12, or the backward-error bound of the pseudo-inverse solve where that is larger
+(oracle.m2l.locals_backward_bound: two correct backward-stable solves differ by that much in the
+check norm at p >= 8, where cond(K_tau) reaches 1e12). FP32 paths: the relative rounding of a
 sum of 189 n products in single precision, bounded by 5e-6 on check potentials.
+
+Per target: every full-size test also bounds the largest relative error of a single target box
+(oracle.m2l.max_target_rel_error), since one wrong box among many barely moves the level-wide
+Eq. 16: 1e-11 in FP64, ten times the level-wide bound in single precision.
 """
 import numpy as np
 import pytest
@@ -22,6 +31,12 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 FP32_TOL = 5e-6
+FP64_TARGET_TOL = 1e-11
+
+
+def locals_tol(p, level, L_ref):
+    """FP64 bound on locals in the check norm: 1e-12, or the pseudo-inverse's backward bound."""
+    return max(FP64_TOL, M.locals_backward_bound(p, level, L_ref))
 
 
 def _qs(wl, dtype=np.float64):
@@ -54,7 +69,7 @@ def test_fp64_high_order(lib, form):
         tg = np.arange(0, 8 ** l, max(1, 8 ** l // 24))
         L_ref, phi_ref = oracle_level(8, l, qs[l], targets=tg)
         assert M.rel_l2_error(phi_ref, chk[l][tg]) < FP64_TOL, (form, l)
-        assert M.check_norm_error(8, l, L_ref, loc[l][tg]) < 1e-11, (form, l)
+        assert M.check_norm_error(8, l, L_ref, loc[l][tg]) < locals_tol(8, l, L_ref), (form, l)
 
 
 def test_fft_odd_grid_equals_dense(lib):
@@ -85,7 +100,8 @@ def test_truncated_blas_matches_compressed_oracle(lib):
     ops = O.compressed_operators(p, tol, 1.0)
     for l in wl.levels:
         _, phi_c = M.m2l_compressed(p, l, qs[l], ops)   # unit-width operators: unit check potential
-        assert M.rel_l2_error(phi_c, chk[l]) < 1e-11
+        assert M.rel_l2_error(phi_c, chk[l]) < FP64_TOL
+        assert M.max_target_rel_error(phi_c, chk[l]) < FP64_TARGET_TOL
         _, phi_d = oracle_level(p, l, qs[l])
         assert M.rel_l2_error(phi_d, chk[l]) < 1e-6      # the truncation itself
 
@@ -196,7 +212,9 @@ def test_c2_full_size_sampled(lib, form, precision):
             _, phi_ref = M.m2l_compressed(wl.p, l, qs[l], ops, targets=sample)
         else:
             _, phi_ref = oracle_level(wl.p, l, qs[l], targets=sample)
-        assert M.rel_l2_error(phi_ref, chk[l][sample]) < bound * (10 if form == "blas" else 1), (l,)
+        assert M.rel_l2_error(phi_ref, chk[l][sample]) < bound, (l,)
+        tbound = FP64_TARGET_TOL if precision == "fp64" else 10 * bound
+        assert M.max_target_rel_error(phi_ref, chk[l][sample]) < tbound, (l,)
 
 
 # Directional recompression (Eq. 15). Where the plan and the oracle keep the same k_t (checked on
@@ -216,7 +234,7 @@ def test_directional_contraction_matches_oracle(lib, precision):
     for l in wl.levels:
         L_ref, phi_ref = _directional_ref(5, l, qs[l], 1e-8, 1e-5)
         e = M.rel_l2_error(phi_ref, chk[l])
-        assert e < (1e-10 if precision == "fp64" else FP32_TOL), (precision, l, e)
+        assert e < (FP64_TOL if precision == "fp64" else FP32_TOL), (precision, l, e)
         # and the factorisation stays close to the unfactored operators (about 10 dir_tol)
         _, phi_dense = oracle_level(5, l, qs[l])
         assert M.rel_l2_error(phi_dense, chk[l]) < 1e-3
@@ -231,9 +249,10 @@ def test_directional_sparse_multi_rhs(lib):
     for l in wl.levels:
         k = None if keys[l] is None else keys[l].astype(np.int64)
         L_ref, phi_ref = _directional_ref(wl.p, l, qs[l], 1e-6, 1e-4, keys=k)
-        assert M.rel_l2_error(phi_ref, chk[l]) < 1e-10, l
+        assert M.rel_l2_error(phi_ref, chk[l]) < FP64_TOL, l
         # locals through the unit-width pseudo-inverse of the oracle's check potentials
-        assert M.check_norm_error(wl.p, 0, M.locals_from_check(wl.p, 0, phi_ref), loc[l]) < 1e-9, l
+        L_ref = M.locals_from_check(wl.p, 0, phi_ref)
+        assert M.check_norm_error(wl.p, 0, L_ref, loc[l]) < locals_tol(wl.p, 0, L_ref), l
 
 
 def test_c2_full_size_sampled_directional(lib):
@@ -246,7 +265,8 @@ def test_c2_full_size_sampled_directional(lib):
         B = wl.n_boxes(l)
         sample = np.sort(rng.choice(B, size=min(B, 32), replace=False))
         _, phi_ref = _directional_ref(wl.p, l, qs[l], wl.rank_tol, wl.rank_tol / 10, targets=sample)
-        assert M.rel_l2_error(phi_ref, chk[l][sample]) < 1e-10, l
+        assert M.rel_l2_error(phi_ref, chk[l][sample]) < FP64_TOL, l
+        assert M.max_target_rel_error(phi_ref, chk[l][sample]) < FP64_TARGET_TOL, l
         _, phi_dense = oracle_level(wl.p, l, qs[l], targets=sample)
         assert M.rel_l2_error(phi_dense, chk[l][sample]) < 2e-6, l
 
@@ -278,9 +298,10 @@ def test_check_order_truncated_directional_sparse(lib):
     for l in wl.levels:
         k = None if keys[l] is None else keys[l].astype(np.int64)
         _, phi_ref = M.m2l_compressed(5, l, qs[l], {**ops, **d}, keys=k, p_c=6)
-        assert M.rel_l2_error(phi_ref, chk[l]) < 1e-10, l
+        assert M.rel_l2_error(phi_ref, chk[l]) < FP64_TOL, l
         L_ref = M.locals_from_check(5, 0, phi_ref, p_c=6)
-        assert M.check_norm_error(5, 0, L_ref, loc[l], p_c=6) < 1e-9, l
+        assert M.check_norm_error(5, 0, L_ref, loc[l], p_c=6) < max(
+            FP64_TOL, M.locals_backward_bound(5, 0, L_ref, p_c=6)), l
         _, phi_dense = M.m2l_dense(5, l, qs[l], keys=k, p_c=6)
         assert M.rel_l2_error(phi_dense / 2.0 ** l, chk[l]) < 1e-3, l
 
@@ -395,6 +416,7 @@ def test_c2_full_size_sampled_tensor_cores(lib, precision):
         sample = np.sort(rng.choice(B, size=min(B, 48), replace=False))
         _, phi_ref = M.m2l_compressed(wl.p, l, qs[l], ops, targets=sample)
         assert M.rel_l2_error(phi_ref, chk[l][sample]) < TC_TOL[precision], (precision, l)
+        assert M.max_target_rel_error(phi_ref, chk[l][sample]) < 10 * TC_TOL[precision], (precision, l)
 
 
 # Stated bounds of the single-precision paths for p = 4..10 (the library's autotuner uses the
@@ -437,16 +459,19 @@ def test_c3_full_size_sampled(lib):
     for l in wl.levels:
         _, ref = M.m2l_compressed(wl.p, l, qs[l], ops, targets=samples[l])
         assert M.rel_l2_error(ref, chk[l][samples[l]]) < TC_TOL["bf16x3"], ("bf16x3", l)
+        assert M.max_target_rel_error(ref, chk[l][samples[l]]) < 10 * TC_TOL["bf16x3"], ("bf16x3", l)
     chk = run_gpu(lib, wl.depth, wl.p, qs, rank_tol=wl.rank_tol, output="check", dir_tol=wl.dir_tol)
     d = O.directional_operators(ops["C"], wl.dir_tol)
     for l in wl.levels:
         _, ref = M.m2l_compressed(wl.p, l, qs[l], {**ops, **d}, targets=samples[l])
-        assert M.rel_l2_error(ref, chk[l][samples[l]]) < 1e-10, ("fp64 directional", l)
+        assert M.rel_l2_error(ref, chk[l][samples[l]]) < FP64_TOL, ("fp64 directional", l)
+        assert M.max_target_rel_error(ref, chk[l][samples[l]]) < FP64_TARGET_TOL, ("fp64 directional", l)
         # the truncation at 1e-7 and the directional cut at 1e-8 against the dense definition
         assert M.rel_l2_error(dense[l], chk[l][samples[l]]) < 2e-8, ("fp64 directional vs dense", l)
     chk = run_gpu(lib, wl.depth, wl.p, qs, form="fft", output="check")
     for l in wl.levels:
         assert M.rel_l2_error(dense[l], chk[l][samples[l]]) < FP64_TOL, ("fft fp64", l)
+        assert M.max_target_rel_error(dense[l], chk[l][samples[l]]) < FP64_TARGET_TOL, ("fft fp64", l)
 
 
 def test_c4_full_size_sampled(lib):
@@ -466,7 +491,9 @@ def test_c4_full_size_sampled(lib):
         for l in wl.levels:
             _, ref = M.m2l_compressed(wl.p, l, qs[l], ops, keys=okeys[l], targets=samples[l])
             assert M.rel_l2_error(ref, chk[l][samples[l]]) < TC_TOL[prec], (prec, l)
+            assert M.max_target_rel_error(ref, chk[l][samples[l]]) < 10 * TC_TOL[prec], (prec, l)
     chk = run_gpu(lib, wl.depth, wl.p, qs, keys=keys, form="fft", precision="fp32", output="check", R=wl.n_rhs)
     for l in wl.levels:
         _, ref = oracle_level(wl.p, l, qs[l], keys=okeys[l], targets=samples[l])
         assert M.rel_l2_error(ref, chk[l][samples[l]]) < SINGLE_BOUND[("fft", "fp32")], ("fft fp32", l)
+        assert M.max_target_rel_error(ref, chk[l][samples[l]]) < 10 * SINGLE_BOUND[("fft", "fp32")], ("fft fp32", l)

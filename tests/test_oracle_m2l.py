@@ -381,3 +381,40 @@ def test_tiny_fmm_error_falls_with_order():
     for p, e in gold.items():
         if p in errs:
             assert errs[p] < 10 * e, (p, errs[p], e)
+
+
+@pytest.mark.parametrize("p,density", [(6, "u11"), (8, "normal"), (8, "u01"), (10, "normal")])
+def test_two_backward_stable_pseudo_inverses_agree_within_the_backward_bound(p, density):
+    """The locals of two different backward-stable two-factor solves (LAPACK's divide-and-conquer
+    SVD, which the oracle uses, and its QR-iteration SVD) agree in the check norm within
+    locals_backward_bound, and that bound is not vacuous."""
+    import scipy.linalg as sl
+    from paper_2408_07436_gb300 import workloads as W
+    wl = W.small(depth=3, p=p, density=density, seed=3)
+    level = 3
+    q = wl.multipoles(level)
+    tg = np.arange(0, 512, 21)
+    L, phi = M.m2l_dense(p, level, q, targets=tg)
+    K = M.down_check_matrix(p, level)
+    U, s, Vt = sl.svd(K, lapack_driver="gesvd")
+    keep = s > max(K.shape) * np.finfo(np.float64).eps * s[0]
+    V2, Ut2 = Vt[keep].T, (U[:, keep] / s[keep]).T
+    L2 = np.einsum("ij,brj->bri", V2, np.einsum("ij,brj->bri", Ut2, phi))
+    b = M.locals_backward_bound(p, level, L)
+    assert M.check_norm_error(p, level, L, L2) <= b
+    assert b < 1e-9
+
+
+def test_explicit_pseudo_inverse_matrix_exceeds_the_backward_bound():
+    """Planted: V_eps Ut_eps multiplied out into one matrix before it is applied (what the
+    footnote of Sec. 2.1.1 warns against) is no backward-stable solve at p = 8, and the bound
+    says so."""
+    from paper_2408_07436_gb300 import workloads as W
+    p, level = 8, 3
+    wl = W.small(depth=3, p=p, density="u01", seed=3)
+    q = wl.multipoles(level)
+    tg = np.arange(0, 512, 21)
+    L, phi = M.m2l_dense(p, level, q, targets=tg)
+    V, Ut = O.down_pinv(p, level)
+    L_bad = np.einsum("ij,brj->bri", V @ Ut, phi)
+    assert M.check_norm_error(p, level, L, L_bad) > 10 * M.locals_backward_bound(p, level, L)

@@ -135,3 +135,60 @@ def test_directional_swapped_factors_are_caught():
         return d
     assert not _directional_worst_error(bad) < 1e-5
 
+
+
+def _check_norm_case(seed=5, p=6, level=3):
+    """Locals of a check potential phi from far point sources, and of phi + e with a second far
+    field e scaled to 1e-6 of phi: the comparator must report ||e|| / ||phi||, because K_tau
+    (K_tau)^+ reproduces a smooth check potential. Built by direct kernel evaluation and the
+    pseudo-inverse only; no M2L code."""
+    rng = np.random.default_rng(seed)
+    w = G.box_width(level)
+    x = G.surface_points(p, np.zeros(3), w, G.ALPHA_INNER)
+    s1 = rng.random((40, 3)) * w + np.array([3.0 * w, -w, 0.5 * w])
+    s2 = rng.random((40, 3)) * w + np.array([-2.5 * w, 2.0 * w, -3.0 * w])
+    phi = O.laplace(x, s1) @ rng.random(40)
+    e = O.laplace(x, s2) @ rng.standard_normal(40)
+    e *= 1e-6 * np.linalg.norm(phi) / np.linalg.norm(e)
+    L = M.locals_from_check(p, level, phi[None, None, :])
+    Le = M.locals_from_check(p, level, (phi + e)[None, None, :])
+    return p, level, L, Le
+
+
+def test_check_norm_comparator_reports_the_check_potential_difference():
+    p, level, L, Le = _check_norm_case()
+    assert abs(M.check_norm_error(p, level, L, Le) - 1e-6) < 1e-11
+    assert M.check_norm_error(p, level, L, L) == 0.0
+
+
+def test_check_norm_comparator_with_swapped_radii_is_caught(monkeypatch):
+    """The comparator's K_tau built with the two radii exchanged (check points on the outer
+    surface, equivalent points on the inner one)."""
+    def bad(p, level, root_width=1.0, p_c=None):
+        w = G.box_width(level, root_width)
+        return O.laplace(G.surface_points(p, np.zeros(3), w, G.ALPHA_OUTER),
+                         G.surface_points(p, np.zeros(3), w, G.ALPHA_INNER))
+    monkeypatch.setattr(M, "down_check_matrix", bad)
+    p, level, L, Le = _check_norm_case()
+    assert not abs(M.check_norm_error(p, level, L, Le) - 1e-6) < 1e-11
+
+
+def test_check_norm_comparator_without_the_kernel_matrix_is_caught(monkeypatch):
+    """Locals compared directly (K_tau replaced by the identity): the pseudo-inverse's
+    amplification of the small perturbation then shows. (A wrong box width is no mistake here:
+    K_tau scales as 1/w, and Eq. 16 is relative.)"""
+    monkeypatch.setattr(M, "down_check_matrix", lambda p, level, root_width=1.0, p_c=None: np.eye(G.n_surface(p)))
+    p, level, L, Le = _check_norm_case()
+    assert not abs(M.check_norm_error(p, level, L, Le) - 1e-6) < 1e-11
+
+
+def test_per_target_error_finds_one_wrong_box():
+    """One wrong box among 4,096 moves the level-wide Eq. 16 by about 1/64 of its own error; the
+    per-target maximum reports it whole."""
+    rng = np.random.default_rng(2)
+    ref = rng.random((4096, 1, 56))
+    bad = ref.copy()
+    bad[1234, 0] *= 1.5
+    assert M.rel_l2_error(ref, bad) < 0.5 / 50
+    assert abs(M.max_target_rel_error(ref, bad) - 0.5) < 1e-12
+    assert M.max_target_rel_error(ref, ref) == 0.0
