@@ -205,6 +205,15 @@ int m2l_set_boxes(m2l_plan_t *plan, int level, const uint64_t *keys, long long n
 int m2l_apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *multipoles,
                     void *const *locals, const int *n_rhs);
 
+/* The relative error bound the library states for a (form, precision) at order p, the one
+ * M2L_FORM_AUTO / M2L_PREC_AUTO compare with M2L_OPT_TARGET_TOL: Eq. 16 on the check potential
+ * (and on the locals through the check potential they reproduce) against the FP64 definition,
+ * before any rank truncation. Measured per p = 4..10 over uniform, signed, Gaussian and physical
+ * (P2M + M2M) multipoles with a margin of at least 1.8. form: M2L_FORM_BLAS or M2L_FORM_FFT;
+ * precision: M2L_PREC_FP64..M2L_PREC_BF16X3 (the FFT form offers FP64 and FP32 only).
+ * Returns M2L_OK, or M2L_EINVAL for a NULL out, a bad form, precision or p outside [2, 16]. */
+int m2l_stated_bound(int form, int precision, int p, double *bound);
+
 /* Integer facts about a plan (enum m2l_query_e). `level` is used by M2L_Q_BOXES/PAIRS. */
 int m2l_query(const m2l_plan_t *plan, int what, int level, long long *out);
 

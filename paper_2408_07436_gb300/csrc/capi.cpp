@@ -521,6 +521,18 @@ int m2l_get_operator(m2l_plan_t *pl, int which, double *dst, long long *count) {
     return M2L_OK;
 }
 
+int m2l_stated_bound(int form, int precision, int p, double *bound) {
+    clear_error();
+    if (!bound || (form != M2L_FORM_BLAS && form != M2L_FORM_FFT) || precision < M2L_PREC_FP64 ||
+        precision > M2L_PREC_BF16X3 || p < 2 || p > 16 ||
+        (form == M2L_FORM_FFT && precision != M2L_PREC_FP64 && precision != M2L_PREC_FP32)) {
+        set_error("m2l_stated_bound: bad form %d, precision %d or order %d", form, precision, p);
+        return M2L_EINVAL;
+    }
+    *bound = stated_bound(form, precision, p);
+    return M2L_OK;
+}
+
 int m2l_selftest_watchdog(m2l_plan_t *pl, long long polls) {
     clear_error();
     if (!pl || pl->device < 0) {

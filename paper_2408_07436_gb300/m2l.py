@@ -184,6 +184,16 @@ def m2l_get_operator(plan, which: int):
     return buf
 
 
+_lib.m2l_stated_bound.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+_lib.m2l_stated_bound.restype = ctypes.c_int
+
+
+def m2l_stated_bound(form: int, precision: int, p: int) -> float:
+    out = ctypes.c_double(0.0)
+    _check(_lib.m2l_stated_bound(form, precision, p, ctypes.byref(out)))
+    return out.value
+
+
 class Plan:
     """A plan handle bound to torch tensors (device or host) and the current torch stream."""
 

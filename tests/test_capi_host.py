@@ -42,6 +42,19 @@ def test_peak_probe_exports_its_declared_symbol():
     assert peaks._lib.m2l_fma_peak(0, 0, 1, None, None, None) == -1   # iters < 1: refused before any launch
 
 
+def test_stated_bounds_match_the_tests_table(lib):
+    from bounds import stated
+    for p in range(2, 17):
+        for form, precs in (("blas", ("fp64", "fp32", "tf32x3", "bf16x3")), ("fft", ("fp64", "fp32"))):
+            for prec in precs:
+                got = lib.m2l_stated_bound(lib.FORMS[form], lib.PRECISIONS[prec], p)
+                assert got == stated(form, prec, p), (form, prec, p)
+    with pytest.raises(lib.M2LError):
+        lib.m2l_stated_bound(lib.M2L_FORM_FFT, lib.M2L_PREC_TF32X3, 6)   # no tensor-core FFT form
+    with pytest.raises(lib.M2LError):
+        lib.m2l_stated_bound(lib.M2L_FORM_BLAS, lib.M2L_PREC_FP32, 1)
+
+
 def test_plan_rejects_bad_arguments(lib):
     for args, word in [((1, 4, 0, 0.0), "depth"), ((9, 4, 0, 0.0), "depth"), ((3, 1, 0, 0.0), "order"),
                        ((3, 4, 7, 0.0), "kernel"), ((3, 4, 0, float("nan")), "rank_tol")]:
