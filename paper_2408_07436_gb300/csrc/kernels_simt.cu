@@ -2,6 +2,7 @@
 // (compress S^T q, uncompress + pseudo-inverse), the gathered contraction over the 189
 // transfer vectors of each target octant, and the three stages of the FFT form.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <type_traits>
 
@@ -20,6 +21,18 @@ namespace m2l {
 __constant__ short c_tidx[7][7][7];
 __constant__ short c_clu[26][64];
 __constant__ signed char c_dir[26][3];
+// exp(-2 pi i m / g) for m in [0, g), for the grid sides of the FP32 transforms specialised on
+// (p, g): g = 2p - 1 and 2p for p = 4, 6, 8, 10, stored one after another (twiddle_offset).
+__constant__ float2 c_twf[108];
+constexpr int kTwiddleSides[8] = {7, 8, 11, 12, 15, 16, 19, 20};
+__host__ __device__ constexpr int twiddle_offset(int g) {
+    int off = 0;
+    for (int i = 0; i < 8; ++i) {
+        if (kTwiddleSides[i] == g) return off;
+        off += kTwiddleSides[i];
+    }
+    return -1;
+}
 
 static void cache_launch_shapes();
 
@@ -49,7 +62,14 @@ int ensure_constants(int device) {
                     }
                 ++d;
             }
-    if (cudaMemcpyToSymbol(c_tidx, tidx, sizeof tidx) != cudaSuccess ||
+    float2 twf[108];
+    for (int i = 0, off = 0; i < 8; off += kTwiddleSides[i], ++i)
+        for (int m = 0; m < kTwiddleSides[i]; ++m) {
+            const double a = -2.0 * M_PI * m / kTwiddleSides[i];
+            twf[off + m] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    if (cudaMemcpyToSymbol(c_twf, twf, sizeof twf) != cudaSuccess ||
+        cudaMemcpyToSymbol(c_tidx, tidx, sizeof tidx) != cudaSuccess ||
         cudaMemcpyToSymbol(c_clu, clu, sizeof clu) != cudaSuccess ||
         cudaMemcpyToSymbol(c_dir, dir, sizeof dir) != cudaSuccess) {
         set_error("uploading constant tables failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -730,6 +750,203 @@ __global__ void __launch_bounds__(128) fft_forward_kernel(LevelView L, int R, in
     }
 }
 
+// The FP32 transforms specialised on (P, G): each thread owns whole lines of the pruned
+// separable DFT and keeps them in registers; twiddles are read from c_twf at indices fixed at
+// compile time (no index arithmetic or table lookups in the sums). One CTA of round_up(G H, 32)
+// threads per (box, rhs).
+template <int G>
+__device__ __forceinline__ float2 twf(int m) {
+    return c_twf[twiddle_offset(G) + m % G];
+}
+template <int P, int G>
+constexpr int fft_pg_threads() {
+    return ((G * (G / 2 + 1)) + 31) / 32 * 32;
+}
+
+// Forward: embed, then z (real -> kz in [0, H)), y, x; the x stage writes the spectrum.
+template <int P, int G>
+__global__ void __launch_bounds__(fft_pg_threads<P, G>()) fft_forward_pg_kernel(LevelView L, int R, int n,
+                                                                                 const int *__restrict__ lattice,
+                                                                                 const float *__restrict__ q,
+                                                                                 float *__restrict__ qhat) {
+    constexpr int H = G / 2 + 1, GH = G * H, F = G * GH;
+    __shared__ float xs[P * P * P];
+    __shared__ float2 Y1[P * P * H];  // [a][b][kz]
+    __shared__ float2 Y2[P * GH];     // [a][ky][kz]
+    const long long row = blockIdx.x + (long long)blockIdx.y * gridDim.x;
+    if (row >= L.nboxes * R) return;
+    const long long b = row / R;
+    const int r = (int)(row % R), tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < P * P * P; i += nt) xs[i] = 0.f;
+    __syncthreads();
+    const float *qrow = q + (b * L.R + L.row0 + r) * (long long)n;
+    for (int i = tid; i < n; i += nt) {
+        const int lat = lattice[i];
+        xs[((lat >> 16) * P + ((lat >> 8) & 255)) * P + (lat & 255)] = qrow[i];
+    }
+    __syncthreads();
+    for (int e = tid; e < P * P; e += nt) {  // line (a, b) along z
+        float x[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) x[c] = xs[e * P + c];
+#pragma unroll
+        for (int kz = 0; kz < H; ++kz) {
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                const float2 w = twf<G>(c * kz);
+                re = fmaf(x[c], w.x, re);
+                im = fmaf(x[c], w.y, im);
+            }
+            Y1[e * H + kz] = make_float2(re, im);
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < P * H; e += nt) {  // line (a, kz) along y
+        const int a = e / H, kz = e % H;
+        float2 y[P];
+#pragma unroll
+        for (int bb = 0; bb < P; ++bb) y[bb] = Y1[(a * P + bb) * H + kz];
+#pragma unroll
+        for (int ky = 0; ky < G; ++ky) {
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int bb = 0; bb < P; ++bb) {
+                const float2 w = twf<G>(bb * ky);
+                re = fmaf(y[bb].x, w.x, fmaf(-y[bb].y, w.y, re));
+                im = fmaf(y[bb].x, w.y, fmaf(y[bb].y, w.x, im));
+            }
+            Y2[(a * G + ky) * H + kz] = make_float2(re, im);
+        }
+    }
+    __syncthreads();
+    const uint32_t xyz = L.xyz[b];
+    const int cl = L.cslot[parent_linear(xyz, L.N / 2)];
+    float2 *out = reinterpret_cast<float2 *>(qhat) + (((L.cbase + cl) * R + r) * 8 + octant_of(xyz)) * (long long)F;
+    if (tid < GH) {  // line (ky, kz) along x, written for every kx
+        float2 y[P];
+#pragma unroll
+        for (int a = 0; a < P; ++a) y[a] = Y2[a * GH + tid];
+#pragma unroll
+        for (int kx = 0; kx < G; ++kx) {
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int a = 0; a < P; ++a) {
+                const float2 w = twf<G>(a * kx);
+                re = fmaf(y[a].x, w.x, fmaf(-y[a].y, w.y, re));
+                im = fmaf(y[a].x, w.y, fmaf(y[a].y, w.x, im));
+            }
+            out[kx * GH + tid] = make_float2(re, im);
+        }
+    }
+}
+
+// Inverse: x (read straight from the spectrum, one column per thread), y, then z at the lattice
+// cube, scaled by 1 / G^3, and the surface points gathered from the cube.
+template <int P, int G>
+__global__ void __launch_bounds__(fft_pg_threads<P, G>()) fft_inverse_pg_kernel(LevelView L, int R, int n,
+                                                                                 const int *__restrict__ lattice,
+                                                                                 const float *__restrict__ phihat,
+                                                                                 float *__restrict__ phi, long long ldphi,
+                                                                                 int acc) {
+    constexpr int H = G / 2 + 1, GH = G * H, F = G * GH;
+    __shared__ float2 Z1[P * GH];     // [a][ky][kz]
+    __shared__ float2 Z2[P * P * H];  // [a][b][kz]
+    __shared__ float cube[P * P * P];
+    const long long row = blockIdx.x + (long long)blockIdx.y * gridDim.x;
+    if (row >= L.nboxes * R) return;
+    const long long b = row / R;
+    const int r = (int)(row % R), tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t xyz = L.xyz[b];
+    const int cl = L.cslot[parent_linear(xyz, L.N / 2)];
+    const float2 *in = reinterpret_cast<const float2 *>(phihat) + (((L.cbase + cl) * R + r) * 8 + octant_of(xyz)) * (long long)F;
+    if (tid < GH) {  // column (ky, kz) along x, for a < P
+        float2 x[G];
+#pragma unroll
+        for (int kx = 0; kx < G; ++kx) x[kx] = in[kx * GH + tid];
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int kx = 0; kx < G; ++kx) {
+                const float2 w = twf<G>(a * kx);  // times conj(w)
+                re = fmaf(x[kx].x, w.x, fmaf(x[kx].y, w.y, re));
+                im = fmaf(x[kx].y, w.x, fmaf(-x[kx].x, w.y, im));
+            }
+            Z1[a * GH + tid] = make_float2(re, im);
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < P * H; e += nt) {  // line (a, kz) along y, for b < P
+        const int a = e / H, kz = e % H;
+        float2 y[G];
+#pragma unroll
+        for (int ky = 0; ky < G; ++ky) y[ky] = Z1[(a * G + ky) * H + kz];
+#pragma unroll
+        for (int bb = 0; bb < P; ++bb) {
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int ky = 0; ky < G; ++ky) {
+                const float2 w = twf<G>(bb * ky);
+                re = fmaf(y[ky].x, w.x, fmaf(y[ky].y, w.y, re));
+                im = fmaf(y[ky].y, w.x, fmaf(-y[ky].x, w.y, im));
+            }
+            Z2[(a * P + bb) * H + kz] = make_float2(re, im);
+        }
+    }
+    __syncthreads();
+    // along z, Hermitian: v(c) = Re Z2[0] + sum_{kz >= 1} wgt Re(Z2[kz] e^{+2 pi i c kz / G})
+    constexpr float scale = 1.f / (float)(G * G * G);
+    for (int e = tid; e < P * P; e += nt) {
+        float2 z[H];
+#pragma unroll
+        for (int kz = 0; kz < H; ++kz) z[kz] = Z2[e * H + kz];
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+            float v = z[0].x;
+#pragma unroll
+            for (int kz = 1; kz < H; ++kz) {
+                const float wgt = (G % 2 == 0 && kz == H - 1) ? 1.f : 2.f;
+                const float2 w = twf<G>(c * kz);
+                v = fmaf(wgt, fmaf(z[kz].x, w.x, z[kz].y * w.y), v);
+            }
+            cube[e * P + c] = v * scale;
+        }
+    }
+    __syncthreads();
+    float *outrow = phi + (b * L.R + L.row0 + r) * ldphi;
+    for (int i = tid; i < n; i += nt) {
+        const int lat = lattice[i];
+        float v = cube[((lat >> 16) * P + ((lat >> 8) & 255)) * P + (lat & 255)];
+        if (acc) v += outrow[i];
+        outrow[i] = v;
+    }
+}
+
+// Launch the (P, G) specialisation for the FP32 transforms, if there is one; false otherwise.
+template <int P, int G>
+static void launch_pg(bool forward, const LevelView &L, int R, int n, const int *lattice, const float *in, float *out,
+                      long long ldphi, int acc, dim3 grid, cudaStream_t s) {
+    if (forward)
+        fft_forward_pg_kernel<P, G><<<grid, fft_pg_threads<P, G>(), 0, s>>>(L, R, n, lattice, in, out);
+    else
+        fft_inverse_pg_kernel<P, G><<<grid, fft_pg_threads<P, G>(), 0, s>>>(L, R, n, lattice, in, out, ldphi, acc);
+}
+static bool launch_fft_pg(bool forward, const LevelView &L, int R, int p, int n, int g, const int *lattice,
+                          const float *in, float *out, long long ldphi, int acc, dim3 grid, cudaStream_t s) {
+    switch (p * 100 + g) {
+        case 407: launch_pg<4, 7>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
+        case 408: launch_pg<4, 8>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
+        case 611: launch_pg<6, 11>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
+        case 612: launch_pg<6, 12>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
+        case 815: launch_pg<8, 15>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
+        case 816: launch_pg<8, 16>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
+        case 1019: launch_pg<10, 19>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
+        case 1020: launch_pg<10, 20>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
+        default: return false;
+    }
+}
+
 template <class T>
 static size_t fft_forward_smem(int p, int g) {
     int H = g / 2 + 1;
@@ -747,11 +964,15 @@ int launch_fft_forward(const LevelView &L, int R, int p, int n, int g, const int
                        const T *q, T *qhat, cudaStream_t s) {
     long long rows = L.nboxes * R;
     if (rows <= 0) return M2L_OK;
+    unsigned gx = (unsigned)(rows < 65535 ? rows : 65535);
+    unsigned gy = (unsigned)((rows + gx - 1) / gx);
+    if constexpr (sizeof(T) == 4) {
+        if (launch_fft_pg(true, L, R, p, n, g, lattice, (const float *)q, (float *)qhat, 0, 0, dim3(gx, gy), s))
+            return check_launch("fft_forward");
+    }
     size_t smem = fft_forward_smem<T>(p, g);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(fft_forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    unsigned gx = (unsigned)(rows < 65535 ? rows : 65535);
-    unsigned gy = (unsigned)((rows + gx - 1) / gx);
     fft_forward_kernel<T><<<dim3(gx, gy), 128, smem, s>>>(L, R, p, n, g, lattice, tw, q, qhat);
     return check_launch("fft_forward");
 }
@@ -868,6 +1089,140 @@ __global__ void __launch_bounds__(256) hadamard_kernel(LevelView L, int R, int F
                 v.x = ar[b][i];
                 v.y = ai[b][i];
                 out[(long long)i * F] = v;
+            }
+        }
+    }
+}
+
+// F3 in FP32 on dense levels. The kernel spectra of a block of 16 frequencies sit in shared
+// memory on the 7 x 7 x 7 grid of transfer vectors t in [-3,3]^3, with zeros at the 27 adjacent
+// offsets |t| <= 1. The transfer vector of target sibling i and source sibling j in direction d is
+// t = 2 d + j - i (App. A.1), so its grid index is a per-direction base plus an offset fixed by
+// (i, j): with i and j unrolled, every kernel value is one shared load at an immediate offset,
+// with no table lookup, index arithmetic or branch. The 152 adjacent products of the 26 x 64
+// (App. A.2's "~10%") are multiplied by those zeros rather than skipped. The source sibling j is
+// the outer loop, so each loaded source value feeds 8 targets, and each kernel value serves the
+// IB items (target cluster, rhs) of the thread.
+template <int IB>
+__global__ void __launch_bounds__(256, 2) hadamard_grid_kernel(LevelView L, int R, int F, const float *__restrict__ Khat,
+                                                               const float *__restrict__ qhat, float *__restrict__ phihat) {
+    constexpr int FB = 16, TC = 256 / FB, NI = TC * IB;
+    __shared__ float2 Ks[343 * FB];
+    __shared__ int s_src[NI][kDirections];  // source row (cluster * R + rhs) of each item and direction, -1: none
+    __shared__ int s_dst[NI];                // target row of each item, -1: past the end
+    __shared__ int s_mask[NI];               // directions with a source, one bit each
+    const int f0 = blockIdx.y * FB;
+    for (int e = threadIdx.x; e < 343 * FB; e += blockDim.x) {
+        const int g3 = e / FB, f = f0 + e % FB;
+        const int ti = c_tidx[g3 / 49][(g3 / 7) % 7][g3 % 7];
+        float2 k = make_float2(0.f, 0.f);
+        if (ti >= 0 && f < F) {
+            k.x = Khat[((long long)ti * F + f) * 2];
+            k.y = Khat[((long long)ti * F + f) * 2 + 1];
+        }
+        Ks[e] = k;
+    }
+    const int fl = threadIdx.x % FB, tcl = threadIdx.x / FB;
+    const int f = f0 + fl;
+    const bool fvalid = f < F;  // threads past F still take part in the block's barriers
+    const int Np = L.N / 2;
+    const long long items = L.nclusters * R;
+    const long long F8 = (long long)F * 8;
+    const float2 *q2 = reinterpret_cast<const float2 *>(qhat) + (fvalid ? f : 0);
+    float2 *o2 = reinterpret_cast<float2 *>(phihat) + f;
+    const float2 *kf = Ks + fl;
+    for (long long base = (long long)blockIdx.x * NI; base < items; base += (long long)gridDim.x * NI) {
+        __syncthreads();  // the spectra block is in place, and the previous group's tables are consumed
+        for (int e = threadIdx.x; e < NI * kDirections; e += blockDim.x) {
+            const int li = e / kDirections, d = e % kDirections;
+            const long long it = base + li;
+            int src = -1;
+            if (it < items) {
+                const long long tc = L.cperm[it / R];
+                const int r = (int)(it % R);
+                const uint32_t pc = L.cxyz[tc];
+                const int sx = (int)(pc & 1023) + c_dir[d][0], sy = (int)((pc >> 10) & 1023) + c_dir[d][1],
+                          sz = (int)((pc >> 20) & 1023) + c_dir[d][2];
+                if (sx >= 0 && sy >= 0 && sz >= 0 && sx < Np && sy < Np && sz < Np) {
+                    const int sc = L.cslot[((long long)sz * Np + sy) * Np + sx];
+                    if (sc >= 0) src = (int)((L.cbase + sc) * R + r);
+                }
+                if (d == 0) s_dst[li] = (int)((L.cbase + tc) * R + r);
+            } else if (d == 0) {
+                s_dst[li] = -1;
+            }
+            s_src[li][d] = src;
+        }
+        __syncthreads();
+        if (threadIdx.x < NI) {
+            int m = 0;
+            for (int d = 0; d < kDirections; ++d) m |= (s_src[threadIdx.x][d] >= 0) << d;
+            s_mask[threadIdx.x] = m;
+        }
+        __syncthreads();
+        int mask = 0;
+#pragma unroll
+        for (int b = 0; b < IB; ++b) mask |= s_mask[tcl * IB + b];
+        float ar[IB][8], ai[IB][8];
+#pragma unroll
+        for (int b = 0; b < IB; ++b)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) ar[b][i] = ai[b][i] = 0.f;
+        int srow[IB];
+        float2 qn[IB];
+        if (mask) {
+            const int d0 = __ffs(mask) - 1;
+#pragma unroll
+            for (int b = 0; b < IB; ++b) {
+                srow[b] = s_src[tcl * IB + b][d0];
+                qn[b] = srow[b] >= 0 ? q2[srow[b] * F8] : make_float2(0.f, 0.f);
+            }
+        }
+        while (mask) {
+            const int d = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int dn = mask ? __ffs(mask) - 1 : -1;  // the next direction with a source
+            int snext[IB];
+#pragma unroll
+            for (int b = 0; b < IB; ++b) snext[b] = dn >= 0 ? s_src[tcl * IB + b][dn] : -1;
+            const int dx = c_dir[d][0], dy = c_dir[d][1], dz = c_dir[d][2];
+            // grid index of t = 2 d + j - i: base of j = 0, i = 0, plus (j offset) - (i offset)
+            const float2 *kd = kf + ((2 * dx + 3) * 49 + (2 * dy + 3) * 7 + (2 * dz + 3)) * FB;
+#pragma unroll 1
+            for (int j = 0; j < 8; ++j) {
+                float2 q[IB];
+#pragma unroll
+                for (int b = 0; b < IB; ++b) q[b] = qn[b];
+                // the values of the next sibling, or of the next direction's first, are in flight
+                // while these are used
+#pragma unroll
+                for (int b = 0; b < IB; ++b) {
+                    const int sr = j < 7 ? srow[b] : snext[b];
+                    const long long off = j < 7 ? (long long)(j + 1) * F : 0;
+                    qn[b] = sr >= 0 ? q2[sr * F8 + off] : make_float2(0.f, 0.f);
+                }
+                const float2 *kj = kd + ((j & 1) * 49 + ((j >> 1) & 1) * 7 + ((j >> 2) & 1)) * FB;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float2 k = kj[-((i & 1) * 49 + ((i >> 1) & 1) * 7 + ((i >> 2) & 1)) * FB];
+#pragma unroll
+                    for (int b = 0; b < IB; ++b) {
+                        ar[b][i] = fmaf(k.x, q[b].x, fmaf(-k.y, q[b].y, ar[b][i]));
+                        ai[b][i] = fmaf(k.x, q[b].y, fmaf(k.y, q[b].x, ai[b][i]));
+                    }
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < IB; ++b) srow[b] = snext[b];
+        }
+        if (fvalid) {
+#pragma unroll
+            for (int b = 0; b < IB; ++b) {
+                const int dst = s_dst[tcl * IB + b];
+                if (dst < 0) continue;
+                float2 *out = o2 + dst * F8;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) out[(long long)i * F] = make_float2(ar[b][i], ai[b][i]);
             }
         }
     }
@@ -1000,9 +1355,57 @@ static int hadamard_resident() {
     return resident;
 }
 
+constexpr int kGridIB = 4;  // items per thread of hadamard_grid_kernel
+
+static int hadamard_grid_resident() {
+    static int resident = 0;
+    if (!resident) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hadamard_grid_kernel<kGridIB>, 256, 0) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        resident = per_sm * sm_count();
+    }
+    return resident;
+}
+
 static void cache_launch_shapes() {
     hadamard_resident<float>();
     hadamard_resident<double>();
+    hadamard_grid_resident();
+}
+
+// Item groups per thread for a launch of `groups` item groups over gy frequency blocks: every CTA
+// does ipt iterations, so the launch takes about ceil(CTAs / resident) x ipt iteration times; the
+// ipt in 1..16 that makes this smallest (a partial last wave costs as much as a full one), the
+// larger on ties (fewer CTAs load the spectra block).
+static long long items_per_thread(long long groups, long long gy, int resident) {
+    long long ipt = 1, best = -1;
+    for (long long c = 1; c <= 16; ++c) {
+        const long long ctas = (groups + c - 1) / c * gy;
+        const long long cost = (ctas + resident - 1) / resident * c;
+        if (best < 0 || cost <= best) {
+            best = cost;
+            ipt = c;
+        }
+    }
+    return ipt;
+}
+
+static int launch_hadamard_grid(const LevelView &L, int R, int F, const float *Khat, const float *qhat, float *phihat,
+                                cudaStream_t s) {
+    constexpr int FB = 16, TC = 256 / FB;
+    const long long items = L.nclusters * R;
+    const unsigned gy = (unsigned)((F + FB - 1) / FB);
+    const long long groups = (items + TC * kGridIB - 1) / (TC * kGridIB);
+    const long long ipt = items_per_thread(groups, gy, hadamard_grid_resident());
+    long long gx = (groups + ipt - 1) / ipt;
+    if (gx < 1) gx = 1;
+    if (gx > (1LL << 30)) gx = 1LL << 30;
+    hadamard_grid_kernel<kGridIB><<<dim3((unsigned)gx, gy), 256, 0, s>>>(L, R, F, Khat, qhat, phihat);
+    return check_launch("hadamard");
 }
 
 template <class T>
@@ -1015,6 +1418,11 @@ int launch_hadamard(const LevelView &L, int R, int F, const T *Khat, const T *qh
     // larger spectra block halves the resident warps (measured 4.4 ms against 7.8 ms on the
     // 1M-point workload, 52 ms against 98 ms on the sphere surface with 32 right-hand sides).
     const bool sparse = L.nboxes * 4 < L.nclusters * 8 * 3;  // fewer than 6 of 8 children on average
+    if constexpr (sizeof(T) == 4) {
+        // FP32 on dense levels: spectra on the transfer-vector grid, four items per thread (the
+        // consecutive right-hand sides of a cluster when R > 1)
+        if (!sparse) return launch_hadamard_grid(L, R, F, Khat, qhat, phihat, s);
+    }
     if (R >= 2) return launch_hadamard_warp<T, 2>(L, R, F, Khat, qhat, phihat, s);
     if (sparse) return launch_hadamard_warp<T, 1>(L, R, F, Khat, qhat, phihat, s);
     // FP32 takes two items per thread (its shared-memory loads, not its FMAs, were the limit);
@@ -1133,11 +1541,15 @@ int launch_fft_inverse(const LevelView &L, int R, int p, int n, int g, const int
                        const T *phihat, T *phi, long long ldphi, int acc, cudaStream_t s) {
     long long rows = L.nboxes * R;
     if (rows <= 0) return M2L_OK;
+    unsigned gx = (unsigned)(rows < 65535 ? rows : 65535);
+    unsigned gy = (unsigned)((rows + gx - 1) / gx);
+    if constexpr (sizeof(T) == 4) {
+        if (launch_fft_pg(false, L, R, p, n, g, lattice, (const float *)phihat, (float *)phi, ldphi, acc, dim3(gx, gy), s))
+            return check_launch("fft_inverse");
+    }
     size_t smem = fft_inverse_smem<T>(p, g);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(fft_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    unsigned gx = (unsigned)(rows < 65535 ? rows : 65535);
-    unsigned gy = (unsigned)((rows + gx - 1) / gx);
     fft_inverse_kernel<T><<<dim3(gx, gy), 128, smem, s>>>(L, R, p, n, g, lattice, tw, phihat, phi, ldphi, acc);
     return check_launch("fft_inverse");
 }
