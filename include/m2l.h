@@ -83,6 +83,10 @@ enum m2l_option_e {
                                 dir_tol > 0 each C_t is factored as Ubar_t Vbar'_t^T keeping its
                                 singular values >= dir_tol s_0(C_t), and the CUDA-core contraction
                                 (FP64, FP32) applies the two factors; the tensor-core forms keep C_t */
+    M2L_OPT_TC_CHUNK = 11,   /* split tensor-core forms: bytes of K per pipeline stage of the contraction,
+                                32, 64 or 128 (0: 128, the default). Smaller stages fit more of them in
+                                shared memory (deeper prefetch of the gathered rows) at more barrier
+                                round trips per MMA; the result does not depend on it */
     M2L_OPT_CHECK_ORDER = 10 /* order p_c of the downward check surface, p <= p_c <= 16 (0: p, the
                                 default). p_c > p gives n_c = 6(p_c-1)^2+2 check points for the n
                                 equivalent points (the BLAS tables' P_c > P_e): K_t and the

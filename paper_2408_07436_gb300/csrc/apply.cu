@@ -612,6 +612,7 @@ int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void
                                     r.pl->exec.tvl, D.C, D.C_hi, D.C_lo, D.Ub, D.Vt, D.dir_meta, D.Khat, D.A, D.V, D.Vlo})
                 sig.push_back((long long)(uintptr_t)ptr);
             sig.push_back(r.pl->tc_group);
+            sig.push_back(r.pl->tc_chunk);
             sig.push_back(r.pl->fft_grid_opt);
         }
     }

@@ -74,7 +74,8 @@ struct DevOps {
     void *Ub = nullptr, *Vt = nullptr;      // directional factors (Eq. 15): Ubar_t [k_pad][k_t8],
                                             // Vbar'_t^T [k_t8][k_pad], concatenated over t
     void *dir_meta = nullptr;               // [316] int4: Ub offset, Vt offset, k_t, k_t8
-    alignas(64) unsigned char tmap[2][128] = {};  // TMA maps (CUtensorMap) of C_hi and C_lo
+    alignas(64) unsigned char tmap[3][2][128] = {};  // TMA maps (CUtensorMap) of C_hi and C_lo per stage
+                                                     // width of the tensor-core contraction (32, 64, 128 B)
     // FFT form
     void *Khat = nullptr;        // [316+1][F] complex kernel spectra (last row zero)
     void *Ut = nullptr;          // [rp][np_]   Ut_eps
@@ -134,6 +135,7 @@ struct m2l_plan_s {
     double target_tol = 1e-6;
     int fft_grid_opt = 0;
     int tc_group = 1;                           // transfer vectors per tensor-memory partial sum
+    int tc_chunk = 0;                           // bytes of K per tensor-core pipeline stage (0: default)
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 148;

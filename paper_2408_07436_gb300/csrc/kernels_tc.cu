@@ -7,15 +7,17 @@
 // result for TF32 pieces, about 2^-16 relative for BF16 pieces).
 //
 // One persistent CTA per SM loops over tiles of 128 (target, rhs) rows of one octant of one
-// level. Per (tile, t, 128-byte K chunk) a pipeline stage holds
-//   A_hi, A_lo: the 128 gathered source rows of q~: cp.async, 8 lanes per 128-byte row piece so
-//               every request is a full line, written with the 128-byte swizzle (measured faster
-//               than TMA tile::gather4 row gathers for these 128-byte pieces);
-//   B_hi, B_lo: the chunk of C_t (k_pad x 128 bytes), loaded by TMA with SWIZZLE_128B.
-// Warps: 0-3 gather A (the next transfer vector's source rows are looked up while the current
-// chunks are in flight); 4 issues TMA for B; 5 owns tensor memory and issues the MMAs (M = 128
-// rows, N = k_pad, K = 32 bytes per instruction); 6-9 drain each transfer vector's partial sum
-// (double-buffered in tensor memory) into the running sum.
+// level. A pipeline stage is one MMA step of K (32 bytes: 16 BF16 or 8 TF32 values) of
+//   A_hi, A_lo: the 128 gathered source rows of q~ (32 bytes each), cp.async by one producer
+//               thread per row, written in the 32-byte swizzle;
+//   B_hi, B_lo: the step of C_t (k_pad rows x 32 bytes), loaded by TMA with SWIZZLE_32B.
+// A stage is 8 KB + 64 k_pad bytes (19 KB at k_pad = 176), so about ten stages are in flight and
+// the gathers' L2 latency is covered; with 128-byte stages only two fit and every stage waited a
+// full round trip.
+// Warps: 0-3 gather A (thread = row; the next transfer vector's source row is looked up while the
+// current steps are in flight); 4 issues TMA for B; 5 owns tensor memory and issues the MMAs
+// (M = 128 rows, N = k_pad, K = 32 bytes); 6-9 drain each transfer vector's partial sum
+// (double-buffered in tensor memory when 3 k_pad <= 512) into the running sum.
 // Every wait is bounded; a wait that runs out sets the plan's device status word and the CTA
 // winds down.
 #include <cuda.h>
@@ -31,7 +33,7 @@ namespace m2l {
 namespace {
 
 constexpr int kRows = 128;            // MMA M, rows per tile
-constexpr int kChunk = 128;           // bytes of K per stage (one 128-byte swizzle row)
+constexpr int kMaxStages = 16;
 constexpr int kThreads = 320;
 constexpr long long kWaitLimit = 1LL << 24;
 
@@ -81,14 +83,16 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+// Shared-memory matrix descriptor: K-major rows of CH bytes (one row of the CH-byte swizzle),
+// 8-row groups 8 CH bytes apart. Layout codes: 32-byte swizzle 6, 64-byte 4, 128-byte 2.
+template <int CH>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
     d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)((8 * CH) >> 4) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
+    d |= (uint64_t)(CH == 32 ? 6 : CH == 64 ? 4 : 2) << 61;
     return d;
 }
 
@@ -142,19 +146,20 @@ __device__ __forceinline__ RowInfo row_info(const LevelView &L, const ContractTi
     return ri;
 }
 
-template <int KIND>
+// CH: bytes of K per pipeline stage (32, 64 or 128), CH / 32 MMA steps per stage.
+template <int KIND, int CH>
 __global__ void __launch_bounds__(kThreads, 1)
     contract_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, const TcParams P) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[4], empty_bar[4], accf_bar[2], acce_bar[2], drain_bar;
+    __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], accf_bar[2], acce_bar[2], drain_bar;
     __shared__ uint32_t tmem_base_s;
     __shared__ volatile int abort_flag;
 
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int S = P.stages;
     const int kp = P.kp;
-    const uint32_t a_bytes = kRows * kChunk;               // 16 KB
-    const uint32_t b_bytes = (uint32_t)kp * kChunk;        // k_pad rows x 128 B
+    const uint32_t a_bytes = kRows * CH;                   // 128 rows x CH bytes
+    const uint32_t b_bytes = (uint32_t)kp * CH;            // k_pad rows x CH bytes
     const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
     auto sA_hi = [&](int s) { return smem + (size_t)s * stage_bytes; };
     auto sA_lo = [&](int s) { return smem + (size_t)s * stage_bytes + a_bytes; };
@@ -185,59 +190,62 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem_base = tmem_base_s;
-    const int chunk_elems = kChunk / P.elt;
+    const int chunk_elems = CH / P.elt;
     const int kbytes = kp * P.elt;  // valid bytes of a row
     // tensor memory: partial sums of one transfer vector in D[0..nbuf), the running sum in R
     const uint32_t tm_R = tmem_base + (uint32_t)(nbuf * kp);
 
     if (warp < 4) {
-        // ---------------- A producers: 8 lanes per row, each a 16-byte piece; 8 rows per thread ----
-        const int piece = tid & 7, rgrp = tid >> 3;  // rows rgrp + 16 i
+        // ---------------- A producers: kPieces lanes per row, each a 16-byte piece, so a warp's
+        // copy instruction covers 32 / kPieces whole row segments; kPieces rows per thread ----
+        constexpr int kPieces = CH / 16, kRowStep = kRows / kPieces;
+        const int piece = tid % kPieces, rgrp = tid / kPieces;  // rows rgrp + kRowStep i
         long long it = 0;
-        long long pend[4];  // stages whose copies are in flight, oldest first
-        int npend = 0;
         for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
             const ContractTile T = P.tiles[tile];
             const LevelView &L = P.lv[T.lev];
-            RowInfo ri[8];
+            RowInfo ri[kPieces];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) ri[i] = row_info(L, T, rgrp + 16 * i);
+            for (int i = 0; i < kPieces; ++i) ri[i] = row_info(L, T, rgrp + kRowStep * i);
             const int N = L.N;
-            // source rows of the 8 rows this thread feeds, for list entry e of the tile
-            auto sources = [&](int e, long long (&src)[8]) {
+            // source rows of this thread's rows for list entry e of the tile
+            auto sources = [&](int e, long long (&src)[kPieces]) {
                 const int pk = P.tvl[T.tv0 + e];
                 const int dx = (pk & 15) - 3, dy = ((pk >> 4) & 15) - 3, dz = ((pk >> 8) & 15) - 3;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < kPieces; ++i) {
                     src[i] = P.zero_row;
                     if (ri[i].b >= 0) {
-                        int x = (int)(ri[i].xyz & 1023) + dx, y = (int)((ri[i].xyz >> 10) & 1023) + dy,
-                            z = (int)((ri[i].xyz >> 20) & 1023) + dz;
+                        const int x = (int)(ri[i].xyz & 1023) + dx, y = (int)((ri[i].xyz >> 10) & 1023) + dy,
+                                  z = (int)((ri[i].xyz >> 20) & 1023) + dz;
                         if (x >= 0 && y >= 0 && z >= 0 && x < N && y < N && z < N) {
-                            int sl = L.slot[((long long)z * N + y) * N + x];
+                            const int sl = L.slot[((long long)z * N + y) * N + x];
                             if (sl >= 0) src[i] = L.row0 + (long long)sl * L.R + ri[i].r;
                         }
                     }
                 }
             };
-            long long src[8], nxt[8];
+            long long src[kPieces], nxt[kPieces];
             sources(0, nxt);
             for (int e = 0; e < T.ntv; ++e) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) src[i] = nxt[i];
-                if (e + 1 < T.ntv) sources(e + 1, nxt);  // in flight while this vector's chunks go out
+                for (int i = 0; i < kPieces; ++i) src[i] = nxt[i];
+                if (e + 1 < T.ntv) sources(e + 1, nxt);  // in flight while this vector's stages go out
                 for (int c = 0; c < P.nchunks; ++c, ++it) {
                     const int s = (int)(it % S);
                     if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) - 1) & 1), &abort_flag,
                                               P.status, M2L_WAIT_GATHER))
                         goto producer_done;
-                    if (c * kChunk + piece * 16 < kbytes) {
-                        const long long goff = (long long)c * kChunk + piece * 16;
+                    const long long goff = (long long)c * CH + piece * 16;
+                    if (goff < kbytes) {  // the last stage of a row may be shorter
                         const uint32_t bh = smem_u32(sA_hi(s)), bl = smem_u32(sA_lo(s));
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int row = rgrp + 16 * i;
-                            const uint32_t off = (uint32_t)(row * kChunk + ((piece ^ (row & 7)) * 16));
+                        for (int i = 0; i < kPieces; ++i) {
+                            const int row = rgrp + kRowStep * i;
+                            // CH-byte swizzle: the piece index is XORed with address bits 7.. of the
+                            // row start, i.e. with row >> (7 - log2 CH) on log2(CH / 16) bits
+                            const int swz = (row >> (CH == 32 ? 2 : CH == 64 ? 1 : 0)) & (kPieces - 1);
+                            const uint32_t off = (uint32_t)(row * CH + ((piece ^ swz) * 16));
                             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(bh + off),
                                          "l"(P.qhi + src[i] * kbytes + goff)
                                          : "memory");
@@ -246,30 +254,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                                          : "memory");
                         }
                     }
-                    asm volatile("cp.async.commit_group;" ::: "memory");
-                    pend[npend++] = it;
-                    if (npend > S - 1) {
-                        // keep S - 1 groups in flight: retire the oldest
-                        if (S == 2) asm volatile("cp.async.wait_group 1;" ::: "memory");
-                        else if (S == 3) asm volatile("cp.async.wait_group 2;" ::: "memory");
-                        else asm volatile("cp.async.wait_group 3;" ::: "memory");
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        mbar_arrive(smem_u32(&full_bar[pend[0] % S]));
-                        for (int q = 1; q < npend; ++q) pend[q - 1] = pend[q];
-                        --npend;
-                    }
+                    // the stage's barrier counts this thread's arrival once all its copies so far
+                    // have landed; the thread itself runs on to the next stage
+                    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full_bar[s]))
+                                 : "memory");
                 }
             }
         }
     producer_done:
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (int q = 0; q < npend; ++q) mbar_arrive(smem_u32(&full_bar[pend[q] % S]));
+        asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == 4) {
         // ---------------- B producer: TMA loads of C_t chunks ----------------
         if (lane == 0) {
             long long it = 0;
-            int last_parity[4] = {-1, -1, -1, -1};
             for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
                 const ContractTile T = P.tiles[tile];
                 for (int e = 0; e < T.ntv; ++e) {
@@ -293,17 +290,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 smem_u32(sB_lo(s))),
                             "l"(&tm_lo), "r"(x), "r"(y), "r"(bar)
                             : "memory");
-                        last_parity[s] = (int)((it / S) & 1);
                     }
                 }
             }
         tma_done:
             if (abort_flag) {
-                // let loads already issued land before the CTA leaves
-                for (int s = 0; s < S; ++s)
-                    if (last_parity[s] >= 0)
-                        for (long long w = 0; w < kWaitLimit && !mbar_try(smem_u32(&full_bar[s]), (uint32_t)last_parity[s]); ++w) {
-                        }
+                // let loads already issued land before the CTA leaves: `it` stages were issued, the
+                // last one of stage s being iteration it - 1 - ((it - 1 - s) mod S)
+                for (int s = 0; s < S && s < it; ++s) {
+                    const long long last = it - 1 - (((it - 1 - s) % S) + S) % S;
+                    const uint32_t parity = (uint32_t)((last / S) & 1);
+                    for (long long w = 0; w < kWaitLimit && !mbar_try(smem_u32(&full_bar[s]), parity); ++w) {
+                    }
+                }
             }
         }
     } else if (warp == 5) {
@@ -326,13 +325,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int c = 0; c < P.nchunks; ++c, ++it) {
                             const int s = (int)(it % S);
                             if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((it / S) & 1), &abort_flag, P.status, M2L_WAIT_OPERANDS)) goto mma_done;
+                            // the gathered rows were written by cp.async (generic proxy); the MMA reads
+                            // them through the async proxy
+                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                            const int steps = min(4, (kbytes - c * kChunk) / 32);
+                            const int steps = min(CH / 32, (kbytes - c * CH) / 32);
                             const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
                             const uint32_t bh = smem_u32(sB_hi(s)), bl = smem_u32(sB_lo(s));
                             for (int k = 0; k < steps; ++k) {
-                                const uint64_t dah = smem_desc(ah + 32 * k), dal = smem_desc(al + 32 * k);
-                                const uint64_t dbh = smem_desc(bh + 32 * k), dbl = smem_desc(bl + 32 * k);
+                                const uint64_t dah = smem_desc<CH>(ah + 32 * k), dal = smem_desc<CH>(al + 32 * k);
+                                const uint64_t dbh = smem_desc<CH>(bh + 32 * k), dbl = smem_desc<CH>(bl + 32 * k);
                                 mma<KIND>(d, dal, dbh, P.idesc, accflag);
                                 accflag = 1;
                                 mma<KIND>(d, dah, dbl, P.idesc, 1);
@@ -542,20 +544,24 @@ int split_tc_operators(m2l_plan_t *pl, int precision) {
         return M2L_ECUDA;
     }
     // C_t as a 2D tensor: inner dimension k_pad elements, kNumTransfer * k_pad rows; a box is one
-    // 128-byte chunk of K for all k_pad output rows of one transfer vector.
+    // stage's CH bytes of K for all k_pad output rows of one transfer vector, in the CH-byte
+    // swizzle; one pair of maps (hi, lo) per stage width CH = 32, 64, 128.
     const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)kNumTransfer * kp};
     const cuuint64_t strides[1] = {(cuuint64_t)kp * elt};
-    const cuuint32_t box[2] = {(cuuint32_t)(128 / elt), (cuuint32_t)kp};
     const cuuint32_t estr[2] = {1, 1};
     const CUtensorMapDataType dt = kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUtensorMapSwizzle swz[3] = {CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_SWIZZLE_128B};
     void *bases[2] = {D.C_hi, D.C_lo};
-    for (int i = 0; i < 2; ++i) {
-        CUresult r = enc(reinterpret_cast<CUtensorMap *>(D.tmap[i]), dt, 2, bases[i], dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) {
-            set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
-            return M2L_ECUDA;
+    for (int w = 0; w < 3; ++w) {
+        const cuuint32_t box[2] = {(cuuint32_t)((32 << w) / elt), (cuuint32_t)kp};
+        for (int i = 0; i < 2; ++i) {
+            CUresult r = enc(reinterpret_cast<CUtensorMap *>(D.tmap[w][i]), dt, 2, bases[i], dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, swz[w], CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+                return M2L_ECUDA;
+            }
         }
     }
     return M2L_OK;
@@ -586,7 +592,11 @@ int launch_watchdog_selftest(int *status, long long polls, cudaStream_t s) {
     return M2L_OK;
 }
 
-size_t tc_stage_bytes(int kp) { return 2 * (size_t)kRows * kChunk + 2 * (size_t)kp * kChunk; }
+size_t tc_stage_bytes(int kp, int ch) { return 2 * (size_t)kRows * ch + 2 * (size_t)kp * ch; }
+
+// Stage width (bytes of K per pipeline stage) of the tensor-core contraction: the plan's
+// M2L_OPT_TC_CHUNK, or 128 by default.
+int tc_chunk_of(const m2l_plan_t *pl) { return pl->tc_chunk ? pl->tc_chunk : 128; }
 
 template <class T>
 int launch_contract_tc(m2l_plan_t *pl, const LevelView *lv, const ContractTile *tiles, long long ntiles, const int *tvl,
@@ -610,11 +620,12 @@ int launch_contract_tc(m2l_plan_t *pl, const LevelView *lv, const ContractTile *
         P.phit = reinterpret_cast<float *>(phit);
         P.kp = kp;
         P.elt = kind == 0 ? 4 : 2;
-        P.nchunks = (kp * P.elt + kChunk - 1) / kChunk;
-        const size_t stage = tc_stage_bytes(kp);
+        const int ch = tc_chunk_of(pl);
+        P.nchunks = (kp * P.elt + ch - 1) / ch;  // k_pad is a multiple of 16: whole 32-byte MMA steps
+        const size_t stage = tc_stage_bytes(kp, ch);
         const size_t budget = 227 * 1024 - 1024 - 256;
         int S = (int)(budget / stage);
-        if (S > 4) S = 4;
+        if (S > kMaxStages) S = kMaxStages;
         if (S < 2) {
             set_error("rank %d too large for the tensor-core pipeline", kp);
             return M2L_EUNSUPPORTED;
@@ -634,16 +645,18 @@ int launch_contract_tc(m2l_plan_t *pl, const LevelView *lv, const ContractTile *
         P.status = pl->dev_status;
         const size_t smem = (size_t)S * stage + 1024;
         const int grid = (int)(ntiles < pl->num_sms ? ntiles : pl->num_sms);
-        const CUtensorMap *thi = reinterpret_cast<const CUtensorMap *>(D.tmap[0]);
-        const CUtensorMap *tlo = reinterpret_cast<const CUtensorMap *>(D.tmap[1]);
+        const int w = ch == 32 ? 0 : ch == 64 ? 1 : 2;
+        const CUtensorMap *thi = reinterpret_cast<const CUtensorMap *>(D.tmap[w][0]);
+        const CUtensorMap *tlo = reinterpret_cast<const CUtensorMap *>(D.tmap[w][1]);
         cudaError_t e;
-        if (kind == 0) {
-            cudaFuncSetAttribute(contract_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            contract_tc_kernel<0><<<grid, kThreads, smem, s>>>(*thi, *tlo, P);
-        } else {
-            cudaFuncSetAttribute(contract_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            contract_tc_kernel<1><<<grid, kThreads, smem, s>>>(*thi, *tlo, P);
-        }
+        auto go = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kern<<<grid, kThreads, smem, s>>>(*thi, *tlo, P);
+        };
+        if (kind == 0)
+            ch == 32 ? go(contract_tc_kernel<0, 32>) : ch == 64 ? go(contract_tc_kernel<0, 64>) : go(contract_tc_kernel<0, 128>);
+        else
+            ch == 32 ? go(contract_tc_kernel<1, 32>) : ch == 64 ? go(contract_tc_kernel<1, 64>) : go(contract_tc_kernel<1, 128>);
         e = cudaGetLastError();
         if (e != cudaSuccess) {
             set_error("tensor-core contraction launch failed: %s", cudaGetErrorString(e));

@@ -55,6 +55,16 @@ def test_stated_bounds_match_the_tests_table(lib):
         lib.m2l_stated_bound(lib.M2L_FORM_BLAS, lib.M2L_PREC_FP32, 1)
 
 
+def test_stage_width_option_is_validated(lib):
+    h = lib.m2l_plan(3, 4, 0, 0.0)
+    try:
+        assert lib.m2l_set_option(h, lib.M2L_OPT_TC_CHUNK, 48) == lib.M2L_EINVAL
+        for v in (0, 32, 64, 128):
+            assert lib.m2l_set_option(h, lib.M2L_OPT_TC_CHUNK, v) == lib.M2L_OK
+    finally:
+        lib.m2l_destroy(h)
+
+
 def test_plan_rejects_bad_arguments(lib):
     for args, word in [((1, 4, 0, 0.0), "depth"), ((9, 4, 0, 0.0), "depth"), ((3, 1, 0, 0.0), "order"),
                        ((3, 4, 7, 0.0), "kernel"), ((3, 4, 0, float("nan")), "rank_tol")]:
