@@ -49,6 +49,9 @@ struct TcParams {
     uint32_t idesc;
     int tmem_cols;
     int nbuf;                          // partial-sum buffers in tensor memory (1 or 2)
+    int rt;                            // running-sum columns in tensor memory (multiple of 16, <= kp)
+    int rs_off;                        // byte offset in dynamic shared memory of the other kp - rt
+                                       // running-sum columns, [kp - rt][128] floats
     int group;                         // transfer vectors per partial sum (drain interval)
     int *status;
 };
@@ -208,29 +211,34 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int i = 0; i < kPieces; ++i) ri[i] = row_info(L, T, rgrp + kRowStep * i);
             const int N = L.N;
-            // source rows of this thread's rows for list entry e of the tile
-            auto sources = [&](int e, long long (&src)[kPieces]) {
-                const int pk = P.tvl[T.tv0 + e];
+            // The source rows of list entry e + 1 are looked up while entry e's stages go out, and
+            // its packed entry was read one entry earlier still: every lookup's result is first used
+            // a whole transfer vector after its load was issued (in-order issue would otherwise
+            // stall the warp at the first use, once per transfer vector).
+            auto lookup = [&](int pk, int (&slot)[kPieces]) {
                 const int dx = (pk & 15) - 3, dy = ((pk >> 4) & 15) - 3, dz = ((pk >> 8) & 15) - 3;
 #pragma unroll
                 for (int i = 0; i < kPieces; ++i) {
-                    src[i] = P.zero_row;
-                    if (ri[i].b >= 0) {
-                        const int x = (int)(ri[i].xyz & 1023) + dx, y = (int)((ri[i].xyz >> 10) & 1023) + dy,
-                                  z = (int)((ri[i].xyz >> 20) & 1023) + dz;
-                        if (x >= 0 && y >= 0 && z >= 0 && x < N && y < N && z < N) {
-                            const int sl = L.slot[((long long)z * N + y) * N + x];
-                            if (sl >= 0) src[i] = L.row0 + (long long)sl * L.R + ri[i].r;
-                        }
-                    }
+                    const int x = (int)(ri[i].xyz & 1023) + dx, y = (int)((ri[i].xyz >> 10) & 1023) + dy,
+                              z = (int)((ri[i].xyz >> 20) & 1023) + dz;
+                    int v = -1;
+                    if (ri[i].b >= 0 && x >= 0 && y >= 0 && z >= 0 && x < N && y < N && z < N)
+                        v = L.slot[((long long)z * N + y) * N + x];
+                    slot[i] = v;
                 }
             };
-            long long src[kPieces], nxt[kPieces];
-            sources(0, nxt);
+            int slot_nxt[kPieces];
+            lookup(P.tvl[T.tv0], slot_nxt);
+            int pk_nxt = T.ntv > 1 ? P.tvl[T.tv0 + 1] : 0;
             for (int e = 0; e < T.ntv; ++e) {
+                long long src[kPieces];
 #pragma unroll
-                for (int i = 0; i < kPieces; ++i) src[i] = nxt[i];
-                if (e + 1 < T.ntv) sources(e + 1, nxt);  // in flight while this vector's stages go out
+                for (int i = 0; i < kPieces; ++i)
+                    src[i] = slot_nxt[i] >= 0 ? L.row0 + (long long)slot_nxt[i] * L.R + ri[i].r : P.zero_row;
+                if (e + 1 < T.ntv) {
+                    lookup(pk_nxt, slot_nxt);
+                    pk_nxt = e + 2 < T.ntv ? P.tvl[T.tv0 + e + 2] : 0;
+                }
                 for (int c = 0; c < P.nchunks; ++c, ++it) {
                     const int s = (int)(it % S);
                     if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) - 1) & 1), &abort_flag,
@@ -269,8 +277,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             long long it = 0;
             for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
                 const ContractTile T = P.tiles[tile];
+                int ti_nxt = P.tvl[T.tv0] >> 12;  // read one transfer vector ahead of its use
                 for (int e = 0; e < T.ntv; ++e) {
-                    const int ti = P.tvl[T.tv0 + e] >> 12;
+                    const int ti = ti_nxt;
+                    if (e + 1 < T.ntv) ti_nxt = P.tvl[T.tv0 + e + 1] >> 12;
                     for (int c = 0; c < P.nchunks; ++c, ++it) {
                         const int s = (int)(it % S);
                         if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) - 1) & 1), &abort_flag,
@@ -359,6 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- epilogue: R += D per transfer vector (FP32, round to nearest); R -> phi~ ----
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
+        float *Rs = reinterpret_cast<float *>(smem + P.rs_off);
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         long long u = 0;
         for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
@@ -378,20 +389,34 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int q = 0; q < 3; ++q)
                         if (q < nc) {
-                            tmem_ld16(tD + c0 + 16 * q, dv[q]);
-                            if (!first) tmem_ld16(tR + c0 + 16 * q, rv[q]);
+                            const int col = c0 + 16 * q;
+                            tmem_ld16(tD + col, dv[q]);
+                            if (!first) {
+                                if (col < P.rt) {
+                                    tmem_ld16(tR + col, rv[q]);
+                                } else {  // running-sum columns past rt live in shared memory
+#pragma unroll
+                                    for (int j = 0; j < 16; ++j) rv[q][j] = __float_as_uint(Rs[(col - P.rt + j) * kRows + row]);
+                                }
+                            }
                         }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         if (q >= nc) continue;
+                        const int col = c0 + 16 * q;
                         if (!first) {
 #pragma unroll
                             for (int j = 0; j < 16; ++j)
                                 dv[q][j] = __float_as_uint(__fadd_rn(__uint_as_float(rv[q][j]), __uint_as_float(dv[q][j])));
                         }
                         if (!last) {
-                            tmem_st16(tR + c0 + 16 * q, dv[q]);
+                            if (col < P.rt) {
+                                tmem_st16(tR + col, dv[q]);
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) Rs[(col - P.rt + j) * kRows + row] = __uint_as_float(dv[q][j]);
+                            }
                         } else if (dst) {
                             float4 *o = reinterpret_cast<float4 *>(dst + c0 + 16 * q);
 #pragma unroll
@@ -637,13 +662,31 @@ int launch_contract_tc(m2l_plan_t *pl, const LevelView *lv, const ContractTile *
         idesc |= (uint32_t)(kp >> 3) << 17;
         idesc |= (uint32_t)(kRows >> 4) << 24;
         P.idesc = idesc;
-        // tensor memory: nbuf partial-sum buffers and the running sum, kp columns each
-        P.nbuf = 3 * kp <= 512 ? 2 : 1;
-        const int need = (P.nbuf + 1) * kp;
+        // tensor memory: nbuf partial-sum buffers of kp columns and the running sum. Two buffers let
+        // the MMAs of one transfer vector run while the previous one drains; when 3 kp > 512 the
+        // running sum keeps rt = 512 - 2 kp columns (rounded down to 16) in tensor memory and the
+        // rest in shared memory, as long as two pipeline stages still fit beside it.
+        P.nbuf = 2;
+        P.rt = kp;
+        size_t rs_bytes = 0;
+        if (3 * kp > 512) {
+            P.rt = (512 - 2 * kp) / 16 * 16;
+            rs_bytes = (size_t)(kp - P.rt) * kRows * sizeof(float);
+            if (P.rt < 0 || (budget - rs_bytes) / stage < 2) {
+                P.nbuf = 1;
+                P.rt = kp;
+                rs_bytes = 0;
+            }
+        }
+        S = (int)((budget - rs_bytes) / stage);
+        if (S > kMaxStages) S = kMaxStages;
+        P.stages = S;
+        P.rs_off = (int)((size_t)S * stage);
+        const int need = P.nbuf * kp + P.rt;
         P.group = pl->tc_group > 0 ? pl->tc_group : 1;
         P.tmem_cols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
         P.status = pl->dev_status;
-        const size_t smem = (size_t)S * stage + 1024;
+        const size_t smem = (size_t)S * stage + rs_bytes + 1024;
         const int grid = (int)(ntiles < pl->num_sms ? ntiles : pl->num_sms);
         const int w = ch == 32 ? 0 : ch == 64 ? 1 : 2;
         const CUtensorMap *thi = reinterpret_cast<const CUtensorMap *>(D.tmap[w][0]);
