@@ -87,6 +87,12 @@ enum m2l_option_e {
                                 32, 64 or 128 (0: 128, the default). Smaller stages fit more of them in
                                 shared memory (deeper prefetch of the gathered rows) at more barrier
                                 round trips per MMA; the result does not depend on it */
+    M2L_OPT_TC_DRAIN = 12,   /* split tensor-core forms: pipeline stages (M2L_OPT_TC_CHUNK bytes of K each)
+                                summed in tensor memory before each round-to-nearest FP32 drain into the
+                                running sum, within one transfer vector; 0 = whole transfer vectors (see
+                                M2L_OPT_TC_GROUP), -1 = the default (2 for TF32x3, 0 for BF16x3). Fewer
+                                stages per drain shorten the truncating tensor-core accumulation chains
+                                (more accurate) at more drain work */
     M2L_OPT_CHECK_ORDER = 10 /* order p_c of the downward check surface, p <= p_c <= 16 (0: p, the
                                 default). p_c > p gives n_c = 6(p_c-1)^2+2 check points for the n
                                 equivalent points (the BLAS tables' P_c > P_e): K_t and the

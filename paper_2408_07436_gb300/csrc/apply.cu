@@ -613,6 +613,7 @@ int apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *q, void
                 sig.push_back((long long)(uintptr_t)ptr);
             sig.push_back(r.pl->tc_group);
             sig.push_back(r.pl->tc_chunk);
+            sig.push_back(r.pl->tc_drain);
             sig.push_back(r.pl->fft_grid_opt);
         }
     }

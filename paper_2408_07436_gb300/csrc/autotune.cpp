@@ -168,6 +168,7 @@ static int tune(m2l_plan_t *pl, int R, int *form, int *prec) {
     proxy->fft_grid_opt = pl->fft_grid_opt;
     proxy->tc_group = pl->tc_group;
     proxy->tc_chunk = pl->tc_chunk;
+    proxy->tc_drain = pl->tc_drain;
     proxy->dir_tol = pl->dir_tol;
     if (pl->pc != pl->p) m2l_set_option(proxy, M2L_OPT_CHECK_ORDER, pl->pc);
     proxy->stream = pl->stream;

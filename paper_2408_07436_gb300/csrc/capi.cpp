@@ -139,6 +139,10 @@ int m2l_set_option(m2l_plan_t *pl, int key, long long value) {
             if (value < 1 || value > kPerOctant) break;
             pl->tc_group = (int)value;
             return M2L_OK;
+        case M2L_OPT_TC_DRAIN:
+            if (value < -1 || value > 64) break;
+            pl->tc_drain = (int)value;
+            return M2L_OK;
         case M2L_OPT_TC_CHUNK:
             if (value != 0 && value != 32 && value != 64 && value != 128) break;
             pl->tc_chunk = (int)value;

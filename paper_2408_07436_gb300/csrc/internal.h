@@ -136,6 +136,7 @@ struct m2l_plan_s {
     int fft_grid_opt = 0;
     int tc_group = 1;                           // transfer vectors per tensor-memory partial sum
     int tc_chunk = 0;                           // bytes of K per tensor-core pipeline stage (0: default)
+    int tc_drain = -1;                          // K stages per tensor-core partial sum (-1: default)
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 148;

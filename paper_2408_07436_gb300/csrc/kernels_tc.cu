@@ -52,7 +52,8 @@ struct TcParams {
     int rt;                            // running-sum columns in tensor memory (multiple of 16, <= kp)
     int rs_off;                        // byte offset in dynamic shared memory of the other kp - rt
                                        // running-sum columns, [kp - rt][128] floats
-    int group;                         // transfer vectors per partial sum (drain interval)
+    int group;                         // transfer vectors per partial sum (drain interval) when seg == 0
+    int seg;                           // > 0: K stages per partial sum, within one transfer vector
     int *status;
 };
 
@@ -316,45 +317,57 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else if (warp == 5) {
-        // ---------------- MMA issuer: one partial sum per transfer vector ----------------
+        // ---------------- MMA issuer: one partial sum per unit ----------------
+        // A tile's work is its (transfer vector, K stage) pairs, vector-major. A unit, summed in one
+        // tensor-memory buffer before its round-to-nearest drain, is `group` whole transfer vectors
+        // (seg == 0) or seg consecutive stages of one transfer vector (seg > 0).
         if (lane == 0) {
             long long it = 0, u = 0;
             bool pending = false;
+            const int nc = P.nchunks, seg = P.seg, group = P.group;
             for (long long tile = blockIdx.x; tile < P.ntiles && !abort_flag; tile += gridDim.x) {
                 const int ntv = P.tiles[tile].ntv;
-                for (int g0 = 0; g0 < ntv; g0 += P.group, ++u) {
-                    const int g1 = min(ntv, g0 + P.group);
-                    const int buf = (int)(u % nbuf);
-                    if (u >= nbuf &&
-                        !mbar_wait(smem_u32(&acce_bar[buf]), (uint32_t)(((u / nbuf) - 1) & 1), &abort_flag, P.status, M2L_WAIT_ACC_FREE))
-                        goto mma_done;
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t d = tmem_base + (uint32_t)(buf * kp);
-                    uint32_t accflag = 0;
-                    for (int tv = g0; tv < g1; ++tv) {
-                        for (int c = 0; c < P.nchunks; ++c, ++it) {
-                            const int s = (int)(it % S);
-                            if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((it / S) & 1), &abort_flag, P.status, M2L_WAIT_OPERANDS)) goto mma_done;
-                            // the gathered rows were written by cp.async (generic proxy); the MMA reads
-                            // them through the async proxy
-                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                            const int steps = min(CH / 32, (kbytes - c * CH) / 32);
-                            const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
-                            const uint32_t bh = smem_u32(sB_hi(s)), bl = smem_u32(sB_lo(s));
-                            for (int k = 0; k < steps; ++k) {
-                                const uint64_t dah = smem_desc<CH>(ah + 32 * k), dal = smem_desc<CH>(al + 32 * k);
-                                const uint64_t dbh = smem_desc<CH>(bh + 32 * k), dbl = smem_desc<CH>(bl + 32 * k);
-                                mma<KIND>(d, dal, dbh, P.idesc, accflag);
-                                accflag = 1;
-                                mma<KIND>(d, dah, dbl, P.idesc, 1);
-                                mma<KIND>(d, dah, dbh, P.idesc, 1);
-                            }
-                            mma_commit(smem_u32(&empty_bar[s]));
-                            pending = true;
-                        }
+                const int total = ntv * nc;
+                uint32_t d = 0, accflag = 0;
+                int buf = 0;
+                for (int x = 0; x < total; ++x, ++it) {
+                    const int tv = x / nc, c = x - tv * nc;
+                    const bool ustart = seg > 0 ? (c % seg == 0) : (c == 0 && tv % group == 0);
+                    const bool uend = seg > 0 ? (c % seg == seg - 1 || c == nc - 1)
+                                              : (c == nc - 1 && (tv % group == group - 1 || tv == ntv - 1));
+                    if (ustart) {
+                        buf = (int)(u % nbuf);
+                        if (u >= nbuf && !mbar_wait(smem_u32(&acce_bar[buf]), (uint32_t)(((u / nbuf) - 1) & 1), &abort_flag,
+                                                    P.status, M2L_WAIT_ACC_FREE))
+                            goto mma_done;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        d = tmem_base + (uint32_t)(buf * kp);
+                        accflag = 0;
                     }
-                    mma_commit(smem_u32(&accf_bar[buf]));
+                    const int s = (int)(it % S);
+                    if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((it / S) & 1), &abort_flag, P.status, M2L_WAIT_OPERANDS))
+                        goto mma_done;
+                    // the gathered rows were written by cp.async (generic proxy); the MMA reads them
+                    // through the async proxy
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int steps = min(CH / 32, (kbytes - c * CH) / 32);
+                    const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
+                    const uint32_t bh = smem_u32(sB_hi(s)), bl = smem_u32(sB_lo(s));
+                    for (int k = 0; k < steps; ++k) {
+                        const uint64_t dah = smem_desc<CH>(ah + 32 * k), dal = smem_desc<CH>(al + 32 * k);
+                        const uint64_t dbh = smem_desc<CH>(bh + 32 * k), dbl = smem_desc<CH>(bl + 32 * k);
+                        mma<KIND>(d, dal, dbh, P.idesc, accflag);
+                        accflag = 1;
+                        mma<KIND>(d, dah, dbl, P.idesc, 1);
+                        mma<KIND>(d, dah, dbh, P.idesc, 1);
+                    }
+                    mma_commit(smem_u32(&empty_bar[s]));
+                    pending = true;
+                    if (uend) {
+                        mma_commit(smem_u32(&accf_bar[buf]));
+                        ++u;
+                    }
                 }
             }
         mma_done:
@@ -377,8 +390,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const LevelView &L = P.lv[T.lev];
             const RowInfo ri = row_info(L, T, row);
             float *dst = ri.b >= 0 ? P.phit + (L.row0 + (long long)ri.b * L.R + ri.r) * (long long)kp : nullptr;
-            for (int g0 = 0; g0 < T.ntv; g0 += P.group, ++u) {
-                const bool first = g0 == 0, last = g0 + P.group >= T.ntv;
+            const int nunits = P.seg > 0 ? T.ntv * ((P.nchunks + P.seg - 1) / P.seg) : (T.ntv + P.group - 1) / P.group;
+            for (int j = 0; j < nunits; ++j, ++u) {
+                const bool first = j == 0, last = j == nunits - 1;
                 const int buf = (int)(u % nbuf);
                 if (!mbar_wait(smem_u32(&accf_bar[buf]), (uint32_t)((u / nbuf) & 1), &abort_flag, P.status, M2L_WAIT_ACC_READY)) goto epi_done;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -623,6 +637,14 @@ size_t tc_stage_bytes(int kp, int ch) { return 2 * (size_t)kRows * ch + 2 * (siz
 // M2L_OPT_TC_CHUNK, or 128 by default.
 int tc_chunk_of(const m2l_plan_t *pl) { return pl->tc_chunk ? pl->tc_chunk : 128; }
 
+// K stages per partial sum of the tensor-core contraction (0: whole transfer vectors): the plan's
+// M2L_OPT_TC_DRAIN, or by default 2 for TF32x3 and 0 for BF16x3. A stage count of nchunks or more
+// is the same as 0.
+int tc_drain_of(const m2l_plan_t *pl, int precision, int nchunks) {
+    int seg = pl->tc_drain >= 0 ? pl->tc_drain : (precision == M2L_PREC_TF32X3 ? 2 : 0);
+    return seg >= nchunks ? 0 : seg;
+}
+
 template <class T>
 int launch_contract_tc(m2l_plan_t *pl, const LevelView *lv, const ContractTile *tiles, long long ntiles, const int *tvl,
                        const void *qt_hi, const void *qt_lo, long long zero_row, T *phit, int precision, cudaStream_t s) {
@@ -684,6 +706,8 @@ int launch_contract_tc(m2l_plan_t *pl, const LevelView *lv, const ContractTile *
         P.rs_off = (int)((size_t)S * stage);
         const int need = P.nbuf * kp + P.rt;
         P.group = pl->tc_group > 0 ? pl->tc_group : 1;
+        P.seg = tc_drain_of(pl, precision, P.nchunks);
+        if (P.seg > 0) P.group = 1;
         P.tmem_cols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
         P.status = pl->dev_status;
         const size_t smem = (size_t)S * stage + rs_bytes + 1024;

@@ -61,6 +61,9 @@ def test_stage_width_option_is_validated(lib):
         assert lib.m2l_set_option(h, lib.M2L_OPT_TC_CHUNK, 48) == lib.M2L_EINVAL
         for v in (0, 32, 64, 128):
             assert lib.m2l_set_option(h, lib.M2L_OPT_TC_CHUNK, v) == lib.M2L_OK
+        assert lib.m2l_set_option(h, lib.M2L_OPT_TC_DRAIN, -2) == lib.M2L_EINVAL
+        for v in (-1, 0, 1, 2, 64):
+            assert lib.m2l_set_option(h, lib.M2L_OPT_TC_DRAIN, v) == lib.M2L_OK
     finally:
         lib.m2l_destroy(h)
 
