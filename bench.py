@@ -205,10 +205,14 @@ def workload_spec(name, depth):
     raise ValueError(name)
 
 
-def make_plan(lib, wl, form, prec, target=None, timing=True):
-    """A plan of one instance with the workload's options, on the current torch stream."""
-    tol = wl.rank_tol if form in ("blas", "auto") else 0.0
+def make_plan(lib, wl, form, prec, target=None, timing=True, rank_tol=None):
+    """A plan of one instance with the workload's options, on the current torch stream. With a
+    target the library also picks the BLAS form's rank threshold (M2L_OPT_RANK_AUTO); `rank_tol`
+    overrides the workload's threshold."""
+    tol = (wl.rank_tol if rank_tol is None else rank_tol) if form in ("blas", "auto") else 0.0
     pl = lib.Plan(wl.depth, wl.p, tol, form=form, precision=prec).set(timing=int(timing))
+    if target is not None and form in ("blas", "auto"):
+        pl.set(rank_auto=1)
     if form in ("fft", "auto") and wl.fft_grid:
         pl.set(fft_grid=wl.fft_grid)
     if form in ("blas", "auto") and prec in ("fp64", "fp32", "auto") and wl.dir_tol:
@@ -266,11 +270,13 @@ def pl_launches_key():
     return lib.M2L_Q_LAUNCHES
 
 
-def roofline_of(lib, wl, form, prec, stages, steps, peaks, alu, args):
+def roofline_of(lib, wl, form, prec, stages, steps, peaks, alu, args, rank_tol=None):
     """Roofline of the dominant stage (longest device time) of one explicit (form, precision)."""
     if not stages:
         return None
-    acct = make_plan(lib, wl, form, prec, timing=False)   # host-side queries only (operators shared)
+    acct = make_plan(lib, wl, form, prec, timing=False, rank_tol=rank_tol)   # host-side queries (operators shared)
+    if rank_tol is not None and wl.dir_tol and prec in ("fp64", "fp32") and form == "blas":
+        acct.set(dir_tol=rank_tol / 10)   # the directional threshold follows the chosen rank
     work = algorithmic_work(acct, form, wl.n_rhs)
     acct.close()
     name = max(stages, key=lambda n: stages[n][0])
@@ -374,9 +380,13 @@ def run_ours(args, rank, world, local_rank):
     value = world * inter / (ms_step / 1e3)
     log(f"headline: {ms_step:.2f} ms per step, {value:.3e} interactions/s")
     head_form, head_prec = forms[0] if len(set(forms)) == 1 else ("mixed", "mixed")
+    head_rank = None
+    if not batched and head_form == "blas":
+        head_rank = {"rank_tol": head[0].current_rank_tol(), "k": head[0].query(lib.M2L_Q_RANK)}
     roofline = None
     if not batched:
-        roofline = roofline_of(lib, insts[0], head_form, head_prec, stages, args.steps, peaks, alu, args)
+        roofline = roofline_of(lib, insts[0], head_form, head_prec, stages, args.steps, peaks, alu, args,
+                               rank_tol=head_rank["rank_tol"] if head_rank else None)
 
     # ---- the FP64 form the autotuner picks at the same target ----
     fp64_out, fp64_plans = None, None
@@ -388,8 +398,11 @@ def run_ours(args, rank, world, local_rank):
         m64 = sum(ms64) / len(ms64)
         fp64_out = {"interactions_per_s": world * inter / (m64 / 1e3), "ms": m64, "steps": k,
                     "forms": sorted(set(f"{a}-{b}" for a, b in f64)), "stages": stage_summary(st64, k)}
+        if not batched and f64[0][0] == "blas":
+            fp64_out["rank"] = {"rank_tol": fp64_plans[0].current_rank_tol(), "k": fp64_plans[0].query(lib.M2L_Q_RANK)}
         if not batched:
-            fp64_out["roofline"] = roofline_of(lib, insts[0], f64[0][0], f64[0][1], st64, k, peaks, alu, args)
+            fp64_out["roofline"] = roofline_of(lib, insts[0], f64[0][0], f64[0][1], st64, k, peaks, alu, args,
+                                               rank_tol=fp64_out.get("rank", {}).get("rank_tol"))
         log(f"fp64 at {target:g}: {fp64_out['forms']} {m64:.1f} ms")
 
     # ---- every explicit variant of the workload, alone ----
@@ -462,8 +475,9 @@ def run_ours(args, rank, world, local_rank):
            "config": {"workload": DESC[args.workload] if args.depth == 5 or args.workload != "c2"
                       else DESC["c2"].replace("depth5", f"depth{args.depth}"),
                       "instances": len(insts), "pairs_x_rhs": int(inter), "target_rel_err": target,
-                      "form": head_form, "precision": head_prec,
-                      "choice": "autotuned among forms whose stated bound and rank truncation are within the target",
+                      "form": head_form, "precision": head_prec, "rank": head_rank,
+                      "choice": "autotuned among forms whose stated bound plus estimated rank truncation is within "
+                                "the target, BLAS rank threshold chosen by the library",
                       "batched": batched, "l2": "flushed between timed steps (512 MB write)",
                       "ranks": "one independent set of instances per rank"},
            "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,

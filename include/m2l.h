@@ -93,6 +93,16 @@ enum m2l_option_e {
                                 M2L_OPT_TC_GROUP), -1 = the default (2 for TF32x3, 0 for BF16x3). Fewer
                                 stages per drain shorten the truncating tensor-core accumulation chains
                                 (more accurate) at more drain work */
+    M2L_OPT_RANK_AUTO = 13,  /* 1: the library picks the SVD rank threshold of the BLAS form for the target
+                                (M2L_OPT_TARGET_TOL), replacing m2l_plan's rank_tol: the coarsest of 1e-3,
+                                3e-4, ..., 1e-9 (else full rank) whose truncation error, estimated on the
+                                host for one target with all 189 transfer vectors and four density draws
+                                (of both signs and of one sign) and taken 1.5 times, plus ten times the
+                                directional threshold, fits in the target beside the precision's stated bound
+                                (m2l_stated_bound). With M2L_OPT_DIR_TOL set, the directional threshold
+                                follows at a tenth of it. Resolved, and the plan's operators rebuilt, at
+                                the first apply or M2L_Q_FORM / M2L_Q_PRECISION query per target; read the
+                                result with M2L_Q_RANK_TOL. 0 (default): rank_tol as given */
     M2L_OPT_CHECK_ORDER = 10 /* order p_c of the downward check surface, p <= p_c <= 16 (0: p, the
                                 default). p_c > p gives n_c = 6(p_c-1)^2+2 check points for the n
                                 equivalent points (the BLAS tables' P_c > P_e): K_t and the
@@ -152,7 +162,9 @@ enum m2l_query_e {
                                   FP32, AUTO), rounded to an integer */
     M2L_Q_DIR_RANK_SUM = 14,   /* sum of k_t over the 316 transfer vectors (0 when M2L_OPT_DIR_TOL is 0) */
     M2L_Q_NC = 15,             /* check points per box, n_c (n unless M2L_OPT_CHECK_ORDER > p) */
-    M2L_Q_RANK_CHECK = 16      /* rank k_c of the check-side basis U (k unless M2L_OPT_CHECK_ORDER > p) */
+    M2L_Q_RANK_CHECK = 16,     /* rank k_c of the check-side basis U (k unless M2L_OPT_CHECK_ORDER > p) */
+    M2L_Q_RANK_TOL = 17        /* the plan's current rank threshold, as the bits of a double (the one
+                                  m2l_plan was given, or the one M2L_OPT_RANK_AUTO chose) */
 };
 
 /* Where a bounded device wait ran out (the value of M2L_Q_DEVICE_STATUS). Every wait of a kernel

@@ -46,12 +46,39 @@ double stated_bound(int form, int precision, int p) {
     return 1.2e-5;                             // BF16x3 (5.5e-6, 5.3e-6, 5.0e-6, 5.9e-6)
 }
 
+// Set a plan's rank threshold (and, when it uses directional factors, their threshold at a tenth
+// of it), dropping every operator built for the old one.
+void set_rank(m2l_plan_t *pl, double rank_tol) {
+    if (rank_tol == pl->rank_tol) return;
+    pl->rank_tol = rank_tol;
+    if (pl->dir_tol > 0) pl->dir_tol = rank_tol > 0 ? rank_tol / 10 : 0.0;
+    pl->blas.reset();
+    pl->dirop.reset();
+    release_operators(pl);
+}
+
+// Rank thresholds the tuner tries, coarsest first; full rank (0) after the last.
+static const double kRankLadder[] = {1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9};
+
+// With M2L_OPT_RANK_AUTO: the coarsest rank threshold whose truncation, estimated on the host
+// (truncation_estimate, times 1.5 for the spread across boxes and levels), fits in the target
+// beside the precision's stated bound; -1 when none does.
+static double choose_rank(m2l_plan_t *pl, int prec) {
+    const double budget = pl->target_tol - stated_bound(M2L_FORM_BLAS, prec, pl->p);
+    if (budget <= 0) return -1.0;
+    const bool dir = pl->dir_tol > 0 && (prec == M2L_PREC_FP64 || prec == M2L_PREC_FP32);
+    for (double r : kRankLadder) {
+        if (1.5 * truncation_estimate(pl, r, dir ? r / 10 : 0.0) <= budget) return r;
+    }
+    return 0.0;
+}
+
 static bool eligible(const m2l_plan_t *pl, int form, int prec) {
     if (form == M2L_FORM_FFT && (prec == M2L_PREC_TF32X3 || prec == M2L_PREC_BF16X3)) return false;
     // a check order above p: BLAS form on CUDA cores only
     if (pl->pc != pl->p && (form == M2L_FORM_FFT || prec == M2L_PREC_TF32X3 || prec == M2L_PREC_BF16X3)) return false;
     double bound = stated_bound(form, prec, pl->p);
-    if (form == M2L_FORM_BLAS && pl->rank_tol > 0) bound = std::max(bound, pl->rank_tol);
+    if (form == M2L_FORM_BLAS && pl->rank_tol > 0 && !pl->rank_auto) bound = std::max(bound, pl->rank_tol);
     if (bound > pl->target_tol) return false;
     if (form == M2L_FORM_BLAS && (prec == M2L_PREC_TF32X3 || prec == M2L_PREC_BF16X3)) {
         // the tensor-core contraction holds k_pad <= 256 columns
@@ -104,59 +131,76 @@ static int time_candidate(m2l_plan_t *pl, int form, int prec, int R, float *ms) 
     return rc;
 }
 
-using TuneKey = std::tuple<int, int, int, double, double, int, int, int, int, double>;
-static std::map<TuneKey, std::pair<int, int>> g_decisions;
+using TuneKey = std::tuple<int, int, int, double, double, int, int, int, int, double, int>;
+struct Decision {
+    int form, prec;
+    double rank;
+};
+static std::map<TuneKey, Decision> g_decisions;
 static std::mutex g_decisions_mu;
 
 // The real plan decides which candidates fit its memory budget; the proxy times them.
-static int tune_on(m2l_plan_t *pl, const m2l_plan_t *real, int R, int *form, int *prec) {
-    std::vector<std::pair<int, int>> fast, slow;
+struct Candidate {
+    int form, prec;
+    double rank;  // rank threshold the candidate runs at (the plan's own unless M2L_OPT_RANK_AUTO)
+};
+
+static int tune_on(m2l_plan_t *pl, const m2l_plan_t *real, int R, int *form, int *prec, double *rank) {
+    std::vector<Candidate> fast, slow;
     const int forms[2] = {M2L_FORM_BLAS, M2L_FORM_FFT};
     const int precs[4] = {M2L_PREC_BF16X3, M2L_PREC_TF32X3, M2L_PREC_FP32, M2L_PREC_FP64};
+    const double own = pl->rank_tol;
     if (pl->rank_tol > 0 || pl->form == M2L_FORM_BLAS) build_blas_host(pl);
     for (int f : forms) {
         if (pl->form != M2L_FORM_AUTO && pl->form != f) continue;
         for (int pr : precs) {
             if (pl->precision != M2L_PREC_AUTO && pl->precision != pr) continue;
             if (!eligible(pl, f, pr)) continue;
+            double r = own;
+            if (f == M2L_FORM_BLAS && pl->rank_auto) {
+                r = choose_rank(pl, pr);
+                if (r < 0) continue;
+            }
             const size_t need = workspace_estimate(real, f, pr, R);
             if (real->mem_budget && need > 2 * real->mem_budget) continue;
-            (pr == M2L_PREC_FP64 ? slow : fast).push_back({f, pr});
+            (pr == M2L_PREC_FP64 ? slow : fast).push_back({f, pr, r});
         }
     }
-    std::vector<std::pair<int, int>> &cands = fast.empty() ? slow : fast;
+    std::vector<Candidate> &cands = fast.empty() ? slow : fast;
     if (cands.empty()) {
         set_error("no form/precision reaches the target tolerance %.3g with this plan", pl->target_tol);
         return M2L_EUNSUPPORTED;
     }
     float best = 1e30f;
-    int bf = cands[0].first, bp = cands[0].second;
+    Candidate win = cands[0];
     for (auto &c : cands) {
         float ms = 1e30f;
-        int rc = time_candidate(pl, c.first, c.second, R, &ms);
+        if (c.form == M2L_FORM_BLAS) set_rank(pl, c.rank);
+        int rc = time_candidate(pl, c.form, c.prec, R, &ms);
         if (rc == M2L_EUNSUPPORTED) continue;
         if (rc) return rc;
         if (ms < best) {
             best = ms;
-            bf = c.first;
-            bp = c.second;
+            win = c;
         }
     }
-    *form = bf;
-    *prec = bp;
+    *form = win.form;
+    *prec = win.prec;
+    *rank = win.form == M2L_FORM_BLAS ? win.rank : own;
     return M2L_OK;
 }
 
-static int tune(m2l_plan_t *pl, int R, int *form, int *prec) {
+static int tune(m2l_plan_t *pl, int R, int *form, int *prec, double *rank) {
     // box counts enter through the memory check, so the decision is shared per tree size too
     const TuneKey key{pl->device, pl->p * 1000 + pl->depth, R, pl->rank_tol, pl->target_tol, pl->form, pl->precision,
-                      pl->fft_grid_opt, pl->pc, pl->dir_tol};
+                      pl->fft_grid_opt, pl->pc, pl->dir_tol, pl->rank_auto};
     {
         std::lock_guard<std::mutex> g(g_decisions_mu);
         auto it = g_decisions.find(key);
         if (it != g_decisions.end()) {
-            *form = it->second.first;
-            *prec = it->second.second;
+            *form = it->second.form;
+            *prec = it->second.prec;
+            *rank = it->second.rank;
             return M2L_OK;
         }
     }
@@ -169,24 +213,37 @@ static int tune(m2l_plan_t *pl, int R, int *form, int *prec) {
     proxy->tc_group = pl->tc_group;
     proxy->tc_chunk = pl->tc_chunk;
     proxy->tc_drain = pl->tc_drain;
+    proxy->rank_auto = pl->rank_auto;
     proxy->dir_tol = pl->dir_tol;
     if (pl->pc != pl->p) m2l_set_option(proxy, M2L_OPT_CHECK_ORDER, pl->pc);
     proxy->stream = pl->stream;
     if (build_level_tables(pl) || build_pinv(pl)) return M2L_ECUDA;
     if (pl->rank_tol > 0 || pl->form != M2L_FORM_FFT) build_blas_host(pl);
     if (pl->form != M2L_FORM_BLAS) build_fft_host(pl);
-    int rc = tune_on(proxy, pl, R, form, prec);
+    int rc = tune_on(proxy, pl, R, form, prec, rank);
     cudaStreamSynchronize(proxy->stream);
     m2l_destroy(proxy);
     if (rc) return rc;
     std::lock_guard<std::mutex> g(g_decisions_mu);
-    g_decisions[key] = {*form, *prec};
+    g_decisions[key] = {*form, *prec, *rank};
     return M2L_OK;
 }
 
 int resolve_form(const m2l_plan_t *cpl, int R, int *form, int *precision) {
     m2l_plan_t *pl = const_cast<m2l_plan_t *>(cpl);
     if (pl->form != M2L_FORM_AUTO && pl->precision != M2L_PREC_AUTO) {
+        // explicit form and precision: with M2L_OPT_RANK_AUTO the BLAS form still takes the coarsest
+        // rank that fits the target (no timing needed)
+        if (pl->rank_auto && pl->form == M2L_FORM_BLAS && pl->rank_auto_tol != pl->target_tol) {
+            const double r = choose_rank(pl, pl->precision);
+            if (r < 0) {
+                set_error("the stated bound of this precision (%.3g) leaves no room for truncation within the target "
+                          "%.3g", stated_bound(M2L_FORM_BLAS, pl->precision, pl->p), pl->target_tol);
+                return M2L_EUNSUPPORTED;
+            }
+            set_rank(pl, r);
+            pl->rank_auto_tol = pl->target_tol;
+        }
         *form = pl->form;
         *precision = pl->precision;
         return M2L_OK;
@@ -194,6 +251,7 @@ int resolve_form(const m2l_plan_t *cpl, int R, int *form, int *precision) {
     for (const auto &d : pl->tuned)
         if (d.R == R && d.tol == pl->target_tol && d.form_opt == pl->form && d.prec_opt == pl->precision &&
             d.levels_version == pl->levels_version) {
+            if (pl->rank_auto && d.form == M2L_FORM_BLAS) set_rank(pl, d.rank);
             *form = d.form;
             *precision = d.precision;
             return M2L_OK;
@@ -203,8 +261,10 @@ int resolve_form(const m2l_plan_t *cpl, int R, int *form, int *precision) {
         return M2L_ECUDA;
     }
     int f, p;
-    int rc = tune(pl, R, &f, &p);
+    double r = pl->rank_tol;
+    int rc = tune(pl, R, &f, &p, &r);
     if (rc) return rc;
+    if (pl->rank_auto && f == M2L_FORM_BLAS) set_rank(pl, r);
     m2l_plan_s::Tuned d;
     d.R = R;
     d.tol = pl->target_tol;
@@ -213,6 +273,7 @@ int resolve_form(const m2l_plan_t *cpl, int R, int *form, int *precision) {
     d.levels_version = pl->levels_version;
     d.form = f;
     d.precision = p;
+    d.rank = pl->rank_tol;
     pl->tuned.push_back(d);
     *form = f;
     *precision = p;

@@ -139,6 +139,14 @@ int m2l_set_option(m2l_plan_t *pl, int key, long long value) {
             if (value < 1 || value > kPerOctant) break;
             pl->tc_group = (int)value;
             return M2L_OK;
+        case M2L_OPT_RANK_AUTO:
+            if (value != 0 && value != 1) break;
+            if ((int)value != pl->rank_auto) {
+                pl->rank_auto = (int)value;
+                pl->rank_auto_tol = -1.0;
+                pl->tuned.clear();
+            }
+            return M2L_OK;
         case M2L_OPT_TC_DRAIN:
             if (value < -1 || value > 64) break;
             pl->tc_drain = (int)value;
@@ -408,6 +416,11 @@ int m2l_query(const m2l_plan_t *cpl, int what, int level, long long *out) {
             if ((rc = build_blas_host(pl))) return rc;
             *out = pl->kc;
             return M2L_OK;
+        case M2L_Q_RANK_TOL: {
+            const double r = pl->rank_tol;
+            std::memcpy(out, &r, sizeof r);
+            return M2L_OK;
+        }
         case M2L_Q_DIR_RANK_SUM: {
             *out = 0;
             if (pl->dir_tol <= 0) return M2L_OK;

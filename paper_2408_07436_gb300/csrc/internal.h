@@ -170,7 +170,9 @@ struct m2l_plan_s {
     m2l::BatchGraph batch_graph;
     long long levels_version = 0;                  // bumped whenever a box set changes
     int capturing = 0;                             // inside a batch capture: no timing events
-    struct Tuned { int R; double tol; int form_opt, prec_opt; long long levels_version; int form, precision; };
+    struct Tuned { int R; double tol; int form_opt, prec_opt; long long levels_version; int form, precision; double rank; };
+    int rank_auto = 0;                             // M2L_OPT_RANK_AUTO
+    double rank_auto_tol = -1.0;                   // target the rank was last chosen for (explicit form)
     std::vector<Tuned> tuned;                      // autotuner decisions
     long long launches = 0;
     int *dev_status = nullptr;                     // device status word written by bounded waits
@@ -187,6 +189,9 @@ namespace m2l {
 int build_pinv(m2l_plan_t *pl);
 int build_blas_host(m2l_plan_t *pl);
 int build_directional(m2l_plan_t *pl);
+// Host estimate of the relative check-potential error that truncation at (rank_tol, dir_tol) adds
+// (plan.cpp): one target with its 189 transfer vectors, four seeded density draws, the largest.
+double truncation_estimate(m2l_plan_t *pl, double rank_tol, double dir_tol);
 void release_operators(m2l_plan_t *pl);
 // Pseudo-inverse factors of Eq. 10 from the SVD of an m x n (m >= n) matrix, U, V column-major:
 // Veps [n][r], Uteps [r][m] with the singular values above (alpha + max(m, n) eps) s_0.
@@ -202,6 +207,7 @@ void free_device(m2l_plan_t *pl);
 // autotune.cpp
 int resolve_form(const m2l_plan_t *pl, int R, int *form, int *precision);
 double stated_bound(int form, int precision, int p);
+void set_rank(m2l_plan_t *pl, double rank_tol);
 // apply.cu
 int prepare_plan(m2l_plan_t *pl, int form, int precision);
 size_t workspace_estimate(const m2l_plan_t *pl, int form, int precision, int R);

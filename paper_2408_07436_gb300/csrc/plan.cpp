@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <random>
 #include <map>
 #include <mutex>
 #include <numeric>
@@ -168,6 +169,43 @@ static OpCache<BlasOps, std::tuple<int, int, int, double>> g_blas_cache;
 static OpCache<DirOps, std::tuple<int, int, int, double, double>> g_dir_cache;
 static OpCache<FftOps, std::tuple<int, int, int>> g_fft_cache;
 
+// The full SVD bases of the stacked operators (Eqs. 12-13) for one (kernel, p, p_c): every rank
+// threshold truncates the same factorisation, so the tuner can try several ranks for the cost of
+// one SVD. Columns are re-orthonormalised (orthonormalize_columns) in order of the singular values,
+// so the leading k columns of each basis are orthonormal for every k.
+struct SvdBasis {
+    std::vector<double> Uf;      // nc x nc, column-major: left singular vectors of K_fat
+    std::vector<double> Sb;      // n x n, column-major: right singular vectors of K_thin
+    std::vector<double> s_fat, s_thin;
+};
+static OpCache<SvdBasis, std::tuple<int, int, int>> g_svd_cache;
+
+static std::shared_ptr<const SvdBasis> svd_basis(const m2l_plan_t *pl, const std::vector<std::vector<double>> &Ks) {
+    const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc);
+    std::shared_ptr<const SvdBasis> b = g_svd_cache.find(key);
+    if (b) return b;
+    auto o = std::make_shared<SvdBasis>();
+    const int n = pl->n, nc = pl->nc;
+    // K_thin = [K_1; ...; K_316] (316 nc x n): stack the column-major K_t. K_fat^T =
+    // [K_1^T; ...] (316 n x nc): a row-major K_t read as column-major is K_t^T.
+    std::vector<std::vector<double>> thin(kNumTransfer), fatT(kNumTransfer);
+    for (int t = 0; t < kNumTransfer; ++t) {
+        fatT[t] = Ks[t];
+        thin[t].resize((size_t)nc * n);
+        for (int i = 0; i < nc; ++i)
+            for (int j = 0; j < n; ++j) thin[t][(size_t)j * nc + i] = Ks[t][(size_t)i * n + j];
+    }
+    std::vector<double> Rf = stacked_r_factor(std::move(fatT), nc);
+    std::vector<double> Rt = stacked_r_factor(std::move(thin), n);
+    std::vector<double> Uf_, Ut_;
+    // left singular vectors of K_fat = right singular vectors of K_fat^T (and of Rf)
+    jacobi_svd(Rf, nc, nc, Uf_, o->s_fat, o->Uf);
+    jacobi_svd(Rt, n, n, Ut_, o->s_thin, o->Sb);
+    orthonormalize_columns(o->Uf.data(), nc, nc);
+    orthonormalize_columns(o->Sb.data(), n, n);
+    return g_svd_cache.publish(key, std::move(o));
+}
+
 static double rank_key(double rank_tol) { return rank_tol > 0 ? rank_tol : 0.0; }
 
 int build_pinv(m2l_plan_t *pl) {
@@ -198,11 +236,10 @@ int build_pinv(m2l_plan_t *pl) {
 
 // SVD compression of Sec. 3.1 (Eqs. 12-14). Full rank (rank_tol <= 0) uses U = S = I: the
 // compressed form is then exact for any orthonormal bases, so no SVD is needed.
-int build_blas_host(m2l_plan_t *pl) {
-    if (pl->blas) return M2L_OK;
-    int rc = build_pinv(pl);
-    if (rc) return rc;
-    const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc, rank_key(pl->rank_tol));
+// The compressed operators at rank threshold `rank_tol` for the plan's kernel and orders, from the
+// shared table (built on a miss). Needs the plan's pseudo-inverse.
+static std::shared_ptr<const BlasOps> make_blas(const m2l_plan_t *pl, double rank_tol) {
+    const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc, rank_key(rank_tol));
     std::shared_ptr<const BlasOps> ops = g_blas_cache.find(key);
     if (!ops) {
         auto o = std::make_shared<BlasOps>();
@@ -211,7 +248,7 @@ int build_blas_host(m2l_plan_t *pl) {
 #pragma omp parallel for schedule(dynamic, 4)
         for (int t = 0; t < kNumTransfer; ++t) m2l_matrix(pl, t, Ks[t]);
         int k, kc;
-        if (pl->rank_tol <= 0) {
+        if (rank_tol <= 0) {
             k = n;
             kc = nc;
             o->U.assign((size_t)nc * kc, 0.0);
@@ -219,40 +256,25 @@ int build_blas_host(m2l_plan_t *pl) {
             o->S.assign((size_t)n * k, 0.0);
             for (int i = 0; i < n; ++i) o->S[(size_t)i * k + i] = 1.0;
         } else {
-            // K_thin = [K_1; ...; K_316] (316 nc x n): stack the column-major K_t. K_fat^T =
-            // [K_1^T; ...] (316 n x nc): a row-major K_t read as column-major is K_t^T.
-            std::vector<std::vector<double>> thin(kNumTransfer), fatT(kNumTransfer);
-            for (int t = 0; t < kNumTransfer; ++t) {
-                fatT[t] = Ks[t];
-                thin[t].resize((size_t)nc * n);
-                for (int i = 0; i < nc; ++i)
-                    for (int j = 0; j < n; ++j) thin[t][(size_t)j * nc + i] = Ks[t][(size_t)i * n + j];
-            }
-            std::vector<double> Rf = stacked_r_factor(std::move(fatT), nc);
-            std::vector<double> Rt = stacked_r_factor(std::move(thin), n);
-            std::vector<double> Uf, Vf, Ut_, Vt_;
-            jacobi_svd(Rf, nc, nc, Uf, o->s_fat, Vf);
-            jacobi_svd(Rt, n, n, Ut_, o->s_thin, Vt_);
+            std::shared_ptr<const SvdBasis> B = svd_basis(pl, Ks);
+            o->s_fat = B->s_fat;
+            o->s_thin = B->s_thin;
             int kf = 0, kt = 0;
-            while (kf < nc && o->s_fat[kf] / o->s_fat[0] >= pl->rank_tol) ++kf;
-            while (kt < n && o->s_thin[kt] / o->s_thin[0] >= pl->rank_tol) ++kt;
+            while (kf < nc && o->s_fat[kf] / o->s_fat[0] >= rank_tol) ++kf;
+            while (kt < n && o->s_thin[kt] / o->s_thin[0] >= rank_tol) ++kt;
             if (nc == n) {
                 k = kc = std::max(std::max(kf, kt), 1);  // equal orders: one k (Sec. 3.1)
             } else {
                 kc = std::max(kf, 1);                    // check and equivalent spaces of different sizes
                 k = std::max(kt, 1);
             }
-            // U: left singular vectors of K_fat = right singular vectors of K_fat^T (and of Rf).
-            // The kept columns of both bases are re-orthonormalised, so that U_k U_k^T and
-            // S_k S_k^T are projectors to rounding.
-            orthonormalize_columns(Vf.data(), nc, kc);
-            orthonormalize_columns(Vt_.data(), n, k);
+            // U, S: the leading columns of the (re-orthonormalised) bases, stored row-major
             o->U.assign((size_t)nc * kc, 0.0);
             o->S.assign((size_t)n * k, 0.0);
             for (int c = 0; c < kc; ++c)
-                for (int i = 0; i < nc; ++i) o->U[(size_t)i * kc + c] = Vf[(size_t)c * nc + i];
+                for (int i = 0; i < nc; ++i) o->U[(size_t)i * kc + c] = B->Uf[(size_t)c * nc + i];
             for (int c = 0; c < k; ++c)
-                for (int i = 0; i < n; ++i) o->S[(size_t)i * k + c] = Vt_[(size_t)c * n + i];
+                for (int i = 0; i < n; ++i) o->S[(size_t)i * k + c] = B->Sb[(size_t)c * n + i];
         }
         o->k = k;
         o->kc = kc;
@@ -293,6 +315,14 @@ int build_blas_host(m2l_plan_t *pl) {
         fold(pl->pinv->Uteps32, pl->pinv->r32, o->Aop32);
         ops = g_blas_cache.publish(key, std::move(o));
     }
+    return ops;
+}
+
+int build_blas_host(m2l_plan_t *pl) {
+    if (pl->blas) return M2L_OK;
+    int rc = build_pinv(pl);
+    if (rc) return rc;
+    std::shared_ptr<const BlasOps> ops = make_blas(pl, pl->rank_tol);
     pl->blas = ops;
     pl->k = ops->k;
     pl->kp = round_up(ops->k, 16);
@@ -305,16 +335,15 @@ int build_blas_host(m2l_plan_t *pl) {
 // k_t singular values of C_t at or above dir_tol s_0(C_t). Packed as the contraction reads them:
 // Ubar_t as [kc_pad][k_t8] (one row per output component) and Vbar'_t^T as [k_t8][k_pad], k_t
 // rounded up to 8 with zero padding.
-int build_directional(m2l_plan_t *pl) {
-    if (pl->dirop) return M2L_OK;
-    int rc = build_blas_host(pl);
-    if (rc) return rc;
-    const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc, rank_key(pl->rank_tol), pl->dir_tol);
+// The directional factors at threshold dir_tol of the compressed operators `B` (rank threshold
+// rank_tol), from the shared table (built on a miss).
+static std::shared_ptr<const DirOps> make_dir(const m2l_plan_t *pl, const BlasOps &B, double rank_tol, double dir_tol) {
+    const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc, rank_key(rank_tol), dir_tol);
     std::shared_ptr<const DirOps> ops = g_dir_cache.find(key);
     if (!ops) {
         auto o = std::make_shared<DirOps>();
-        const int k = pl->k, kp = pl->kp, kc = pl->kc, kcp = pl->kcp;
-        const std::vector<double> &Call = pl->blas->C;
+        const int k = B.k, kp = round_up(B.k, 16), kc = B.kc, kcp = round_up(B.kc, 16);
+        const std::vector<double> &Call = B.C;
         std::vector<int> kt(kNumTransfer);
         std::vector<std::vector<double>> ub(kNumTransfer), vt(kNumTransfer);
 #pragma omp parallel for schedule(dynamic, 2)
@@ -336,7 +365,7 @@ int build_directional(m2l_plan_t *pl) {
             // left singular vectors of C_t (check side, kc values)
             auto left = [&](int j, int a) { return tall ? U[(size_t)j * kc + a] : V[(size_t)j * kc + a]; };
             int r = 0;
-            while (r < nn && sv[r] >= pl->dir_tol * sv[0]) ++r;
+            while (r < nn && sv[r] >= dir_tol * sv[0]) ++r;
             if (r < 1) r = 1;
             const int r8 = round_up(r, 8);
             kt[t] = r;
@@ -373,9 +402,113 @@ int build_directional(m2l_plan_t *pl) {
         }
         ops = g_dir_cache.publish(key, std::move(o));
     }
+    return ops;
+}
+
+int build_directional(m2l_plan_t *pl) {
+    if (pl->dirop) return M2L_OK;
+    int rc = build_blas_host(pl);
+    if (rc) return rc;
+    std::shared_ptr<const DirOps> ops = make_dir(pl, *pl->blas, pl->rank_tol, pl->dir_tol);
     pl->dirop = ops;
     pl->dir_kt8_max = ops->kt8_max;
     return M2L_OK;
+}
+
+// Relative error (Eq. 16) that truncating the compressed operators at rank threshold rank_tol adds to
+// the check potential of one target box of octant 0 with all 189 of its transfer vectors, against
+// the full K_t: U_k U_k^T K_t S_k S_k^T q summed over the transfer vectors, for four seeded draws
+// of the source densities (two uniform in [-1, 1], two uniform in [0, 1)), the largest of the
+// four. A directional threshold dir_tol > 0 adds 10 dir_tol, the size of the error a directional
+// cut was measured to add (p = 4..10). Only the SVD bases are needed, so trying many ranks costs
+// one SVD. FP64, on the host.
+double truncation_estimate(m2l_plan_t *pl, double rank_tol, double dir_tol) {
+    if (build_pinv(pl)) return 1.0;
+    const int n = pl->n, nc = pl->nc;
+    int k = n, kc = nc;
+    std::shared_ptr<const SvdBasis> B;
+    if (rank_tol > 0) {
+        B = g_svd_cache.find(std::make_tuple(pl->kernel, pl->p, pl->pc));
+        if (!B) {
+            std::vector<std::vector<double>> Ks(kNumTransfer);
+#pragma omp parallel for schedule(dynamic, 4)
+            for (int t = 0; t < kNumTransfer; ++t) m2l_matrix(pl, t, Ks[t]);
+            B = svd_basis(pl, Ks);
+        }
+        int kf = 0, kt = 0;
+        while (kf < nc && B->s_fat[kf] / B->s_fat[0] >= rank_tol) ++kf;
+        while (kt < n && B->s_thin[kt] / B->s_thin[0] >= rank_tol) ++kt;
+        k = nc == n ? std::max(std::max(kf, kt), 1) : std::max(kt, 1);
+        kc = nc == n ? k : std::max(kf, 1);
+    }
+    std::vector<int> ts;
+    for (int x = -2; x <= 3; ++x)
+        for (int y = -2; y <= 3; ++y)
+            for (int z = -2; z <= 3; ++z) {
+                const int t = transfer_index(x, y, z);
+                if (t >= 0) ts.push_back(t);
+            }
+    std::vector<std::vector<double>> Kp(ts.size());
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < (int)ts.size(); ++i) m2l_matrix(pl, ts[i], Kp[i]);
+    double worst = 0.0;
+    std::mt19937_64 gen(24080);
+    std::uniform_real_distribution<double> u11(-1.0, 1.0), u01(0.0, 1.0);
+    std::vector<double> phi((size_t)nc), apx((size_t)nc), q((size_t)n), sq((size_t)n), w((size_t)nc), c((size_t)std::max(k, kc));
+    for (int draw = 0; draw < 4; ++draw) {
+        std::fill(phi.begin(), phi.end(), 0.0);
+        std::fill(apx.begin(), apx.end(), 0.0);
+        for (size_t it = 0; it < ts.size(); ++it) {
+            for (int j = 0; j < n; ++j) q[j] = draw < 2 ? u11(gen) : u01(gen);
+            const std::vector<double> &K = Kp[it];
+            // S_k S_k^T q (the full q at full rank)
+            if (B) {
+                for (int a = 0; a < k; ++a) {
+                    double v = 0.0;
+                    for (int j = 0; j < n; ++j) v += B->Sb[(size_t)a * n + j] * q[j];
+                    c[a] = v;
+                }
+                for (int j = 0; j < n; ++j) {
+                    double v = 0.0;
+                    for (int a = 0; a < k; ++a) v += B->Sb[(size_t)a * n + j] * c[a];
+                    sq[j] = v;
+                }
+            } else {
+                sq = q;
+            }
+            for (int i = 0; i < nc; ++i) {
+                double a = 0.0, b = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    a += K[(size_t)i * n + j] * q[j];
+                    b += K[(size_t)i * n + j] * sq[j];
+                }
+                phi[i] += a;
+                w[i] = b;
+            }
+            // U_k U_k^T (K_t S_k S_k^T q)
+            if (B) {
+                for (int a = 0; a < kc; ++a) {
+                    double v = 0.0;
+                    for (int i = 0; i < nc; ++i) v += B->Uf[(size_t)a * nc + i] * w[i];
+                    c[a] = v;
+                }
+                for (int i = 0; i < nc; ++i) {
+                    double v = 0.0;
+                    for (int a = 0; a < kc; ++a) v += B->Uf[(size_t)a * nc + i] * c[a];
+                    apx[i] += v;
+                }
+            } else {
+                for (int i = 0; i < nc; ++i) apx[i] += w[i];
+            }
+        }
+        double num = 0.0, den = 0.0;
+        for (int i = 0; i < nc; ++i) {
+            num += (apx[i] - phi[i]) * (apx[i] - phi[i]);
+            den += phi[i] * phi[i];
+        }
+        worst = std::max(worst, den > 0 ? std::sqrt(num / den) : 0.0);
+    }
+    return worst + (dir_tol > 0 ? 10.0 * dir_tol : 0.0);
 }
 
 // Algorithmic flops of the BLAS contraction for one right-hand side at `level` (-1: levels

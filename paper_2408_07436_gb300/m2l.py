@@ -33,6 +33,8 @@ M2L_OPT_DIR_TOL = 9
 M2L_OPT_CHECK_ORDER = 10
 M2L_OPT_TC_CHUNK = 11
 M2L_OPT_TC_DRAIN = 12
+M2L_OPT_RANK_AUTO = 13
+M2L_Q_RANK_TOL = 17
 M2L_Q_CONTRACT_FLOPS, M2L_Q_DIR_RANK_SUM, M2L_Q_NC, M2L_Q_RANK_CHECK = 13, 14, 15, 16
 STAGES = ["compress", "contract", "expand", "fft_forward", "hadamard", "fft_inverse", "pinv"]
 M2L_NUM_STAGES = 7
@@ -205,7 +207,8 @@ class Plan:
         self.set(form=form, precision=precision)
 
     def set(self, form=None, precision=None, accumulate=None, output=None, target_tol=None, fft_grid=None,
-            timing=None, tc_group=None, dir_tol=None, check_order=None, tc_chunk=None, tc_drain=None):
+            timing=None, tc_group=None, dir_tol=None, check_order=None, tc_chunk=None, tc_drain=None,
+            rank_auto=None):
         if form is not None:
             _check(m2l_set_option(self.handle, M2L_OPT_FORM, FORMS[form]))
         if precision is not None:
@@ -231,6 +234,8 @@ class Plan:
             _check(m2l_set_option(self.handle, M2L_OPT_TC_CHUNK, int(tc_chunk)))
         if tc_drain is not None:
             _check(m2l_set_option(self.handle, M2L_OPT_TC_DRAIN, int(tc_drain)))
+        if rank_auto is not None:
+            _check(m2l_set_option(self.handle, M2L_OPT_RANK_AUTO, int(bool(rank_auto))))
         return self
 
     def stage_times(self):
@@ -252,6 +257,10 @@ class Plan:
 
     def query(self, what: int, level: int = -1) -> int:
         return m2l_query(self.handle, what, level)
+
+    def current_rank_tol(self) -> float:
+        """The plan's current rank threshold (as given, or as M2L_OPT_RANK_AUTO chose it)."""
+        return struct.unpack("<d", struct.pack("<q", self.query(M2L_Q_RANK_TOL)))[0]
 
     @property
     def n(self) -> int:

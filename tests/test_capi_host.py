@@ -357,3 +357,35 @@ def test_plans_built_from_several_threads_get_one_operator_set(lib):
         for h in handles:
             if h is not None:
                 lib.m2l_destroy(h)
+
+
+@pytest.mark.parametrize("p,target", [(4, 1e-4), (5, 1e-6), (6, 1e-5)])
+def test_rank_auto_choice_meets_the_target_in_the_oracle(lib, p, target):
+    """M2L_OPT_RANK_AUTO on an explicit FP64 BLAS plan picks its rank threshold on the host (at the
+    first form query); the oracle's own compressed form at that threshold, with densities of both
+    signs, must then meet the target against the dense definition (Eq. 16), and a looser target
+    must not give a finer rank."""
+    from paper_2408_07436_gb300 import workloads as W
+    pl = lib.Plan(3, p, 1e-9, form="blas", precision="fp64").set(target_tol=target, rank_auto=1)
+    try:
+        pl.query(lib.M2L_Q_FORM, 1)
+        r = pl.current_rank_tol()
+        k = pl.query(lib.M2L_Q_RANK)
+    finally:
+        pl.close()
+    assert r == 0.0 or 1e-9 <= r <= 1e-3
+    wl = W.small(depth=3, p=p, density="u11", seed=21)
+    ops = O.compressed_operators(p, r, 1.0)
+    assert ops["k"] == k
+    for level in wl.levels:
+        q = wl.multipoles(level)
+        tg = np.arange(0, 8 ** level, 7)
+        _, phi_c = M.m2l_compressed(p, level, q, ops, targets=tg)
+        _, phi_d = M.m2l_dense(p, level, q, targets=tg)
+        assert M.rel_l2_error(phi_d / 2.0 ** level, phi_c) <= target, (level, r)
+    loose = lib.Plan(3, p, 1e-9, form="blas", precision="fp64").set(target_tol=target * 100, rank_auto=1)
+    try:
+        loose.query(lib.M2L_Q_FORM, 1)
+        assert loose.current_rank_tol() >= r or r == 0.0
+    finally:
+        loose.close()
