@@ -103,6 +103,12 @@ enum m2l_option_e {
                                 follows at a tenth of it. Resolved, and the plan's operators rebuilt, at
                                 the first apply or M2L_Q_FORM / M2L_Q_PRECISION query per target; read the
                                 result with M2L_Q_RANK_TOL. 0 (default): rank_tol as given */
+    M2L_OPT_SVD = 14,        /* SVD of the stacked operators K_fat, K_thin (Eqs. 12-13) for a truncated rank:
+                                0 exact (default: tall-skinny QR, then one-sided Jacobi), 1 one-shot
+                                randomised (Sec. 3.1: Gaussian sketch with ten oversamples, no power
+                                iterations, its width grown from 0.6 n + 10 until the sketch's smallest
+                                singular value falls below rank_tol times the largest). Setup only; the
+                                rank tuner (M2L_OPT_RANK_AUTO) estimates with the exact bases */
     M2L_OPT_CHECK_ORDER = 10 /* order p_c of the downward check surface, p <= p_c <= 16 (0: p, the
                                 default). p_c > p gives n_c = 6(p_c-1)^2+2 check points for the n
                                 equivalent points (the BLAS tables' P_c > P_e): K_t and the

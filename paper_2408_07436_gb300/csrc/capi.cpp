@@ -139,6 +139,16 @@ int m2l_set_option(m2l_plan_t *pl, int key, long long value) {
             if (value < 1 || value > kPerOctant) break;
             pl->tc_group = (int)value;
             return M2L_OK;
+        case M2L_OPT_SVD:
+            if (value != 0 && value != 1) break;
+            if ((int)value != pl->svd_mode) {
+                pl->svd_mode = (int)value;
+                pl->blas.reset();
+                pl->dirop.reset();
+                pl->tuned.clear();
+                release_operators(pl);
+            }
+            return M2L_OK;
         case M2L_OPT_RANK_AUTO:
             if (value != 0 && value != 1) break;
             if ((int)value != pl->rank_auto) {

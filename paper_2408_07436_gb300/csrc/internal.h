@@ -172,6 +172,7 @@ struct m2l_plan_s {
     int capturing = 0;                             // inside a batch capture: no timing events
     struct Tuned { int R; double tol; int form_opt, prec_opt; long long levels_version; int form, precision; double rank; };
     int rank_auto = 0;                             // M2L_OPT_RANK_AUTO
+    int svd_mode = 0;                              // M2L_OPT_SVD: 0 exact, 1 one-shot randomised
     double rank_auto_tol = -1.0;                   // target the rank was last chosen for (explicit form)
     std::vector<Tuned> tuned;                      // autotuner decisions
     long long launches = 0;

@@ -165,8 +165,8 @@ class OpCache {
 
 // keys: (kernel, p, p_c[, rank_tol[, dir_tol]]) and (kernel, p, grid)
 static OpCache<PinvOps, std::tuple<int, int, int>> g_pinv_cache;
-static OpCache<BlasOps, std::tuple<int, int, int, double>> g_blas_cache;
-static OpCache<DirOps, std::tuple<int, int, int, double, double>> g_dir_cache;
+static OpCache<BlasOps, std::tuple<int, int, int, double, int>> g_blas_cache;   // last: SVD mode
+static OpCache<DirOps, std::tuple<int, int, int, double, double, int>> g_dir_cache;
 static OpCache<FftOps, std::tuple<int, int, int>> g_fft_cache;
 
 // The full SVD bases of the stacked operators (Eqs. 12-13) for one (kernel, p, p_c): every rank
@@ -179,6 +179,87 @@ struct SvdBasis {
     std::vector<double> s_fat, s_thin;
 };
 static OpCache<SvdBasis, std::tuple<int, int, int>> g_svd_cache;
+// randomised bases, by (kernel, p, p_c, rank threshold): their width depends on the threshold
+static OpCache<SvdBasis, std::tuple<int, int, int, double>> g_rsvd_cache;
+
+// One-shot randomised SVD (Sec. 3.1; Halko, Martinsson and Tropp, SIAM Review 2011, Alg. 4.1 and
+// 5.1) of the wide stacked matrix A = [A_1 ... A_T] (m rows), A_t = K_t (m = nc, the fat stack) or
+// A_t = K_t^T (m = n, the transposed thin stack): Y = A Omega with a Gaussian Omega of width l,
+// Q = orth(Y), then the SVD of B = Q^T A through the R factor of B^T (tall-skinny QR of the blocks
+// A_t^T Q, then Jacobi on l x l); the left singular vectors are Q times those of B. No power
+// iterations. The width starts at 0.6 m + 10 (ten oversamples beyond the ranks the thresholds of
+// interest keep: 143 of 152 at p = 6, 173 of 296 at p = 8 for 1e-7) and grows by half while the
+// smallest sketched singular value is still at or above rank_tol times the largest, so every
+// singular value the threshold keeps lies inside the sketch; at l = m it spans the column space.
+static void rsvd_left(const std::vector<std::vector<double>> &Ks, int nc, int n, bool transpose, double rank_tol,
+                      std::vector<double> &U, std::vector<double> &sv) {
+    const int m = transpose ? n : nc, w = transpose ? nc : n;  // A_t is m x w
+    auto at = [&](int t, int i, int j) {                        // A_t[i][j]
+        return transpose ? Ks[t][(size_t)j * n + i] : Ks[t][(size_t)i * n + j];
+    };
+    int l = std::min(m, (3 * m) / 5 + 10);
+    for (;;) {
+        std::vector<double> Y((size_t)m * l, 0.0);  // column-major m x l
+#pragma omp parallel
+        {
+            std::vector<double> Yp((size_t)m * l, 0.0), om((size_t)w * l);
+#pragma omp for schedule(static)
+            for (int t = 0; t < kNumTransfer; ++t) {
+                std::mt19937_64 gen(0x5eed0000ULL + (uint64_t)t * 7919ULL + (uint64_t)l);
+                std::normal_distribution<double> g(0.0, 1.0);
+                for (auto &v : om) v = g(gen);
+                for (int i = 0; i < m; ++i)
+                    for (int j = 0; j < w; ++j) {
+                        const double a = at(t, i, j);
+                        const double *o = &om[(size_t)j * l];
+                        for (int c = 0; c < l; ++c) Yp[(size_t)c * m + i] += a * o[c];
+                    }
+            }
+#pragma omp critical
+            for (size_t e = 0; e < Y.size(); ++e) Y[e] += Yp[e];
+        }
+        orthonormalize_columns(Y.data(), m, l);  // Q
+        // blocks of B^T: A_t^T Q (w x l, column-major)
+        std::vector<std::vector<double>> blocks(kNumTransfer);
+#pragma omp parallel for schedule(static)
+        for (int t = 0; t < kNumTransfer; ++t) {
+            std::vector<double> &b = blocks[t];
+            b.assign((size_t)w * l, 0.0);
+            for (int c = 0; c < l; ++c)
+                for (int i = 0; i < m; ++i) {
+                    const double qv = Y[(size_t)c * m + i];
+                    if (qv == 0.0) continue;
+                    for (int j = 0; j < w; ++j) b[(size_t)c * w + j] += at(t, i, j) * qv;
+                }
+        }
+        std::vector<double> R = stacked_r_factor(std::move(blocks), l);
+        std::vector<double> Ur, Vr;
+        jacobi_svd(R, l, l, Ur, sv, Vr);  // B = R^T Q2^T: left singular vectors of B = Vr
+        const bool complete = l == m || sv[l - 1] < rank_tol * sv[0];
+        if (complete) {
+            U.assign((size_t)m * l, 0.0);
+            for (int c = 0; c < l; ++c)
+                for (int a = 0; a < l; ++a) {
+                    const double v = Vr[(size_t)c * l + a];
+                    for (int i = 0; i < m; ++i) U[(size_t)c * m + i] += Y[(size_t)a * m + i] * v;
+                }
+            orthonormalize_columns(U.data(), m, l);
+            return;
+        }
+        l = std::min(m, l + l / 2);
+    }
+}
+
+static std::shared_ptr<const SvdBasis> rsvd_basis(const m2l_plan_t *pl, const std::vector<std::vector<double>> &Ks,
+                                                  double rank_tol) {
+    const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc, rank_tol);
+    std::shared_ptr<const SvdBasis> b = g_rsvd_cache.find(key);
+    if (b) return b;
+    auto o = std::make_shared<SvdBasis>();
+    rsvd_left(Ks, pl->nc, pl->n, false, rank_tol, o->Uf, o->s_fat);  // left singular vectors of K_fat
+    rsvd_left(Ks, pl->nc, pl->n, true, rank_tol, o->Sb, o->s_thin);  // right singular vectors of K_thin
+    return g_rsvd_cache.publish(key, std::move(o));
+}
 
 static std::shared_ptr<const SvdBasis> svd_basis(const m2l_plan_t *pl, const std::vector<std::vector<double>> &Ks) {
     const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc);
@@ -239,7 +320,7 @@ int build_pinv(m2l_plan_t *pl) {
 // The compressed operators at rank threshold `rank_tol` for the plan's kernel and orders, from the
 // shared table (built on a miss). Needs the plan's pseudo-inverse.
 static std::shared_ptr<const BlasOps> make_blas(const m2l_plan_t *pl, double rank_tol) {
-    const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc, rank_key(rank_tol));
+    const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc, rank_key(rank_tol), pl->svd_mode);
     std::shared_ptr<const BlasOps> ops = g_blas_cache.find(key);
     if (!ops) {
         auto o = std::make_shared<BlasOps>();
@@ -256,14 +337,16 @@ static std::shared_ptr<const BlasOps> make_blas(const m2l_plan_t *pl, double ran
             o->S.assign((size_t)n * k, 0.0);
             for (int i = 0; i < n; ++i) o->S[(size_t)i * k + i] = 1.0;
         } else {
-            std::shared_ptr<const SvdBasis> B = svd_basis(pl, Ks);
+            std::shared_ptr<const SvdBasis> B = pl->svd_mode ? rsvd_basis(pl, Ks, rank_tol) : svd_basis(pl, Ks);
             o->s_fat = B->s_fat;
             o->s_thin = B->s_thin;
             int kf = 0, kt = 0;
-            while (kf < nc && o->s_fat[kf] / o->s_fat[0] >= rank_tol) ++kf;
-            while (kt < n && o->s_thin[kt] / o->s_thin[0] >= rank_tol) ++kt;
+            const int lf = (int)o->s_fat.size(), lt = (int)o->s_thin.size();  // sketch widths (rSVD)
+            while (kf < lf && o->s_fat[kf] / o->s_fat[0] >= rank_tol) ++kf;
+            while (kt < lt && o->s_thin[kt] / o->s_thin[0] >= rank_tol) ++kt;
             if (nc == n) {
-                k = kc = std::max(std::max(kf, kt), 1);  // equal orders: one k (Sec. 3.1)
+                // equal orders: one k (Sec. 3.1), within both sketches when they are randomised
+                k = kc = std::min(std::max(std::max(kf, kt), 1), std::min(lf, lt));
             } else {
                 kc = std::max(kf, 1);                    // check and equivalent spaces of different sizes
                 k = std::max(kt, 1);
@@ -338,7 +421,7 @@ int build_blas_host(m2l_plan_t *pl) {
 // The directional factors at threshold dir_tol of the compressed operators `B` (rank threshold
 // rank_tol), from the shared table (built on a miss).
 static std::shared_ptr<const DirOps> make_dir(const m2l_plan_t *pl, const BlasOps &B, double rank_tol, double dir_tol) {
-    const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc, rank_key(rank_tol), dir_tol);
+    const auto key = std::make_tuple(pl->kernel, pl->p, pl->pc, rank_key(rank_tol), dir_tol, pl->svd_mode);
     std::shared_ptr<const DirOps> ops = g_dir_cache.find(key);
     if (!ops) {
         auto o = std::make_shared<DirOps>();

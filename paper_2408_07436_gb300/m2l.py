@@ -34,6 +34,7 @@ M2L_OPT_CHECK_ORDER = 10
 M2L_OPT_TC_CHUNK = 11
 M2L_OPT_TC_DRAIN = 12
 M2L_OPT_RANK_AUTO = 13
+M2L_OPT_SVD = 14
 M2L_Q_RANK_TOL = 17
 M2L_Q_CONTRACT_FLOPS, M2L_Q_DIR_RANK_SUM, M2L_Q_NC, M2L_Q_RANK_CHECK = 13, 14, 15, 16
 STAGES = ["compress", "contract", "expand", "fft_forward", "hadamard", "fft_inverse", "pinv"]
@@ -208,7 +209,7 @@ class Plan:
 
     def set(self, form=None, precision=None, accumulate=None, output=None, target_tol=None, fft_grid=None,
             timing=None, tc_group=None, dir_tol=None, check_order=None, tc_chunk=None, tc_drain=None,
-            rank_auto=None):
+            rank_auto=None, svd=None):
         if form is not None:
             _check(m2l_set_option(self.handle, M2L_OPT_FORM, FORMS[form]))
         if precision is not None:
@@ -236,6 +237,8 @@ class Plan:
             _check(m2l_set_option(self.handle, M2L_OPT_TC_DRAIN, int(tc_drain)))
         if rank_auto is not None:
             _check(m2l_set_option(self.handle, M2L_OPT_RANK_AUTO, int(bool(rank_auto))))
+        if svd is not None:
+            _check(m2l_set_option(self.handle, M2L_OPT_SVD, {"exact": 0, "randomised": 1}[svd]))
         return self
 
     def stage_times(self):

@@ -389,3 +389,29 @@ def test_rank_auto_choice_meets_the_target_in_the_oracle(lib, p, target):
         assert loose.current_rank_tol() >= r or r == 0.0
     finally:
         loose.close()
+
+
+@pytest.mark.parametrize("p,tol", [(5, 1e-6), (6, 1e-7), (8, 1e-7)])
+def test_randomised_setup_svd_matches_the_exact_truncation(lib, p, tol):
+    """M2L_OPT_SVD = 1 (one-shot randomised SVD of the stacked operators, Sec. 3.1) against the
+    oracle's exact compression at the same threshold: orthonormal bases, the same rank within one
+    symmetry triplet (the sketch underestimates tail singular values, having no power iterations),
+    and a truncation error of every K_t within three times the exact one or below tol itself (a
+    one-shot sketch is near-optimal within a modest factor), and always below 10 tol."""
+    n = G.n_surface(p)
+    pl = lib.Plan(3, p, tol).set(svd="randomised")
+    try:
+        k = pl.query(lib.M2L_Q_RANK)
+        U = lib.m2l_get_operator(pl.handle, 0).reshape(n, k)
+        S = lib.m2l_get_operator(pl.handle, 1).reshape(n, k)
+    finally:
+        pl.close()
+    ops = O.compressed_operators(p, tol, 1.0)
+    assert abs(k - ops["k"]) <= 3
+    assert np.allclose(U.T @ U, np.eye(k), atol=1e-12) and np.allclose(S.T @ S, np.eye(k), atol=1e-12)
+    for t in range(0, 316, 7):
+        K = ops["K"][t]
+        nk = np.linalg.norm(K, 2)
+        mine = np.linalg.norm(U @ (U.T @ K @ S) @ S.T - K, 2) / nk
+        exact = np.linalg.norm(ops["U"] @ ops["C"][t] @ ops["S"].T - K, 2) / nk
+        assert mine <= max(3 * exact, tol) and mine < 10 * tol, (t, mine, exact)
