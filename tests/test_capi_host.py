@@ -396,8 +396,9 @@ def test_randomised_setup_svd_matches_the_exact_truncation(lib, p, tol):
     """M2L_OPT_SVD = 1 (one-shot randomised SVD of the stacked operators, Sec. 3.1) against the
     oracle's exact compression at the same threshold: orthonormal bases, the same rank within one
     symmetry triplet (the sketch underestimates tail singular values, having no power iterations),
-    and a truncation error of every K_t within three times the exact one or below tol itself (a
-    one-shot sketch is near-optimal within a modest factor), and always below 10 tol."""
+    and a truncation error of every K_t within three times the exact one or below 2 tol (a one-shot
+    sketch is near-optimal within a modest factor, and a triplet dropped at the cut has singular
+    values just above tol: 1.06e-7 at p = 8, tol 1e-7), and always below 10 tol."""
     n = G.n_surface(p)
     pl = lib.Plan(3, p, tol).set(svd="randomised")
     try:
@@ -414,4 +415,4 @@ def test_randomised_setup_svd_matches_the_exact_truncation(lib, p, tol):
         nk = np.linalg.norm(K, 2)
         mine = np.linalg.norm(U @ (U.T @ K @ S) @ S.T - K, 2) / nk
         exact = np.linalg.norm(ops["U"] @ ops["C"][t] @ ops["S"].T - K, 2) / nk
-        assert mine <= max(3 * exact, tol) and mine < 10 * tol, (t, mine, exact)
+        assert mine <= max(3 * exact, 2 * tol) and mine < 10 * tol, (t, mine, exact)
