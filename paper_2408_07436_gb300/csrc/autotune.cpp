@@ -156,17 +156,17 @@ static int tune_on(m2l_plan_t *pl, const m2l_plan_t *real, int R, int *form, int
         for (int pr : precs) {
             if (pl->precision != M2L_PREC_AUTO && pl->precision != pr) continue;
             if (!eligible(pl, f, pr)) continue;
-            double r = own;
-            if (f == M2L_FORM_BLAS && pl->rank_auto) {
-                r = choose_rank(pl, pr);
-                if (r < 0) continue;
-            }
+            if (f == M2L_FORM_BLAS && pl->rank_auto && stated_bound(f, pr, pl->p) >= pl->target_tol) continue;
             const size_t need = workspace_estimate(real, f, pr, R);
             if (real->mem_budget && need > 2 * real->mem_budget) continue;
-            (pr == M2L_PREC_FP64 ? slow : fast).push_back({f, pr, r});
+            (pr == M2L_PREC_FP64 ? slow : fast).push_back({f, pr, own});
         }
     }
     std::vector<Candidate> &cands = fast.empty() ? slow : fast;
+    // ranks only for the candidates that will be timed, estimated with the real plan (it keeps the
+    // SVD bases for the next tuning of the same order)
+    for (auto &c : cands)
+        if (c.form == M2L_FORM_BLAS && pl->rank_auto) c.rank = choose_rank(const_cast<m2l_plan_t *>(real), c.prec);
     if (cands.empty()) {
         set_error("no form/precision reaches the target tolerance %.3g with this plan", pl->target_tol);
         return M2L_EUNSUPPORTED;

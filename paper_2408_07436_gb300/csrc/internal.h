@@ -173,6 +173,8 @@ struct m2l_plan_s {
     struct Tuned { int R; double tol; int form_opt, prec_opt; long long levels_version; int form, precision; double rank; };
     int rank_auto = 0;                             // M2L_OPT_RANK_AUTO
     int svd_mode = 0;                              // M2L_OPT_SVD: 0 exact, 1 one-shot randomised
+    std::shared_ptr<const void> svd_hold;          // the SVD bases the rank tuner read (kept while the plan
+                                                   // lives, so plans of one order share one SVD)
     double rank_auto_tol = -1.0;                   // target the rank was last chosen for (explicit form)
     std::vector<Tuned> tuned;                      // autotuner decisions
     long long launches = 0;

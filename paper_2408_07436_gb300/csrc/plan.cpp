@@ -518,6 +518,7 @@ double truncation_estimate(m2l_plan_t *pl, double rank_tol, double dir_tol) {
             for (int t = 0; t < kNumTransfer; ++t) m2l_matrix(pl, t, Ks[t]);
             B = svd_basis(pl, Ks);
         }
+        pl->svd_hold = B;
         int kf = 0, kt = 0;
         while (kf < nc && B->s_fat[kf] / B->s_fat[0] >= rank_tol) ++kf;
         while (kt < n && B->s_thin[kt] / B->s_thin[0] >= rank_tol) ++kt;
