@@ -9,7 +9,8 @@ and no other communication. With the halo added, the rank applies M2L to the spa
 which see every source they would see on a single GPU.
 
 This module holds only the host-side bookkeeping (which boxes, which rows) and the exchange over
-torch.distributed; it works with any backend (NCCL on GPUs, gloo on CPU).
+torch.distributed point-to-point messages; it works with any backend that has isend/irecv (gloo
+on CPU, NCCL on GPUs with device tensors).
 """
 
 from __future__ import annotations
@@ -54,13 +55,32 @@ def partition(keys: np.ndarray, level: int, rank: int, world: int):
     return own_rows, halo_rows, keys[local_rows], own_in_local
 
 
-def exchange_halo(q_level: np.ndarray, keys: np.ndarray, level: int, group=None):
-    """Gather, on every rank, the multipoles of its own and halo boxes of one level.
+def halo_routes(keys: np.ndarray, level: int, world: int):
+    """Who sends which rows to whom in one level's halo exchange.
+
+    routes[r][s] = positions in `keys` of the boxes rank r owns that rank s needs as halo (empty
+    for r == s). Every rank computes the same table from the keys alone, so no sizes are sent.
+    """
+    keys = np.asarray(keys, dtype=np.uint64)
+    parts = [partition(keys, level, r, world) for r in range(world)]
+    routes = [[np.zeros(0, dtype=np.int64) for _ in range(world)] for _ in range(world)]
+    for r in range(world):
+        own = parts[r][0]
+        for s in range(world):
+            if s != r:
+                routes[r][s] = np.intersect1d(own, parts[s][1], assume_unique=True)
+    return routes
+
+
+def exchange_halo(q_level: np.ndarray, keys: np.ndarray, level: int, group=None, return_stats=False):
+    """Fetch, by point-to-point messages, the multipoles of this rank's halo boxes of one level.
 
     q_level: (B_own, R, n) multipoles of the boxes this rank owns, in Morton order.
     keys:    sorted Morton keys of ALL boxes of the level (known to every rank).
-    Returns (local_keys, q_local, own_in_local) for the rank's sparse box set own + halo.
-    Each rank sends its own rows; the exchange is an all-gather of variable-size blocks.
+    Returns (local_keys, q_local, own_in_local) for the rank's sparse box set own + halo (and, with
+    return_stats, the number of rows received). Each rank sends to each other rank only the rows
+    of its slab that lie within 3 planes of the other's slab, and receives exactly its halo:
+    O(halo) data per rank, one exchange step per level.
     """
     import torch
     import torch.distributed as dist
@@ -68,17 +88,32 @@ def exchange_halo(q_level: np.ndarray, keys: np.ndarray, level: int, group=None)
     world = dist.get_world_size(group)
     rank = dist.get_rank(group)
     keys = np.asarray(keys, dtype=np.uint64)
-    owners = [partition(keys, level, r, world)[0] for r in range(world)]
-    R, n = q_level.shape[1], q_level.shape[2]
-    sizes = [len(o) for o in owners]
-    mx = max(sizes) if sizes else 0
-    send = torch.zeros((mx, R, n), dtype=torch.float64)
-    send[: len(owners[rank])] = torch.from_numpy(np.ascontiguousarray(q_level, dtype=np.float64))
-    recv = [torch.zeros_like(send) for _ in range(world)]
-    dist.all_gather(recv, send, group=group)
-    full = np.zeros((len(keys), R, n))
-    for r in range(world):
-        full[owners[r]] = recv[r][: sizes[r]].numpy()
     own_rows, halo_rows, local_keys, own_in_local = partition(keys, level, rank, world)
+    routes = halo_routes(keys, level, world)
+    q_level = np.ascontiguousarray(q_level)
+    R, n = q_level.shape[1], q_level.shape[2]
+    pos_in_own = {int(g): i for i, g in enumerate(own_rows)}
+    reqs, recvs = [], []
+    for s in range(world):
+        rows = routes[rank][s]
+        if s != rank and len(rows):
+            buf = torch.from_numpy(np.ascontiguousarray(q_level[[pos_in_own[int(g)] for g in rows]]))
+            reqs.append(dist.isend(buf, dst=s, group=group))
+    for s in range(world):
+        rows = routes[s][rank]
+        if s != rank and len(rows):
+            buf = torch.empty((len(rows), R, n), dtype=torch.from_numpy(q_level[:0]).dtype)
+            reqs.append(dist.irecv(buf, src=s, group=group))
+            recvs.append((rows, buf))
+    for rq in reqs:
+        rq.wait()
     local_rows = np.sort(np.concatenate([own_rows, halo_rows]))
-    return local_keys, full[local_rows], own_in_local
+    q_local = np.zeros((len(local_rows), R, n), dtype=q_level.dtype)
+    q_local[own_in_local] = q_level
+    received = 0
+    for rows, buf in recvs:
+        q_local[np.searchsorted(local_rows, rows)] = buf.numpy()
+        received += len(rows)
+    if return_stats:
+        return local_keys, q_local, own_in_local, received
+    return local_keys, q_local, own_in_local

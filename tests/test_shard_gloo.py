@@ -27,8 +27,12 @@ def _worker(rank, world, port, keys, q, p, level, out_path):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        own_rows, _, _, _ = shard.partition(keys, level, rank, world)
-        local_keys, q_local, own_in_local = shard.exchange_halo(q[own_rows], keys, level)
+        own_rows, halo_rows, _, _ = shard.partition(keys, level, rank, world)
+        local_keys, q_local, own_in_local, received = shard.exchange_halo(q[own_rows], keys, level,
+                                                                         return_stats=True)
+        assert received == len(halo_rows)   # exactly the halo, nothing else
+        assert np.array_equal(q_local[np.searchsorted(np.sort(np.concatenate([own_rows, halo_rows])), halo_rows)],
+                              q[halo_rows])
         _, phi = M.m2l_dense(p, level, q_local, keys=local_keys.astype(np.int64), targets=own_in_local)
         np.save(out_path, np.concatenate([own_rows[:, None].astype(np.float64).repeat(1, 1),
                                           phi.reshape(len(own_rows), -1)], axis=1))
@@ -82,3 +86,17 @@ def test_halo_is_within_three_planes():
     # slabs tile the level exactly
     b = shard.slab_bounds(level, 3)
     assert b[0][0] == 0 and b[-1][1] == 16 and all(b[i][1] == b[i + 1][0] for i in range(2))
+
+
+def test_halo_routes_cover_each_halo_once():
+    """Every halo box of every rank is sent by exactly its owner, once; nothing else is sent."""
+    rng = np.random.default_rng(6)
+    level = 4
+    keys = np.sort(rng.choice(8 ** level, size=2000, replace=False)).astype(np.uint64)
+    for world in (2, 3, 5):
+        routes = shard.halo_routes(keys, level, world)
+        for s in range(world):
+            _, halo, _, _ = shard.partition(keys, level, s, world)
+            got = np.sort(np.concatenate([routes[r][s] for r in range(world)]))
+            assert np.array_equal(got, np.sort(halo))
+            assert len(routes[s][s]) == 0
