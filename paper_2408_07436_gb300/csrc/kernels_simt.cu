@@ -280,10 +280,113 @@ int launch_gemm_xwt_ff(const float *X, long long ldx, const float *Wh, const flo
     return check_launch("gemm_ff");
 }
 
+// Y = X W^T (+ Y) in FP32 with 16-byte loads: 128 rows x 64 columns per CTA, a thread 8 rows x
+// 4 columns (two groups of 4 consecutive rows, 64 apart, read as two 16-byte shared loads), K in
+// blocks of 16 loaded into registers one block ahead of their use and stored to shared memory
+// transposed. Each block of 16 terms is summed on its own, then added to the running sum (the
+// same blocked accumulation as gemm_xwt_kernel). Needs K, ldx and ldw multiples of 4 and 16-byte
+// aligned X and W.
+__global__ void __launch_bounds__(256) gemm_xwt_f32v_kernel(const float *__restrict__ X, long long ldx,
+                                                            const float *__restrict__ W, long long ldw,
+                                                            float *__restrict__ Y, long long ldy, long long rows,
+                                                            int O, int K, int acc) {
+    constexpr int BM = 128, BN = 64, BK = 16;
+    __shared__ __align__(16) float Xs[BK][BM + 4];
+    __shared__ __align__(16) float Ws[BK][BN + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const long long row0 = (long long)blockIdx.x * BM;
+    const int col0 = blockIdx.y * BN;
+    // loaders: X rows tid / 4 and 64 + tid / 4, W row tid / 4, K offset (tid % 4) * 4
+    const int lr = tid >> 2, lk = (tid & 3) * 4;
+    float4 xr[2], wr;
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const long long gr = row0 + lr + 64 * h;
+            xr[h] = (gr < rows && k0 + lk < K) ? *reinterpret_cast<const float4 *>(X + gr * ldx + k0 + lk)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int gc = col0 + lr;
+        wr = (gc < O && k0 + lk < K) ? *reinterpret_cast<const float4 *>(W + (long long)gc * ldw + k0 + lk)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    float a[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[i][j] = 0.f;
+    load(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        __syncthreads();  // the previous block's operands are consumed
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            Xs[lk + 0][lr + 64 * h] = xr[h].x;
+            Xs[lk + 1][lr + 64 * h] = xr[h].y;
+            Xs[lk + 2][lr + 64 * h] = xr[h].z;
+            Xs[lk + 3][lr + 64 * h] = xr[h].w;
+        }
+        Ws[lk + 0][lr] = wr.x;
+        Ws[lk + 1][lr] = wr.y;
+        Ws[lk + 2][lr] = wr.z;
+        Ws[lk + 3][lr] = wr.w;
+        __syncthreads();
+        if (k0 + BK < K) load(k0 + BK);  // in flight while this block is summed
+        float bl[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bl[i][j] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            const float4 x0 = *reinterpret_cast<const float4 *>(&Xs[kk][ty * 4]);
+            const float4 x1 = *reinterpret_cast<const float4 *>(&Xs[kk][64 + ty * 4]);
+            const float4 w = *reinterpret_cast<const float4 *>(&Ws[kk][tx * 4]);
+            const float xa[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            const float wb[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bl[i][j] = fmaf(xa[i], wb[j], bl[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a[i][j] += bl[i][j];
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const long long r = row0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+        if (r >= rows) continue;
+        const int c = col0 + tx * 4;
+        float *y = Y + r * ldy + c;
+        if (c + 3 < O && (ldy & 3) == 0) {
+            float4 v = make_float4(a[i][0], a[i][1], a[i][2], a[i][3]);
+            if (acc) {
+                const float4 o = *reinterpret_cast<const float4 *>(y);
+                v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+            }
+            *reinterpret_cast<float4 *>(y) = v;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (c + j < O) y[j] = acc ? y[j] + a[i][j] : a[i][j];
+        }
+    }
+}
+
 template <class T>
 int launch_gemm_xwt(const T *X, long long ldx, const T *W, long long ldw, T *Y, long long ldy,
                     long long rows, int O, int K, int acc, cudaStream_t s) {
     if (rows <= 0 || O <= 0) return M2L_OK;
+    if constexpr (sizeof(T) == 4) {
+        const bool vec = K % 4 == 0 && ldx % 4 == 0 && ldw % 4 == 0 && ((uintptr_t)X & 15) == 0 && ((uintptr_t)W & 15) == 0;
+        if (vec) {
+            dim3 grid((unsigned)((rows + 127) / 128), (unsigned)((O + 63) / 64));
+            gemm_xwt_f32v_kernel<<<grid, 256, 0, s>>>((const float *)X, ldx, (const float *)W, ldw, (float *)Y, ldy, rows,
+                                                       O, K, acc);
+            return check_launch("gemm");
+        }
+    }
     switch (contract_tn(O, sizeof(T) == 8 ? 12 : 8)) {
         case 1: launch_gemm_tn<T, 1>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
         case 2: launch_gemm_tn<T, 2>(X, ldx, W, ldw, Y, ldy, rows, O, K, acc, s); break;
