@@ -272,9 +272,101 @@ __global__ void __launch_bounds__(256) gemm_xwt_ff_kernel(const float *__restric
     }
 }
 
+// gemm_xwt_ff_kernel on 128 x 64 tiles with 16-byte loads (as gemm_xwt_f32v_kernel): a thread
+// 8 rows x 4 columns, operands one K block ahead in registers. Same compensated arithmetic, term
+// for term in the same order, so results equal gemm_xwt_ff_kernel's. Needs K, ldx, ldw multiples
+// of 4 and 16-byte aligned X, Wh, Wl.
+__global__ void __launch_bounds__(256) gemm_xwt_ff_v_kernel(const float *__restrict__ X, long long ldx,
+                                                            const float *__restrict__ Wh, const float *__restrict__ Wl,
+                                                            long long ldw, float *__restrict__ Y, long long ldy,
+                                                            long long rows, int O, int K, int acc) {
+    constexpr int BM = 128, BN = 64, BK = 16;
+    __shared__ __align__(16) float Xs[BK][BM + 4];
+    __shared__ __align__(16) float Whs[BK][BN + 4];
+    __shared__ __align__(16) float Wls[BK][BN + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const long long row0 = (long long)blockIdx.x * BM;
+    const int col0 = blockIdx.y * BN;
+    const int lr = tid >> 2, lk = (tid & 3) * 4;
+    float4 xr[2], hr, lr4;
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const long long gr = row0 + lr + 64 * h;
+            xr[h] = (gr < rows && k0 + lk < K) ? *reinterpret_cast<const float4 *>(X + gr * ldx + k0 + lk)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int gc = col0 + lr;
+        const bool w = gc < O && k0 + lk < K;
+        hr = w ? *reinterpret_cast<const float4 *>(Wh + (long long)gc * ldw + k0 + lk) : make_float4(0.f, 0.f, 0.f, 0.f);
+        lr4 = w ? *reinterpret_cast<const float4 *>(Wl + (long long)gc * ldw + k0 + lk) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    float sh[8][4], sl[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
+    load(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            Xs[lk + 0][lr + 64 * h] = xr[h].x;
+            Xs[lk + 1][lr + 64 * h] = xr[h].y;
+            Xs[lk + 2][lr + 64 * h] = xr[h].z;
+            Xs[lk + 3][lr + 64 * h] = xr[h].w;
+        }
+        Whs[lk + 0][lr] = hr.x; Whs[lk + 1][lr] = hr.y; Whs[lk + 2][lr] = hr.z; Whs[lk + 3][lr] = hr.w;
+        Wls[lk + 0][lr] = lr4.x; Wls[lk + 1][lr] = lr4.y; Wls[lk + 2][lr] = lr4.z; Wls[lk + 3][lr] = lr4.w;
+        __syncthreads();
+        if (k0 + BK < K) load(k0 + BK);
+#pragma unroll 4
+        for (int kk = 0; kk < BK; ++kk) {
+            const float4 x0 = *reinterpret_cast<const float4 *>(&Xs[kk][ty * 4]);
+            const float4 x1 = *reinterpret_cast<const float4 *>(&Xs[kk][64 + ty * 4]);
+            const float4 wh4 = *reinterpret_cast<const float4 *>(&Whs[kk][tx * 4]);
+            const float4 wl4 = *reinterpret_cast<const float4 *>(&Wls[kk][tx * 4]);
+            const float xa[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            const float wh[4] = {wh4.x, wh4.y, wh4.z, wh4.w}, wl[4] = {wl4.x, wl4.y, wl4.z, wl4.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float p = __fmul_rn(xa[i], wh[j]);
+                    const float e = __fmaf_rn(xa[i], wh[j], -p);  // x w_hi = p + e exactly
+                    const float t = __fadd_rn(sh[i][j], p);
+                    const float z = __fsub_rn(t, sh[i][j]);
+                    const float d = __fadd_rn(__fsub_rn(sh[i][j], __fsub_rn(t, z)), __fsub_rn(p, z));  // s + p = t + d
+                    sh[i][j] = t;
+                    sl[i][j] = __fmaf_rn(xa[i], wl[j], __fadd_rn(sl[i][j], __fadd_rn(d, e)));
+                }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const long long r = row0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+        if (r >= rows) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = col0 + tx * 4 + j;
+            if (c < O) {
+                float v = __fadd_rn(sh[i][j], sl[i][j]);
+                if (acc) v = __fadd_rn(Y[r * ldy + c], v);
+                Y[r * ldy + c] = v;
+            }
+        }
+    }
+}
+
 int launch_gemm_xwt_ff(const float *X, long long ldx, const float *Wh, const float *Wl, long long ldw, float *Y,
                        long long ldy, long long rows, int O, int K, int acc, cudaStream_t s) {
     if (rows <= 0 || O <= 0) return M2L_OK;
+    if (K % 4 == 0 && ldx % 4 == 0 && ldw % 4 == 0 && ((uintptr_t)X & 15) == 0 && ((uintptr_t)Wh & 15) == 0 &&
+        ((uintptr_t)Wl & 15) == 0) {
+        dim3 grid((unsigned)((rows + 127) / 128), (unsigned)((O + 63) / 64));
+        gemm_xwt_ff_v_kernel<<<grid, 256, 0, s>>>(X, ldx, Wh, Wl, ldw, Y, ldy, rows, O, K, acc);
+        return check_launch("gemm_ff");
+    }
     dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((O + 63) / 64));
     gemm_xwt_ff_kernel<<<grid, 256, 0, s>>>(X, ldx, Wh, Wl, ldw, Y, ldy, rows, O, K, acc);
     return check_launch("gemm_ff");
