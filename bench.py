@@ -195,9 +195,10 @@ def workload_spec(name, depth):
     """(instances, explicit variants timed beside the headline, batched) of a named workload."""
     if name == "c2":
         return [W.c2(depth=depth)], ["blas-fp64", "blas-fp32", "blas-tf32x3", "blas-bf16x3", "fft-fp64",
-                                     "fft-fp32"], False
+                                     "fft-tf32x3", "fft-fp32"], False
     if name == "c3":
-        return [W.c3()], ["blas-bf16x3", "blas-tf32x3", "blas-fp32", "blas-fp64", "fft-fp32", "fft-fp64"], False
+        return [W.c3()], ["blas-bf16x3", "blas-tf32x3", "blas-fp32", "blas-fp64", "fft-tf32x3", "fft-fp32",
+                          "fft-fp64"], False
     if name == "c4":
         return [W.c4()], ["blas-bf16x3", "blas-tf32x3", "fft-fp32"], False
     if name == "c5":

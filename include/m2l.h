@@ -109,6 +109,12 @@ enum m2l_option_e {
                                 iterations, its width grown from 0.6 n + 10 until the sketch's smallest
                                 singular value falls below rank_tol times the largest). Setup only; the
                                 rank tuner (M2L_OPT_RANK_AUTO) estimates with the exact bases */
+    M2L_OPT_HADAMARD_CHAINS = 15, /* FFT form in TF32x3: partial sums per tile of the tensor-core Hadamard
+                                products, 1, 2, 4 or 8 (0: 4, the default). Each sums the products of a
+                                fixed subset of the 26 source-cluster directions in tensor memory (every
+                                subset holds an in-plane direction); the epilogue adds them in FP32 with
+                                round-to-nearest. More partial sums shorten the truncating tensor-core
+                                accumulation chains (more accurate); the result is otherwise the same */
     M2L_OPT_CHECK_ORDER = 10 /* order p_c of the downward check surface, p <= p_c <= 16 (0: p, the
                                 default). p_c > p gives n_c = 6(p_c-1)^2+2 check points for the n
                                 equivalent points (the BLAS tables' P_c > P_e): K_t and the
@@ -136,7 +142,9 @@ enum m2l_precision_e {
     M2L_PREC_AUTO = -1,   /* chosen per (p, n_rhs, M2L_OPT_TARGET_TOL) by the library */
     M2L_PREC_FP64 = 0,    /* FP64 data and arithmetic */
     M2L_PREC_FP32 = 1,    /* FP32 data and arithmetic (CUDA cores) */
-    M2L_PREC_TF32X3 = 2,  /* FP32 data; BLAS contractions as three TF32 tensor-core products */
+    M2L_PREC_TF32X3 = 2,  /* FP32 data; BLAS contractions as three TF32 tensor-core products; FFT form:
+                             FP32 transforms and pseudo-inverse, the Hadamard products of full levels
+                             ((N/2)^3 clusters, N/2 a multiple of 16) on the tensor cores in TF32x3 */
     M2L_PREC_BF16X3 = 3   /* FP32 data; BLAS contractions as three BF16 tensor-core products */
 };
 
@@ -238,7 +246,7 @@ int m2l_apply_batch(m2l_plan_t *const *plans, int n_inst, const void *const *mul
  * (and on the locals through the check potential they reproduce) against the FP64 definition,
  * before any rank truncation. Measured per p = 4..10 over uniform, signed, Gaussian and physical
  * (P2M + M2M) multipoles with a margin of at least 1.8. form: M2L_FORM_BLAS or M2L_FORM_FFT;
- * precision: M2L_PREC_FP64..M2L_PREC_BF16X3 (the FFT form offers FP64 and FP32 only).
+ * precision: M2L_PREC_FP64..M2L_PREC_BF16X3 (the FFT form offers FP64, FP32 and TF32x3).
  * Returns M2L_OK, or M2L_EINVAL for a NULL out, a bad form, precision or p outside [2, 16]. */
 int m2l_stated_bound(int form, int precision, int p, double *bound);
 

@@ -94,8 +94,8 @@ static int ensure_lattice(m2l_plan_t *pl) {
 int prepare_plan(m2l_plan_t *pl, int form, int precision) {
     M2L_TRY(ensure_constants(pl->device));
     M2L_TRY(upload_level_tables(pl));
-    if (form == M2L_FORM_FFT && (precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3)) {
-        set_error("the FFT form runs in FP64 or FP32; split tensor-core precisions apply to the BLAS form");
+    if (form == M2L_FORM_FFT && precision == M2L_PREC_BF16X3) {
+        set_error("the FFT form runs in FP64, FP32 or TF32x3 (Hadamard products on the tensor cores)");
         return M2L_EUNSUPPORTED;
     }
     if (pl->pc != pl->p && form == M2L_FORM_FFT) {
@@ -483,19 +483,29 @@ static int fft_run(const Run &r, int precision, Workspace &ws, Workspace &spec, 
         L.R = R;           // row stride of densities and check potentials
         const T *ql = q + (L.base - base0) * R * n;
         T *dst = check_out ? out + (L.base - base0) * R * n : Phi + L.base * R * n;
+        // TF32x3: the Hadamard products of full levels on the tensor cores, with the spectra
+        // sibling-minor; other levels (and FP32) on the CUDA cores
+        const bool tcl = precision == M2L_PREC_TF32X3 && D.Bhad && hadamard_tc_eligible(L) && fft_pg_available(p, g);
         for (int r0 = 0; r0 < R; r0 += Rc) {
             const int rc = std::min(Rc, R - r0);
             L.row0 = r0;
             stage_begin(pl, M2L_STAGE_FFT_FORWARD);
             cudaMemsetAsync(qhat, 0, (size_t)L.nclusters * rc * F * 16 * e, s);  // missing children stay zero
-            M2L_TRY(launch_fft_forward<T>(L, rc, p, n, g, pl->lattice_dev, (const T *)D.tw, ql, qhat, s));
+            M2L_TRY(launch_fft_forward<T>(L, rc, p, n, g, pl->lattice_dev, (const T *)D.tw, ql, qhat, s, tcl));
             stage_end(pl, 1);
             stage_begin(pl, M2L_STAGE_HADAMARD);
-            M2L_TRY(launch_hadamard<T>(L, rc, F, (const T *)D.Khat, qhat, phihat, s));
+            if constexpr (sizeof(T) == 4) {
+                if (tcl)
+                    M2L_TRY(launch_hadamard_tc(L, rc, F, D.Bhad, qhat, phihat, pl->had_chains, pl->num_sms, pl->dev_status, s));
+                else
+                    M2L_TRY(launch_hadamard<T>(L, rc, F, (const T *)D.Khat, qhat, phihat, s));
+            } else {
+                M2L_TRY(launch_hadamard<T>(L, rc, F, (const T *)D.Khat, qhat, phihat, s));
+            }
             stage_end(pl, 1);
             stage_begin(pl, M2L_STAGE_FFT_INVERSE);
             M2L_TRY(launch_fft_inverse<T>(L, rc, p, n, g, pl->lattice_dev, (const T *)D.tw, phihat, dst, n,
-                                          check_out ? pl->accumulate : 0, s));
+                                          check_out ? pl->accumulate : 0, s, tcl));
             stage_end(pl, 1);
         }
     }

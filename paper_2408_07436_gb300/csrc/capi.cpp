@@ -161,6 +161,10 @@ int m2l_set_option(m2l_plan_t *pl, int key, long long value) {
             if (value < -1 || value > 64) break;
             pl->tc_drain = (int)value;
             return M2L_OK;
+        case M2L_OPT_HADAMARD_CHAINS:
+            if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8) break;
+            pl->had_chains = (int)value;
+            return M2L_OK;
         case M2L_OPT_TC_CHUNK:
             if (value != 0 && value != 32 && value != 64 && value != 128) break;
             pl->tc_chunk = (int)value;
@@ -556,7 +560,7 @@ int m2l_stated_bound(int form, int precision, int p, double *bound) {
     clear_error();
     if (!bound || (form != M2L_FORM_BLAS && form != M2L_FORM_FFT) || precision < M2L_PREC_FP64 ||
         precision > M2L_PREC_BF16X3 || p < 2 || p > 16 ||
-        (form == M2L_FORM_FFT && precision != M2L_PREC_FP64 && precision != M2L_PREC_FP32)) {
+        (form == M2L_FORM_FFT && precision == M2L_PREC_BF16X3)) {
         set_error("m2l_stated_bound: bad form %d, precision %d or order %d", form, precision, p);
         return M2L_EINVAL;
     }

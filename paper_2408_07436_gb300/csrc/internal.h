@@ -80,6 +80,7 @@ struct DevOps {
     void *Khat = nullptr;        // [316+1][F] complex kernel spectra (last row zero)
     void *Ut = nullptr;          // [rp][np_]   Ut_eps
     void *tw = nullptr;          // [g] complex twiddles exp(-2 pi i m / g)
+    void *Bhad = nullptr;        // TF32x3 FFT form: [F][26] kernel matrices of the tensor-core Hadamard
 };
 
 struct LevelDev {
@@ -137,6 +138,7 @@ struct m2l_plan_s {
     int tc_group = 1;                           // transfer vectors per tensor-memory partial sum
     int tc_chunk = 0;                           // bytes of K per tensor-core pipeline stage (0: default)
     int tc_drain = -1;                          // K stages per tensor-core partial sum (-1: default)
+    int had_chains = 0;                         // partial sums of the tensor-core Hadamard (0: default)
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 148;

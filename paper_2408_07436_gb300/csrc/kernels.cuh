@@ -74,16 +74,27 @@ int launch_contract_simt_dir(const LevelView *levels, const ContractTile *tiles,
                              const T *qt, const T *Ub, const T *Vt, const int *meta, int k, int kp, int kcp,
                              int kt8max, long long zero_row, T *phit, cudaStream_t s);
 
-// FFT form, one level at a time.
+// FFT form, one level at a time. Spectra rows (cluster * R + rhs) hold the 8 siblings' half
+// spectra as [8][F] complex values, or as [F][8] with sib_minor (the FP32 transforms specialised
+// on (p, g) only, fft_pg_available): the layout of the tensor-core Hadamard product.
 template <class T>
 int launch_fft_forward(const LevelView &L, int R, int p, int n, int g, const int *lattice,
-                       const T *tw, const T *q, T *qhat, cudaStream_t s);
+                       const T *tw, const T *q, T *qhat, cudaStream_t s, bool sib_minor = false);
 template <class T>
 int launch_hadamard(const LevelView &L, int R, int F, const T *Khat, const T *qhat, T *phihat,
                     cudaStream_t s);
 template <class T>
 int launch_fft_inverse(const LevelView &L, int R, int p, int n, int g, const int *lattice,
-                       const T *tw, const T *phihat, T *phi, long long ldphi, int acc, cudaStream_t s);
+                       const T *tw, const T *phihat, T *phi, long long ldphi, int acc, cudaStream_t s,
+                       bool sib_minor = false);
+bool fft_pg_available(int p, int g);
+
+// F3 on the tensor cores in TF32x3 for a full level (every cluster of the (N/2)^3 grid present,
+// N/2 a multiple of 16) with sibling-minor spectra; B: the per-frequency kernel matrices of
+// build_hadamard_tc_operand. Returns M2L_EUNSUPPORTED, launching nothing, for other levels.
+bool hadamard_tc_eligible(const LevelView &L);
+int launch_hadamard_tc(const LevelView &L, int R, int F, const void *B, const float *qhat, float *phihat,
+                       int chains, int num_sms, int *status, cudaStream_t s);
 
 // Constant tables (transfer index lookup and the cluster-pair table); once per device.
 int ensure_constants(int device);

@@ -984,7 +984,7 @@ template <int P, int G>
 __global__ void __launch_bounds__(fft_pg_threads<P, G>()) fft_forward_pg_kernel(LevelView L, int R, int n,
                                                                                  const int *__restrict__ lattice,
                                                                                  const float *__restrict__ q,
-                                                                                 float *__restrict__ qhat) {
+                                                                                 float *__restrict__ qhat, int sib) {
     constexpr int H = G / 2 + 1, GH = G * H, F = G * GH;
     __shared__ float xs[P * P * P];
     __shared__ float2 Y1[P * P * H];  // [a][b][kz]
@@ -1038,7 +1038,11 @@ __global__ void __launch_bounds__(fft_pg_threads<P, G>()) fft_forward_pg_kernel(
     __syncthreads();
     const uint32_t xyz = L.xyz[b];
     const int cl = L.cslot[parent_linear(xyz, L.N / 2)];
-    float2 *out = reinterpret_cast<float2 *>(qhat) + (((L.cbase + cl) * R + r) * 8 + octant_of(xyz)) * (long long)F;
+    // spectrum row of the cluster: [8][F] (sibling-major), or [F][8] (sibling-minor, sib != 0)
+    const int oct = octant_of(xyz);
+    float2 *out = reinterpret_cast<float2 *>(qhat) + ((L.cbase + cl) * R + r) * 8 * (long long)F +
+                  (sib ? (long long)oct : (long long)oct * F);
+    const int fstride = sib ? 8 : 1;
     if (tid < GH) {  // line (ky, kz) along x, written for every kx
         float2 y[P];
 #pragma unroll
@@ -1052,7 +1056,7 @@ __global__ void __launch_bounds__(fft_pg_threads<P, G>()) fft_forward_pg_kernel(
                 re = fmaf(y[a].x, w.x, fmaf(-y[a].y, w.y, re));
                 im = fmaf(y[a].x, w.y, fmaf(y[a].y, w.x, im));
             }
-            out[kx * GH + tid] = make_float2(re, im);
+            out[(long long)(kx * GH + tid) * fstride] = make_float2(re, im);
         }
     }
 }
@@ -1064,7 +1068,7 @@ __global__ void __launch_bounds__(fft_pg_threads<P, G>()) fft_inverse_pg_kernel(
                                                                                  const int *__restrict__ lattice,
                                                                                  const float *__restrict__ phihat,
                                                                                  float *__restrict__ phi, long long ldphi,
-                                                                                 int acc) {
+                                                                                 int acc, int sib) {
     constexpr int H = G / 2 + 1, GH = G * H, F = G * GH;
     __shared__ float2 Z1[P * GH];     // [a][ky][kz]
     __shared__ float2 Z2[P * P * H];  // [a][b][kz]
@@ -1075,11 +1079,13 @@ __global__ void __launch_bounds__(fft_pg_threads<P, G>()) fft_inverse_pg_kernel(
     const int r = (int)(row % R), tid = threadIdx.x, nt = blockDim.x;
     const uint32_t xyz = L.xyz[b];
     const int cl = L.cslot[parent_linear(xyz, L.N / 2)];
-    const float2 *in = reinterpret_cast<const float2 *>(phihat) + (((L.cbase + cl) * R + r) * 8 + octant_of(xyz)) * (long long)F;
+    const int oct = octant_of(xyz), fstride = sib ? 8 : 1;
+    const float2 *in = reinterpret_cast<const float2 *>(phihat) + ((L.cbase + cl) * R + r) * 8 * (long long)F +
+                       (sib ? (long long)oct : (long long)oct * F);
     if (tid < GH) {  // column (ky, kz) along x, for a < P
         float2 x[G];
 #pragma unroll
-        for (int kx = 0; kx < G; ++kx) x[kx] = in[kx * GH + tid];
+        for (int kx = 0; kx < G; ++kx) x[kx] = in[(long long)(kx * GH + tid) * fstride];
 #pragma unroll
         for (int a = 0; a < P; ++a) {
             float re = 0.f, im = 0.f;
@@ -1142,23 +1148,29 @@ __global__ void __launch_bounds__(fft_pg_threads<P, G>()) fft_inverse_pg_kernel(
 // Launch the (P, G) specialisation for the FP32 transforms, if there is one; false otherwise.
 template <int P, int G>
 static void launch_pg(bool forward, const LevelView &L, int R, int n, const int *lattice, const float *in, float *out,
-                      long long ldphi, int acc, dim3 grid, cudaStream_t s) {
+                      long long ldphi, int acc, int sib, dim3 grid, cudaStream_t s) {
     if (forward)
-        fft_forward_pg_kernel<P, G><<<grid, fft_pg_threads<P, G>(), 0, s>>>(L, R, n, lattice, in, out);
+        fft_forward_pg_kernel<P, G><<<grid, fft_pg_threads<P, G>(), 0, s>>>(L, R, n, lattice, in, out, sib);
     else
-        fft_inverse_pg_kernel<P, G><<<grid, fft_pg_threads<P, G>(), 0, s>>>(L, R, n, lattice, in, out, ldphi, acc);
+        fft_inverse_pg_kernel<P, G><<<grid, fft_pg_threads<P, G>(), 0, s>>>(L, R, n, lattice, in, out, ldphi, acc, sib);
+}
+bool fft_pg_available(int p, int g) {
+    switch (p * 100 + g) {
+        case 407: case 408: case 611: case 612: case 815: case 816: case 1019: case 1020: return true;
+        default: return false;
+    }
 }
 static bool launch_fft_pg(bool forward, const LevelView &L, int R, int p, int n, int g, const int *lattice,
-                          const float *in, float *out, long long ldphi, int acc, dim3 grid, cudaStream_t s) {
+                          const float *in, float *out, long long ldphi, int acc, int sib, dim3 grid, cudaStream_t s) {
     switch (p * 100 + g) {
-        case 407: launch_pg<4, 7>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
-        case 408: launch_pg<4, 8>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
-        case 611: launch_pg<6, 11>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
-        case 612: launch_pg<6, 12>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
-        case 815: launch_pg<8, 15>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
-        case 816: launch_pg<8, 16>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
-        case 1019: launch_pg<10, 19>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
-        case 1020: launch_pg<10, 20>(forward, L, R, n, lattice, in, out, ldphi, acc, grid, s); return true;
+        case 407: launch_pg<4, 7>(forward, L, R, n, lattice, in, out, ldphi, acc, sib, grid, s); return true;
+        case 408: launch_pg<4, 8>(forward, L, R, n, lattice, in, out, ldphi, acc, sib, grid, s); return true;
+        case 611: launch_pg<6, 11>(forward, L, R, n, lattice, in, out, ldphi, acc, sib, grid, s); return true;
+        case 612: launch_pg<6, 12>(forward, L, R, n, lattice, in, out, ldphi, acc, sib, grid, s); return true;
+        case 815: launch_pg<8, 15>(forward, L, R, n, lattice, in, out, ldphi, acc, sib, grid, s); return true;
+        case 816: launch_pg<8, 16>(forward, L, R, n, lattice, in, out, ldphi, acc, sib, grid, s); return true;
+        case 1019: launch_pg<10, 19>(forward, L, R, n, lattice, in, out, ldphi, acc, sib, grid, s); return true;
+        case 1020: launch_pg<10, 20>(forward, L, R, n, lattice, in, out, ldphi, acc, sib, grid, s); return true;
         default: return false;
     }
 }
@@ -1177,14 +1189,19 @@ static size_t fft_inverse_smem(int p, int g) {
 
 template <class T>
 int launch_fft_forward(const LevelView &L, int R, int p, int n, int g, const int *lattice, const T *tw,
-                       const T *q, T *qhat, cudaStream_t s) {
+                       const T *q, T *qhat, cudaStream_t s, bool sib_minor) {
     long long rows = L.nboxes * R;
     if (rows <= 0) return M2L_OK;
     unsigned gx = (unsigned)(rows < 65535 ? rows : 65535);
     unsigned gy = (unsigned)((rows + gx - 1) / gx);
     if constexpr (sizeof(T) == 4) {
-        if (launch_fft_pg(true, L, R, p, n, g, lattice, (const float *)q, (float *)qhat, 0, 0, dim3(gx, gy), s))
+        if (launch_fft_pg(true, L, R, p, n, g, lattice, (const float *)q, (float *)qhat, 0, 0, sib_minor ? 1 : 0,
+                          dim3(gx, gy), s))
             return check_launch("fft_forward");
+    }
+    if (sib_minor) {
+        set_error("sibling-minor spectra need the FP32 transforms specialised on (p, g) = (%d, %d)", p, g);
+        return M2L_EUNSUPPORTED;
     }
     size_t smem = fft_forward_smem<T>(p, g);
     if (smem > 48 * 1024)
@@ -1754,14 +1771,19 @@ __global__ void __launch_bounds__(128) fft_inverse_kernel(LevelView L, int R, in
 
 template <class T>
 int launch_fft_inverse(const LevelView &L, int R, int p, int n, int g, const int *lattice, const T *tw,
-                       const T *phihat, T *phi, long long ldphi, int acc, cudaStream_t s) {
+                       const T *phihat, T *phi, long long ldphi, int acc, cudaStream_t s, bool sib_minor) {
     long long rows = L.nboxes * R;
     if (rows <= 0) return M2L_OK;
     unsigned gx = (unsigned)(rows < 65535 ? rows : 65535);
     unsigned gy = (unsigned)((rows + gx - 1) / gx);
     if constexpr (sizeof(T) == 4) {
-        if (launch_fft_pg(false, L, R, p, n, g, lattice, (const float *)phihat, (float *)phi, ldphi, acc, dim3(gx, gy), s))
+        if (launch_fft_pg(false, L, R, p, n, g, lattice, (const float *)phihat, (float *)phi, ldphi, acc,
+                          sib_minor ? 1 : 0, dim3(gx, gy), s))
             return check_launch("fft_inverse");
+    }
+    if (sib_minor) {
+        set_error("sibling-minor spectra need the FP32 transforms specialised on (p, g) = (%d, %d)", p, g);
+        return M2L_EUNSUPPORTED;
     }
     size_t smem = fft_inverse_smem<T>(p, g);
     if (smem > 48 * 1024)
@@ -1785,10 +1807,10 @@ size_t fft_smem_bytes(int p, int g, int elt) {
     template int launch_contract_simt<T>(const LevelView *, const ContractTile *, long long, const int *,       \
                                          const T *, const T *, int, int, long long, T *, cudaStream_t); \
     template int launch_fft_forward<T>(const LevelView &, int, int, int, int, const int *, const T *,   \
-                                       const T *, T *, cudaStream_t);                                   \
+                                       const T *, T *, cudaStream_t, bool);                             \
     template int launch_hadamard<T>(const LevelView &, int, int, const T *, const T *, T *, cudaStream_t); \
     template int launch_fft_inverse<T>(const LevelView &, int, int, int, int, const int *, const T *,   \
-                                       const T *, T *, long long, int, cudaStream_t);
+                                       const T *, T *, long long, int, cudaStream_t, bool);
 M2L_INSTANTIATE(double)
 M2L_INSTANTIATE(float)
 

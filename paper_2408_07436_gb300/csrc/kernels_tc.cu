@@ -27,15 +27,17 @@
 
 #include "internal.h"
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace m2l {
 
 namespace {
 
+using namespace tc;
+
 constexpr int kRows = 128;            // MMA M, rows per tile
 constexpr int kMaxStages = 16;
 constexpr int kThreads = 320;
-constexpr long long kWaitLimit = 1LL << 24;
 
 struct TcParams {
     const LevelView *lv;               // device array indexed by ContractTile::lev
@@ -57,36 +59,6 @@ struct TcParams {
     int *status;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok)
-                 : "r"(bar), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
-
-// Bounded wait; on expiry records `code` in the status word and raises the CTA's abort flag.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *status, int code,
-                                          long long limit = kWaitLimit) {
-    for (long long it = 0; it < limit; ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-    }
-    atomicCAS(status, 0, code);
-    *abort_flag = 1;
-    return false;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
 // Shared-memory matrix descriptor: K-major rows of CH bytes (one row of the CH-byte swizzle),
 // 8-row groups 8 CH bytes apart. Layout codes: 32-byte swizzle 6, 64-byte 4, 128-byte 2.
 template <int CH>
@@ -98,34 +70,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)(CH == 32 ? 6 : CH == 64 ? 4 : 2) << 61;
     return d;
-}
-
-template <int KIND>
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    if (KIND == 0)
-        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                     "l"(a), "l"(b), "r"(idesc), "r"(acc));
-    else
-        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                     "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-                   "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                 : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
-                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-                 "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
-                 : "memory");
 }
 
 struct RowInfo {
@@ -510,33 +454,7 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// Host rounding of a double to the pieces the tensor cores read (round to nearest).
-inline uint32_t f32_bits(float f) {
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    return u;
-}
-inline float bits_f32(uint32_t u) {
-    float f;
-    std::memcpy(&f, &u, 4);
-    return f;
-}
-inline float tf32_round(float x) {  // nearest, ties away from zero, on the 10-bit mantissa
-    uint32_t u = f32_bits(x);
-    if ((u & 0x7F800000u) == 0x7F800000u) return x;
-    u = (u + 0x1000u) & 0xFFFFE000u;
-    return bits_f32(u);
-}
-inline uint16_t bf16_round(float x) {  // nearest, ties to even
-    uint32_t u = f32_bits(x);
-    if ((u & 0x7F800000u) == 0x7F800000u) return (uint16_t)(u >> 16);
-    u += 0x7FFFu + ((u >> 16) & 1u);
-    return (uint16_t)(u >> 16);
-}
-inline float bf16_value(uint16_t h) { return bits_f32((uint32_t)h << 16); }
-
 }  // namespace
-
 
 // Split C_t (FP64 on the host) into hi/lo pieces, upload them and encode their TMA maps.
 int split_tc_operators(m2l_plan_t *pl, int precision) {

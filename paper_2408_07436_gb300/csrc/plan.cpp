@@ -923,6 +923,7 @@ static int upload_vec(void *&dst, const std::vector<T> &v) {
 }
 
 int split_tc_operators(m2l_plan_t *pl, int precision);  // kernels_tc.cu
+int build_hadamard_tc_operand(m2l_plan_t *pl, DevOps &D);  // hadamard_tc.cu
 
 // The directional factors, when the plan asks for them and they are not on the device yet.
 template <class T>
@@ -1007,6 +1008,7 @@ int upload_ops(m2l_plan_t *pl, int precision, int form) {
         rc = upload_typed<float>(pl, D, form);
         if (!rc && form == M2L_FORM_BLAS && (precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3))
             rc = split_tc_operators(pl, precision);
+        if (!rc && form == M2L_FORM_FFT && precision == M2L_PREC_TF32X3) rc = build_hadamard_tc_operand(pl, D);
     }
     D.ready = rc == M2L_OK;
     return rc;
@@ -1016,7 +1018,7 @@ int upload_ops(m2l_plan_t *pl, int precision, int form) {
 void release_operators(m2l_plan_t *pl) {
     for (auto &D : pl->dev) {
         void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Vlo, &D.Uc, &D.C_hi, &D.C_lo, &D.Ub, &D.Vt, &D.dir_meta,
-                         &D.Khat, &D.Ut, &D.tw};
+                         &D.Khat, &D.Ut, &D.tw, &D.Bhad};
         for (void **pp : ptrs) {
             if (*pp) cudaFree(*pp);
             *pp = nullptr;
@@ -1028,7 +1030,7 @@ void release_operators(m2l_plan_t *pl) {
 void free_device(m2l_plan_t *pl) {
     for (auto &D : pl->dev) {
         void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Vlo, &D.Uc, &D.C_hi, &D.C_lo, &D.Ub, &D.Vt, &D.dir_meta,
-                         &D.Khat, &D.Ut, &D.tw};
+                         &D.Khat, &D.Ut, &D.tw, &D.Bhad};
         for (void **pp : ptrs) {
             if (*pp) cudaFree(*pp);
             *pp = nullptr;

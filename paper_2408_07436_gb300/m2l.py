@@ -35,6 +35,7 @@ M2L_OPT_TC_CHUNK = 11
 M2L_OPT_TC_DRAIN = 12
 M2L_OPT_RANK_AUTO = 13
 M2L_OPT_SVD = 14
+M2L_OPT_HADAMARD_CHAINS = 15
 M2L_Q_RANK_TOL = 17
 M2L_Q_CONTRACT_FLOPS, M2L_Q_DIR_RANK_SUM, M2L_Q_NC, M2L_Q_RANK_CHECK = 13, 14, 15, 16
 STAGES = ["compress", "contract", "expand", "fft_forward", "hadamard", "fft_inverse", "pinv"]
@@ -209,7 +210,7 @@ class Plan:
 
     def set(self, form=None, precision=None, accumulate=None, output=None, target_tol=None, fft_grid=None,
             timing=None, tc_group=None, dir_tol=None, check_order=None, tc_chunk=None, tc_drain=None,
-            rank_auto=None, svd=None):
+            rank_auto=None, svd=None, had_chains=None):
         if form is not None:
             _check(m2l_set_option(self.handle, M2L_OPT_FORM, FORMS[form]))
         if precision is not None:
@@ -239,6 +240,8 @@ class Plan:
             _check(m2l_set_option(self.handle, M2L_OPT_RANK_AUTO, int(bool(rank_auto))))
         if svd is not None:
             _check(m2l_set_option(self.handle, M2L_OPT_SVD, {"exact": 0, "randomised": 1}[svd]))
+        if had_chains is not None:
+            _check(m2l_set_option(self.handle, M2L_OPT_HADAMARD_CHAINS, int(had_chains)))
         return self
 
     def stage_times(self):

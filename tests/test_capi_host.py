@@ -45,12 +45,12 @@ def test_peak_probe_exports_its_declared_symbol():
 def test_stated_bounds_match_the_tests_table(lib):
     from bounds import stated
     for p in range(2, 17):
-        for form, precs in (("blas", ("fp64", "fp32", "tf32x3", "bf16x3")), ("fft", ("fp64", "fp32"))):
+        for form, precs in (("blas", ("fp64", "fp32", "tf32x3", "bf16x3")), ("fft", ("fp64", "fp32", "tf32x3"))):
             for prec in precs:
                 got = lib.m2l_stated_bound(lib.FORMS[form], lib.PRECISIONS[prec], p)
                 assert got == stated(form, prec, p), (form, prec, p)
     with pytest.raises(lib.M2LError):
-        lib.m2l_stated_bound(lib.M2L_FORM_FFT, lib.M2L_PREC_TF32X3, 6)   # no tensor-core FFT form
+        lib.m2l_stated_bound(lib.M2L_FORM_FFT, lib.M2L_PREC_BF16X3, 6)   # no BF16x3 FFT form
     with pytest.raises(lib.M2LError):
         lib.m2l_stated_bound(lib.M2L_FORM_BLAS, lib.M2L_PREC_FP32, 1)
 

@@ -185,7 +185,7 @@ def test_error_codes(lib):
         q = torch.zeros(584 * 56, dtype=torch.float32, device="cuda")
         o = torch.zeros_like(q)
         lib.m2l_set_option(h, lib.M2L_OPT_FORM, lib.M2L_FORM_FFT)
-        lib.m2l_set_option(h, lib.M2L_OPT_PRECISION, lib.M2L_PREC_TF32X3)
+        lib.m2l_set_option(h, lib.M2L_OPT_PRECISION, lib.M2L_PREC_BF16X3)   # no BF16x3 FFT form
         assert lib.m2l_apply(h, q.data_ptr(), o.data_ptr(), -1, 1) == lib.M2L_EUNSUPPORTED
         lib.m2l_set_option(h, lib.M2L_OPT_PRECISION, lib.M2L_PREC_FP32)
         assert lib.m2l_apply(h, q.data_ptr(), q.data_ptr() + 64, -1, 1) == lib.M2L_EINVAL   # overlap
