@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libm2l_gb300.so")
-SOURCES = ["plan.cpp", "linalg.cpp", "capi.cpp", "autotune.cpp", "apply.cu", "kernels_simt.cu", "kernels_tc.cu", "hadamard_tc.cu", "noalloc.cu",
+SOURCES = ["plan.cpp", "linalg.cpp", "capi.cpp", "autotune.cpp", "apply.cu", "kernels_simt.cu", "kernels_tc.cu", "hadamard_tc.cu", "pinv_tc.cu", "noalloc.cu",
            "fmm.cpp", "fmm_kernels.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 PEAKS_SOURCES = ["peaks.cu"]

@@ -319,10 +319,13 @@ static long long max_clusters(const m2l_plan_t *pl) {
     return m;
 }
 
+// Phi [rows][n], Z [rows][rp], and for TF32x3 the slices of the tensor-core V_eps product.
 static size_t fft_rows_bytes(const m2l_plan_t *pl, int R, int precision) {
     const size_t e = precision == M2L_PREC_FP64 ? 8 : 4;
     const long long allrows = pl->total_rows * R;
-    return al256((size_t)allrows * pl->n * e) + al256((size_t)allrows * pl->rp * e);
+    size_t b = al256((size_t)allrows * pl->n * e) + al256((size_t)allrows * pl->rp * e);
+    if (precision == M2L_PREC_TF32X3 && pinv_tc_k(pl)) b += al256(pinv_tc_workspace(allrows, pinv_tc_k(pl)));
+    return b;
 }
 
 static size_t fft_spec_bytes_per_rhs(const m2l_plan_t *pl, int precision) {
@@ -510,11 +513,22 @@ static int fft_run(const Run &r, int precision, Workspace &ws, Workspace &spec, 
         }
     }
     if (!check_out) {
-        // F6: locals = V_eps (Ut_eps Phi)
+        // F6: locals = V_eps (Ut_eps Phi); in TF32x3 the second product on the tensor cores, exact
         stage_begin(pl, M2L_STAGE_PINV);
         M2L_TRY(launch_gemm_xwt<T>(Phi + base0 * R * n, n, (const T *)D.Ut, n, Z, rp, r.rows, rp, n, 0, s));
-        M2L_TRY(apply_veps<T>(pl, D, Z, out, r.rows, pl->accumulate, true, s));
-        stage_end(pl, 2);
+        long long nl = 2;
+        if constexpr (sizeof(T) == 4) {
+            if (precision == M2L_PREC_TF32X3 && pinv_tc_usable(D, n, n, (const float *)out)) {
+                void *tws = (char *)ws.buf + al256(phi_b) + al256((size_t)pl->total_rows * R * rp * e);
+                M2L_TRY(launch_pinv_tc(pl, D, (const float *)Z, rp, r.rows, (float *)out, n, pl->accumulate, tws, s));
+                nl = 3;
+            } else {
+                M2L_TRY(apply_veps<T>(pl, D, Z, out, r.rows, pl->accumulate, true, s));
+            }
+        } else {
+            M2L_TRY(apply_veps<T>(pl, D, Z, out, r.rows, pl->accumulate, true, s));
+        }
+        stage_end(pl, nl);
     }
     return M2L_OK;
 }

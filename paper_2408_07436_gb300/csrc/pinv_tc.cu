@@ -1,0 +1,431 @@
+// F6's second factor, out = V_eps Z (+ out) (Eq. 9, the factor of the pseudo-inverse stored apart
+// as the footnote of Sec. 2.1.1 recommends), on the tensor cores, exactly.
+//
+// The product must be carried beyond FP32: the locals are measured through the check potential
+// they reproduce, which FP32 accumulation error over the r terms roughly doubles (the CUDA-core
+// path uses a float-float sum). Here both operands are cut into integer slices, so every
+// tensor-core product and every partial sum is an exact integer in FP32 (the error-free
+// splitting of Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59, 2012):
+//   a row z of Z (K = r values) is scaled by 2^-e_z (e_z: the exponent of its largest entry, so
+//   |z| 2^-e_z < 1) and written as sum_s q_s 2^-8(s+1), s = 0..3, with integers |q_0| <= 256 and
+//   |q_s| <= 128 after it (round to nearest, each slice the rounded residual of the previous);
+//   a row v of V_eps likewise with 2^e_v and integers p_t.
+// Then z.v = 2^(e_z + e_v) sum_{s,t} 2^-8(s+t+2) (q_s . p_t). Every q_s . p_t with K <= 256 is an
+// integer of magnitude at most 2^24, exact in the FP32 accumulator whatever its rounding; the
+// products on the same diagonal s + t share an accumulator (their exactness matters only on the
+// leading diagonal, which holds one pair). Slices are BF16 (8-bit integers exactly); the 10 pairs
+// with s + t <= 3 are kept, which reproduces the float-float product's result to rounding
+// (host emulation over p = 6, 8, 10: the locals' check-norm error equal to three digits).
+//
+// Tiles of 128 rows x 64 outputs, K in stages of 64 (128-byte swizzled rows, TMA); per stage the
+// 4 K steps x 10 slice pairs are 40 MMAs (M = 128, N = 64, K = 16, BF16) into 4 diagonal
+// accumulators, double-buffered in tensor memory across tiles. Warps: 0-3 epilogue (the four
+// diagonals added in FP32 from the smallest, scaled by the row and column exponents), 4 TMA, 5 MMA
+// issue (warp-uniform, elected lane). Every wait is bounded; an expired wait records where in the
+// plan's device status word and the CTA winds down.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+#include "tcgen05.cuh"
+
+namespace m2l {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kSl = 4;                          // slices per operand
+constexpr int kRowsP = 128;                     // M
+constexpr int kNP = 64;                         // outputs per tile (N)
+constexpr int kKS = 64;                         // K per stage: one 128-byte row of BF16
+constexpr int kStagesP = 2;
+constexpr int kThreadsP = 192;
+constexpr uint32_t kASlice = kRowsP * 128;      // 16 KB: one slice of a stage's A
+constexpr uint32_t kBSlice = kNP * 128;         // 8 KB
+constexpr uint32_t kStageP = kSl * (kASlice + kBSlice);
+constexpr uint32_t kSmemP = kStagesP * kStageP;
+constexpr int kDiag = 4;                        // accumulators: s + t = 0..3
+constexpr uint32_t kBufCols = kDiag * kNP;      // 256 columns per tile; two tiles in flight
+
+struct PtcParams {
+    const int *zexp;         // [rows_pad] exponents of the Z rows
+    const float *vscale;     // [O_pad] 2^e_v of the V rows
+    float *out;              // [rows][ldo]
+    long long rows, ldo;
+    int O, nk;               // outputs; K stages (K_pad / 64)
+    long long mtiles, ntiles;
+    int acc;
+    int *status;
+    uint32_t idesc;
+};
+
+// One BF16 slice pair (s, t) of the 10 with s + t <= 3, diagonal-major.
+__host__ __device__ constexpr int pair_s(int j) { return j == 0 ? 0 : j < 3 ? j - 1 : j < 6 ? j - 3 : j - 6; }
+__host__ __device__ constexpr int pair_d(int j) { return j == 0 ? 0 : j < 3 ? 1 : j < 6 ? 2 : 3; }
+
+// Shared-memory descriptor of a K-major operand in the 128-byte swizzle (8-row groups 1024 B apart).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Z rows -> 4 BF16 integer slices [4][rows_pad][K_pad] and exponents (one warp per row; rows past
+// `rows` and columns past K are zeros).
+__global__ void slice_rows_kernel(const float *__restrict__ Z, long long ldz, long long rows, long long rows_pad, int K,
+                                  int Kp, __nv_bfloat16 *__restrict__ Zs, int *__restrict__ zexp) {
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long row = wid; row < rows_pad; row += nw) {
+        const bool live = row < rows;
+        float mx = 0.f;
+        if (live)
+            for (int k = lane; k < K; k += 32) mx = fmaxf(mx, fabsf(Z[row * ldz + k]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int e = 0;
+        if (mx > 0.f) frexpf(mx, &e);  // mx < 2^e
+        if (lane == 0) zexp[row] = e;
+        for (int k = lane; k < Kp; k += 32) {
+            float R = (live && k < K) ? ldexpf(Z[row * ldz + k], -e) : 0.f;  // |R| < 1
+#pragma unroll
+            for (int s = 0; s < kSl; ++s) {
+                const float t = R * 256.f;  // exact
+                const float q = rintf(t);
+                R = t - q;                  // exact, |R| <= 1/2
+                Zs[((long long)s * rows_pad + row) * Kp + k] = __float2bfloat16_rn(q);  // |q| <= 256: exact
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreadsP, 1)
+    pinv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const PtcParams P,
+                   long long rows_pad, int opad) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[kStagesP], empty_bar[kStagesP], accf_bar[2], acce_bar[2], drain_bar;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ volatile int abort_flag;
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t s0 = smem_u32(smem);
+    auto sA = [&](int st, int s) { return s0 + (uint32_t)st * kStageP + (uint32_t)s * kASlice; };
+    auto sB = [&](int st, int t) { return s0 + (uint32_t)st * kStageP + kSl * kASlice + (uint32_t)t * kBSlice; };
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long total = P.mtiles * P.ntiles;
+    if (tid == 0) {
+        for (int i = 0; i < kStagesP; ++i) {
+            mbar_init(smem_u32(&full_bar[i]), 1);
+            mbar_init(smem_u32(&empty_bar[i]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&accf_bar[b]), 1);
+            mbar_init(smem_u32(&acce_bar[b]), 128);
+        }
+        mbar_init(smem_u32(&drain_bar), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(2 * kBufCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_s;
+
+    if (warp == 4) {
+        // ---------------- TMA: the 4 Z slices and 4 V slices of each K stage ----------------
+        if (lane == 0) {
+            long long it = 0;
+            for (long long tile = blockIdx.x; tile < total && !abort_flag; tile += gridDim.x) {
+                const long long mt = tile / P.ntiles, nt = tile % P.ntiles;
+                for (int kc = 0; kc < P.nk; ++kc, ++it) {
+                    const int st = (int)(it % kStagesP);
+                    if (it >= kStagesP && !mbar_wait(smem_u32(&empty_bar[st]), (uint32_t)(((it / kStagesP) - 1) & 1),
+                                                     &abort_flag, P.status, M2L_WAIT_TMA))
+                        goto tma_done;
+                    const uint32_t bar = smem_u32(&full_bar[st]);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kStageP) : "memory");
+                    for (int s = 0; s < kSl; ++s) {
+                        const int x = kc * kKS, y = (int)(s * rows_pad + mt * kRowsP);
+                        asm volatile(
+                            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                                sA(st, s)),
+                            "l"(&tmA), "r"(x), "r"(y), "r"(bar)
+                            : "memory");
+                    }
+                    for (int t = 0; t < kSl; ++t) {
+                        const int x = kc * kKS, y = (int)(t * opad + nt * kNP);
+                        asm volatile(
+                            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                                sB(st, t)),
+                            "l"(&tmB), "r"(x), "r"(y), "r"(bar)
+                            : "memory");
+                    }
+                }
+            }
+        tma_done:
+            if (abort_flag) {
+                // let loads already issued land before the CTA leaves
+                for (int st = 0; st < kStagesP && st < it; ++st) {
+                    const long long last = it - 1 - (((it - 1 - st) % kStagesP) + kStagesP) % kStagesP;
+                    const uint32_t parity = (uint32_t)((last / kStagesP) & 1);
+                    for (long long w = 0; w < kWaitLimit && !mbar_try(smem_u32(&full_bar[st]), parity); ++w) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 5) {
+        // ---------------- MMA issue: warp-uniform, one elected lane ----------------
+        long long it = 0, u = 0;
+        bool pending = false;
+        for (long long tile = blockIdx.x; tile < total && !abort_flag; tile += gridDim.x, ++u) {
+            const int buf = (int)(u & 1);
+            if (u >= 2 && !mbar_wait(smem_u32(&acce_bar[buf]), (uint32_t)(((u >> 1) - 1) & 1), &abort_flag, P.status,
+                                     M2L_WAIT_ACC_FREE))
+                goto mma_done;
+            const uint32_t d0 = tmem + (uint32_t)buf * kBufCols;
+            for (int kc = 0; kc < P.nk; ++kc, ++it) {
+                const int st = (int)(it % kStagesP);
+                if (!mbar_wait(smem_u32(&full_bar[st]), (uint32_t)((it / kStagesP) & 1), &abort_flag, P.status,
+                               M2L_WAIT_OPERANDS))
+                    goto mma_done;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (elect_one()) {
+#pragma unroll
+                    for (int k = 0; k < kKS / 16; ++k)
+#pragma unroll
+                        for (int j = 0; j < 10; ++j) {
+                            const int s = pair_s(j), dg = pair_d(j), t = dg - s;
+                            const bool first = kc == 0 && k == 0 && (j == 0 || j == 1 || j == 3 || j == 6);
+                            mma<1>(d0 + (uint32_t)(dg * kNP), desc_sw128(sA(st, s) + 32 * k), desc_sw128(sB(st, t) + 32 * k),
+                                   P.idesc, first ? 0u : 1u);
+                        }
+                    mma_commit(smem_u32(&empty_bar[st]));
+                }
+                __syncwarp();
+            }
+            if (elect_one()) mma_commit(smem_u32(&accf_bar[buf]));
+            __syncwarp();
+            pending = true;
+        }
+    mma_done:
+        __syncwarp();
+        if (abort_flag && pending) {
+            // no MMA may still write tensor memory when it is released
+            if (elect_one()) mma_commit(smem_u32(&drain_bar));
+            __syncwarp();
+            for (long long w = 0; w < kWaitLimit && !mbar_try(smem_u32(&drain_bar), 0); ++w) {
+            }
+        }
+    } else {
+        // ---------------- epilogue: out = 2^(e_z + e_v - 16) (D0 + D1 2^-8 + D2 2^-16 + D3 2^-24) ----
+        const int quarter = warp & 3;
+        const int rl = quarter * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        long long u = 0;
+        for (long long tile = blockIdx.x; tile < total && !abort_flag; tile += gridDim.x, ++u) {
+            const long long mt = tile / P.ntiles, nt = tile % P.ntiles;
+            const int buf = (int)(u & 1);
+            if (!mbar_wait(smem_u32(&accf_bar[buf]), (uint32_t)((u >> 1) & 1), &abort_flag, P.status, M2L_WAIT_ACC_READY))
+                goto epi_done;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const long long r = mt * kRowsP + rl;
+            const bool live = r < P.rows;
+            const int ez = live ? P.zexp[r] : 0;
+            float *orow = P.out + r * P.ldo;
+            for (int cg = 0; cg < kNP / 16; ++cg) {
+                uint32_t v[kDiag][16];
+#pragma unroll
+                for (int dg = 0; dg < kDiag; ++dg)
+                    tmem_ld16(tmem + lane_off + (uint32_t)buf * kBufCols + (uint32_t)(dg * kNP + cg * 16), v[dg]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (!live) continue;
+                const int c0 = (int)nt * kNP + cg * 16;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = c0 + 4 * q;
+                    if (c >= P.O) break;
+                    float y[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int j = 4 * q + i;
+                        // the diagonals from the smallest; every D is an exact integer
+                        float a = fmaf(__uint_as_float(v[3][j]), 5.9604644775390625e-8f, __uint_as_float(v[2][j]) * 1.52587890625e-5f);
+                        a = fmaf(__uint_as_float(v[1][j]), 3.90625e-3f, a);
+                        a = __fadd_rn(__uint_as_float(v[0][j]), a);
+                        y[i] = ldexpf(a, ez - 16) * P.vscale[c + i];
+                    }
+                    float4 *o = reinterpret_cast<float4 *>(orow + c);
+                    if (P.acc) {
+                        const float4 old = *o;
+                        y[0] += old.x;
+                        y[1] += old.y;
+                        y[2] += old.z;
+                        y[3] += old.w;
+                    }
+                    *o = make_float4(y[0], y[1], y[2], y[3]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(smem_u32(&acce_bar[buf]));
+        }
+    epi_done:;
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 5) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kBufCols));
+    }
+}
+
+}  // namespace
+
+// K of the sliced product: r (the single-precision pseudo-inverse's rank) rounded up to whole
+// stages; 0 when r > 256, where the leading diagonal's sums could pass 2^24.
+int pinv_tc_k(const m2l_plan_t *pl) {
+    const int kp = (pl->r32 + kKS - 1) / kKS * kKS;
+    return pl->r32 >= 1 && kp <= 256 ? kp : 0;
+}
+
+// V_eps (FP64, n x r) as 4 BF16 integer slices [4][O_pad][K_pad] with its row scales 2^e_v, and the
+// TMA map of the slices (box 64 x 64, 128-byte swizzle). Nothing is built when pinv_tc_k is 0.
+int build_pinv_tc_operand(m2l_plan_t *pl, DevOps &D) {
+    if (D.Vsl) return M2L_OK;
+    const int Kp = pinv_tc_k(pl);
+    if (!Kp) return M2L_OK;
+    const int n = pl->n, r = pl->r32;
+    const int opad = (n + kNP - 1) / kNP * kNP;
+    const std::vector<double> &V = pl->pinv->Veps32;  // n x r
+    std::vector<uint16_t> sl((size_t)kSl * opad * Kp, 0);
+    std::vector<float> scale(opad, 1.f);
+    for (int o = 0; o < n; ++o) {
+        double mx = 0;
+        for (int k = 0; k < r; ++k) mx = std::max(mx, std::fabs(V[(size_t)o * r + k]));
+        int e = 0;
+        if (mx > 0) std::frexp(mx, &e);
+        scale[o] = std::ldexp(1.0f, e);
+        for (int k = 0; k < r; ++k) {
+            double R = std::ldexp(V[(size_t)o * r + k], -e);
+            for (int s = 0; s < kSl; ++s) {
+                const double t = R * 256.0;
+                const double q = std::nearbyint(t);
+                R = t - q;
+                sl[((size_t)s * opad + o) * Kp + k] = bf16_round((float)q);  // an integer of at most 9 bits
+            }
+        }
+    }
+    for (void **pp : {&D.Vsl, &D.Vscale})
+        if (*pp) cudaFree(*pp);
+    D.Vsl = D.Vscale = nullptr;
+    if (cudaMalloc(&D.Vsl, sl.size() * 2) != cudaSuccess || cudaMalloc(&D.Vscale, scale.size() * 4) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("allocating the sliced pseudo-inverse factor failed");
+        return M2L_ENOMEM;
+    }
+    cudaMemcpy(D.Vsl, sl.data(), sl.size() * 2, cudaMemcpyHostToDevice);
+    cudaMemcpy(D.Vscale, scale.data(), scale.size() * 4, cudaMemcpyHostToDevice);
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return M2L_ECUDA;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)kSl * opad};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kKS, (cuuint32_t)kNP};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult rc = enc(reinterpret_cast<CUtensorMap *>(D.vmap), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, D.Vsl, dims, strides, box,
+                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (rc != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)rc);
+        return M2L_ECUDA;
+    }
+    D.pinv_kp = Kp;
+    return M2L_OK;
+}
+
+// Workspace of launch_pinv_tc for `rows` rows: the Z slices, then the row exponents.
+size_t pinv_tc_workspace(long long rows, int Kp) {
+    const long long rows_pad = (rows + kRowsP - 1) / kRowsP * kRowsP;
+    return (((size_t)kSl * rows_pad * Kp * 2 + 255) / 256) * 256 + (size_t)rows_pad * 4;
+}
+
+bool pinv_tc_usable(const DevOps &D, long long ldo, int O, const float *out) {
+    return D.Vsl && D.pinv_kp > 0 && ldo % 4 == 0 && O % 4 == 0 && ((uintptr_t)out & 15) == 0;
+}
+
+int launch_pinv_tc(const m2l_plan_t *pl, const DevOps &D, const float *Z, long long ldz, long long rows, float *out,
+                   long long ldo, int acc, void *ws, cudaStream_t s) {
+    if (rows <= 0) return M2L_OK;
+    const int Kp = D.pinv_kp, n = pl->n;
+    if (!pinv_tc_usable(D, ldo, n, out)) {
+        set_error("sliced pseudo-inverse product: operand or output layout not supported");
+        return M2L_EUNSUPPORTED;
+    }
+    const long long rows_pad = (rows + kRowsP - 1) / kRowsP * kRowsP;
+    const int opad = (n + kNP - 1) / kNP * kNP;
+    __nv_bfloat16 *Zs = (__nv_bfloat16 *)ws;
+    int *zexp = (int *)((char *)ws + (((size_t)kSl * rows_pad * Kp * 2 + 255) / 256) * 256);
+    {
+        long long blocks = (rows_pad + 7) / 8;  // 8 warps per block, a warp per row
+        if (blocks > 65535) blocks = 65535;
+        slice_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(Z, ldz, rows, rows_pad, pl->r32, Kp, Zs, zexp);
+    }
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return M2L_ECUDA;
+    }
+    alignas(64) CUtensorMap tmA;
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)(kSl * rows_pad)};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kKS, (cuuint32_t)kRowsP};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult rc = enc(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Zs, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (rc != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)rc);
+        return M2L_ECUDA;
+    }
+    PtcParams P;
+    P.zexp = zexp;
+    P.vscale = (const float *)D.Vscale;
+    P.out = out;
+    P.rows = rows;
+    P.ldo = ldo;
+    P.O = n;
+    P.nk = Kp / kKS;
+    P.mtiles = rows_pad / kRowsP;
+    P.ntiles = opad / kNP;
+    P.acc = acc;
+    P.status = pl->dev_status;
+    P.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kNP >> 3) << 17) | ((uint32_t)(kRowsP >> 4) << 24);
+    const long long total = P.mtiles * P.ntiles;
+    const int grid = (int)(total < pl->num_sms ? total : pl->num_sms);
+    const size_t smem = kSmemP + 1024;
+    cudaFuncSetAttribute(pinv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    pinv_tc_kernel<<<grid, kThreadsP, smem, s>>>(tmA, *reinterpret_cast<const CUtensorMap *>(D.vmap), P, rows_pad, opad);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("sliced pseudo-inverse launch failed: %s", cudaGetErrorString(e));
+        return M2L_ECUDA;
+    }
+    return M2L_OK;
+}
+
+}  // namespace m2l

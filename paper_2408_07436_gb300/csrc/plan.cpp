@@ -924,6 +924,7 @@ static int upload_vec(void *&dst, const std::vector<T> &v) {
 
 int split_tc_operators(m2l_plan_t *pl, int precision);  // kernels_tc.cu
 int build_hadamard_tc_operand(m2l_plan_t *pl, DevOps &D);  // hadamard_tc.cu
+int build_pinv_tc_operand(m2l_plan_t *pl, DevOps &D);      // pinv_tc.cu
 
 // The directional factors, when the plan asks for them and they are not on the device yet.
 template <class T>
@@ -1009,6 +1010,7 @@ int upload_ops(m2l_plan_t *pl, int precision, int form) {
         if (!rc && form == M2L_FORM_BLAS && (precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3))
             rc = split_tc_operators(pl, precision);
         if (!rc && form == M2L_FORM_FFT && precision == M2L_PREC_TF32X3) rc = build_hadamard_tc_operand(pl, D);
+        if (!rc && form == M2L_FORM_FFT && precision == M2L_PREC_TF32X3) rc = build_pinv_tc_operand(pl, D);
     }
     D.ready = rc == M2L_OK;
     return rc;
@@ -1018,11 +1020,12 @@ int upload_ops(m2l_plan_t *pl, int precision, int form) {
 void release_operators(m2l_plan_t *pl) {
     for (auto &D : pl->dev) {
         void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Vlo, &D.Uc, &D.C_hi, &D.C_lo, &D.Ub, &D.Vt, &D.dir_meta,
-                         &D.Khat, &D.Ut, &D.tw, &D.Bhad};
+                         &D.Khat, &D.Ut, &D.tw, &D.Bhad, &D.Vsl, &D.Vscale};
         for (void **pp : ptrs) {
             if (*pp) cudaFree(*pp);
             *pp = nullptr;
         }
+        D.pinv_kp = 0;
         D.ready = false;
     }
 }
@@ -1030,11 +1033,12 @@ void release_operators(m2l_plan_t *pl) {
 void free_device(m2l_plan_t *pl) {
     for (auto &D : pl->dev) {
         void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Vlo, &D.Uc, &D.C_hi, &D.C_lo, &D.Ub, &D.Vt, &D.dir_meta,
-                         &D.Khat, &D.Ut, &D.tw, &D.Bhad};
+                         &D.Khat, &D.Ut, &D.tw, &D.Bhad, &D.Vsl, &D.Vscale};
         for (void **pp : ptrs) {
             if (*pp) cudaFree(*pp);
             *pp = nullptr;
         }
+        D.pinv_kp = 0;
         D.ready = false;
     }
     for (int l = 0; l <= kMaxDepth; ++l) free_level(pl->ldev[l]);

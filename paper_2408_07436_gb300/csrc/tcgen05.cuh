@@ -1,6 +1,7 @@
 // tcgen05 / mbarrier helpers shared by the tensor-core kernels (inline PTX for sm_103a), and the
 // host rounding of values to the pieces those kernels read.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstring>
@@ -111,6 +112,25 @@ inline uint16_t bf16_round(float x) {  // nearest, ties to even
     return (uint16_t)(u >> 16);
 }
 inline float bf16_value(uint16_t h) { return bits_f32((uint32_t)h << 16); }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver (no link against libcuda); null when unavailable.
+inline EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
 
 }  // namespace tc
 }  // namespace m2l

@@ -138,3 +138,20 @@ def test_c3_full_size_sampled_fft_tf32x3(lib):
         _, ref = oracle_level(wl.p, l, qs[l], targets=tg)
         assert M.rel_l2_error(ref, chk[l][tg]) < bound, l
         assert M.max_target_rel_error(ref, chk[l][tg]) < 10 * bound, l
+
+
+@pytest.mark.parametrize("p", [4, 6, 8])
+def test_tensor_core_pseudo_inverse_equals_the_float_float_one(lib, p):
+    """Below level 5 the TF32x3 FFT form differs from FP32 only in F6's V_eps product: exact BF16
+    integer slices on the tensor cores against the float-float CUDA-core sum. Both carry the
+    product beyond FP32, so their locals agree to the FP32 rounding of the result, in the check
+    norm, and both meet the oracle."""
+    wl = W.small(depth=4, p=p, density="u11", seed=60 + p)
+    qs = {l: wl.multipoles(l) for l in wl.levels}
+    tc = run_gpu(lib, 4, p, qs, form="fft", precision="tf32x3", output="locals")
+    ff = run_gpu(lib, 4, p, qs, form="fft", precision="fp32", output="locals")
+    for l in wl.levels:
+        assert M.check_norm_error(p, l, ff[l], tc[l]) < 1.5e-7, l
+        tg = _sample(8 ** l, l, 24, l)
+        L_ref, _ = oracle_level(p, l, qs[l], targets=tg)
+        assert M.check_norm_error(p, l, L_ref, tc[l][tg]) < stated("fft", "tf32x3", p), l
