@@ -57,7 +57,14 @@ DEFAULT_TARGET = 1e-6
 # one ncu capture, keyed by (workload, depth, kernel), with the SHA-256 of the source file the
 # kernel was built from; the summary and the command are in profiles/. A source that has changed
 # since the capture reports null.
-TRAFFIC = {}
+TRAFFIC = {
+    # hadamard_tc_kernel<4> at level 5 (4,096 clusters, F = 2304): 726,848,768 B read + 558,801,152 B
+    # written in one launch; scaled by the clusters of levels 2-6 (9.1426 x level 5's) over the
+    # stage's 5 launches (the ncu summary is under profiles/)
+    ("c3", 6, "fft-tf32x3:hadamard"): {
+        "bytes": 2350830967, "source": "paper_2408_07436_gb300/csrc/hadamard_tc.cu",
+        "sha256": "b08805a5e0ee8629272aa625d18c62fbc22391aa86f7bc585c9efc4523d7e7a9"},
+}
 
 
 def measured_traffic(workload, depth, kernel):
@@ -364,7 +371,12 @@ def run_ours(args, rank, world, local_rank):
         p_.close()
 
     # ---- headline: the autotuned reduced-precision form at the target ----
-    head = [make_plan(lib, wl, "auto", "auto", target=target, timing=not batched) for wl in insts]
+    if args.headline:
+        # fixed form (for profiling: under a profiler the tuner's timings, so its choice, change)
+        hf, hp = args.headline.split("-")
+        head = [make_plan(lib, wl, hf, hp, timing=not batched) for wl in insts]
+    else:
+        head = [make_plan(lib, wl, "auto", "auto", target=target, timing=not batched) for wl in insts]
     forms = [resolved(lib, pl, wl.n_rhs) for pl, wl in zip(head, insts)]
     log(f"headline forms at {target:g}: {sorted(set(forms))}")
     run_head = runner(head)
@@ -477,8 +489,9 @@ def run_ours(args, rank, world, local_rank):
                       else DESC["c2"].replace("depth5", f"depth{args.depth}"),
                       "instances": len(insts), "pairs_x_rhs": int(inter), "target_rel_err": target,
                       "form": head_form, "precision": head_prec, "rank": head_rank,
-                      "choice": "autotuned among forms whose stated bound plus estimated rank truncation is within "
-                                "the target, BLAS rank threshold chosen by the library",
+                      "choice": (f"fixed by --headline {args.headline}" if args.headline else
+                                 "autotuned among forms whose stated bound plus estimated rank truncation is within "
+                                 "the target, BLAS rank threshold chosen by the library"),
                       "batched": batched, "l2": "flushed between timed steps (512 MB write)",
                       "ranks": "one independent set of instances per rank"},
            "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
@@ -735,6 +748,8 @@ def main():
                     help="relative error (Eq. 16) the headline and the FP64 comparison must meet")
     ap.add_argument("--variants", default=None, help="comma list of form-precision timed beside the headline "
                                                      "(default: the workload's; empty: none)")
+    ap.add_argument("--headline", default=None, help="form-precision of the headline instead of the autotuner's "
+                    "choice at the target (e.g. fft-tf32x3; for profiling runs, whose timings mislead the tuner)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison at the same target")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-instance key")
     ap.add_argument("--no-e2e", action="store_true")
