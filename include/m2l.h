@@ -110,7 +110,7 @@ enum m2l_option_e {
                                 singular value falls below rank_tol times the largest). Setup only; the
                                 rank tuner (M2L_OPT_RANK_AUTO) estimates with the exact bases */
     M2L_OPT_HADAMARD_CHAINS = 15, /* FFT form in TF32x3: partial sums per tile of the tensor-core Hadamard
-                                products, 1, 2, 4 or 8 (0: 4, the default). Each sums the products of a
+                                products, 1, 2 or 4 (0: 4, the default). Each sums the products of a
                                 fixed subset of the 26 source-cluster directions in tensor memory (every
                                 subset holds an in-plane direction); the epilogue adds them in FP32 with
                                 round-to-nearest. More partial sums shorten the truncating tensor-core
@@ -142,9 +142,12 @@ enum m2l_precision_e {
     M2L_PREC_AUTO = -1,   /* chosen per (p, n_rhs, M2L_OPT_TARGET_TOL) by the library */
     M2L_PREC_FP64 = 0,    /* FP64 data and arithmetic */
     M2L_PREC_FP32 = 1,    /* FP32 data and arithmetic (CUDA cores) */
-    M2L_PREC_TF32X3 = 2,  /* FP32 data; BLAS contractions as three TF32 tensor-core products; FFT form:
-                             FP32 transforms and pseudo-inverse, the Hadamard products of full levels
-                             ((N/2)^3 clusters, N/2 a multiple of 16) on the tensor cores in TF32x3 */
+    M2L_PREC_TF32X3 = 2,  /* FP32 data; BLAS contractions as three TF32 tensor-core products. FFT form:
+                             FP32 transforms; the Hadamard products of full levels ((N/2)^3 clusters,
+                             N/2 a multiple of 16) on the tensor cores as split products accurate to
+                             FP32 rounding (three BF16 pieces per operand, six products), and the
+                             pseudo-inverse's second factor on the tensor cores exactly (BF16
+                             integer slices) when its rank is at most 256 */
     M2L_PREC_BF16X3 = 3   /* FP32 data; BLAS contractions as three BF16 tensor-core products */
 };
 

@@ -39,7 +39,7 @@ double stated_bound(int form, int precision, int p) {
         return p >= 8 ? 1e-11 : 1e-12;
     }
     if (form == M2L_FORM_FFT) return 1e-6;   // FP32 FFT (3.9e-7, 3.9e-7, 5.1e-7, 5.3e-7); TF32x3 FFT, whose
-                                             // tensor-core levels measured 2.6e-7, 3.2e-7, 3.6e-7 (p = 4..8)
+                                             // tensor-core levels measured 1.6e-7, 2.2e-7, 2.6e-7 (p = 4..8)
     if (precision == M2L_PREC_TF32X3)          // FP32 accumulation of 22-bit pieces
         return p <= 4 ? 1e-6 : 3e-6;           // (5.2e-7, 1.4e-6, 1.1e-6, 1.3e-6)
     if (precision == M2L_PREC_FP32)            // FP32 CUDA-core contraction

@@ -162,7 +162,7 @@ int m2l_set_option(m2l_plan_t *pl, int key, long long value) {
             pl->tc_drain = (int)value;
             return M2L_OK;
         case M2L_OPT_HADAMARD_CHAINS:
-            if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8) break;
+            if (value != 0 && value != 1 && value != 2 && value != 4) break;
             pl->had_chains = (int)value;
             return M2L_OK;
         case M2L_OPT_TC_CHUNK:

@@ -1,5 +1,6 @@
-// F3 (App. A.1 step 4, the Hadamard products of the FFT form) on the 5th-generation tensor cores
-// in TF32x3, for full levels.
+// F3 (App. A.1 step 4, the Hadamard products of the FFT form) on the 5th-generation tensor cores,
+// as split BF16 products accurate to FP32 rounding, for full levels (the FFT form's TF32x3
+// precision class: FP32 data, tensor-core products of FP32 accuracy).
 //
 // At one frequency f the products of a target cluster are
 //   phihat_i = sum over the 26 source-cluster directions d of sum_j Khat_{t(d,i,j)}(f) qhat_j(d),
@@ -18,23 +19,26 @@
 // the planes of a (frequency, rhs, x block, y block) column in z through a ring of 7 planes.
 // Halo clusters outside the domain are zeros.
 //
-// TF32x3: q = q_hi + q_lo and B = B_hi + B_lo (TF32 pieces, round to nearest); the product is
-// q_hi B_hi + q_hi B_lo + q_lo B_hi with FP32 accumulation in tensor memory. B is stored with its
-// hi and lo pieces as the 32 rows of one N = 32 operand, so q_hi meets both in one MMA (columns
-// 0-15: q_hi B_hi, columns 16-31: q_hi B_lo), and q_lo meets B_hi in an N = 16 MMA into columns
-// 16-31 beside the other small term. Each piece of the halo is read by one MMA per K step.
-// The tensor cores accumulate by truncation, so an error of up to an ulp of the running sum
-// enters at every MMA into it; the 26 directions are therefore split into chains (default 4,
-// each led by an in-plane direction, present in every tile) with accumulators of their own, and
-// the epilogue adds the chains' main parts, then their small parts, with round-to-nearest.
+// Split products: q = q_hi + q_mid + q_lo and B = B_hi + B_mid + B_lo, BF16 pieces each the
+// nearest to what the previous ones leave (three cover an FP32 significand exactly); the six
+// products with piece orders summing to at most 2 are kept (the dropped ones lie 2^-24 and
+// further below), with FP32 accumulation in tensor memory. A direction (K = 16, one BF16 MMA
+// step) takes three MMAs: q_hi x [B_hi; B_mid; B_lo] (N = 48), q_mid x [B_hi; B_mid] (N = 32) into
+// columns 16-47, q_lo x B_hi (N = 16) into columns 32-47, so columns 0-15 hold the leading
+// products and 16-31, 32-47 those 2^-8 and 2^-16 below. The tensor cores accumulate by
+// truncation, so an error of up to an ulp of the running sum enters at every MMA into it; the 26
+// directions are therefore split into chains (default 4, each led by an in-plane direction,
+// present in every tile) with accumulators of their own, and the epilogue adds the chains'
+// leading parts, then their small parts, with round-to-nearest.
 //
 // Warps: 0-3 load halo planes (16-byte cp.async of (cluster, frequency, sibling pair) from
-// sibling-minor spectra) and split each value into TF32 hi/lo in place; 4 loads the 26 kernel
-// matrices of a frequency (one 52 KB bulk copy) when the column's frequency changes; 5 owns
-// tensor memory and issues the MMAs (accumulators double-buffered across tiles); 6-9 read the
-// accumulators and write phihat. Every wait is bounded; a wait that runs out records where in the
-// plan's device status word, and the CTA winds down.
+// sibling-minor spectra into a staging slot) and split them into the ring's BF16 pieces; 4 loads
+// the 26 kernel matrices of a frequency (one 39 KB bulk copy) when the column's frequency
+// changes; 5 owns tensor memory and issues the MMAs (accumulators double-buffered across tiles);
+// 6-9 read the accumulators and write phihat. Every wait is bounded; a wait that runs out records
+// where in the plan's device status word, and the CTA winds down.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cstring>
 #include <utility>
 #include <vector>
@@ -53,18 +57,21 @@ constexpr int kThreadsH = 320;
 constexpr int kTX = 8, kTY = 16;              // tile: 8 x 16 target clusters of one plane (M = 128)
 constexpr int kHX = kTX + 2, kHY = kTY + 2;   // halo of one plane: 10 x 18 clusters
 constexpr int kHRows = kHX * kHY;             // 180
-constexpr int kPieces = 4 * kHRows;           // 16-byte pieces of one plane and one TF32 piece
+constexpr int kPieces = 4 * kHRows;           // 16-byte pieces of a loaded plane (4 per halo row)
 constexpr uint32_t kSBO = kHX * 16;           // 160: between y lines (8-row groups)
 constexpr uint32_t kLBO = kHY * kSBO;         // 2880: between 16-byte K chunks
-constexpr uint32_t kPieceB = 4 * kLBO;        // 11520: one plane, one TF32 piece
-constexpr uint32_t kPlaneB = 2 * kPieceB;     // hi, then lo
+constexpr uint32_t kPieceB = 2 * kLBO;        // 5760: one plane, one BF16 piece (16 values a row)
+constexpr uint32_t kPlaneB = 3 * kPieceB;     // hi, mid, lo
+constexpr uint32_t kStageRow = 64;            // a halo row as loaded: 8 complex FP32 values
+constexpr uint32_t kStageB = kHRows * kStageRow;
+constexpr int kStageSlots = 3;                // loaded planes awaiting their split
 constexpr int kRing = 7;                      // halo planes in shared memory
 constexpr int kBBuf = 1;                      // kernel-matrix buffers (one frequency each)
-constexpr uint32_t kBDir = 2048;              // one direction: [4 K chunks][4 row groups][8 rows][16 B]
-constexpr uint32_t kBLBO = 512, kBSBO = 128;
+constexpr uint32_t kBDir = 1536;              // one direction: [2 K chunks][6 row groups][8 rows][16 B]
+constexpr uint32_t kBLBO = 768, kBSBO = 128;
 constexpr uint32_t kBFreq = 26 * kBDir;       // the 26 matrices of one frequency
-constexpr uint32_t kSmemH = kRing * kPlaneB + kBBuf * kBFreq;
-constexpr int kMaxChains = 8;                 // two buffers x 8 chains x 32 columns = 512
+constexpr uint32_t kSmemH = kRing * kPlaneB + kStageSlots * kStageB + kBBuf * kBFreq;
+constexpr int kMaxChains = 4;                 // two buffers x 4 chains x 64 columns = 512
 
 struct HtcParams {
     const float *qhat;       // [(cluster R + rhs)][F][8] complex, sibling-minor
@@ -73,7 +80,7 @@ struct HtcParams {
     int Np, R, F, XB, YB;
     long long ncols;         // F R XB YB columns, frequency slowest
     int *status;
-    uint32_t idesc32, idesc16;
+    uint32_t idesc48, idesc32, idesc16;
 };
 
 // The 26 source-cluster directions d in [-1,1]^3 \ {0} are indexed x slowest (di = 0..25). NCH
@@ -116,13 +123,6 @@ __device__ __forceinline__ void column_of(const HtcParams &P, long long c, int &
     f = (int)(c / P.R);
 }
 
-// Byte offset inside one plane piece of 16-byte piece e (row = halo cluster, kq = sibling pair).
-__device__ __forceinline__ uint32_t piece_offset(int e) {
-    const int row = e >> 2, kq = e & 3;
-    const int hy = row / kHX, hx = row - hy * kHX;
-    return (uint32_t)kq * kLBO + (uint32_t)hy * kSBO + (uint32_t)hx * 16;
-}
-
 // Cluster of grid point (x, y, z) of a full level: clusters are numbered in Morton order of their
 // keys (x in the lowest bit of each triple), and a full level holds all of them.
 __device__ __forceinline__ uint32_t spread3(uint32_t v) {
@@ -137,59 +137,71 @@ __device__ __forceinline__ long long morton3(int x, int y, int z) {
     return (long long)(spread3((uint32_t)x) | spread3((uint32_t)y) << 1 | spread3((uint32_t)z) << 2);
 }
 
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    return h;
+__device__ __forceinline__ uint32_t pack_bf16(float lo_half, float hi_half) {
+    const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo_half));
+    const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi_half));
+    return a | b << 16;
 }
 
-// q -> (q_hi, q_lo) in place for the pieces this thread loaded (its own cp.async have landed).
-__device__ __forceinline__ void split_plane(uint32_t plane, int tid) {
+// The plane loaded into staging slot `stage` -> ring slot `plane` as three BF16 pieces
+// q = q_hi + q_mid + q_lo (each the nearest BF16 of the remainder; exact: 8 + 8 + 8 bits cover
+// an FP32 significand), for the 16-byte pieces this thread loaded (its own cp.async have landed).
+__device__ __forceinline__ void split_plane(uint32_t stage, uint32_t plane, int tid) {
     for (int e = tid; e < kPieces; e += 128) {
-        const uint32_t a = plane + piece_offset(e);
+        const int row = e >> 2, kq = e & 3;
+        const int hy = row / kHX, hx = row - hy * kHX;
         float v[4];
-        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "r"(a)
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                     : "r"(stage + (uint32_t)row * kStageRow + (uint32_t)kq * 16)
                      : "memory");
-        uint32_t h[4], l[4];
+        float h[4], m[4], l[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            h[i] = tf32_rna(v[i]);
-            l[i] = tf32_rna(v[i] - __uint_as_float(h[i]));
+            h[i] = __bfloat162float(__float2bfloat16_rn(v[i]));
+            const float r1 = v[i] - h[i];
+            m[i] = __bfloat162float(__float2bfloat16_rn(r1));
+            l[i] = r1 - m[i];
         }
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(h[0]), "r"(h[1]), "r"(h[2]), "r"(h[3])
+        // values 4 kq .. 4 kq + 3 of the row: half of 16-byte K chunk kq / 2
+        const uint32_t a = plane + (uint32_t)(kq >> 1) * kLBO + (uint32_t)hy * kSBO + (uint32_t)hx * 16 + (uint32_t)(kq & 1) * 8;
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(pack_bf16(h[0], h[1])), "r"(pack_bf16(h[2], h[3]))
                      : "memory");
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a + kPieceB), "r"(l[0]), "r"(l[1]), "r"(l[2]),
-                     "r"(l[3])
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + kPieceB), "r"(pack_bf16(m[0], m[1])), "r"(pack_bf16(m[2], m[3]))
+                     : "memory");
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + 2 * kPieceB), "r"(pack_bf16(l[0], l[1])),
+                     "r"(pack_bf16(l[2], l[3]))
                      : "memory");
     }
 }
 
-// The four MMAs of slot K of a tile (one direction, chain order), all operands warp-uniform:
-// q_hi x [B_hi; B_lo] (N = 32) for both K steps, then q_lo x B_hi (N = 16) into the small half.
+// The three MMAs of slot K of a tile (one direction, chain order; K = 16, the whole direction),
+// all operands warp-uniform: q_hi x [B_hi; B_mid; B_lo] (N = 48), q_mid x [B_hi; B_mid] (N = 32)
+// into columns 16-47, q_lo x B_hi (N = 16) into columns 32-47 of the chain: columns 0-15 gather
+// the leading products, 16-31 those 2^-8 below, 32-47 those 2^-16 below.
 // pdm, pd0, pdp: descriptors of the planes z - 1, z, z + 1 (0 outside the domain).
 template <int NCH, int K>
 __device__ __forceinline__ void issue_slot(uint32_t dtile, uint64_t pdm, uint64_t pd0, uint64_t pdp, uint64_t bdesc,
-                                           uint32_t idesc32, uint32_t idesc16) {
+                                           uint32_t idesc48, uint32_t idesc32, uint32_t idesc16) {
     constexpr Slot sl = slot_of<NCH>(K);
     static_assert(sl.di >= 0, "direction slot");
     constexpr int id = sl.di + (sl.di >= 13 ? 1 : 0);
     constexpr int dx = id / 9 - 1, dy = (id / 3) % 3 - 1, dz = id % 3 - 1;
     constexpr uint32_t aoff = (uint32_t)((dy + 1) * (int)(kSBO / 16) + (dx + 1));  // 16-byte units
     constexpr uint32_t boff = (uint32_t)sl.di * (kBDir / 16);
-    constexpr uint32_t kA2 = 2 * kLBO / 16, kLo = kPieceB / 16, kB2 = 2 * kBLBO / 16;  // K step, lo piece
+    constexpr uint32_t kP = kPieceB / 16;  // next piece
     const uint64_t base = dz < 0 ? pdm : (dz == 0 ? pd0 : pdp);
     if (dz != 0 && base == 0) return;  // the source plane lies outside the domain
     const uint64_t a = base + aoff, b = bdesc + boff;
-    const uint32_t d = dtile + 32u * (uint32_t)sl.chain;
-    mma<0>(d, a, b, idesc32, sl.first ? 0u : 1u);
-    mma<0>(d, a + kA2, b + kB2, idesc32, 1);
-    mma<0>(d + 16, a + kLo, b, idesc16, 1);
-    mma<0>(d + 16, a + kLo + kA2, b + kB2, idesc16, 1);
+    const uint32_t d = dtile + 64u * (uint32_t)sl.chain;
+    mma<1>(d, a, b, idesc48, sl.first ? 0u : 1u);
+    mma<1>(d + 16, a + kP, b, idesc32, 1);
+    mma<1>(d + 32, a + 2 * kP, b, idesc16, 1);
 }
 template <int NCH, int... K>
 __device__ __forceinline__ void issue_tile(std::integer_sequence<int, K...>, uint32_t dtile, uint64_t pdm, uint64_t pd0,
-                                           uint64_t pdp, uint64_t bdesc, uint32_t idesc32, uint32_t idesc16) {
-    (issue_slot<NCH, K>(dtile, pdm, pd0, pdp, bdesc, idesc32, idesc16), ...);
+                                           uint64_t pdp, uint64_t bdesc, uint32_t idesc48, uint32_t idesc32,
+                                           uint32_t idesc16) {
+    (issue_slot<NCH, K>(dtile, pdm, pd0, pdp, bdesc, idesc48, idesc32, idesc16), ...);
 }
 
 template <int NCH>
@@ -202,11 +214,12 @@ __global__ void __launch_bounds__(kThreadsH, 1) hadamard_tc_kernel(const HtcPara
 
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     const uint32_t s_planes = smem_u32(smem);
-    const uint32_t s_B = s_planes + kRing * kPlaneB;
+    const uint32_t s_stage = s_planes + kRing * kPlaneB;
+    const uint32_t s_B = s_stage + kStageSlots * kStageB;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Np = P.Np;
-    constexpr uint32_t bufcols = 32u * NCH;                  // one tile's accumulators
-    constexpr uint32_t tmem_cols = bufcols <= 32 ? 64 : 2 * bufcols;  // two tiles' (a power of two >= 64)
+    constexpr uint32_t bufcols = 64u * NCH;                  // one tile's accumulators (48 used per chain)
+    constexpr uint32_t tmem_cols = 2 * bufcols;              // two tiles' (a power of two)
     // columns dealt round-robin: the CTAs resident at one time work on consecutive columns, i.e.
     // the same few frequencies of neighbouring tiles, so halo rows shared by neighbouring tiles
     // meet in L2 and the spectra rows read at one time lie close together in memory
@@ -239,25 +252,32 @@ __global__ void __launch_bounds__(kThreadsH, 1) hadamard_tc_kernel(const HtcPara
     const uint32_t tmem = tmem_base_s;
 
     if (warp < 4) {
-        // ---------------- halo planes: load plane ps, then split plane ps - 2 ----------------
-        // (the MMAs that free plane ps's slot, ps - kRing, need planes up to ps - kRing + 2 only)
+        // ---------------- halo planes: load plane ps into staging, then split plane ps - 2 ----------
+        // into its ring slot (the MMAs that free that slot, of plane ps - 2 - kRing, need planes up to
+        // ps - kRing only, all split before)
         long long ps = 0;
-        int prev1 = -1, prev2 = -1;  // ring slots of planes ps - 1 and ps - 2, loaded, not yet split
+        // split loaded plane q (its copies landed) into ring slot q mod kRing, once that slot is free
+        auto finish = [&](long long q) -> bool {
+            const int slot = (int)(q % kRing);
+            if (q >= kRing && !mbar_wait(smem_u32(&empty_bar[slot]), (uint32_t)(((q / kRing) - 1) & 1), &abort_flag,
+                                         P.status, M2L_WAIT_GATHER))
+                return false;
+            split_plane(s_stage + (uint32_t)(q % kStageSlots) * kStageB, s_planes + (uint32_t)slot * kPlaneB, tid);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(smem_u32(&full_bar[slot]));
+            return true;
+        };
         for (long long c = c0; c < P.ncols && !abort_flag; c += cstep) {
             int f, r, xb, yb;
             column_of(P, c, f, r, xb, yb);
             const int x0 = xb * kTX - 1, y0 = yb * kTY - 1;
             for (int z = 0; z < Np; ++z, ++ps) {
-                const int slot = (int)(ps % kRing);
-                if (ps >= kRing && !mbar_wait(smem_u32(&empty_bar[slot]), (uint32_t)(((ps / kRing) - 1) & 1), &abort_flag,
-                                              P.status, M2L_WAIT_GATHER))
-                    goto producer_done;
-                const uint32_t plane = s_planes + (uint32_t)slot * kPlaneB;
+                const uint32_t stage = s_stage + (uint32_t)(ps % kStageSlots) * kStageB;
                 for (int e = tid; e < kPieces; e += 128) {
                     const int row = e >> 2, kq = e & 3;
                     const int hy = row / kHX, hx = row - hy * kHX;
                     const int x = x0 + hx, y = y0 + hy;
-                    const uint32_t dst = plane + piece_offset(e);
+                    const uint32_t dst = stage + (uint32_t)row * kStageRow + (uint32_t)kq * 16;
                     if (x >= 0 && y >= 0 && x < Np && y < Np) {
                         const long long cl = morton3(x, y, z);
                         const float *src = P.qhat + (((long long)cl * P.R + r) * P.F + f) * 16 + kq * 4;
@@ -267,29 +287,21 @@ __global__ void __launch_bounds__(kThreadsH, 1) hadamard_tc_kernel(const HtcPara
                     }
                 }
                 asm volatile("cp.async.commit_group;" ::: "memory");
-                if (prev2 >= 0) {
+                if (ps >= 2) {
                     // every copy but the two newest groups (planes ps, ps - 1) has landed
                     asm volatile("cp.async.wait_group 2;" ::: "memory");
-                    split_plane(s_planes + (uint32_t)prev2 * kPlaneB, tid);
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_arrive(smem_u32(&full_bar[prev2]));
+                    if (!finish(ps - 2)) goto producer_done;
                 }
-                prev2 = prev1;
-                prev1 = slot;
             }
         }
         if (!abort_flag) {
-            if (prev2 >= 0) {
+            if (ps >= 2) {
                 asm volatile("cp.async.wait_group 1;" ::: "memory");
-                split_plane(s_planes + (uint32_t)prev2 * kPlaneB, tid);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(smem_u32(&full_bar[prev2]));
+                if (!finish(ps - 2)) goto producer_done;
             }
-            if (prev1 >= 0) {
+            if (ps >= 1) {
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
-                split_plane(s_planes + (uint32_t)prev1 * kPlaneB, tid);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(smem_u32(&full_bar[prev1]));
+                finish(ps - 1);
             }
         }
     producer_done:
@@ -375,7 +387,7 @@ __global__ void __launch_bounds__(kThreadsH, 1) hadamard_tc_kernel(const HtcPara
                     // direction is in-plane, so always present, and its first MMA clears the 32 columns
                     if (elect_one())
                         issue_tile<NCH>(std::make_integer_sequence<int, 26>{}, tmem + buf * bufcols, pd0, pd1, pd2, bdesc,
-                                        P.idesc32, P.idesc16);
+                                        P.idesc48, P.idesc32, P.idesc16);
                     __syncwarp();
                     if (elect_one()) {
                         mma_commit(smem_u32(&accf_bar[buf]));
@@ -415,20 +427,29 @@ __global__ void __launch_bounds__(kThreadsH, 1) hadamard_tc_kernel(const HtcPara
                 if (!mbar_wait(smem_u32(&accf_bar[buf]), (uint32_t)((u >> 1) & 1), &abort_flag, P.status, M2L_WAIT_ACC_READY))
                     goto epi_done;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                // the chains' main parts, then their small parts, added with round-to-nearest
-                float hi[16], lo[16];
+                // the chains' leading products, then the parts 2^-8 and 2^-16 below, added with
+                // round-to-nearest
+                float g0[16], g1[16], g2[16];
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
-                    uint32_t v0[16], v1[16];
-                    const uint32_t t = tmem + lane_off + buf * bufcols + 32u * (uint32_t)ch;
+                    uint32_t v0[16], v1[16], v2[16];
+                    const uint32_t t = tmem + lane_off + buf * bufcols + 64u * (uint32_t)ch;
                     tmem_ld16(t, v0);
                     tmem_ld16(t + 16, v1);
+                    tmem_ld16(t + 32, v2);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        hi[j] = ch ? __fadd_rn(hi[j], __uint_as_float(v0[j])) : __uint_as_float(v0[j]);
-                        lo[j] = ch ? __fadd_rn(lo[j], __uint_as_float(v1[j])) : __uint_as_float(v1[j]);
+                        g0[j] = ch ? __fadd_rn(g0[j], __uint_as_float(v0[j])) : __uint_as_float(v0[j]);
+                        g1[j] = ch ? __fadd_rn(g1[j], __uint_as_float(v1[j])) : __uint_as_float(v1[j]);
+                        g2[j] = ch ? __fadd_rn(g2[j], __uint_as_float(v2[j])) : __uint_as_float(v2[j]);
                     }
+                }
+                float hi[16], lo[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    hi[j] = g0[j];
+                    lo[j] = __fadd_rn(g1[j], g2[j]);
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 mbar_arrive(smem_u32(&acce_bar[buf]));
@@ -453,10 +474,10 @@ __global__ void __launch_bounds__(kThreadsH, 1) hadamard_tc_kernel(const HtcPara
     }
 }
 
-uint32_t idesc_tf32(int N) {
+uint32_t idesc_bf16(int N) {
     uint32_t d = 1u << 4;                 // FP32 accumulator
-    d |= 2u << 7;                         // A: TF32
-    d |= 2u << 10;                        // B: TF32
+    d |= 1u << 7;                         // A: BF16
+    d |= 1u << 10;                        // B: BF16
     d |= (uint32_t)(N >> 3) << 17;        // N
     d |= (uint32_t)(128 >> 4) << 24;      // M = 128
     return d;
@@ -470,17 +491,17 @@ bool hadamard_tc_eligible(const LevelView &L) {
 }
 
 // The kernel matrices B_d(f) of every frequency as the kernel's shared memory holds them: for each
-// f and direction d (dx slowest, then dy, dz; the origin left out), 32 rows n x 16 columns k, rows
-// 0-15 the TF32 hi piece and 16-31 the lo piece of
+// f and direction d (dx slowest, then dy, dz; the origin left out), 48 rows n x 16 columns k of
+// BF16, rows 0-15 the hi piece, 16-31 the mid piece and 32-47 the lo piece of
 //   B[2i + a][2j + b] = (Re K, -Im K; Im K, Re K)[a][b],  K = Khat_{t}(f),  t = 2 d + j - i,
-// zero where the two boxes are adjacent; K-major core matrices (8 rows x 4 values), row groups
-// 128 bytes apart, 16-byte K chunks 512 bytes apart. Built from the FP64 spectra.
+// zero where the two boxes are adjacent; K-major core matrices (8 rows x 8 values), row groups
+// 128 bytes apart, 16-byte K chunks 768 bytes apart. Built from the FP64 spectra.
 int build_hadamard_tc_operand(m2l_plan_t *pl, DevOps &D) {
     if (D.Bhad) return M2L_OK;
     const FftOps &Fo = *pl->fft;
     const int F = Fo.F;
-    const size_t per = kBFreq / sizeof(float);
-    std::vector<float> img((size_t)F * per, 0.f);
+    const size_t per = kBFreq / 2;  // BF16 values per frequency
+    std::vector<uint16_t> img((size_t)F * per, 0);
     int tix[26][8][8];
     {
         int dd = 0;
@@ -498,28 +519,35 @@ int build_hadamard_tc_operand(m2l_plan_t *pl, DevOps &D) {
 #pragma omp parallel for schedule(static)
     for (int f = 0; f < F; ++f)
         for (int dd = 0; dd < 26; ++dd) {
-            float *blk = &img[(size_t)f * per + (size_t)dd * (kBDir / sizeof(float))];
-            for (int n = 0; n < 32; ++n)
+            uint16_t *blk = &img[(size_t)f * per + (size_t)dd * (kBDir / 2)];
+            for (int n = 0; n < 16; ++n)
                 for (int k = 0; k < 16; ++k) {
-                    const int nn = n & 15, i = nn >> 1, a = nn & 1, j = k >> 1, b = k & 1;
+                    const int i = n >> 1, a = n & 1, j = k >> 1, b = k & 1;
                     const int ti = tix[dd][i][j];
                     double v = 0.0;
                     if (ti >= 0) {
                         const double kr = Fo.Khat[((size_t)ti * F + f) * 2], ki = Fo.Khat[((size_t)ti * F + f) * 2 + 1];
                         v = a == 0 ? (b == 0 ? kr : -ki) : (b == 0 ? ki : kr);
                     }
-                    const float h = tf32_round((float)v);
-                    const float l = tf32_round((float)(v - (double)h));
-                    blk[(k >> 2) * 128 + (n >> 3) * 32 + (n & 7) * 4 + (k & 3)] = n < 16 ? h : l;
+                    // three BF16 pieces, each the nearest to what the previous ones leave
+                    const uint16_t h = bf16_round((float)v);
+                    const double r1 = v - (double)bf16_value(h);
+                    const uint16_t m = bf16_round((float)r1);
+                    const uint16_t l = bf16_round((float)(r1 - (double)bf16_value(m)));
+                    const uint16_t pc[3] = {h, m, l};
+                    for (int pi = 0; pi < 3; ++pi) {
+                        const int nr = pi * 16 + n;  // row of the N = 48 operand
+                        blk[(k >> 3) * (kBLBO / 2) + (nr >> 3) * 64 + (nr & 7) * 8 + (k & 7)] = pc[pi];
+                    }
                 }
         }
-    if (cudaMalloc(&D.Bhad, img.size() * sizeof(float)) != cudaSuccess) {
+    if (cudaMalloc(&D.Bhad, img.size() * sizeof(uint16_t)) != cudaSuccess) {
         cudaGetLastError();
         D.Bhad = nullptr;
         set_error("allocating the tensor-core Hadamard operand failed");
         return M2L_ENOMEM;
     }
-    if (cudaMemcpy(D.Bhad, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemcpy(D.Bhad, img.data(), img.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         set_error("uploading the tensor-core Hadamard operand failed");
         return M2L_ECUDA;
@@ -530,8 +558,8 @@ int build_hadamard_tc_operand(m2l_plan_t *pl, DevOps &D) {
 int launch_hadamard_tc(const LevelView &L, int R, int F, const void *B, const float *qhat, float *phihat, int chains,
                        int num_sms, int *status, cudaStream_t s) {
     if (chains == 0) chains = 4;
-    if (chains != 1 && chains != 2 && chains != 4 && chains != kMaxChains) {
-        set_error("tensor-core Hadamard product: %d partial sums per tile (1, 2, 4 or 8)", chains);
+    if (chains != 1 && chains != 2 && chains != kMaxChains) {
+        set_error("tensor-core Hadamard product: %d partial sums per tile (1, 2 or 4)", chains);
         return M2L_EINVAL;
     }
     if (!hadamard_tc_eligible(L) || !B || R < 1 || F < 1) {
@@ -549,8 +577,9 @@ int launch_hadamard_tc(const LevelView &L, int R, int F, const void *B, const fl
     P.YB = P.Np / kTY;
     P.ncols = (long long)F * R * P.XB * P.YB;
     P.status = status;
-    P.idesc32 = idesc_tf32(32);
-    P.idesc16 = idesc_tf32(16);
+    P.idesc48 = idesc_bf16(48);
+    P.idesc32 = idesc_bf16(32);
+    P.idesc16 = idesc_bf16(16);
     const int grid = (int)(P.ncols < num_sms ? P.ncols : num_sms);
     const size_t smem = kSmemH + 128;
     auto go = [&](auto kern) {
@@ -559,8 +588,7 @@ int launch_hadamard_tc(const LevelView &L, int R, int F, const void *B, const fl
     };
     if (chains == 1) go(hadamard_tc_kernel<1>);
     else if (chains == 2) go(hadamard_tc_kernel<2>);
-    else if (chains == 4) go(hadamard_tc_kernel<4>);
-    else go(hadamard_tc_kernel<8>);
+    else go(hadamard_tc_kernel<4>);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("tensor-core Hadamard launch failed: %s", cudaGetErrorString(e));

@@ -1,6 +1,7 @@
 """GPU parity of the FFT form in TF32x3: the Hadamard products of full levels whose cluster grid
-side is a multiple of 16 (levels >= 5) run on the tensor cores (tcgen05, split TF32 pieces), with
-the spectra stored sibling-minor; the other levels take the FP32 CUDA-core kernels.
+side is a multiple of 16 (levels >= 5) run on the tensor cores (tcgen05, three BF16 pieces per
+operand, six products), with the spectra stored sibling-minor; the other levels take the FP32
+CUDA-core kernels. The pseudo-inverse's second factor runs on the tensor cores exactly.
 
 References: the FP64 oracle on sampled targets (check potentials, and locals through the check
 potential they reproduce), the FP64 FFT form of the library on whole levels (itself held to 1e-12
@@ -61,10 +62,10 @@ def test_all_levels_and_rhs_against_fp64_fft(lib, R):
         assert M.max_target_rel_error(ref[l], got[l]) < 10 * bound, l
 
 
-@pytest.mark.parametrize("chains", [1, 2, 8])
+@pytest.mark.parametrize("chains", [1, 2])
 def test_accumulator_chains_give_the_same_products(lib, chains):
     """M2L_OPT_HADAMARD_CHAINS only splits the sums over directions into separately accumulated
-    parts: every setting stays within the bound of the default one's result (1: a single
+    parts: every setting stays within the bound of the default one's (4) result (1: a single
     truncating chain of 26 directions, the loosest)."""
     import torch
     level, p = 5, 6
