@@ -324,7 +324,10 @@ static size_t fft_rows_bytes(const m2l_plan_t *pl, int R, int precision) {
     const size_t e = precision == M2L_PREC_FP64 ? 8 : 4;
     const long long allrows = pl->total_rows * R;
     size_t b = al256((size_t)allrows * pl->n * e) + al256((size_t)allrows * pl->rp * e);
-    if (precision == M2L_PREC_TF32X3 && pinv_tc_k(pl)) b += al256(pinv_tc_workspace(allrows, pinv_tc_k(pl)));
+    if (precision == M2L_PREC_TF32X3) {
+        const int ku = (pl->n + 63) / 64 * 64, kv = (pl->r32 + 63) / 64 * 64;
+        b += al256(sliced_workspace(allrows, std::max(ku, kv)));
+    }
     return b;
 }
 
@@ -513,20 +516,38 @@ static int fft_run(const Run &r, int precision, Workspace &ws, Workspace &spec, 
         }
     }
     if (!check_out) {
-        // F6: locals = V_eps (Ut_eps Phi); in TF32x3 the second product on the tensor cores, exact
+        // F6: locals = V_eps (Ut_eps Phi); in TF32x3 both products on the tensor cores, exact
         stage_begin(pl, M2L_STAGE_PINV);
-        M2L_TRY(launch_gemm_xwt<T>(Phi + base0 * R * n, n, (const T *)D.Ut, n, Z, rp, r.rows, rp, n, 0, s));
-        long long nl = 2;
+        long long nl = 0;
+        bool done_u = false, done_v = false;
         if constexpr (sizeof(T) == 4) {
-            if (precision == M2L_PREC_TF32X3 && pinv_tc_usable(D, n, n, (const float *)out)) {
+            if (precision == M2L_PREC_TF32X3) {
                 void *tws = (char *)ws.buf + al256(phi_b) + al256((size_t)pl->total_rows * R * rp * e);
-                M2L_TRY(launch_pinv_tc(pl, D, (const float *)Z, rp, r.rows, (float *)out, n, pl->accumulate, tws, s));
-                nl = 3;
-            } else {
-                M2L_TRY(apply_veps<T>(pl, D, Z, out, r.rows, pl->accumulate, true, s));
+                if (sliced_usable(D.Us, rp, rp, (const float *)Z)) {  // every column of Z (zeros past r)
+                    M2L_TRY(launch_sliced(pl, D.Us, (const float *)(Phi + base0 * R * n), n, r.rows, (float *)Z, rp, rp, 0,
+                                          tws, s));
+                    done_u = true;
+                    nl += 2;
+                }
+                if (sliced_usable(D.Vs, n, n, (const float *)out)) {
+                    if (!done_u) {
+                        M2L_TRY(launch_gemm_xwt<T>(Phi + base0 * R * n, n, (const T *)D.Ut, n, Z, rp, r.rows, rp, n, 0, s));
+                        done_u = true;
+                        nl += 1;
+                    }
+                    M2L_TRY(launch_sliced(pl, D.Vs, (const float *)Z, rp, r.rows, (float *)out, n, n, pl->accumulate, tws, s));
+                    done_v = true;
+                    nl += 2;
+                }
             }
-        } else {
+        }
+        if (!done_u) {
+            M2L_TRY(launch_gemm_xwt<T>(Phi + base0 * R * n, n, (const T *)D.Ut, n, Z, rp, r.rows, rp, n, 0, s));
+            nl += 1;
+        }
+        if (!done_v) {
             M2L_TRY(apply_veps<T>(pl, D, Z, out, r.rows, pl->accumulate, true, s));
+            nl += 1;
         }
         stage_end(pl, nl);
     }

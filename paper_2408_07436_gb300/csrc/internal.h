@@ -60,6 +60,15 @@ struct LevelSet {
 };
 
 // Device copy of the operators in one arithmetic precision.
+// A matrix W (O x K) as 4 BF16 integer slices of `beta` bits under a power-of-two scale per row,
+// for the exact sliced tensor-core products (pinv_tc.cu).
+struct SlicedOp {
+    void *sl = nullptr;          // [4][O_pad][K_pad] BF16
+    void *scale = nullptr;       // [O_pad] float, 2^e_w
+    int K = 0, kp = 0, O = 0, opad = 0, beta = 8;  // kp = 0: not built
+    alignas(64) unsigned char map[128] = {};        // TMA map (CUtensorMap) of the slices
+};
+
 struct DevOps {
     bool ready = false;
     int elt = 8;                 // bytes per real (8: double, 4: float)
@@ -81,10 +90,7 @@ struct DevOps {
     void *Ut = nullptr;          // [rp][np_]   Ut_eps
     void *tw = nullptr;          // [g] complex twiddles exp(-2 pi i m / g)
     void *Bhad = nullptr;        // TF32x3 FFT form: [F][26] kernel matrices of the tensor-core Hadamard
-    void *Vsl = nullptr;         // TF32x3 FFT form: V_eps as 4 BF16 integer slices [4][n_pad][K_pad]
-    void *Vscale = nullptr;      //   and its row scales 2^e_v [n_pad]
-    int pinv_kp = 0;             //   K_pad (0: not built)
-    alignas(64) unsigned char vmap[128] = {};  //   TMA map (CUtensorMap) of the slices
+    SlicedOp Us, Vs;             // TF32x3 FFT form: Ut_eps and V_eps as BF16 integer slices
 };
 
 struct LevelDev {
@@ -225,13 +231,13 @@ void free_exec(m2l_plan_t *pl);
 void stage_begin(m2l_plan_t *pl, int stage);
 void stage_end(m2l_plan_t *pl, long long launches);
 int apply_device(m2l_plan_t *pl, const void *q, void *L, int level, int nrhs);
-// pinv_tc.cu: F6's V_eps product on the tensor cores, exact (4 BF16 integer slices per operand,
-// 10 slice pairs), for the TF32x3 FFT form when the single-precision rank is at most 256:
-// out[row][0..n) (+)= V_eps Z[row] for `rows` rows of Z (row stride ldz), output row stride ldo;
-// `ws` holds pinv_tc_workspace(rows, K_pad) bytes.
-int pinv_tc_k(const m2l_plan_t *pl);
-size_t pinv_tc_workspace(long long rows, int Kp);
-bool pinv_tc_usable(const DevOps &D, long long ldo, int O, const float *out);
-int launch_pinv_tc(const m2l_plan_t *pl, const DevOps &D, const float *Z, long long ldz, long long rows, float *out,
-                   long long ldo, int acc, void *ws, cudaStream_t s);
+// pinv_tc.cu: exact sliced products on the tensor cores (4 BF16 integer slices per operand, 10
+// slice pairs): out[row][0..O) (+)= W X[row] for `rows` rows of X (row stride ldx, W.K values),
+// output row stride ldo, O a multiple of 4 and at most W's padded rows; `ws` holds
+// sliced_workspace(rows, W.kp) bytes. Used for both factors of F6 in the TF32x3 FFT form.
+int build_sliced_operand(const std::vector<double> &W, int O, int K, int beta, SlicedOp &op);
+size_t sliced_workspace(long long rows, int Kp);
+bool sliced_usable(const SlicedOp &W, long long ldo, int O, const float *out);
+int launch_sliced(const m2l_plan_t *pl, const SlicedOp &W, const float *X, long long ldx, long long rows, float *out,
+                  long long ldo, int O, int acc, void *ws, cudaStream_t s);
 }  // namespace m2l

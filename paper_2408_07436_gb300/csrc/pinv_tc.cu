@@ -1,21 +1,23 @@
-// F6's second factor, out = V_eps Z (+ out) (Eq. 9, the factor of the pseudo-inverse stored apart
-// as the footnote of Sec. 2.1.1 recommends), on the tensor cores, exactly.
+// F6, the pseudo-inverse's two factors (Eq. 9, stored apart as the footnote of Sec. 2.1.1
+// recommends), on the tensor cores, exactly: Z = Ut_eps phi, then locals = V_eps Z (+ locals).
 //
-// The product must be carried beyond FP32: the locals are measured through the check potential
-// they reproduce, which FP32 accumulation error over the r terms roughly doubles (the CUDA-core
-// path uses a float-float sum). Here both operands are cut into integer slices, so every
-// tensor-core product and every partial sum is an exact integer in FP32 (the error-free
+// The V_eps product must be carried beyond FP32: the locals are measured through the check
+// potential they reproduce, which FP32 accumulation error over the r terms roughly doubles (the
+// CUDA-core path uses a float-float sum). Here both operands are cut into integer slices, so
+// every tensor-core product and every partial sum is an exact integer in FP32 (the error-free
 // splitting of Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59, 2012):
-//   a row z of Z (K = r values) is scaled by 2^-e_z (e_z: the exponent of its largest entry, so
-//   |z| 2^-e_z < 1) and written as sum_s q_s 2^-8(s+1), s = 0..3, with integers |q_0| <= 256 and
-//   |q_s| <= 128 after it (round to nearest, each slice the rounded residual of the previous);
-//   a row v of V_eps likewise with 2^e_v and integers p_t.
-// Then z.v = 2^(e_z + e_v) sum_{s,t} 2^-8(s+t+2) (q_s . p_t). Every q_s . p_t with K <= 256 is an
-// integer of magnitude at most 2^24, exact in the FP32 accumulator whatever its rounding; the
-// products on the same diagonal s + t share an accumulator (their exactness matters only on the
-// leading diagonal, which holds one pair). Slices are BF16 (8-bit integers exactly); the 10 pairs
-// with s + t <= 3 are kept, which reproduces the float-float product's result to rounding
-// (host emulation over p = 6, 8, 10: the locals' check-norm error equal to three digits).
+//   a row x of X (K values) is scaled by 2^-e_x (e_x: the exponent of its largest entry, so
+//   |x| 2^-e_x < 1) and written as sum_s q_s 2^-beta(s+1), s = 0..3, with integers |q_0| <= 2^beta
+//   and |q_s| <= 2^(beta-1) after it (round to nearest, each slice the rounded residual of the
+//   previous); a row w of W likewise with 2^e_w and integers p_t.
+// Then x.w = 2^(e_x + e_w) sum_{s,t} 2^-beta(s+t+2) (q_s . p_t). Every q_s . p_t is an integer of
+// magnitude at most 2^(2 beta) K, exact in the FP32 accumulator whatever its rounding while that
+// is at most 2^24 (beta = 8: K <= 256, the V_eps product over the rank r; beta = 7: K <= 1024,
+// the Ut_eps product over the n check points); the products on the same diagonal s + t share an
+// accumulator (exactness matters on the leading diagonal, which holds one pair). Slices are BF16
+// (integers of up to 9 bits exactly); the 10 pairs with s + t <= 3 are kept, which reproduces the
+// float-float V_eps product's result to rounding (host emulation over p = 6, 8, 10: the locals'
+// check-norm error equal to three digits).
 //
 // Tiles of 128 rows x 64 outputs, K in stages of 64 (128-byte swizzled rows, TMA); per stage the
 // 4 K steps x 10 slice pairs are 40 MMAs (M = 128, N = 64, K = 16, BF16) into 4 diagonal
@@ -53,8 +55,8 @@ constexpr int kDiag = 4;                        // accumulators: s + t = 0..3
 constexpr uint32_t kBufCols = kDiag * kNP;      // 256 columns per tile; two tiles in flight
 
 struct PtcParams {
-    const int *zexp;         // [rows_pad] exponents of the Z rows
-    const float *vscale;     // [O_pad] 2^e_v of the V rows
+    const int *zexp;         // [rows_pad] exponents of the X rows
+    const float *vscale;     // [O_pad] 2^e_w of the W rows
     float *out;              // [rows][ldo]
     long long rows, ldo;
     int O, nk;               // outputs; K stages (K_pad / 64)
@@ -62,6 +64,8 @@ struct PtcParams {
     int acc;
     int *status;
     uint32_t idesc;
+    float d1, d2, d3;        // 2^-beta, 2^-2 beta, 2^-3 beta: the diagonals' weights
+    int eshift;              // 2 beta
 };
 
 // One BF16 slice pair (s, t) of the 10 with s + t <= 3, diagonal-major.
@@ -79,10 +83,11 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
     return d;
 }
 
-// Z rows -> 4 BF16 integer slices [4][rows_pad][K_pad] and exponents (one warp per row; rows past
-// `rows` and columns past K are zeros).
+// X rows -> 4 BF16 integer slices of beta bits [4][rows_pad][K_pad] and exponents (one warp per
+// row; rows past `rows` and columns past K are zeros).
 __global__ void slice_rows_kernel(const float *__restrict__ Z, long long ldz, long long rows, long long rows_pad, int K,
-                                  int Kp, __nv_bfloat16 *__restrict__ Zs, int *__restrict__ zexp) {
+                                  int Kp, int beta, __nv_bfloat16 *__restrict__ Zs, int *__restrict__ zexp) {
+    const float sc = (float)(1 << beta);
     const int lane = threadIdx.x & 31;
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -100,10 +105,10 @@ __global__ void slice_rows_kernel(const float *__restrict__ Z, long long ldz, lo
             float R = (live && k < K) ? ldexpf(Z[row * ldz + k], -e) : 0.f;  // |R| < 1
 #pragma unroll
             for (int s = 0; s < kSl; ++s) {
-                const float t = R * 256.f;  // exact
+                const float t = R * sc;     // exact
                 const float q = rintf(t);
                 R = t - q;                  // exact, |R| <= 1/2
-                Zs[((long long)s * rows_pad + row) * Kp + k] = __float2bfloat16_rn(q);  // |q| <= 256: exact
+                Zs[((long long)s * rows_pad + row) * Kp + k] = __float2bfloat16_rn(q);  // |q| <= 2^beta: exact
             }
         }
     }
@@ -231,7 +236,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             }
         }
     } else {
-        // ---------------- epilogue: out = 2^(e_z + e_v - 16) (D0 + D1 2^-8 + D2 2^-16 + D3 2^-24) ----
+        // ---------------- epilogue: out = 2^(e_x + e_w - 2 beta) sum_d D_d 2^-beta d ----------------
         const int quarter = warp & 3;
         const int rl = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
@@ -263,10 +268,10 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     for (int i = 0; i < 4; ++i) {
                         const int j = 4 * q + i;
                         // the diagonals from the smallest; every D is an exact integer
-                        float a = fmaf(__uint_as_float(v[3][j]), 5.9604644775390625e-8f, __uint_as_float(v[2][j]) * 1.52587890625e-5f);
-                        a = fmaf(__uint_as_float(v[1][j]), 3.90625e-3f, a);
+                        float a = fmaf(__uint_as_float(v[3][j]), P.d3, __uint_as_float(v[2][j]) * P.d2);
+                        a = fmaf(__uint_as_float(v[1][j]), P.d1, a);
                         a = __fadd_rn(__uint_as_float(v[0][j]), a);
-                        y[i] = ldexpf(a, ez - 16) * P.vscale[c + i];
+                        y[i] = ldexpf(a, ez - P.eshift) * P.vscale[c + i];
                     }
                     float4 *o = reinterpret_cast<float4 *>(orow + c);
                     if (P.acc) {
@@ -295,50 +300,44 @@ __global__ void __launch_bounds__(kThreadsP, 1)
 
 }  // namespace
 
-// K of the sliced product: r (the single-precision pseudo-inverse's rank) rounded up to whole
-// stages; 0 when r > 256, where the leading diagonal's sums could pass 2^24.
-int pinv_tc_k(const m2l_plan_t *pl) {
-    const int kp = (pl->r32 + kKS - 1) / kKS * kKS;
-    return pl->r32 >= 1 && kp <= 256 ? kp : 0;
-}
 
-// V_eps (FP64, n x r) as 4 BF16 integer slices [4][O_pad][K_pad] with its row scales 2^e_v, and the
-// TMA map of the slices (box 64 x 64, 128-byte swizzle). Nothing is built when pinv_tc_k is 0.
-int build_pinv_tc_operand(m2l_plan_t *pl, DevOps &D) {
-    if (D.Vsl) return M2L_OK;
-    const int Kp = pinv_tc_k(pl);
-    if (!Kp) return M2L_OK;
-    const int n = pl->n, r = pl->r32;
-    const int opad = (n + kNP - 1) / kNP * kNP;
-    const std::vector<double> &V = pl->pinv->Veps32;  // n x r
+// Largest K_pad for which the leading diagonal's sums (at most 2^(2 beta) K) stay exact in FP32.
+static int max_kp(int beta) { return 1 << (24 - 2 * beta); }
+
+// W (FP64, O x K, row-major) as 4 BF16 integer slices of beta bits [4][O_pad][K_pad] with its row
+// scales 2^e_w, and the TMA map of the slices (box 64 x 64, 128-byte swizzle). op.kp stays 0 when
+// K_pad is past max_kp(beta).
+int build_sliced_operand(const std::vector<double> &W, int O, int K, int beta, SlicedOp &op) {
+    if (op.sl) return M2L_OK;
+    const int Kp = (K + kKS - 1) / kKS * kKS;
+    if (K < 1 || Kp > max_kp(beta)) return M2L_OK;
+    const int opad = (O + kNP - 1) / kNP * kNP;
+    const double sc = std::ldexp(1.0, beta);
     std::vector<uint16_t> sl((size_t)kSl * opad * Kp, 0);
     std::vector<float> scale(opad, 1.f);
-    for (int o = 0; o < n; ++o) {
+    for (int o = 0; o < O; ++o) {
         double mx = 0;
-        for (int k = 0; k < r; ++k) mx = std::max(mx, std::fabs(V[(size_t)o * r + k]));
+        for (int k = 0; k < K; ++k) mx = std::max(mx, std::fabs(W[(size_t)o * K + k]));
         int e = 0;
-        if (mx > 0) std::frexp(mx, &e);
+        if (mx > 0) std::frexp(mx, &e);  // mx < 2^e
         scale[o] = std::ldexp(1.0f, e);
-        for (int k = 0; k < r; ++k) {
-            double R = std::ldexp(V[(size_t)o * r + k], -e);
+        for (int k = 0; k < K; ++k) {
+            double R = std::ldexp(W[(size_t)o * K + k], -e);
             for (int s = 0; s < kSl; ++s) {
-                const double t = R * 256.0;
+                const double t = R * sc;
                 const double q = std::nearbyint(t);
                 R = t - q;
-                sl[((size_t)s * opad + o) * Kp + k] = bf16_round((float)q);  // an integer of at most 9 bits
+                sl[((size_t)s * opad + o) * Kp + k] = bf16_round((float)q);  // an integer of at most beta + 1 bits
             }
         }
     }
-    for (void **pp : {&D.Vsl, &D.Vscale})
-        if (*pp) cudaFree(*pp);
-    D.Vsl = D.Vscale = nullptr;
-    if (cudaMalloc(&D.Vsl, sl.size() * 2) != cudaSuccess || cudaMalloc(&D.Vscale, scale.size() * 4) != cudaSuccess) {
+    if (cudaMalloc(&op.sl, sl.size() * 2) != cudaSuccess || cudaMalloc(&op.scale, scale.size() * 4) != cudaSuccess) {
         cudaGetLastError();
-        set_error("allocating the sliced pseudo-inverse factor failed");
+        set_error("allocating a sliced operand failed");
         return M2L_ENOMEM;
     }
-    cudaMemcpy(D.Vsl, sl.data(), sl.size() * 2, cudaMemcpyHostToDevice);
-    cudaMemcpy(D.Vscale, scale.data(), scale.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(op.sl, sl.data(), sl.size() * 2, cudaMemcpyHostToDevice);
+    cudaMemcpy(op.scale, scale.data(), scale.size() * 4, cudaMemcpyHostToDevice);
     EncodeTiledFn enc = encode_fn();
     if (!enc) {
         set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -348,43 +347,59 @@ int build_pinv_tc_operand(m2l_plan_t *pl, DevOps &D) {
     const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
     const cuuint32_t box[2] = {(cuuint32_t)kKS, (cuuint32_t)kNP};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult rc = enc(reinterpret_cast<CUtensorMap *>(D.vmap), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, D.Vsl, dims, strides, box,
+    CUresult rc = enc(reinterpret_cast<CUtensorMap *>(op.map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, op.sl, dims, strides, box,
                       estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (rc != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d)", (int)rc);
         return M2L_ECUDA;
     }
-    D.pinv_kp = Kp;
+    op.kp = Kp;
+    op.K = K;
+    op.O = O;
+    op.opad = opad;
+    op.beta = beta;
     return M2L_OK;
 }
 
-// Workspace of launch_pinv_tc for `rows` rows: the Z slices, then the row exponents.
-size_t pinv_tc_workspace(long long rows, int Kp) {
+// F6's two factors for the TF32x3 FFT form: Ut_eps (r x n) in slices of 7 bits (K = n up to 1024),
+// V_eps (n x r) in slices of 8 bits (K = r up to 256); the product with a factor is taken on the
+// tensor cores when its slices exist.
+int build_pinv_tc_operand(m2l_plan_t *pl, DevOps &D) {
+    // Ut_eps padded with zero rows to r_pad: the product writes every column of Z's rows (the
+    // CUDA-core V_eps product, where that one is taken, reads them all)
+    std::vector<double> ut((size_t)pl->rp * pl->n, 0.0);
+    std::copy(pl->pinv->Uteps32.begin(), pl->pinv->Uteps32.begin() + (size_t)pl->r32 * pl->n, ut.begin());
+    int rc = build_sliced_operand(ut, pl->rp, pl->n, 7, D.Us);
+    if (rc) return rc;
+    return build_sliced_operand(pl->pinv->Veps32, pl->n, pl->r32, 8, D.Vs);
+}
+
+// Workspace of launch_sliced for `rows` rows of K_pad: the X slices, then the row exponents.
+size_t sliced_workspace(long long rows, int Kp) {
     const long long rows_pad = (rows + kRowsP - 1) / kRowsP * kRowsP;
     return (((size_t)kSl * rows_pad * Kp * 2 + 255) / 256) * 256 + (size_t)rows_pad * 4;
 }
 
-bool pinv_tc_usable(const DevOps &D, long long ldo, int O, const float *out) {
-    return D.Vsl && D.pinv_kp > 0 && ldo % 4 == 0 && O % 4 == 0 && ((uintptr_t)out & 15) == 0;
+bool sliced_usable(const SlicedOp &W, long long ldo, int O, const float *out) {
+    return W.sl && W.kp > 0 && O <= W.opad && ldo % 4 == 0 && O % 4 == 0 && ((uintptr_t)out & 15) == 0;
 }
 
-int launch_pinv_tc(const m2l_plan_t *pl, const DevOps &D, const float *Z, long long ldz, long long rows, float *out,
-                   long long ldo, int acc, void *ws, cudaStream_t s) {
+int launch_sliced(const m2l_plan_t *pl, const SlicedOp &W, const float *X, long long ldx, long long rows, float *out,
+                  long long ldo, int O, int acc, void *ws, cudaStream_t s) {
     if (rows <= 0) return M2L_OK;
-    const int Kp = D.pinv_kp, n = pl->n;
-    if (!pinv_tc_usable(D, ldo, n, out)) {
-        set_error("sliced pseudo-inverse product: operand or output layout not supported");
+    if (!sliced_usable(W, ldo, O, out)) {
+        set_error("sliced tensor-core product: operand or output layout not supported");
         return M2L_EUNSUPPORTED;
     }
+    const int Kp = W.kp, beta = W.beta;
     const long long rows_pad = (rows + kRowsP - 1) / kRowsP * kRowsP;
-    const int opad = (n + kNP - 1) / kNP * kNP;
-    __nv_bfloat16 *Zs = (__nv_bfloat16 *)ws;
-    int *zexp = (int *)((char *)ws + (((size_t)kSl * rows_pad * Kp * 2 + 255) / 256) * 256);
+    __nv_bfloat16 *Xs = (__nv_bfloat16 *)ws;
+    int *xexp = (int *)((char *)ws + (((size_t)kSl * rows_pad * Kp * 2 + 255) / 256) * 256);
     {
         long long blocks = (rows_pad + 7) / 8;  // 8 warps per block, a warp per row
         if (blocks > 65535) blocks = 65535;
-        slice_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(Z, ldz, rows, rows_pad, pl->r32, Kp, Zs, zexp);
+        slice_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, rows, rows_pad, W.K, Kp, beta, Xs, xexp);
     }
     EncodeTiledFn enc = encode_fn();
     if (!enc) {
@@ -396,33 +411,37 @@ int launch_pinv_tc(const m2l_plan_t *pl, const DevOps &D, const float *Z, long l
     const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
     const cuuint32_t box[2] = {(cuuint32_t)kKS, (cuuint32_t)kRowsP};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult rc = enc(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Zs, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    CUresult rc = enc(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Xs, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                       CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (rc != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d)", (int)rc);
         return M2L_ECUDA;
     }
     PtcParams P;
-    P.zexp = zexp;
-    P.vscale = (const float *)D.Vscale;
+    P.zexp = xexp;
+    P.vscale = (const float *)W.scale;
     P.out = out;
     P.rows = rows;
     P.ldo = ldo;
-    P.O = n;
+    P.O = O;
     P.nk = Kp / kKS;
     P.mtiles = rows_pad / kRowsP;
-    P.ntiles = opad / kNP;
+    P.ntiles = (O + kNP - 1) / kNP;
     P.acc = acc;
     P.status = pl->dev_status;
     P.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kNP >> 3) << 17) | ((uint32_t)(kRowsP >> 4) << 24);
+    P.d1 = std::ldexp(1.0f, -beta);
+    P.d2 = std::ldexp(1.0f, -2 * beta);
+    P.d3 = std::ldexp(1.0f, -3 * beta);
+    P.eshift = 2 * beta;
     const long long total = P.mtiles * P.ntiles;
     const int grid = (int)(total < pl->num_sms ? total : pl->num_sms);
     const size_t smem = kSmemP + 1024;
     cudaFuncSetAttribute(pinv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    pinv_tc_kernel<<<grid, kThreadsP, smem, s>>>(tmA, *reinterpret_cast<const CUtensorMap *>(D.vmap), P, rows_pad, opad);
+    pinv_tc_kernel<<<grid, kThreadsP, smem, s>>>(tmA, *reinterpret_cast<const CUtensorMap *>(W.map), P, rows_pad, W.opad);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
-        set_error("sliced pseudo-inverse launch failed: %s", cudaGetErrorString(e));
+        set_error("sliced tensor-core product launch failed: %s", cudaGetErrorString(e));
         return M2L_ECUDA;
     }
     return M2L_OK;

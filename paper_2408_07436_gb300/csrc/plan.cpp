@@ -1020,12 +1020,12 @@ int upload_ops(m2l_plan_t *pl, int precision, int form) {
 void release_operators(m2l_plan_t *pl) {
     for (auto &D : pl->dev) {
         void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Vlo, &D.Uc, &D.C_hi, &D.C_lo, &D.Ub, &D.Vt, &D.dir_meta,
-                         &D.Khat, &D.Ut, &D.tw, &D.Bhad, &D.Vsl, &D.Vscale};
+                         &D.Khat, &D.Ut, &D.tw, &D.Bhad, &D.Us.sl, &D.Us.scale, &D.Vs.sl, &D.Vs.scale};
         for (void **pp : ptrs) {
             if (*pp) cudaFree(*pp);
             *pp = nullptr;
         }
-        D.pinv_kp = 0;
+        D.Us.kp = D.Vs.kp = 0;
         D.ready = false;
     }
 }
@@ -1033,12 +1033,12 @@ void release_operators(m2l_plan_t *pl) {
 void free_device(m2l_plan_t *pl) {
     for (auto &D : pl->dev) {
         void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Vlo, &D.Uc, &D.C_hi, &D.C_lo, &D.Ub, &D.Vt, &D.dir_meta,
-                         &D.Khat, &D.Ut, &D.tw, &D.Bhad, &D.Vsl, &D.Vscale};
+                         &D.Khat, &D.Ut, &D.tw, &D.Bhad, &D.Us.sl, &D.Us.scale, &D.Vs.sl, &D.Vs.scale};
         for (void **pp : ptrs) {
             if (*pp) cudaFree(*pp);
             *pp = nullptr;
         }
-        D.pinv_kp = 0;
+        D.Us.kp = D.Vs.kp = 0;
         D.ready = false;
     }
     for (int l = 0; l <= kMaxDepth; ++l) free_level(pl->ldev[l]);

@@ -1,7 +1,7 @@
 """GPU parity of the FFT form in TF32x3: the Hadamard products of full levels whose cluster grid
 side is a multiple of 16 (levels >= 5) run on the tensor cores (tcgen05, three BF16 pieces per
 operand, six products), with the spectra stored sibling-minor; the other levels take the FP32
-CUDA-core kernels. The pseudo-inverse's second factor runs on the tensor cores exactly.
+CUDA-core kernels. Both factors of the pseudo-inverse run on the tensor cores exactly.
 
 References: the FP64 oracle on sampled targets (check potentials, and locals through the check
 potential they reproduce), the FP64 FFT form of the library on whole levels (itself held to 1e-12
@@ -142,17 +142,21 @@ def test_c3_full_size_sampled_fft_tf32x3(lib):
 
 
 @pytest.mark.parametrize("p", [4, 6, 8])
-def test_tensor_core_pseudo_inverse_equals_the_float_float_one(lib, p):
-    """Below level 5 the TF32x3 FFT form differs from FP32 only in F6's V_eps product: exact BF16
-    integer slices on the tensor cores against the float-float CUDA-core sum. Both carry the
-    product beyond FP32, so their locals agree to the FP32 rounding of the result, in the check
-    norm, and both meet the oracle."""
+def test_tensor_core_pseudo_inverse_is_as_accurate_as_the_float_float_one(lib, p):
+    """Below level 5 the TF32x3 FFT form differs from FP32 only in F6: both factors as exact
+    products of BF16 integer slices on the tensor cores, against an FP32 GEMM for Ut_eps and the
+    float-float CUDA-core sum for V_eps. Z = Ut_eps phi cancels heavily in the directions the
+    check matrix damps, so the two paths' locals differ by their own rounding noise; measured in
+    the check norm against the oracle, the tensor-core locals are at least as accurate (host
+    emulation at p = 8: 1.40e-7 against 1.74e-7) and within the stated bound."""
     wl = W.small(depth=4, p=p, density="u11", seed=60 + p)
     qs = {l: wl.multipoles(l) for l in wl.levels}
     tc = run_gpu(lib, 4, p, qs, form="fft", precision="tf32x3", output="locals")
     ff = run_gpu(lib, 4, p, qs, form="fft", precision="fp32", output="locals")
     for l in wl.levels:
-        assert M.check_norm_error(p, l, ff[l], tc[l]) < 1.5e-7, l
-        tg = _sample(8 ** l, l, 24, l)
+        tg = _sample(8 ** l, l, 48, l)
         L_ref, _ = oracle_level(p, l, qs[l], targets=tg)
-        assert M.check_norm_error(p, l, L_ref, tc[l][tg]) < stated("fft", "tf32x3", p), l
+        e_tc = M.check_norm_error(p, l, L_ref, tc[l][tg])
+        e_ff = M.check_norm_error(p, l, L_ref, ff[l][tg])
+        assert e_tc < stated("fft", "tf32x3", p), l
+        assert e_tc <= 1.25 * e_ff + 2e-8, (l, e_tc, e_ff)
