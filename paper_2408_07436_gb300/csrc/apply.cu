@@ -496,7 +496,8 @@ static int fft_run(const Run &r, int precision, Workspace &ws, Workspace &spec, 
             const int rc = std::min(Rc, R - r0);
             L.row0 = r0;
             stage_begin(pl, M2L_STAGE_FFT_FORWARD);
-            cudaMemsetAsync(qhat, 0, (size_t)L.nclusters * rc * F * 16 * e, s);  // missing children stay zero
+            // missing children's spectra stay zero; on a full level the transform writes every one
+            if (L.nboxes != 8 * L.nclusters) cudaMemsetAsync(qhat, 0, (size_t)L.nclusters * rc * F * 16 * e, s);
             M2L_TRY(launch_fft_forward<T>(L, rc, p, n, g, pl->lattice_dev, (const T *)D.tw, ql, qhat, s, tcl));
             stage_end(pl, 1);
             stage_begin(pl, M2L_STAGE_HADAMARD);
