@@ -145,9 +145,9 @@ enum m2l_precision_e {
     M2L_PREC_TF32X3 = 2,  /* FP32 data; BLAS contractions as three TF32 tensor-core products. FFT form:
                              FP32 transforms; the Hadamard products of full levels ((N/2)^3 clusters,
                              N/2 a multiple of 16) on the tensor cores as split products accurate to
-                             FP32 rounding (three BF16 pieces per operand, six products), and the
-                             pseudo-inverse's second factor on the tensor cores exactly (BF16
-                             integer slices) when its rank is at most 256 */
+                             FP32 rounding (three BF16 pieces per operand, six products), and both
+                             factors of the pseudo-inverse on the tensor cores exactly (BF16 integer
+                             slices; the second one when the rank is at most 256) */
     M2L_PREC_BF16X3 = 3   /* FP32 data; BLAS contractions as three BF16 tensor-core products */
 };
 
