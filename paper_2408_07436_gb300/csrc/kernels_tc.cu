@@ -264,8 +264,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- MMA issuer: one partial sum per unit ----------------
         // A tile's work is its (transfer vector, K stage) pairs, vector-major. A unit, summed in one
         // tensor-memory buffer before its round-to-nearest drain, is `group` whole transfer vectors
-        // (seg == 0) or seg consecutive stages of one transfer vector (seg > 0).
-        if (lane == 0) {
+        // (seg == 0) or seg consecutive stages of one transfer vector (seg > 0). The whole warp runs
+        // the bookkeeping, so descriptors and counters are warp-uniform (uniform registers); one
+        // elected lane issues the MMAs and commits.
+        {
             long long it = 0, u = 0;
             bool pending = false;
             const int nc = P.nchunks, seg = P.seg, group = P.group;
@@ -298,26 +300,31 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int steps = min(CH / 32, (kbytes - c * CH) / 32);
                     const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
                     const uint32_t bh = smem_u32(sB_hi(s)), bl = smem_u32(sB_lo(s));
-                    for (int k = 0; k < steps; ++k) {
-                        const uint64_t dah = smem_desc<CH>(ah + 32 * k), dal = smem_desc<CH>(al + 32 * k);
-                        const uint64_t dbh = smem_desc<CH>(bh + 32 * k), dbl = smem_desc<CH>(bl + 32 * k);
-                        mma<KIND>(d, dal, dbh, P.idesc, accflag);
-                        accflag = 1;
-                        mma<KIND>(d, dah, dbl, P.idesc, 1);
-                        mma<KIND>(d, dah, dbh, P.idesc, 1);
+                    if (elect_one()) {
+                        uint32_t af = accflag;
+                        for (int k = 0; k < steps; ++k) {
+                            const uint64_t dah = smem_desc<CH>(ah + 32 * k), dal = smem_desc<CH>(al + 32 * k);
+                            const uint64_t dbh = smem_desc<CH>(bh + 32 * k), dbl = smem_desc<CH>(bl + 32 * k);
+                            mma<KIND>(d, dal, dbh, P.idesc, af);
+                            af = 1;
+                            mma<KIND>(d, dah, dbl, P.idesc, 1);
+                            mma<KIND>(d, dah, dbh, P.idesc, 1);
+                        }
+                        mma_commit(smem_u32(&empty_bar[s]));
+                        if (uend) mma_commit(smem_u32(&accf_bar[buf]));
                     }
-                    mma_commit(smem_u32(&empty_bar[s]));
+                    __syncwarp();
+                    accflag = 1;  // every stage issues at least one K step
                     pending = true;
-                    if (uend) {
-                        mma_commit(smem_u32(&accf_bar[buf]));
-                        ++u;
-                    }
+                    if (uend) ++u;
                 }
             }
         mma_done:
+            __syncwarp();
             if (abort_flag && pending) {
                 // no MMA may still write tensor memory when it is released
-                mma_commit(smem_u32(&drain_bar));
+                if (elect_one()) mma_commit(smem_u32(&drain_bar));
+                __syncwarp();
                 for (long long w = 0; w < kWaitLimit && !mbar_try(smem_u32(&drain_bar), 0); ++w) {
                 }
             }
