@@ -296,8 +296,8 @@ static int ensure_exec(m2l_plan_t *owner, std::vector<Run> &runs, int rows_per_t
 static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct BlasLayout {
-    size_t qt_b, ph_b, z_b, split_b;
-    size_t total() const { return al256(qt_b) + al256(ph_b) + al256(z_b) + 2 * al256(split_b); }
+    size_t qt_b, ph_b, z_b, split_b, sl_b;
+    size_t total() const { return al256(qt_b) + al256(ph_b) + al256(z_b) + 2 * al256(split_b) + al256(sl_b); }
 };
 
 static BlasLayout blas_layout(const m2l_plan_t *pl, long long total_rows, int precision) {
@@ -308,6 +308,7 @@ static BlasLayout blas_layout(const m2l_plan_t *pl, long long total_rows, int pr
     b.ph_b = (size_t)total_rows * pl->kcp * e;
     b.z_b = (size_t)total_rows * pl->rp * e;
     b.split_b = tc ? (size_t)(total_rows + 1) * pl->kp * (precision == M2L_PREC_TF32X3 ? 4 : 2) : 0;
+    b.sl_b = tc ? sliced_workspace(total_rows, sliced_kmax(pl)) : 0;  // B1 and B3 as sliced products
     return b;
 }
 
@@ -403,12 +404,25 @@ static int blas_group(std::vector<Run> &runs, int precision, Workspace &ws, cuda
     T *Z = (T *)(w + al256(lay.qt_b) + al256(lay.ph_b));
     char *hi = w + al256(lay.qt_b) + al256(lay.ph_b) + al256(lay.z_b);
     char *lo = hi + al256(lay.split_b);
-    // B1: compressed multipoles of every instance, one zero row after the last
+    void *sl = lo + al256(lay.split_b);  // slices of the sliced products (split forms)
+    // B1: compressed multipoles of every instance, one zero row after the last; the split forms
+    // take it on the tensor cores, exactly
     stage_begin(own, M2L_STAGE_COMPRESS);
-    for (const Run &r : runs)
-        M2L_TRY(launch_gemm_xwt<T>((const T *)r.q, n, (const T *)D.St, n, qt + r.row_off * kp, kp, r.rows, kp, n, 0, s));
+    long long nl1 = 0;
+    for (const Run &r : runs) {
+        T *dst = qt + r.row_off * kp;
+        if constexpr (sizeof(T) == 4) {
+            if (tc && sliced_usable(D.Ss, kp, kp, (const float *)dst)) {
+                M2L_TRY(launch_sliced(own, D.Ss, (const float *)r.q, n, r.rows, (float *)dst, kp, kp, 0, sl, s));
+                nl1 += 2;
+                continue;
+            }
+        }
+        M2L_TRY(launch_gemm_xwt<T>((const T *)r.q, n, (const T *)D.St, n, dst, kp, r.rows, kp, n, 0, s));
+        nl1 += 1;
+    }
     cudaMemsetAsync(qt + total * kp, 0, kp * sizeof(T), s);
-    stage_end(own, (long long)runs.size());
+    stage_end(own, nl1);
     // B2: one contraction launch over the tiles of every instance
     const LevelView *lv = (const LevelView *)own->exec.levels;
     const ContractTile *tl = (const ContractTile *)own->exec.tiles;
@@ -441,11 +455,39 @@ static int blas_group(std::vector<Run> &runs, int precision, Workspace &ws, cuda
     long long nl = 0;
     for (const Run &r : runs) {
         const T *ph = phit + r.row_off * kcp;
+        T *zr = Z + r.row_off * rp;
         if (r.pl->output == M2L_OUT_LOCALS) {
-            M2L_TRY(launch_gemm_xwt<T>(ph, kcp, (const T *)D.A, kcp, Z + r.row_off * rp, rp, r.rows, rp, kcp, 0, s));
-            M2L_TRY(apply_veps<T>(own, D, Z + r.row_off * rp, (T *)r.L, r.rows, r.pl->accumulate, false, s));
-            nl += 2;
+            bool done_a = false, done_v = false;
+            if constexpr (sizeof(T) == 4) {
+                if (tc && sliced_usable(D.As, rp, rp, (const float *)zr)) {  // every column of Z (zeros past r)
+                    M2L_TRY(launch_sliced(own, D.As, (const float *)ph, kcp, r.rows, (float *)zr, rp, rp, 0, sl, s));
+                    done_a = true;
+                    nl += 2;
+                }
+                if (tc && done_a && sliced_usable(D.Vs, n, n, (const float *)r.L)) {
+                    M2L_TRY(launch_sliced(own, D.Vs, (const float *)zr, rp, r.rows, (float *)r.L, n, n, r.pl->accumulate, sl,
+                                          s));
+                    done_v = true;
+                    nl += 2;
+                }
+            }
+            if (!done_a) {
+                M2L_TRY(launch_gemm_xwt<T>(ph, kcp, (const T *)D.A, kcp, zr, rp, r.rows, rp, kcp, 0, s));
+                nl += 1;
+            }
+            if (!done_v) {
+                M2L_TRY(apply_veps<T>(own, D, zr, (T *)r.L, r.rows, r.pl->accumulate, false, s));
+                nl += 1;
+            }
         } else {
+            if constexpr (sizeof(T) == 4) {
+                if (tc && sliced_usable(D.Ucs, nc, nc, (const float *)r.L)) {
+                    M2L_TRY(launch_sliced(own, D.Ucs, (const float *)ph, kcp, r.rows, (float *)r.L, nc, nc, r.pl->accumulate,
+                                          sl, s));
+                    nl += 2;
+                    continue;
+                }
+            }
             M2L_TRY(launch_gemm_xwt<T>(ph, kcp, (const T *)D.Uc, kcp, (T *)r.L, nc, r.rows, nc, kcp, r.pl->accumulate, s));
             nl += 1;
         }

@@ -91,6 +91,7 @@ struct DevOps {
     void *tw = nullptr;          // [g] complex twiddles exp(-2 pi i m / g)
     void *Bhad = nullptr;        // TF32x3 FFT form: [F][26] kernel matrices of the tensor-core Hadamard
     SlicedOp Us, Vs;             // TF32x3 FFT form: Ut_eps and V_eps as BF16 integer slices
+    SlicedOp Ss, As, Ucs;        // split BLAS forms: S^T, Ut_eps U and U as BF16 integer slices
 };
 
 struct LevelDev {
@@ -236,6 +237,8 @@ int apply_device(m2l_plan_t *pl, const void *q, void *L, int level, int nrhs);
 // output row stride ldo, O a multiple of 4 and at most W's padded rows; `ws` holds
 // sliced_workspace(rows, W.kp) bytes. Used for both factors of F6 in the TF32x3 FFT form.
 int build_sliced_operand(const std::vector<double> &W, int O, int K, int beta, SlicedOp &op);
+int build_blas_sliced_operands(m2l_plan_t *pl, DevOps &D);
+int sliced_kmax(const m2l_plan_t *pl);
 size_t sliced_workspace(long long rows, int Kp);
 bool sliced_usable(const SlicedOp &W, long long ldo, int O, const float *out);
 int launch_sliced(const m2l_plan_t *pl, const SlicedOp &W, const float *X, long long ldx, long long rows, float *out,

@@ -375,6 +375,30 @@ int build_pinv_tc_operand(m2l_plan_t *pl, DevOps &D) {
     return build_sliced_operand(pl->pinv->Veps32, pl->n, pl->r32, 8, D.Vs);
 }
 
+// B1 and B3 of the split BLAS forms as sliced products: S^T (k_pad x n, zero rows past k) and
+// U (n_c x k_c) in 7-bit slices, A = Ut_eps U (padded to r_pad rows) in 7-bit slices, V_eps as
+// for the FFT form. Each product is taken on the tensor cores when its slices exist.
+int build_blas_sliced_operands(m2l_plan_t *pl, DevOps &D) {
+    const BlasOps &B = *pl->blas;
+    const int n = pl->n, k = pl->k, kp = pl->kp, kc = pl->kc, nc = pl->nc;
+    std::vector<double> st((size_t)kp * n, 0.0);
+    for (int c = 0; c < k; ++c)
+        for (int i = 0; i < n; ++i) st[(size_t)c * n + i] = B.S[(size_t)i * k + c];
+    int rc = build_sliced_operand(st, kp, n, 7, D.Ss);
+    if (rc) return rc;
+    if ((rc = build_sliced_operand(B.U, nc, kc, 7, D.Ucs))) return rc;
+    std::vector<double> a((size_t)pl->rp * kc, 0.0);
+    std::copy(B.Aop32.begin(), B.Aop32.begin() + (size_t)pl->r32 * kc, a.begin());
+    if ((rc = build_sliced_operand(a, pl->rp, kc, 7, D.As))) return rc;
+    return build_sliced_operand(pl->pinv->Veps32, pl->n, pl->r32, 8, D.Vs);
+}
+
+// Largest K_pad any sliced product of a plan takes (workspace sizing).
+int sliced_kmax(const m2l_plan_t *pl) {
+    auto up = [](int v) { return (v + kKS - 1) / kKS * kKS; };
+    return std::max(std::max(up(pl->n), up(pl->kc)), up(pl->r32));
+}
+
 // Workspace of launch_sliced for `rows` rows of K_pad: the X slices, then the row exponents.
 size_t sliced_workspace(long long rows, int Kp) {
     const long long rows_pad = (rows + kRowsP - 1) / kRowsP * kRowsP;

@@ -1009,6 +1009,8 @@ int upload_ops(m2l_plan_t *pl, int precision, int form) {
         rc = upload_typed<float>(pl, D, form);
         if (!rc && form == M2L_FORM_BLAS && (precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3))
             rc = split_tc_operators(pl, precision);
+        if (!rc && form == M2L_FORM_BLAS && (precision == M2L_PREC_TF32X3 || precision == M2L_PREC_BF16X3))
+            rc = build_blas_sliced_operands(pl, D);
         if (!rc && form == M2L_FORM_FFT && precision == M2L_PREC_TF32X3) rc = build_hadamard_tc_operand(pl, D);
         if (!rc && form == M2L_FORM_FFT && precision == M2L_PREC_TF32X3) rc = build_pinv_tc_operand(pl, D);
     }
@@ -1020,12 +1022,13 @@ int upload_ops(m2l_plan_t *pl, int precision, int form) {
 void release_operators(m2l_plan_t *pl) {
     for (auto &D : pl->dev) {
         void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Vlo, &D.Uc, &D.C_hi, &D.C_lo, &D.Ub, &D.Vt, &D.dir_meta,
-                         &D.Khat, &D.Ut, &D.tw, &D.Bhad, &D.Us.sl, &D.Us.scale, &D.Vs.sl, &D.Vs.scale};
+                         &D.Khat, &D.Ut, &D.tw, &D.Bhad, &D.Us.sl, &D.Us.scale, &D.Vs.sl, &D.Vs.scale,
+                         &D.Ss.sl, &D.Ss.scale, &D.As.sl, &D.As.scale, &D.Ucs.sl, &D.Ucs.scale};
         for (void **pp : ptrs) {
             if (*pp) cudaFree(*pp);
             *pp = nullptr;
         }
-        D.Us.kp = D.Vs.kp = 0;
+        D.Us.kp = D.Vs.kp = D.Ss.kp = D.As.kp = D.Ucs.kp = 0;
         D.ready = false;
     }
 }
@@ -1033,12 +1036,13 @@ void release_operators(m2l_plan_t *pl) {
 void free_device(m2l_plan_t *pl) {
     for (auto &D : pl->dev) {
         void **ptrs[] = {&D.St, &D.C, &D.A, &D.V, &D.Vlo, &D.Uc, &D.C_hi, &D.C_lo, &D.Ub, &D.Vt, &D.dir_meta,
-                         &D.Khat, &D.Ut, &D.tw, &D.Bhad, &D.Us.sl, &D.Us.scale, &D.Vs.sl, &D.Vs.scale};
+                         &D.Khat, &D.Ut, &D.tw, &D.Bhad, &D.Us.sl, &D.Us.scale, &D.Vs.sl, &D.Vs.scale,
+                         &D.Ss.sl, &D.Ss.scale, &D.As.sl, &D.As.scale, &D.Ucs.sl, &D.Ucs.scale};
         for (void **pp : ptrs) {
             if (*pp) cudaFree(*pp);
             *pp = nullptr;
         }
-        D.Us.kp = D.Vs.kp = 0;
+        D.Us.kp = D.Vs.kp = D.Ss.kp = D.As.kp = D.Ucs.kp = 0;
         D.ready = false;
     }
     for (int l = 0; l <= kMaxDepth; ++l) free_level(pl->ldev[l]);
