@@ -64,6 +64,11 @@ def test_stage_width_option_is_validated(lib):
         assert lib.m2l_set_option(h, lib.M2L_OPT_TC_DRAIN, -2) == lib.M2L_EINVAL
         for v in (-1, 0, 1, 2, 64):
             assert lib.m2l_set_option(h, lib.M2L_OPT_TC_DRAIN, v) == lib.M2L_OK
+        # accumulator chains of the tensor-core Hadamard: 1, 2 or 4 (0: the default)
+        for v in (3, 8, -1):
+            assert lib.m2l_set_option(h, lib.M2L_OPT_HADAMARD_CHAINS, v) == lib.M2L_EINVAL
+        for v in (0, 1, 2, 4):
+            assert lib.m2l_set_option(h, lib.M2L_OPT_HADAMARD_CHAINS, v) == lib.M2L_OK
     finally:
         lib.m2l_destroy(h)
 
