@@ -25,7 +25,7 @@ are within the target (default 1e-6). Nothing else runs in the timed region.
                  boxes on this host's cores; the same leg measures the relative error of every
                  timed form against it (per level, check potentials and locals).
 
---impl reference times the oracle itself (the CPU program the driver's ratio is taken against).
+--impl reference times the oracle itself: the reference arm, a deliberately simple FP64 CPU program.
 Multi-GPU (torchrun): every rank runs its own independent instance (weak scaling, no collective on
 the data path).
 """
